@@ -1,0 +1,773 @@
+/*
+ * sidm_oracle.c -- plain, slow FP64 CPU oracle of the SIDM scattering pass.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, __graft_entry__.smoke() and the
+ * cpu_baseline leg of bench.py may load this library.  It shares no code,
+ * header, table or constant generator with the CUDA path.
+ *
+ * What it computes (Fischer, Yu & Dolag 2025, "Accurately simulating
+ * core-collapse self-interacting dark matter halos"):
+ *   Sect. 2   : spline kernel (Monaghan 1985), kernel size set adaptively by
+ *               the next N_ngb neighbours, explicit energy and linear-momentum
+ *               conservation of each scattering.
+ *   Sect. 3.5 : geometric factor Lambda for the interaction probability (the
+ *               kernel overlap); Eq. hDl ties h to the sphere holding N_ngb
+ *               particles.
+ *   Sect. 3.8 : velocity-dependent cross-section, Eq. vel_dep.
+ *   Sect. 5   : energy conservation of the pairwise scheme is independent of
+ *               the kernel ("by construction").
+ *   App. A    : viscosity cross-section normalised to the total one for
+ *               isotropic scattering (so sigma_V = sigma here).
+ * Readings where the paper is silent (all listed in the design doc):
+ *   h_i      = distance to the N_ngb-th nearest *other* particle of the halo,
+ *              ties broken by id; the kernel support radius is h_i.
+ *   W(r,h)   = 8/(pi h^3) {1-6q^2+6q^3 (q<1/2); 2(1-q)^3 (q<1); 0}, q=r/h.
+ *   Lambda   = int W(|x-x_i|,h_i) W(|x-x_j|,h_j) d^3x  (symmetric overlap).
+ *   P_ij     = (sigma(v_ij)/m) m_j v_ij Lambda_ij dt, v_ij=|v_i-v_j|; a pair
+ *              is in range iff d_ij < h_i + h_j; each unordered pair once.
+ *   draw     = Philox4x32-10 (Salmon et al., SC'11), key = seed, counter =
+ *              (step mod 2^32, min id, max id, halo); u_k = x_k 2^-32;
+ *              event iff u_0 < P (no clamp for P > 1).
+ *   scatter  = isotropic in the pair's centre-of-mass frame:
+ *              cos(theta) = 2 u_1 - 1, phi = 2 pi u_2; the particle with the
+ *              smaller id gets v_cm + (m_j/M)|dv| n, the other v_cm - (m_i/M)|dv| n.
+ *   multi-hit: events are accepted from step-start velocities and applied
+ *              one after another in ascending (halo, min id, max id) order,
+ *              each with the *current* velocities.
+ *   mixed form: the FP32 pair distance is computed from FP32 offsets to
+ *              power-of-two cell origins (see "canonical FP32 geometry").
+ *
+ * Parity pins (tests/test_oracle_*.py): brute-force kNN, Lambda normalised to
+ * one, Lambda symmetry / support / small-kernel limit / Monte Carlo, Philox
+ * known-answer vectors, per-event conservation, isotropy, the closed-form
+ * collision rate of a uniform Maxwellian box, exact sums.
+ *
+ * Build: gcc -O2 -fPIC -shared -ffp-contract=off -fopenmp  (no fast-math).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_LEAF 32           /* particles per leaf of the canonical geometry */
+#define ORC_MBITS 17          /* Morton bits per axis                          */
+#define ORC_PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10, from its published definition (Salmon et al. 2011):        */
+/* round: (hi0,lo0)=M0*c0, (hi1,lo1)=M1*c2;                                   */
+/*        c' = (hi1^c1^k0, lo1, hi0^c3^k1, lo0); key bumped by the Weyl pair  */
+/*        between rounds.                                                     */
+/* ------------------------------------------------------------------------- */
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; ++r) {
+        uint64_t p0 = (uint64_t)M0 * c0, p1 = (uint64_t)M1 * c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += W0; k1 += W1;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Cubic spline kernel with compact support h, normalised to one (Sect. 2).  */
+/* ------------------------------------------------------------------------- */
+double orc_kernel_w(double r, double h)
+{
+    double q = r / h;
+    if (q >= 1.0 || q < 0.0) return 0.0;
+    double norm = 8.0 / (ORC_PI * h * h * h);
+    if (q < 0.5) return norm * (1.0 - 6.0 * q * q + 6.0 * q * q * q);
+    double t = 1.0 - q;
+    return norm * 2.0 * t * t * t;
+}
+
+/* 8-point Gauss-Legendre nodes/weights on [-1,1] (exact to degree 15). */
+static const double GL8_X[8] = {
+    -0.9602898564975363, -0.7966664774136267, -0.5255324099163290, -0.1834346424956498,
+     0.1834346424956498,  0.5255324099163290,  0.7966664774136267,  0.9602898564975363};
+static const double GL8_W[8] = {
+     0.1012285362903763,  0.2223810344533745,  0.3137066458778873,  0.3626837833783620,
+     0.3626837833783620,  0.3137066458778873,  0.2223810344533745,  0.1012285362903763};
+
+/* int_a^b s W(s,h) ds, piecewise GL (breakpoint h/2), exact for the spline. */
+static double inner_sw(double a, double b, double h)
+{
+    if (b > h) b = h;
+    if (a < 0.0) a = 0.0;
+    if (b <= a) return 0.0;
+    double brk[3] = {a, b, b};
+    int nb = 2;
+    if (0.5 * h > a && 0.5 * h < b) { brk[1] = 0.5 * h; brk[2] = b; nb = 3; }
+    double acc = 0.0;
+    for (int p = 0; p + 1 < nb; ++p) {
+        double lo = brk[p], hi = brk[p + 1], m = 0.5 * (lo + hi), hw = 0.5 * (hi - lo);
+        for (int g = 0; g < 8; ++g) {
+            double s = m + hw * GL8_X[g];
+            acc += GL8_W[g] * hw * s * orc_kernel_w(s, h);
+        }
+    }
+    return acc;
+}
+
+static int cmp_dbl(const void* a, const void* b)
+{
+    double x = *(const double*)a, y = *(const double*)b;
+    return (x > y) - (x < y);
+}
+
+/*
+ * Geometric factor Lambda(d; h_i, h_j) = int W_i W_j d^3x  (Sect. 3.5 reading),
+ * in FP64.  Bipolar coordinates (r = |x-x_i|, s = |x-x_j|, d^3x = 2 pi r s
+ * dr ds / d over |r-s| <= d <= r+s) give
+ *   Lambda = (2 pi / d) int_0^{h_i} r W_i(r) [ int_{|r-d|}^{r+d} s W_j(s) ds ] dr.
+ * The outer integrand is a polynomial between the breakpoints
+ * {h_i/2, h_i, d, d +- h_j/2, d +- h_j, h_j/2 - d, h_j - d}; 8-point
+ * Gauss-Legendre per piece is exact there (degree <= 9), as is the inner one.
+ * For d -> 0 the limit 4 pi int r^2 W_i W_j dr is used.
+ */
+double orc_lambda(double d, double hi, double hj)
+{
+    if (d < 0.0) d = -d;
+    if (d >= hi + hj) return 0.0;
+    if (d < 1e-9 * (hi + hj)) {
+        double top = hi < hj ? hi : hj;
+        double brk[4] = {0.0, 0.5 * hi, 0.5 * hj, top};
+        qsort(brk, 4, sizeof(double), cmp_dbl);
+        double acc = 0.0;
+        for (int p = 0; p < 3; ++p) {
+            double lo = brk[p], up = brk[p + 1];
+            if (up > top) up = top;
+            if (up <= lo) continue;
+            double m = 0.5 * (lo + up), hw = 0.5 * (up - lo);
+            for (int g = 0; g < 8; ++g) {
+                double r = m + hw * GL8_X[g];
+                acc += GL8_W[g] * hw * r * r * orc_kernel_w(r, hi) * orc_kernel_w(r, hj);
+            }
+        }
+        return 4.0 * ORC_PI * acc;
+    }
+    double lo = d - hj; if (lo < 0.0) lo = 0.0;
+    double up = d + hj; if (up > hi) up = hi;
+    if (up <= lo) return 0.0;
+    double cand[11] = {lo, up, 0.5 * hi, hi, d, d - 0.5 * hj, d + 0.5 * hj,
+                       d - hj, d + hj, 0.5 * hj - d, hj - d};
+    double brk[11];
+    int nb = 0;
+    for (int c = 0; c < 11; ++c)
+        if (cand[c] >= lo && cand[c] <= up) brk[nb++] = cand[c];
+    qsort(brk, nb, sizeof(double), cmp_dbl);
+    double acc = 0.0;
+    for (int p = 0; p + 1 < nb; ++p) {
+        double a = brk[p], b = brk[p + 1];
+        if (b <= a) continue;
+        double m = 0.5 * (a + b), hw = 0.5 * (b - a);
+        for (int g = 0; g < 8; ++g) {
+            double r = m + hw * GL8_X[g];
+            double sl = fabs(r - d), su = r + d;
+            acc += GL8_W[g] * hw * r * orc_kernel_w(r, hi) * inner_sw(sl, su, hj);
+        }
+    }
+    return 2.0 * ORC_PI * acc / d;
+}
+
+/* Velocity-dependent cross-section per unit mass, Eq. vel_dep (Sect. 3.8);
+ * kind 0: constant s0; kind 1: s0 / (1 + (v/w)^2)^2 with v the pair speed. */
+double orc_sigma(int kind, double s0, double w, double v)
+{
+    if (kind == 0) return s0;
+    double q = v / w;
+    double t = 1.0 + q * q;
+    return s0 / (t * t);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Canonical FP32 geometry of the mixed form.                                 */
+/* Per halo: cube exponent E (2^E > largest bbox extent), origin O (per axis  */
+/* a multiple of 2^E below the minimum), cube [O, O + 2^(E+1))^3.  Morton key */
+/* of 3 x 17 bits, stable sort, leaves of 32 consecutive particles.  A leaf's */
+/* frame origin is the corner c (relative to O) of the finest Morton cell     */
+/* (edge 2^(E+1-17)) of its first particle, exact in FP32.                    */
+/* Offsets o = RN32(RN64(x - (O + c))).                                       */
+/* Distance from query i (leaf A) to j (leaf B):                              */
+/*   s = c_B - c_A (exact), dx = RN32(RN32(o_j + s) - o_i),                   */
+/*   d2 = fmaf(dz,dz, fmaf(dy,dy, dx*dx)).                                    */
+/* A pair uses the frame of its lower leaf (Morton order).                    */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int n;                 /* particles in the halo                          */
+    int nleaf;
+    int E;
+    double O[3];
+    uint32_t* order;       /* sorted position -> local input index           */
+    uint32_t* rank;        /* local input index -> sorted position           */
+    float* off;            /* [3][n] offsets by local input index            */
+    float* cell;           /* [3][nleaf] cell origins relative to O          */
+} orc_geom;
+
+static uint64_t spread3(uint32_t v)
+{
+    uint64_t x = v & 0x1FFFFFu, r = 0;
+    for (int b = 0; b < 21; ++b) r |= ((x >> b) & 1u) << (3 * b);
+    return r;
+}
+
+static uint64_t* g_sort_keys;  /* used by the qsort comparator only */
+static int cmp_key_stable(const void* a, const void* b)
+{
+    uint32_t i = *(const uint32_t*)a, j = *(const uint32_t*)b;
+    uint64_t ki = g_sort_keys[i], kj = g_sort_keys[j];
+    if (ki != kj) return ki < kj ? -1 : 1;
+    return (i > j) - (i < j);   /* stable: input order */
+}
+
+static void geom_build(orc_geom* g, int n, const double* px, const double* py, const double* pz)
+{
+    const double* p[3] = {px, py, pz};
+    memset(g, 0, sizeof(*g));
+    g->n = n;
+    g->nleaf = (n + ORC_LEAF - 1) / ORC_LEAF;
+    double mn[3], mx[3], ext = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        mn[a] = INFINITY; mx[a] = -INFINITY;
+        for (int i = 0; i < n; ++i) { if (p[a][i] < mn[a]) mn[a] = p[a][i]; if (p[a][i] > mx[a]) mx[a] = p[a][i]; }
+        if (n > 0 && mx[a] - mn[a] > ext) ext = mx[a] - mn[a];
+    }
+    int E = 0;
+    if (ext > 0.0) frexp(ext, &E);            /* ext = m 2^E, m in [1/2,1) => 2^E > ext */
+    g->E = E;
+    for (int a = 0; a < 3; ++a) g->O[a] = n > 0 ? ldexp(floor(ldexp(mn[a], -E)), E) : 0.0;
+    uint64_t* key = (uint64_t*)malloc(sizeof(uint64_t) * (n ? n : 1));
+    uint32_t* q = (uint32_t*)malloc(sizeof(uint32_t) * 3 * (n ? n : 1));
+    const uint32_t qmax = (1u << ORC_MBITS) - 1u;
+    for (int i = 0; i < n; ++i) {
+        for (int a = 0; a < 3; ++a) {
+            double t = ldexp(p[a][i] - g->O[a], ORC_MBITS - E - 1);
+            double f = floor(t);
+            uint32_t v = f <= 0.0 ? 0u : (f >= (double)qmax ? qmax : (uint32_t)f);
+            q[3 * i + a] = v;
+        }
+        key[i] = spread3(q[3 * i]) | (spread3(q[3 * i + 1]) << 1) | (spread3(q[3 * i + 2]) << 2);
+    }
+    g->order = (uint32_t*)malloc(sizeof(uint32_t) * (n ? n : 1));
+    g->rank = (uint32_t*)malloc(sizeof(uint32_t) * (n ? n : 1));
+    for (int i = 0; i < n; ++i) g->order[i] = (uint32_t)i;
+    g_sort_keys = key;
+    qsort(g->order, n, sizeof(uint32_t), cmp_key_stable);
+    for (int s = 0; s < n; ++s) g->rank[g->order[s]] = (uint32_t)s;
+    g->cell = (float*)malloc(sizeof(float) * 3 * (g->nleaf ? g->nleaf : 1));
+    g->off = (float*)malloc(sizeof(float) * 3 * (n ? n : 1));
+    const double fine = ldexp(1.0, E + 1 - ORC_MBITS);   /* finest Morton cell */
+    for (int L = 0; L < g->nleaf; ++L) {
+        int s0 = L * ORC_LEAF, s1 = s0 + ORC_LEAF - 1;
+        if (s1 >= n) s1 = n - 1;
+        uint32_t fi = g->order[s0];
+        for (int a = 0; a < 3; ++a)
+            g->cell[3 * L + a] = (float)((double)q[3 * fi + a] * fine);
+        for (int s = s0; s <= s1; ++s) {
+            uint32_t i = g->order[s];
+            for (int a = 0; a < 3; ++a) {
+                double C = g->O[a] + (double)g->cell[3 * L + a];
+                g->off[3 * i + a] = (float)(p[a][i] - C);
+            }
+        }
+    }
+    free(key);
+    free(q);
+}
+
+static void geom_free(orc_geom* g)
+{
+    free(g->order); free(g->rank); free(g->cell); free(g->off);
+    memset(g, 0, sizeof(*g));
+}
+
+/* canonical FP32 squared distance from i (its leaf frame) to j; local indices */
+static float d2_mixed(const orc_geom* g, uint32_t i, uint32_t j)
+{
+    volatile float dx[3];
+    int A = (int)(g->rank[i] / ORC_LEAF), B = (int)(g->rank[j] / ORC_LEAF);
+    for (int a = 0; a < 3; ++a) {
+        float s = g->cell[3 * B + a] - g->cell[3 * A + a];       /* exact */
+        float t = g->off[3 * j + a] + s;
+        dx[a] = t - g->off[3 * i + a];
+    }
+    float xx = dx[0] * dx[0];
+    return fmaf(dx[2], dx[2], fmaf(dx[1], dx[1], xx));
+}
+
+static double d2_fp64(const double* px, const double* py, const double* pz, uint32_t i, uint32_t j)
+{
+    double dx = px[j] - px[i], dy = py[j] - py[i], dz = pz[j] - pz[i];
+    double xx = dx * dx;
+    return fma(dz, dz, fma(dy, dy, xx));
+}
+
+/* float/double -> order-preserving unsigned bits (non-negative values) */
+static uint32_t fbits(float f) { uint32_t u; memcpy(&u, &f, 4); return u; }
+static uint64_t dbits(double f) { uint64_t u; memcpy(&u, &f, 8); return u; }
+
+/* ------------------------------------------------------------------------- */
+/* Uniform search grid (a plain accelerator; the kNN result is defined by     */
+/* the exhaustive order of (d2, id), which the grid search reproduces).       */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int n, dim[3];
+    double lo[3], cs;
+    int* start;     /* [ncell+1] */
+    int* items;     /* [n] local indices */
+} orc_grid;
+
+static void grid_build(orc_grid* G, int n, const double* px, const double* py, const double* pz, double occ)
+{
+    const double* p[3] = {px, py, pz};
+    double hi[3], vol = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        G->lo[a] = INFINITY; hi[a] = -INFINITY;
+        for (int i = 0; i < n; ++i) { if (p[a][i] < G->lo[a]) G->lo[a] = p[a][i]; if (p[a][i] > hi[a]) hi[a] = p[a][i]; }
+        double e = hi[a] - G->lo[a];
+        vol *= (e > 0 ? e : 1e-30);
+    }
+    double cs = cbrt(vol * occ / (n > 0 ? n : 1));
+    double ext = 0.0;
+    for (int a = 0; a < 3; ++a) if (hi[a] - G->lo[a] > ext) ext = hi[a] - G->lo[a];
+    if (!(cs > 0.0)) cs = ext > 0 ? ext : 1.0;
+    if (ext / cs > 256.0) cs = ext / 256.0;
+    G->cs = cs; G->n = n;
+    long ncell = 1;
+    for (int a = 0; a < 3; ++a) { G->dim[a] = (int)floor((hi[a] - G->lo[a]) / cs) + 1; ncell *= G->dim[a]; }
+    G->start = (int*)calloc((size_t)ncell + 1, sizeof(int));
+    G->items = (int*)malloc(sizeof(int) * (n ? n : 1));
+    int* cid = (int*)malloc(sizeof(int) * (n ? n : 1));
+    for (int i = 0; i < n; ++i) {
+        int c[3];
+        for (int a = 0; a < 3; ++a) {
+            c[a] = (int)floor((p[a][i] - G->lo[a]) / cs);
+            if (c[a] < 0) c[a] = 0;
+            if (c[a] >= G->dim[a]) c[a] = G->dim[a] - 1;
+        }
+        cid[i] = (c[2] * G->dim[1] + c[1]) * G->dim[0] + c[0];
+        G->start[cid[i] + 1]++;
+    }
+    for (long c = 0; c < ncell; ++c) G->start[c + 1] += G->start[c];
+    int* fill = (int*)malloc(sizeof(int) * (size_t)ncell);
+    for (long c = 0; c < ncell; ++c) fill[c] = G->start[c];
+    for (int i = 0; i < n; ++i) G->items[fill[cid[i]]++] = i;
+    free(fill); free(cid);
+}
+
+static void grid_free(orc_grid* G) { free(G->start); free(G->items); memset(G, 0, sizeof(*G)); }
+
+static void grid_cell_of(const orc_grid* G, const double x[3], int c[3])
+{
+    for (int a = 0; a < 3; ++a) {
+        c[a] = (int)floor((x[a] - G->lo[a]) / G->cs);
+        if (c[a] < 0) c[a] = 0;
+        if (c[a] >= G->dim[a]) c[a] = G->dim[a] - 1;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* kNN kernel size h_i (Sect. 2: set by the next N_ngb neighbours).          */
+/* Exact k-th smallest of the total order (d2, id) over other particles of   */
+/* the halo.  mode 0: mixed (canonical FP32 d2), mode 1: FP64.               */
+/* Outputs per local particle (input order): h (as double), d2k bits, and    */
+/* optionally the k neighbour ids in ascending (d2, id) order.               */
+/* brute != 0 scans all particles (O(N^2)); otherwise the grid shells.       */
+/* ------------------------------------------------------------------------- */
+typedef struct { uint64_t d; uint32_t id; uint32_t idx; } knn_ent;
+
+static int ent_less(const knn_ent* a, const knn_ent* b)
+{
+    if (a->d != b->d) return a->d < b->d;
+    return a->id < b->id;
+}
+
+static void topk_insert(knn_ent* list, int* cnt, int k, knn_ent e)
+{
+    if (*cnt == k && !ent_less(&e, &list[k - 1])) return;
+    int pos = *cnt < k ? (*cnt)++ : k - 1;
+    while (pos > 0 && ent_less(&e, &list[pos - 1])) { list[pos] = list[pos - 1]; --pos; }
+    list[pos] = e;
+}
+
+int orc_knn_halo(int n, const double* px, const double* py, const double* pz, const uint32_t* ids,
+                 int k, int mode, int brute, const uint8_t* query_mask,
+                 double* h_out, uint64_t* d2k_bits_out, uint32_t* nbr_ids_out)
+{
+    if (k < 1 || k > n - 1) return -1;
+    orc_geom g; memset(&g, 0, sizeof(g));
+    if (mode == 0) geom_build(&g, n, px, py, pz);
+    orc_grid G; memset(&G, 0, sizeof(G));
+    if (!brute) grid_build(&G, n, px, py, pz, 8.0);
+    int err = 0;
+    /* the canonical FP32 distance is within (cube edge) * 2^-22 of the exact one */
+    const double absmargin = mode == 0 ? ldexp(1.0, g.E + 1 - 20) : 0.0;
+    #pragma omp parallel
+    {
+        knn_ent* list = (knn_ent*)malloc(sizeof(knn_ent) * (size_t)k);
+        #pragma omp for schedule(dynamic, 64)
+        for (int i = 0; i < n; ++i) {
+            if (query_mask && !query_mask[i]) continue;
+            int cnt = 0;
+            if (brute) {
+                for (int j = 0; j < n; ++j) {
+                    if (j == i) continue;
+                    knn_ent e;
+                    e.d = mode == 0 ? (uint64_t)fbits(d2_mixed(&g, (uint32_t)i, (uint32_t)j))
+                                    : dbits(d2_fp64(px, py, pz, (uint32_t)i, (uint32_t)j));
+                    e.id = ids[j]; e.idx = (uint32_t)j;
+                    topk_insert(list, &cnt, k, e);
+                }
+            } else {
+                double xi[3] = {px[i], py[i], pz[i]};
+                int ci[3]; grid_cell_of(&G, xi, ci);
+                int maxs = G.dim[0] > G.dim[1] ? G.dim[0] : G.dim[1];
+                if (G.dim[2] > maxs) maxs = G.dim[2];
+                for (int s = 0; s <= maxs; ++s) {
+                    for (int cz = ci[2] - s; cz <= ci[2] + s; ++cz) {
+                        if (cz < 0 || cz >= G.dim[2]) continue;
+                        for (int cy = ci[1] - s; cy <= ci[1] + s; ++cy) {
+                            if (cy < 0 || cy >= G.dim[1]) continue;
+                            for (int cx = ci[0] - s; cx <= ci[0] + s; ++cx) {
+                                if (cx < 0 || cx >= G.dim[0]) continue;
+                                int cheb = abs(cx - ci[0]);
+                                if (abs(cy - ci[1]) > cheb) cheb = abs(cy - ci[1]);
+                                if (abs(cz - ci[2]) > cheb) cheb = abs(cz - ci[2]);
+                                if (cheb != s) continue;
+                                long c = ((long)cz * G.dim[1] + cy) * G.dim[0] + cx;
+                                for (int t = G.start[c]; t < G.start[c + 1]; ++t) {
+                                    int j = G.items[t];
+                                    if (j == i) continue;
+                                    knn_ent e;
+                                    e.d = mode == 0 ? (uint64_t)fbits(d2_mixed(&g, (uint32_t)i, (uint32_t)j))
+                                                    : dbits(d2_fp64(px, py, pz, (uint32_t)i, (uint32_t)j));
+                                    e.id = ids[j]; e.idx = (uint32_t)j;
+                                    topk_insert(list, &cnt, k, e);
+                                }
+                            }
+                        }
+                    }
+                    if (cnt == k) {
+                        /* every unvisited particle lies at exact distance >= s*cs;
+                         * the canonical distance differs from the exact one by far
+                         * less than the 1e-5 relative margin used here.           */
+                        double kth;
+                        if (mode == 0) { float f; uint32_t u = (uint32_t)list[k - 1].d; memcpy(&f, &u, 4); kth = sqrt((double)f); }
+                        else { double f; uint64_t u = list[k - 1].d; memcpy(&f, &u, 8); kth = sqrt(f); }
+                        if ((double)s * G.cs > kth * (1.0 + 1e-5) + absmargin) break;
+                    }
+                }
+            }
+            if (cnt < k) {
+                #pragma omp atomic write
+                err = -2;
+                continue;
+            }
+            if (mode == 0) {
+                float f; uint32_t u = (uint32_t)list[k - 1].d; memcpy(&f, &u, 4);
+                h_out[i] = (double)sqrtf(f);
+            } else {
+                double f; uint64_t u = list[k - 1].d; memcpy(&f, &u, 8);
+                h_out[i] = sqrt(f);
+            }
+            if (d2k_bits_out) d2k_bits_out[i] = list[k - 1].d;
+            if (nbr_ids_out)
+                for (int t = 0; t < k; ++t) nbr_ids_out[(size_t)i * k + t] = list[t].id;
+        }
+        free(list);
+    }
+    if (!brute) grid_free(&G);
+    if (mode == 0) geom_free(&g);
+    return err;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Pair probabilities and draws (Sect. 3.5, Eq. vel_dep).                    */
+/* Every unordered in-range pair of the halo once: found from the endpoint   */
+/* with the larger h (d < h_i + h_j <= 2 h_big), kept iff h_i > h_j or       */
+/* (h_i == h_j and i < j).  Mixed: range test d2 < RN32(RN32(h_i+h_j)^2) on  */
+/* the canonical FP32 d2 in the lower leaf's frame; FP64: d2 < (h_i+h_j)^2.  */
+/* Lambda uses the FP64 distance of the FP64 positions.                      */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    uint64_t key;     /* halo<<54 | min id<<27 | max id                       */
+    uint32_t i, j;    /* local input indices; i has the smaller id            */
+    uint32_t x1, x2;  /* Philox words for the scattering direction           */
+    double P, u;
+} orc_event;
+
+typedef struct {
+    int64_t n_pairs, n_events, n_p_gt1, n_near;
+    double max_sum_p;
+} orc_pair_stats;
+
+int orc_pairs_halo(int n, const double* px, const double* py, const double* pz,
+                   const double* vx, const double* vy, const double* vz,
+                   const uint32_t* ids, const double* h, int mode,
+                   int xs_kind, double s0, double w, double mass, double dt,
+                   uint64_t seed, uint64_t step, uint32_t halo,
+                   orc_event* ev_out, int64_t ev_cap, orc_pair_stats* st, double* sum_p_out)
+{
+    orc_geom g; memset(&g, 0, sizeof(g));
+    if (mode == 0) geom_build(&g, n, px, py, pz);
+    orc_grid G; memset(&G, 0, sizeof(G));
+    grid_build(&G, n, px, py, pz, 8.0);
+    double* sump = (double*)calloc((size_t)(n ? n : 1), sizeof(double));
+    int64_t n_pairs = 0, n_gt1 = 0, n_near = 0, n_ev = 0;
+    int overflow = 0;
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    #pragma omp parallel reduction(+:n_pairs, n_gt1, n_near)
+    {
+        #pragma omp for schedule(dynamic, 64)
+        for (int i = 0; i < n; ++i) {
+            double xi[3] = {px[i], py[i], pz[i]};
+            double rad = 2.0 * h[i] * (1.0 + 1e-5) + (mode == 0 ? ldexp(1.0, g.E + 1 - 20) : 0.0);
+            int lo[3], hi[3];
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = (int)floor((xi[a] - rad - G.lo[a]) / G.cs);
+                hi[a] = (int)floor((xi[a] + rad - G.lo[a]) / G.cs);
+                if (lo[a] < 0) lo[a] = 0;
+                if (hi[a] >= G.dim[a]) hi[a] = G.dim[a] - 1;
+            }
+            for (int cz = lo[2]; cz <= hi[2]; ++cz)
+            for (int cy = lo[1]; cy <= hi[1]; ++cy)
+            for (int cx = lo[0]; cx <= hi[0]; ++cx) {
+                long c = ((long)cz * G.dim[1] + cy) * G.dim[0] + cx;
+                for (int t = G.start[c]; t < G.start[c + 1]; ++t) {
+                    int j = G.items[t];
+                    if (j == i) continue;
+                    if (!(h[i] > h[j] || (h[i] == h[j] && i < j))) continue;
+                    int inr;
+                    if (mode == 0) {
+                        int Ai = (int)(g.rank[i] / ORC_LEAF), Aj = (int)(g.rank[j] / ORC_LEAF);
+                        float d2 = Ai <= Aj ? d2_mixed(&g, (uint32_t)i, (uint32_t)j)
+                                            : d2_mixed(&g, (uint32_t)j, (uint32_t)i);
+                        volatile float hs = (float)h[i] + (float)h[j];
+                        volatile float lim = hs * hs;
+                        inr = d2 < lim;
+                    } else {
+                        double hs = h[i] + h[j];
+                        inr = d2_fp64(px, py, pz, (uint32_t)i, (uint32_t)j) < hs * hs;
+                    }
+                    if (!inr) continue;
+                    n_pairs++;
+                    double dx = px[j] - px[i], dy = py[j] - py[i], dz = pz[j] - pz[i];
+                    double d = sqrt(dx * dx + dy * dy + dz * dz);
+                    double lam = orc_lambda(d, h[i], h[j]);
+                    double ux = vx[i] - vx[j], uy = vy[i] - vy[j], uz = vz[i] - vz[j];
+                    double v = sqrt(ux * ux + uy * uy + uz * uz);
+                    double P = orc_sigma(xs_kind, s0, w, v) * mass * v * lam * dt;
+                    uint32_t a = ids[i] < ids[j] ? ids[i] : ids[j];
+                    uint32_t b = ids[i] < ids[j] ? ids[j] : ids[i];
+                    uint32_t ctr[4] = {(uint32_t)step, a, b, halo}, x[4];
+                    orc_philox4x32_10(ctr, key, x);
+                    double u = ldexp((double)x[0], -32);
+                    if (P > 1.0) n_gt1++;
+                    if (fabs(P - u) < 1e-6) n_near++;
+                    #pragma omp atomic
+                    sump[i] += P;
+                    #pragma omp atomic
+                    sump[j] += P;
+                    if (u < P) {
+                        int64_t slot;
+                        #pragma omp atomic capture
+                        slot = n_ev++;
+                        if (slot < ev_cap) {
+                            orc_event* e = &ev_out[slot];
+                            e->key = ((uint64_t)halo << 54) | ((uint64_t)a << 27) | (uint64_t)b;
+                            e->i = ids[i] < ids[j] ? (uint32_t)i : (uint32_t)j;
+                            e->j = ids[i] < ids[j] ? (uint32_t)j : (uint32_t)i;
+                            e->x1 = x[1]; e->x2 = x[2];
+                            e->P = P; e->u = u;
+                        } else {
+                            #pragma omp atomic write
+                            overflow = 1;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    double mx = 0.0;
+    for (int i = 0; i < n; ++i) if (sump[i] > mx) mx = sump[i];
+    if (sum_p_out) memcpy(sum_p_out, sump, sizeof(double) * (size_t)n);
+    free(sump);
+    st->n_pairs = n_pairs; st->n_events = n_ev; st->n_p_gt1 = n_gt1; st->n_near = n_near;
+    st->max_sum_p = mx;
+    grid_free(&G);
+    if (mode == 0) geom_free(&g);
+    return overflow ? -3 : 0;
+}
+
+static int cmp_event(const void* a, const void* b)
+{
+    uint64_t x = ((const orc_event*)a)->key, y = ((const orc_event*)b)->key;
+    return (x > y) - (x < y);
+}
+
+void orc_sort_events(orc_event* ev, int64_t n) { qsort(ev, (size_t)n, sizeof(orc_event), cmp_event); }
+
+/* ------------------------------------------------------------------------- */
+/* Sequential application in ascending key order (multi-hit reading), each   */
+/* event from the *current* FP64 velocities; isotropic direction in the CM   */
+/* frame; pair momentum and energy conserved (Sect. 2, Sect. 5).             */
+/* masses: per-particle masses m_i.  dE_out (optional) gets the per-event    */
+/* change of the pair's kinetic energy (zero in exact arithmetic).           */
+/* ------------------------------------------------------------------------- */
+void orc_apply_events(const orc_event* ev, int64_t n_ev, const double* m,
+                      double* vx, double* vy, double* vz, double* dE_out)
+{
+    for (int64_t e = 0; e < n_ev; ++e) {
+        uint32_t i = ev[e].i, j = ev[e].j;
+        double mi = m[i], mj = m[j], M = mi + mj;
+        double vi[3] = {vx[i], vy[i], vz[i]}, vj[3] = {vx[j], vy[j], vz[j]};
+        double vcm[3], dv2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            vcm[a] = (mi * vi[a] + mj * vj[a]) / M;
+            double t = vi[a] - vj[a];
+            dv2 += t * t;
+        }
+        double dv = sqrt(dv2);
+        double ct = 2.0 * ldexp((double)ev[e].x1, -32) - 1.0;
+        double st = sqrt(fmax(0.0, 1.0 - ct * ct));
+        double phi = 2.0 * ORC_PI * ldexp((double)ev[e].x2, -32);
+        double nh[3] = {st * cos(phi), st * sin(phi), ct};
+        double e0 = 0.5 * mi * (vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2])
+                  + 0.5 * mj * (vj[0] * vj[0] + vj[1] * vj[1] + vj[2] * vj[2]);
+        double e1 = 0.0;
+        double wi = mj / M * dv, wj = mi / M * dv;
+        double ni[3], nj[3];
+        for (int a = 0; a < 3; ++a) { ni[a] = vcm[a] + wi * nh[a]; nj[a] = vcm[a] - wj * nh[a]; }
+        vx[i] = ni[0]; vy[i] = ni[1]; vz[i] = ni[2];
+        vx[j] = nj[0]; vy[j] = nj[1]; vz[j] = nj[2];
+        e1 = 0.5 * mi * (ni[0] * ni[0] + ni[1] * ni[1] + ni[2] * ni[2])
+           + 0.5 * mj * (nj[0] * nj[0] + nj[1] * nj[1] + nj[2] * nj[2]);
+        if (dE_out) dE_out[e] = e1 - e0;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Exact sums (Shewchuk's non-overlapping expansions, as in Python's fsum):  */
+/* total kinetic energy 1/2 m |v|^2 and momentum m v of a set of particles.  */
+/* Each term is formed in FP64 as term = (0.5*m) * (vx*vx + vy*vy + vz*vz)   */
+/* (left to right, no FMA) and p = m*v; only the summation is exact.          */
+/* ------------------------------------------------------------------------- */
+typedef struct { double* p; int n, cap; } orc_xsum;
+
+static void xsum_add(orc_xsum* s, double x)
+{
+    int k = 0;
+    for (int t = 0; t < s->n; ++t) {
+        double y = s->p[t];
+        if (fabs(x) < fabs(y)) { double tmp = x; x = y; y = tmp; }
+        double hi = x + y;
+        double lo = y - (hi - x);
+        if (lo != 0.0) s->p[k++] = lo;
+        x = hi;
+    }
+    if (k >= s->cap) { s->cap = 2 * s->cap + 8; s->p = (double*)realloc(s->p, sizeof(double) * (size_t)s->cap); }
+    s->n = k;
+    s->p[s->n++] = x;
+}
+
+static double xsum_value(const orc_xsum* s)
+{
+    /* round the expansion to nearest (expansion components are non-overlapping) */
+    if (s->n == 0) return 0.0;
+    int t = s->n - 1;
+    double hi = s->p[t], lo = 0.0;
+    while (t > 0) {
+        double x = hi, y = s->p[--t];
+        hi = x + y;
+        double yr = hi - x;
+        lo = y - yr;
+        if (lo != 0.0) break;
+    }
+    if (t > 0 && ((lo < 0.0 && s->p[t - 1] < 0.0) || (lo > 0.0 && s->p[t - 1] > 0.0))) {
+        double y = lo * 2.0, x = hi + y, yr = x - hi;
+        if (y == yr) hi = x;
+    }
+    return hi;
+}
+
+void orc_energy_momentum(int n, double m, const double* vx, const double* vy, const double* vz, double out[4])
+{
+    orc_xsum s[4];
+    for (int a = 0; a < 4; ++a) { s[a].p = NULL; s[a].n = 0; s[a].cap = 0; }
+    double hm = 0.5 * m;
+    for (int i = 0; i < n; ++i) {
+        double q = vx[i] * vx[i];
+        q = q + vy[i] * vy[i];
+        q = q + vz[i] * vz[i];
+        xsum_add(&s[0], hm * q);
+        xsum_add(&s[1], m * vx[i]);
+        xsum_add(&s[2], m * vy[i]);
+        xsum_add(&s[3], m * vz[i]);
+    }
+    for (int a = 0; a < 4; ++a) { out[a] = xsum_value(&s[a]); free(s[a].p); }
+}
+
+double orc_exact_sum(const double* x, int64_t n)
+{
+    orc_xsum s = {NULL, 0, 0};
+    for (int64_t i = 0; i < n; ++i) xsum_add(&s, x[i]);
+    double v = xsum_value(&s);
+    free(s.p);
+    return v;
+}
+
+/* Expose the canonical FP32 geometry for tests: sorted order, offsets, leaf
+ * cells, cube exponent and origin. */
+int orc_geometry(int n, const double* px, const double* py, const double* pz,
+                 uint32_t* order_out, float* off_out, float* cell_out, int* E_out, double* O_out)
+{
+    orc_geom g;
+    geom_build(&g, n, px, py, pz);
+    if (order_out) memcpy(order_out, g.order, sizeof(uint32_t) * (size_t)n);
+    if (off_out) memcpy(off_out, g.off, sizeof(float) * 3 * (size_t)n);
+    if (cell_out) memcpy(cell_out, g.cell, sizeof(float) * 3 * (size_t)g.nleaf);
+    if (E_out) *E_out = g.E;
+    if (O_out) memcpy(O_out, g.O, sizeof(double) * 3);
+    geom_free(&g);
+    return 0;
+}
+
+/* canonical mixed d2 for a list of (i, j) local pairs (query i's frame) */
+int orc_d2_mixed_pairs(int n, const double* px, const double* py, const double* pz,
+                       int64_t npairs, const uint32_t* qi, const uint32_t* qj, float* d2_out)
+{
+    orc_geom g;
+    geom_build(&g, n, px, py, pz);
+    for (int64_t t = 0; t < npairs; ++t) d2_out[t] = d2_mixed(&g, qi[t], qj[t]);
+    geom_free(&g);
+    return 0;
+}
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void orc_set_num_threads(int t)
+{
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
+}
