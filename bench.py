@@ -1,0 +1,523 @@
+"""Benchmark of the SIDM scattering pass on GB300.
+
+Workload (one "step" = one pass of the whole hot path over the halo):
+  NFW halo, r_s = 1, truncated at 10 r_s, N = 1,048,576 equal-mass particles,
+  isotropic Maxwellian velocities with the Jeans dispersion (seed 1),
+  sigma(v)/m = 100 / (1 + (v/v_max)^2)^2 with v_max the halo's maximum circular
+  velocity, N_ngb = 64, FP32 storage with FP64 reductions (mixed form),
+  fixed dt from the SIDM time-step proxy dt = 0.04 / q99.9(sum_j P_ij / dt)
+  on the initial state.  Synthetic inputs (seeded), no datasets.
+  A step = ballistic drift + cell build + kernel sizes + pair probabilities,
+  draws and scatter + FP64 energy/momentum.  L2 is flushed (256 MiB write)
+  before every timed step, outside the step's events.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs an independent halo (seed + rank):
+weak scaling, no data-path collective; rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_PART = 1 << 20
+N_NGB = 64
+S0 = 100.0
+SEED_IC = 1
+TAU = 0.04
+METRIC = "SIDM particle-steps/s"
+UNIT = "particle-steps/s"
+WORKLOAD = "nfw_rcut10_N1048576_ngb64_veldep_s0_100_w_vmax"
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# issue slots of the FP32/INT32 pipes: SMs x lanes per SM (GB300, 152 SMs x 128)
+N_SM, LANES_PER_SM = 152, 128
+# algorithmic lane operations per unit of the two ALU-bound kernels (derived in the design doc)
+OPS_PER_TEST = 10          # canonical d^2 (3 sub, 1 mul, 2 fma), sum, square, compare, ballot
+OPS_PER_PAIR = 170         # d^2 + sqrt + Lambda table + |v_ij| + sigma(v) + P + Philox4x32-10 + draw
+OPS_PER_KNN_CAND = 8       # canonical d^2 (6) + key compare (2)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_PART)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--use-tma", type=int, default=0)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_halo(n, seed):
+    from paper_2506_06269_gb300 import ics
+    h = ics.nfw(n, seed)
+    return h, ics.nfw_vmax()
+
+
+def load_peaks():
+    try:
+        with open(PEAKS) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0])); mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def source_sha(path):
+    import hashlib
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def load_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if still current.
+
+    profiles/ncu_traffic.json maps kernel -> {"bytes_per_launch", "units_per_launch",
+    "source_sha"}; an entry whose kernel source changed since the capture is ignored.
+    """
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    src = {"pairs": "sidm_pairs.cu", "knn": "sidm_knn.cu"}
+    out = {}
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except Exception:
+        return out
+    for k, v in d.items():
+        f = os.path.join(ROOT, "paper_2506_06269_gb300", "csrc", src.get(k, ""))
+        if os.path.isfile(f) and v.get("source_sha") == source_sha(f):
+            out[k] = v
+    return out
+
+
+def dt_rule(ctx_cls, halo, vmax, device):
+    """dt = 0.04 / q99.9(sum_j P_ij / dt) on the initial state (SIDM time-step proxy)."""
+    import torch
+    from paper_2506_06269_gb300 import sidm
+    n = halo.n
+    c = ctx_cls(n_max=n, halo_max=1, ngb_max=N_NGB, event_cap=16, precision="mixed", device=device,
+                flags=sidm.SIDM_FLAG_SUM_P)
+    dev = c.device
+    pos = torch.tensor(halo.pos, device=dev)
+    vel = torch.tensor(halo.vel.astype(np.float32), device=dev)
+    ids = torch.tensor(halo.ids.astype(np.int64), device=dev).to(torch.int32)
+    h = torch.zeros(n, dtype=torch.float32, device=dev)
+    c.build_cells([0, n], pos, vel, ids)
+    c.kernel_sizes([N_NGB], h)
+    c.scatter_step(0, 0, c.xs_tensor([(1, S0, vmax)]), c.f64([1.0]), c.f64([halo.mass]), vel)
+    c.status()                        # event overflow is expected here (dt = 1)
+    sp = c.sum_p(n).cpu().numpy().astype(np.float64)
+    c.close()
+    q = float(np.quantile(sp, 0.999))
+    return TAU / q, q
+
+
+def time_steps(ctx, step_fn, k, flush, first_step):
+    import torch
+    s = torch.cuda.current_stream()
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+    for i in range(k):
+        flush.zero_()
+        e0[i].record(s)
+        step_fn(first_step + i, i)
+        e1[i].record(s)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in zip(e0, e1)]
+
+
+def run_ours(args):
+    import torch
+    from paper_2506_06269_gb300 import build, sidm
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    build.build()
+    torch.cuda.set_device(local)
+    n = args.n
+    halo, vmax = make_halo(n, SEED_IC + rank)
+    dt, q999 = dt_rule(sidm.Context, halo, vmax, local)
+    ctx = sidm.Context(n_max=n, halo_max=1, ngb_max=N_NGB, event_cap=max(1 << 16, n // 8), precision="mixed",
+                       device=local, flags=sidm.SIDM_FLAG_TIMING, use_tma=args.use_tma)
+    dev = ctx.device
+    off = [0, n]
+    pos = torch.tensor(halo.pos, device=dev)
+    vel = torch.tensor(halo.vel.astype(np.float32), device=dev)
+    ids = torch.tensor(halo.ids.astype(np.int64), device=dev).to(torch.int32)
+    h = torch.zeros(n, dtype=torch.float32, device=dev)
+    xs = ctx.xs_tensor([(1, S0, vmax)])
+    dt_t = ctx.f64([dt])
+    mass_t = ctx.f64([halo.mass])
+    K, W = args.steps, args.warmup
+    stats = torch.zeros((max(K, W, 1), sidm.STATS_DTYPE.itemsize), dtype=torch.uint8, device=dev)
+    energy = torch.zeros((max(K, 1) + 1, 4), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    seed = 20250617 + rank
+
+    def step(step_no, slot):
+        ctx.drift(dt_t, pos, vel)
+        ctx.build_cells(off, pos, vel, ids)
+        ctx.kernel_sizes([N_NGB], h)
+        ctx.scatter_step(seed, step_no, xs, dt_t, mass_t, vel, stats[slot])
+        ctx.energy_momentum(mass_t, vel, energy[slot + 1])
+
+    ctx.build_cells(off, pos, vel, ids)          # layout upload happens here, once
+    for i in range(W):
+        step(i, i)
+    torch.cuda.synchronize()
+    if ctx.status() != 0:
+        raise RuntimeError(f"device status after warm-up: {ctx.status()}")
+    ctx.energy_momentum(mass_t, vel, energy[0])
+    ctx.kernel_times(reset=True)
+    l0 = ctx.launch_count()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    times = time_steps(ctx, step, K, flush, W)
+    clocks = clk.stop()
+    gpu_launches = ctx.launch_count() - l0
+    kms, kcnt = ctx.kernel_times(reset=True)
+    status = ctx.status()
+    total_ms = float(sum(times))
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    st = [sidm.parse_stats(stats[i]) for i in range(K)]
+    E = energy.cpu().numpy()
+    e0 = E[0, 0]
+    drift = float(np.max(np.abs(E[1:K + 1, 0] - e0)) / abs(e0)) if K else 0.0
+    book = float(sum(s.d_energy for s in st))
+    n_pairs = sum(s.n_pairs for s in st)
+    n_tested = sum(s.n_tested for s in st)
+    n_events = sum(s.n_events for s in st)
+
+    res = {
+        "ctx": ctx, "halo": halo, "vmax": vmax, "dt": dt, "q999": q999, "times": times, "total_ms": total_ms,
+        "clocks": clocks, "gpu_launches": gpu_launches, "kms": kms, "kcnt": kcnt, "status": status,
+        "drift": drift, "book": book, "n_pairs": n_pairs, "n_tested": n_tested, "n_events": n_events,
+        "stats": st, "ws": ws, "rank": rank, "local": local, "tensors": (pos, vel, ids, h, xs, dt_t, mass_t),
+        "step": step, "seed": seed,
+    }
+    return res
+
+
+def run_e2e(res, steps):
+    """Same metric through the C ABI with host buffers: every step copies its
+    inputs (positions, velocities, ids) from pinned host memory and reads the
+    results (velocities and the energy/momentum) back."""
+    import torch
+    ctx = res["ctx"]
+    halo = res["halo"]
+    n = halo.n
+    pos, vel, ids, h, xs, dt_t, mass_t = res["tensors"]
+    hp = torch.tensor(halo.pos).pin_memory()
+    hv = torch.tensor(halo.vel.astype(np.float32)).pin_memory()
+    hi = torch.tensor(halo.ids.astype(np.int64)).to(torch.int32).pin_memory()
+    out_v = torch.empty_like(hv).pin_memory()
+    out_e = torch.empty((steps, 4), dtype=torch.float64).pin_memory()
+    energy = torch.zeros(4, dtype=torch.float64, device=ctx.device)
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for i in range(steps):
+        pos.copy_(hp, non_blocking=True)
+        vel.copy_(hv, non_blocking=True)
+        ids.copy_(hi, non_blocking=True)
+        ctx.drift(dt_t, pos, vel)
+        ctx.build_cells([0, n], pos, vel, ids)
+        ctx.kernel_sizes([N_NGB], h)
+        ctx.scatter_step(res["seed"], 10_000 + i, xs, dt_t, mass_t, vel)
+        ctx.energy_momentum(mass_t, vel, energy)
+        out_v.copy_(vel, non_blocking=True)
+        out_e[i].copy_(energy, non_blocking=True)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    h2d = hp.numel() * 8 + hv.numel() * 4 + hi.numel() * 4
+    d2h = out_v.numel() * 4 + 4 * 8
+    return {"value": n * steps / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "steps": steps}
+
+
+def run_fp64(res, steps):
+    """All-FP64 form of the same pass on identical inputs (FP64 positions,
+    velocities, distances, kernel sizes, probabilities and updates)."""
+    import torch
+    from paper_2506_06269_gb300 import sidm
+    halo, vmax, dt = res["halo"], res["vmax"], res["dt"]
+    n = halo.n
+    c = sidm.Context(n_max=n, halo_max=1, ngb_max=N_NGB, event_cap=max(1 << 16, n // 8), precision="fp64",
+                     device=res["local"])
+    dev = c.device
+    pos = torch.tensor(halo.pos, device=dev)
+    vel = torch.tensor(halo.vel.astype(np.float32).astype(np.float64), device=dev)
+    ids = torch.tensor(halo.ids.astype(np.int64), device=dev).to(torch.int32)
+    h = torch.zeros(n, dtype=torch.float64, device=dev)
+    xs = c.xs_tensor([(1, S0, vmax)]); dt_t = c.f64([dt]); mass_t = c.f64([halo.mass])
+    energy = torch.zeros((steps + 1, 4), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step(step_no, slot):
+        c.drift(dt_t, pos, vel)
+        c.build_cells([0, n], pos, vel, ids)
+        c.kernel_sizes([N_NGB], h)
+        c.scatter_step(res["seed"], step_no, xs, dt_t, mass_t, vel)
+        c.energy_momentum(mass_t, vel, energy[slot + 1])
+
+    c.build_cells([0, n], pos, vel, ids)
+    step(0, 0)
+    torch.cuda.synchronize()
+    c.energy_momentum(mass_t, vel, energy[0])
+    times = time_steps(c, step, steps, flush, 1)
+    E = energy.cpu().numpy()
+    st = c.status()
+    c.close()
+    ms = float(sum(times))
+    return {"value": n * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+            "energy_drift": float(np.max(np.abs(E[1:, 0] - E[0, 0])) / abs(E[0, 0])), "status": st}
+
+
+def cpu_baseline(dt, vmax, threads=None):
+    """The oracle as it stands, on the host cores: one full oracle step on an
+    NFW halo of 32,768 particles drawn the same way (same profile, N_ngb, sigma(v),
+    dt).  Per-particle work depends on N_ngb, not on N."""
+    from oracle import oracle as O
+    from paper_2506_06269_gb300 import ics
+    ns = 32768
+    th = threads or os.cpu_count() or 1
+    O.set_num_threads(th)
+    halo = ics.nfw(ns, SEED_IC)
+    vel = halo.vel.astype(np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    r = O.step(halo.pos, vel, halo.ids, [0, ns], [N_NGB], [halo.mass], [(1, S0, vmax)], [dt], 1, 0, O.MODE_MIXED)
+    sec = time.perf_counter() - t0
+    return {"value": ns / sec, "unit": UNIT, "cores": int(O.num_threads()), "kind": "oracle",
+            "sample": f"one full oracle step (kNN, pair probabilities with exact Lambda quadrature, draws, "
+                      f"sequential scatter) of a {ns}-particle NFW halo, same profile/N_ngb/sigma(v)/dt; "
+                      f"{sec:.2f} s", "seconds": sec, "pairs": int(r["stats"][0]["n_pairs"])}
+
+
+def roofline(res, peaks, peak_src):
+    """Roofline of the dominant hot kernel (by measured event time)."""
+    kms, kcnt = res["kms"], res["kcnt"]
+    K = max(1, len(res["times"]))
+    clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = N_SM * LANES_PER_SM * clock_mhz * 1e6 / 1e12          # T lane-ops/s
+    traffic = load_traffic()
+    names = {0: "build", 1: "knn", 2: "pairs", 3: "resolve"}
+    dom = max(range(4), key=lambda i: kms[i])
+    name = names[dom]
+    launches = max(1, int(kcnt[dom]))
+    per_launch_ms = kms[dom] / launches
+    n = res["halo"].n
+    if name == "pairs":
+        ops = (res["n_tested"] * OPS_PER_TEST + res["n_pairs"] * OPS_PER_PAIR) / K
+        achieved = ops / (per_launch_ms * 1e-3) / 1e12
+        tr = traffic.get("pairs")
+        return {"kernel": "k_pairs", "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
+                "frac": achieved / alu_peak, "traffic": (tr["bytes_per_launch"] * n / tr["units_per_launch"]) if tr else None,
+                "peak_source": f"derived: {N_SM} SMs x {LANES_PER_SM} FP32/INT32 lanes x {clock_mhz:.0f} MHz "
+                               f"({peak_src} sm_max_mhz)",
+                "ops_per_unit": {"candidate_test": OPS_PER_TEST, "pair_eval": OPS_PER_PAIR},
+                "ms_per_launch": per_launch_ms}
+    if name == "knn":
+        cand = res.get("knn_candidates_per_step")
+        tr = traffic.get("knn")
+        achieved = (cand * OPS_PER_KNN_CAND) / (per_launch_ms * 1e-3) / 1e12 if cand else None
+        return {"kernel": "k_knn", "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
+                "frac": (achieved / alu_peak) if achieved else None,
+                "traffic": (tr["bytes_per_launch"] * n / tr["units_per_launch"]) if tr else None,
+                "peak_source": f"derived: {N_SM} SMs x {LANES_PER_SM} lanes x {clock_mhz:.0f} MHz ({peak_src})",
+                "ms_per_launch": per_launch_ms}
+    # the cell build is a streaming (HBM) sequence
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    bytes_per_particle = 520.0
+    achieved = bytes_per_particle * n / (per_launch_ms * 1e-3) / 1e9
+    return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": None, "peak_source": f"{peak_src} hbm_gbs",
+            "ms_per_launch": per_launch_ms}
+
+
+def emit(line):
+    print(json.dumps(line), flush=True)
+
+
+def main_ours(args):
+    import torch
+    res = run_ours(args)
+    ws, rank = res["ws"], res["rank"]
+    K, W = args.steps, args.warmup
+    n = res["halo"].n
+    total_ms = res["total_ms"]
+    value = ws * n * K / (total_ms * 1e-3)
+    peaks, peak_src = load_peaks()
+    line = None
+    if rank == 0:
+        e2e = run_e2e(res, min(K, 10))
+        fp64 = run_fp64(res, args.fp64_steps) if args.fp64_steps > 0 else None
+        kms = res["kms"]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
+            "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_particles": n, "n_ngb": N_NGB,
+                       "cross_section": f"sigma/m = {S0}/(1+(v/{res['vmax']:.4f})^2)^2", "dt": res["dt"],
+                       "dt_rule": "0.04 / q99.9(sum_j P_ij/dt) on the initial state", "precision": "mixed",
+                       "step": "drift + cell build + kernel sizes + pairs/draws/scatter + FP64 E,p",
+                       "l2": "flushed before every timed step (256 MiB write, outside the step events)",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU", "use_tma": args.use_tma},
+            "pair_evals_per_s": ws * res["n_pairs"] / (total_ms * 1e-3),
+            "events_per_step": res["n_events"] / K,
+            "energy_drift": res["drift"],
+            "energy_bookkeeping_dE": res["book"],
+            "kernel_ms_per_step": {"build": kms[0] / K, "knn": kms[1] / K, "pairs": kms[2] / K, "resolve": kms[3] / K},
+            "roofline": roofline(res, peaks, peak_src),
+            "e2e": e2e,
+            "clocks": res["clocks"],
+            "gpu_launches": int(res["gpu_launches"]),
+            "device_status": res["status"],
+        }
+        if fp64:
+            line["fp64_form"] = fp64
+            line["mixed_over_fp64"] = value / ws / fp64["value"]
+        if not args.no_cpu_baseline and ws == 1:
+            line["cpu_baseline"] = cpu_baseline(res["dt"], res["vmax"])
+        emit(line)
+    res["ctx"].close()
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+def main_reference(args):
+    """The oracle (CPU, FP64, as it stands) timed on the host cores: each step
+    is one full oracle step on a bounded sample of the workload."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2506_06269_gb300 import ics
+    O.build()
+    ns = 32768
+    th = os.cpu_count() or 1
+    O.set_num_threads(th)
+    halo = ics.nfw(ns, SEED_IC)
+    vmax = ics.nfw_vmax()
+    # dt of the same rule, evaluated on the oracle's own sample
+    h, _, _ = O.knn(halo.pos, halo.ids, N_NGB, O.MODE_MIXED)
+    vel = halo.vel.astype(np.float32).astype(np.float64)
+    _, _, sump = O.pairs(halo.pos, vel, halo.ids, h, O.MODE_MIXED, (1, S0, vmax), halo.mass, 1.0, 0, 0, 0,
+                         ev_cap=1 << 22)
+    dt = TAU / float(np.quantile(sump, 0.999))
+    pos = halo.pos.copy()
+
+    def one(step_no):
+        nonlocal pos, vel
+        pos = pos + vel * dt
+        r = O.step(pos, vel.astype(np.float32).astype(np.float64), halo.ids, [0, ns], [N_NGB], [halo.mass],
+                   [(1, S0, vmax)], [dt], 7, step_no, O.MODE_MIXED)
+        vel = r["vel_out"]
+        O.energy_momentum(halo.mass, vel)
+
+    for i in range(args.warmup):
+        one(i)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        one(args.warmup + i)
+    sec = time.perf_counter() - t0
+    value = ns * args.steps / sec
+    emit({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+          "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / max(args.steps, 1),
+          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+          "config": {"workload": WORKLOAD, "sample_particles": ns, "n_ngb": N_NGB, "dt": dt},
+          "cpu_baseline": {"value": value, "unit": UNIT, "cores": int(O.num_threads()), "kind": "oracle",
+                           "sample": f"each step: drift + full oracle step of a {ns}-particle NFW halo "
+                                     f"(same profile, N_ngb, sigma(v), dt rule)"},
+          "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        main_reference(a)
+    else:
+        main_ours(a)

@@ -1,0 +1,245 @@
+/*
+ * sidm.h -- C ABI of the GB300 (sm_103a) SIDM scattering pass.
+ *
+ * The pass is the per-step self-interaction step of the N-body method of
+ * Fischer, Yu & Dolag (2025), "Accurately simulating core-collapse
+ * self-interacting dark matter halos":
+ *   (a) kernel sizes h_i from the N_ngb nearest neighbours (Sect. 2),
+ *   (b) pair interaction probabilities over kernel overlaps
+ *       P_ij = (sigma(v_ij)/m) m_j |v_ij| Lambda_ij dt (Sect. 3.5, Eq. vel_dep),
+ *   (c) scatter draws and isotropic, energy- and momentum-conserving velocity
+ *       updates (Sect. 2, Sect. 5), with a deterministic order for particles
+ *       hit more than once in a step.
+ *
+ * Conventions for every call
+ *   - All pointers named *_dev are device pointers on the context's device;
+ *     pointers without that suffix are host pointers.  Particle arrays are SoA:
+ *     a "[3][N]" array holds x[0..N), then y[0..N), then z[0..N).
+ *   - The caller owns every particle array and every output.  The context owns
+ *     only its scratch, allocated once by sidm_create; no other call allocates.
+ *   - Calls are asynchronous on the given stream (0 = legacy default stream)
+ *     unless stated otherwise.  A call that returns non-zero has enqueued
+ *     nothing that writes a caller array.
+ *   - Return value: 0 on success, a negative SIDM_E* code otherwise;
+ *     sidm_last_error() gives a one-line message.
+ *   - Failures found on the device (capacity, round limit, bad input) set bits
+ *     of a device-side status word, read by sidm_status().  Nothing traps, and
+ *     every wait inside a kernel is bounded.
+ *   - Halo layout: particles of halo h are [halo_off[h], halo_off[h+1]) of the
+ *     particle arrays.  Every particle of a halo has the same mass, ids are
+ *     unique within a halo and smaller than 2^27; at most 1024 halos.
+ */
+#ifndef SIDM_H
+#define SIDM_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* error codes */
+#define SIDM_OK          0
+#define SIDM_EINVAL     -1   /* bad argument or call order                        */
+#define SIDM_ECAPACITY  -2   /* a capacity given to sidm_create is too small      */
+#define SIDM_ECUDA      -3   /* a CUDA runtime call failed                        */
+#define SIDM_EROUNDS    -4   /* the resolve round limit was hit (see sidm_status) */
+#define SIDM_EDEVICE    -5   /* the device status word is non-zero               */
+
+/* device status word bits (sidm_status) */
+#define SIDM_DEV_EVENT_OVERFLOW  0x1u  /* more events than event_cap: velocities untouched */
+#define SIDM_DEV_ROUNDS          0x2u  /* resolve stopped at max_rounds                     */
+#define SIDM_DEV_STACK           0x4u  /* tree traversal stack overflow (results invalid)   */
+#define SIDM_DEV_BAD_INPUT       0x8u  /* id >= 2^27 or non-finite position                 */
+#define SIDM_DEV_WAIT_TIMEOUT    0x10u /* a bounded wait on an async copy gave up           */
+
+/* precision forms */
+#define SIDM_MIXED 0   /* FP32 offsets/velocities/probabilities, FP64 reductions */
+#define SIDM_FP64  1   /* every step in FP64                                     */
+
+/* sidm_config.flags */
+#define SIDM_FLAG_SUM_P   0x1  /* accumulate sum_j P_ij per particle (diagnostic) */
+#define SIDM_FLAG_TIMING  0x2  /* time hot kernels with CUDA events (sidm_kernel_times) */
+
+typedef struct sidm_ctx sidm_ctx;
+
+typedef struct {
+    int64_t n_max;       /* particle capacity (all halos together), >= 1            */
+    int32_t halo_max;    /* halo capacity, 1..1024                                  */
+    int32_t ngb_max;     /* largest N_ngb of any halo, 1..128                       */
+    int64_t event_cap;   /* scatter events kept per step, >= 1                      */
+    int32_t precision;   /* SIDM_MIXED or SIDM_FP64                                 */
+    int32_t device;      /* CUDA device ordinal                                      */
+    int32_t knn_warps;   /* warps per CTA of the neighbour kernel, 0 = default       */
+    int32_t pair_warps;  /* warps per CTA of the pair kernel, 0 = default            */
+    int32_t max_rounds;  /* resolve round limit, 0 = default (256)                   */
+    int32_t flags;       /* SIDM_FLAG_*                                              */
+    int32_t grid_ctas;   /* persistent CTAs per kernel, 0 = SM count x occupancy     */
+    int32_t use_tma;     /* 1: stage candidate tiles with bulk async copies (TMA)    */
+} sidm_config;
+
+/* Cross-section per unit mass of one halo (Sect. 3.8, Eq. vel_dep):
+ * kind 0: sigma/m = s0 (velocity independent);
+ * kind 1: sigma/m = s0 / (1 + (v/w)^2)^2, v = |v_i - v_j| the pair speed.
+ * Isotropic scattering, so the viscosity normalisation of App. A gives
+ * sigma_V = sigma.  Code units. */
+typedef struct {
+    int32_t kind;
+    int32_t pad_;
+    double s0;
+    double w;
+} sidm_xs;
+
+/* Per-step statistics, written by sidm_scatter_step (device memory). */
+typedef struct {
+    unsigned long long n_pairs;   /* in-range pairs whose P was formed            */
+    unsigned long long n_events;  /* accepted events (can exceed event_cap)       */
+    unsigned long long n_p_gt1;   /* pairs with P > 1 (no clamp; always fire)     */
+    unsigned long long n_near;    /* pairs with |P - u| < 1e-6                   */
+    unsigned long long n_multi;   /* particles in more than one event            */
+    unsigned int rounds;          /* resolve rounds used                          */
+    unsigned int status;          /* SIDM_DEV_* bits raised by this step          */
+    double d_energy;              /* sum over events of the change of the pair's  */
+                                  /* kinetic energy from the stored velocities    */
+                                  /* (FP64, exact fixed-point accumulation)       */
+    float max_sum_p;              /* max_i sum_j P_ij (SIDM_FLAG_SUM_P only)      */
+    float pad_;
+    unsigned long long n_tested;  /* candidate pairs given the in-range test      */
+} sidm_step_stats;
+
+/* One accepted scatter event, as kept for the current step. */
+typedef struct {
+    unsigned long long key;       /* halo<<54 | min id<<27 | max id               */
+    uint32_t i, j;                /* particle indices (i has the smaller id)      */
+    uint32_t x1, x2;              /* Philox words 1, 2 (scattering direction)     */
+    float P;                      /* interaction probability                      */
+    uint32_t x0;                  /* Philox word 0 (u = x0 * 2^-32)               */
+} sidm_event;
+
+/* Create a context on cfg->device: checks the configuration, allocates all
+ * scratch for n_max particles / halo_max halos / event_cap events, and fills
+ * the Lambda lookup table (FP64 quadrature of the spline overlap, Sect. 3.5).
+ * Synchronous.  On failure *ctx is NULL. */
+int sidm_create(sidm_ctx** ctx, const sidm_config* cfg);
+
+/* Free the context and all its scratch (synchronous). NULL is a no-op. */
+int sidm_destroy(sidm_ctx* ctx);
+
+/* Message of the last failed call on this context (never NULL). */
+const char* sidm_last_error(const sidm_ctx* ctx);
+
+/* Message of the last failed sidm_create (thread-local). */
+const char* sidm_create_error(void);
+
+/* (a0) Cell build.  Sorts the particles of every halo by a 3 x 17-bit Morton
+ * key of a power-of-two cube around the halo, permutes pos/vel/id in place
+ * into that order, and builds leaves of 32 consecutive particles with FP32
+ * offsets to power-of-two cell origins, bounding boxes and a bounding-volume
+ * tree.  Replaces the neighbour-search structure of Sect. 2.
+ *   n_halos    : 1..halo_max
+ *   halo_off   : host int64[n_halos+1], non-decreasing, halo_off[0] == 0,
+ *                halo_off[n_halos] <= n_max.  A changed layout is uploaded by
+ *                this call (host -> device copy); an unchanged one is not.
+ *   pos_dev    : f64 [3][N] positions (reordered in place)
+ *   vel_dev    : [3][N] velocities, f32 (SIDM_MIXED) or f64 (SIDM_FP64)
+ *                (reordered in place)
+ *   id_dev     : u32 [N] particle ids (reordered in place)
+ * Must be called again after any change of the positions. */
+int sidm_build_cells(sidm_ctx* ctx, int32_t n_halos, const int64_t* halo_off,
+                     double* pos_dev, void* vel_dev, uint32_t* id_dev, cudaStream_t stream);
+
+/* (a1) Kernel sizes (Sect. 2; Eq. hDl): h_i = distance to the N_ngb-th nearest
+ * other particle of the same halo, in the precision form's distance (FP32
+ * canonical offset distance or FP64).
+ *   n_ngb   : host int32[n_halos], 1 <= n_ngb[h] <= ngb_max and
+ *             n_ngb[h] < particles of halo h (empty halos are skipped)
+ *   h_dev   : out, f32 (SIDM_MIXED) or f64 (SIDM_FP64) [N], in the order left
+ *             by sidm_build_cells
+ * Requires a preceding sidm_build_cells. */
+int sidm_kernel_sizes(sidm_ctx* ctx, const int32_t* n_ngb, void* h_dev, cudaStream_t stream);
+
+/* (a2-a4) Scatter step.  For every unordered pair of a halo with
+ * d_ij < h_i + h_j: Lambda_ij, P_ij = (sigma(v_ij)/m) m |v_ij| Lambda_ij dt
+ * from the step-start velocities, u = Philox4x32-10(key = seed,
+ * counter = (step mod 2^32, min id, max id, halo)) word 0 times 2^-32, event iff
+ * u < P.  Events are applied in ascending (halo, min id, max id) order, each
+ * from the current velocities: v_cm +- (m_j/M)|dv| n, n isotropic from Philox
+ * words 1 and 2 (cos theta = 2 u1 - 1, phi = 2 pi u2); the smaller id gets +.
+ *   seed, step  : Philox key and counter word 0
+ *   xs_dev      : device sidm_xs[n_halos]
+ *   dt_dev      : device f64[n_halos] time step per halo
+ *   mass_dev    : device f64[n_halos] particle mass per halo
+ *   vel_dev     : [3][N] velocities (f32 or f64 by precision), updated in place
+ *   stats_dev   : device sidm_step_stats, overwritten (may be NULL)
+ * If more than event_cap events are drawn, no velocity is changed and
+ * SIDM_DEV_EVENT_OVERFLOW is raised.  Requires sidm_kernel_sizes. */
+int sidm_scatter_step(sidm_ctx* ctx, uint64_t seed, uint64_t step, const sidm_xs* xs_dev,
+                      const double* dt_dev, const double* mass_dev, void* vel_dev,
+                      sidm_step_stats* stats_dev, cudaStream_t stream);
+
+/* (a5) Per-halo kinetic energy and momentum, E = sum 1/2 m |v|^2,
+ * p = sum m v, in FP64 with compensated (two-sum) accumulation in a fixed
+ * order, so repeated calls give identical bits (the paper tracks energy
+ * conservation throughout, Sect. 3.4).
+ *   mass_dev : device f64[n_halos]
+ *   vel_dev  : [3][N] velocities (f32 or f64 by precision)
+ *   out_dev  : device f64[n_halos][4] = (E, px, py, pz)
+ *   comp_dev : device f64[n_halos][4] residual compensation terms, or NULL
+ * Requires sidm_build_cells (for the halo layout). */
+int sidm_energy_momentum(sidm_ctx* ctx, const double* mass_dev, const void* vel_dev,
+                         double* out_dev, double* comp_dev, cudaStream_t stream);
+
+/* Synchronise the stream, return the device status word (SIDM_DEV_* bits
+ * raised since the last sidm_status) in *status and clear it.  Returns
+ * SIDM_EDEVICE if it was non-zero, SIDM_ECUDA on a CUDA error. */
+int sidm_status(sidm_ctx* ctx, cudaStream_t stream, uint32_t* status);
+
+/* ---- harness and test entry points -------------------------------------- */
+
+/* Permutation of the last sidm_build_cells: perm_dev[s] = index, before that
+ * call, of the particle now at position s.  device u32[N]. */
+int sidm_get_perm(sidm_ctx* ctx, uint32_t* perm_dev, cudaStream_t stream);
+
+/* Neighbour ids of the last kernel-size pass (mixed form only): for particle s
+ * the ids of its n_ngb nearest others in ascending (canonical d^2, id) order.
+ *   nbr_dev : device u32[N][k_stride], k_stride >= max n_ngb. */
+int sidm_neighbours(sidm_ctx* ctx, const int32_t* n_ngb, int32_t k_stride,
+                    uint32_t* nbr_dev, cudaStream_t stream);
+
+/* Copy the events kept by the last sidm_scatter_step, in the order they were
+ * drawn (not sorted), to ev_dev[0..min(cap, n)); *n_host receives the event
+ * count (synchronises the stream). */
+int sidm_get_events(sidm_ctx* ctx, int64_t cap, sidm_event* ev_dev, int64_t* n_host,
+                    cudaStream_t stream);
+
+/* Evaluate the device Lambda(d; h_i, h_j) (lookup table of the context's
+ * precision) for n triples; all device f64 arrays. */
+int sidm_lambda_eval(sidm_ctx* ctx, int64_t n, const double* d_dev, const double* hi_dev,
+                     const double* hj_dev, double* out_dev, cudaStream_t stream);
+
+/* Ballistic drift x += v dt per halo (harness for multi-step runs):
+ * dt_dev device f64[n_halos]; pos f64 [3][N]; vel f32/f64 [3][N]. */
+int sidm_drift(sidm_ctx* ctx, const double* dt_dev, double* pos_dev, const void* vel_dev,
+               cudaStream_t stream);
+
+/* Per-particle sum_j P_ij of the last scatter step (SIDM_FLAG_SUM_P), f32 [N]. */
+int sidm_get_sum_p(sidm_ctx* ctx, float* out_dev, cudaStream_t stream);
+
+/* Kernels launched by the calls above since the context was created. */
+int64_t sidm_launch_count(const sidm_ctx* ctx);
+
+/* Device time of the hot kernels, measured with CUDA events recorded on the
+ * launching stream around each launch (contexts created with
+ * SIDM_FLAG_TIMING; at most 4096 launches are recorded between resets).
+ *   ms_out[4]    : milliseconds of {cell build (whole a0 sequence), kernel-size
+ *                  kernel, pair kernel, resolve kernel} since the last reset
+ *   count_out[4] : launches recorded per slot (may be NULL)
+ *   reset        : non-zero clears the record afterwards
+ * Synchronises the device. */
+int sidm_kernel_times(sidm_ctx* ctx, double* ms_out, int64_t* count_out, int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SIDM_H */

@@ -1,0 +1,1306 @@
+// sidm_api.cu -- C ABI of libsidm: context, cell build (a0), scatter resolve
+// (a4), energy/momentum reduction (a5), harness kernels, and the host-side
+// FP64 quadrature that fills the Lambda lookup table.
+//
+// Paper: Fischer, Yu & Dolag (2025).  Sect. 2 (spline kernel, N_ngb-adaptive
+// kernel size, explicit energy and momentum conservation), Sect. 3.5 (the
+// geometric factor Lambda of the interaction probability), Sect. 5
+// (conservation independent of the kernel).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+
+#include "sidm_internal.cuh"
+
+using namespace sidm;
+
+namespace {
+
+thread_local std::string g_create_err;
+
+constexpr int kChunk = 16384;        // particles per reduction chunk
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kSortWarps = kSortThreads / 32;
+
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+__device__ __forceinline__ int halo_of(const int64_t* __restrict__ off, int H, int64_t s)
+{
+    int lo = 0, hi = H - 1;               // largest h with off[h] <= s
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(off + mid) <= s) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int bsearch32(const int32_t* __restrict__ off, int H, int32_t s)
+{
+    int lo = 0, hi = H - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(off + mid) <= s) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ unsigned long long spread3(uint32_t v)
+{
+    unsigned long long x = v & 0x1FFFFFu;
+    x = (x | (x << 32)) & 0x1F00000000FFFFull;
+    x = (x | (x << 16)) & 0x1F0000FF0000FFull;
+    x = (x | (x << 8)) & 0x100F00F00F00F00Full;
+    x = (x | (x << 4)) & 0x10C30C30C30C30C3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+__device__ __forceinline__ uint32_t compact3(unsigned long long x)
+{
+    x &= 0x1249249249249249ull;
+    x = (x ^ (x >> 2)) & 0x10C30C30C30C30C3ull;
+    x = (x ^ (x >> 4)) & 0x100F00F00F00F00Full;
+    x = (x ^ (x >> 8)) & 0x1F0000FF0000FFull;
+    x = (x ^ (x >> 16)) & 0x1F00000000FFFFull;
+    x = (x ^ (x >> 32)) & 0x1FFFFFull;
+    return (uint32_t)x;
+}
+
+// ------------------------------------------------------------------ a0 kernels
+// Per-halo bounding box (exact FP64 min/max through order-preserving atomics).
+__global__ void k_bbox(const double* __restrict__ pos, int64_t N, const int32_t* __restrict__ chunk_halo,
+                       const int64_t* __restrict__ chunk_begin, const int64_t* __restrict__ halo_off,
+                       int H, unsigned long long* __restrict__ bb)
+{
+    const int c = blockIdx.x;
+    const int h = chunk_halo[c];
+    const int64_t b = chunk_begin[c];
+    int64_t e = b + kChunk;
+    if (e > halo_off[h + 1]) e = halo_off[h + 1];
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t s = b + threadIdx.x; s < e; s += blockDim.x) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double v = pos[a * N + s];
+            mn[a] = fmin(mn[a], v);
+            mx[a] = fmax(mx[a], v);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[a] = fmin(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+            mx[a] = fmax(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (mn[a] <= mx[a]) {
+                atomicMin(&bb[a * H + h], dbl_to_ord(mn[a]));
+                atomicMax(&bb[(3 + a) * H + h], dbl_to_ord(mx[a]));
+            }
+        }
+    }
+}
+
+// Halo frame: 2^E > largest extent, O = floor(min / 2^E) 2^E per axis.
+__global__ void k_frame(int H, const int64_t* __restrict__ halo_off, const unsigned long long* __restrict__ bb,
+                        HaloFrame* __restrict__ fr)
+{
+    int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= H) return;
+    HaloFrame f;
+    double mn[3], ext = 0.0;
+    const bool empty = halo_off[h + 1] == halo_off[h];
+    for (int a = 0; a < 3; ++a) {
+        mn[a] = empty ? 0.0 : ord_to_dbl(bb[a * H + h]);
+        double mx = empty ? 0.0 : ord_to_dbl(bb[(3 + a) * H + h]);
+        ext = fmax(ext, mx - mn[a]);
+    }
+    int E = 0;
+    if (ext > 0.0) frexp(ext, &E);           // ext = m 2^E, m in [1/2, 1)
+    for (int a = 0; a < 3; ++a) f.O[a] = ldexp(floor(ldexp(mn[a], -E)), E);
+    f.E = E;
+    f.cube = (float)ldexp(1.0, E + 1);
+    f.margin = (float)ldexp(1.0, E + 1 - 20);
+    f.fine = (float)ldexp(1.0, E + 1 - kMortonBits);
+    fr[h] = f;
+}
+
+// Sort key = halo << 51 | Morton(q), q = floor((x - O) 2^(17-E-1)) clamped.
+__global__ void k_keys(const double* __restrict__ pos, int64_t N, const int64_t* __restrict__ halo_off, int H,
+                       const HaloFrame* __restrict__ fr, unsigned long long* __restrict__ key, uint32_t* __restrict__ val)
+{
+    const uint32_t qmax = (1u << kMortonBits) - 1u;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+        const int h = halo_of(halo_off, H, s);
+        const HaloFrame f = fr[h];
+        uint32_t q[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double t = ldexp(__dsub_rn(pos[a * N + s], f.O[a]), kMortonBits - f.E - 1);
+            double fl = floor(t);
+            q[a] = fl <= 0.0 ? 0u : (fl >= (double)qmax ? qmax : (uint32_t)fl);
+        }
+        key[s] = ((unsigned long long)h << kHaloShift) | spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2);
+        val[s] = (uint32_t)s;
+    }
+}
+
+// ---- stable LSD radix sort of (u64 key, u32 value), 8-bit digits -----------
+__global__ void k_sort_hist(const unsigned long long* __restrict__ key, int64_t n, int shift, int nblk,
+                            uint32_t* __restrict__ hist)
+{
+    __shared__ uint32_t cnt[256];
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+#pragma unroll 4
+    for (int i = 0; i < kSortItems; ++i) {
+        int64_t s = base + i * kSortThreads + threadIdx.x;
+        if (s < n) atomicAdd(&cnt[(uint32_t)(key[s] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// exclusive scan of hist[0..len) by one CTA of 1024 threads (contiguous segments)
+__global__ void k_sort_scan(uint32_t* __restrict__ hist, int64_t len)
+{
+    __shared__ uint32_t part[1024];
+    const int64_t seg = (len + 1023) / 1024;
+    const int64_t b = threadIdx.x * seg;
+    int64_t e = b + seg; if (e > len) e = len;
+    uint32_t sum = 0;
+    for (int64_t i = b; i < e; ++i) sum += hist[i];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        uint32_t v = threadIdx.x >= o ? part[threadIdx.x - o] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
+    for (int64_t i = b; i < e; ++i) { uint32_t v = hist[i]; hist[i] = run; run += v; }
+}
+
+// Scatter of one tile in 16 rounds of 256 consecutive keys; the rank of a key
+// among equal digits is (earlier rounds) + (earlier warps) + (earlier lanes),
+// which keeps the sort stable.
+__global__ void k_sort_scatter(const unsigned long long* __restrict__ key, const uint32_t* __restrict__ val,
+                               int64_t n, int shift, int nblk, const uint32_t* __restrict__ hist,
+                               unsigned long long* __restrict__ okey, uint32_t* __restrict__ oval)
+{
+    __shared__ uint32_t run[256];
+    __shared__ uint32_t woff[kSortWarps][256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    run[threadIdx.x] = hist[(int64_t)threadIdx.x * nblk + blockIdx.x];
+    const int64_t tile = (int64_t)blockIdx.x * kSortTile;
+    for (int r = 0; r < kSortItems; ++r) {
+        if (tile + r * kSortThreads >= n) break;          // uniform across the CTA
+#pragma unroll
+        for (int w = 0; w < kSortWarps; ++w) woff[w][threadIdx.x] = 0u;
+        __syncthreads();
+        const int64_t s = tile + r * kSortThreads + threadIdx.x;
+        const bool ok = s < n;
+        const unsigned long long k = ok ? key[s] : 0ull;
+        const uint32_t v = ok ? val[s] : 0u;
+        const uint32_t d = ok ? ((uint32_t)(k >> shift) & 255u) : (256u + lane);
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        if (ok && rank == 0) woff[warp][d] = (uint32_t)__popc(peers);
+        __syncthreads();
+        {
+            uint32_t acc = run[threadIdx.x];
+#pragma unroll
+            for (int w = 0; w < kSortWarps; ++w) {
+                uint32_t c = woff[w][threadIdx.x];
+                woff[w][threadIdx.x] = acc;
+                acc += c;
+            }
+            run[threadIdx.x] = acc;
+        }
+        __syncthreads();
+        if (ok) {
+            const uint32_t dst = woff[warp][d] + (uint32_t)rank;
+            okey[dst] = k;
+            oval[dst] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// Leaf bookkeeping: halo of each leaf, and its frame origin = corner of the
+// finest Morton cell of its first particle (relative to O, exact in FP32).
+__global__ void k_leaf_fill(int L, int H, const int32_t* __restrict__ leaf_off, const int64_t* __restrict__ halo_off,
+                            const unsigned long long* __restrict__ skey, const HaloFrame* __restrict__ fr,
+                            int32_t* __restrict__ leaf_halo, float4* __restrict__ cell)
+{
+    int leaf = blockIdx.x * blockDim.x + threadIdx.x;
+    if (leaf >= L) return;
+    const int h = bsearch32(leaf_off, H, leaf);
+    leaf_halo[leaf] = h;
+    const int64_t s = halo_off[h] + (int64_t)(leaf - leaf_off[h]) * kLeaf;
+    const unsigned long long k = skey[s] & ((1ull << kHaloShift) - 1ull);
+    const float fine = fr[h].fine;
+    cell[leaf] = make_float4((float)compact3(k) * fine, (float)compact3(k >> 1) * fine,
+                             (float)compact3(k >> 2) * fine, 0.f);
+}
+
+// Gather into Morton order: sorted user arrays (scratch), internal padded
+// tracks, permutation.  Mixed form: FP32 offsets o = RN32(RN64(x - (O + c))).
+template <class R, bool MIXED>
+__global__ void k_gather(int64_t N, int H, const int64_t* __restrict__ halo_off, const int64_t* __restrict__ halo_pad,
+                         const int32_t* __restrict__ leaf_off, const HaloFrame* __restrict__ fr,
+                         const float4* __restrict__ cell, const unsigned long long* __restrict__ skey,
+                         const uint32_t* __restrict__ sval, const double* __restrict__ pos, const R* __restrict__ vel,
+                         const uint32_t* __restrict__ id, double* __restrict__ tpos, R* __restrict__ tvel,
+                         uint32_t* __restrict__ tid, uint32_t* __restrict__ perm,
+                         typename Vec4<R>::T* __restrict__ P4, uint32_t* __restrict__ ID, DevCounters* cnt)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t src = sval[s];
+        const int h = (int)(skey[s] >> kHaloShift);
+        const int64_t local = s - halo_off[h];
+        const int64_t slot = halo_pad[h] + local;
+        const int leaf = leaf_off[h] + (int)(local / kLeaf);
+        double x[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            x[a] = pos[a * N + src];
+            tpos[a * N + s] = x[a];
+            tvel[a * N + s] = vel[a * N + src];
+        }
+        const uint32_t myid = id[src];
+        tid[s] = myid;
+        perm[s] = src;
+        ID[slot] = myid;
+        if (myid >= kIdLimit || !isfinite(x[0]) || !isfinite(x[1]) || !isfinite(x[2]))
+            raise_status(cnt, SIDM_DEV_BAD_INPUT);
+        typename Vec4<R>::T p;
+        if (MIXED) {
+            const HaloFrame f = fr[h];
+            const float4 c = cell[leaf];
+            p.x = (R)__double2float_rn(__dsub_rn(x[0], __dadd_rn(f.O[0], (double)c.x)));
+            p.y = (R)__double2float_rn(__dsub_rn(x[1], __dadd_rn(f.O[1], (double)c.y)));
+            p.z = (R)__double2float_rn(__dsub_rn(x[2], __dadd_rn(f.O[2], (double)c.z)));
+        } else {
+            p.x = (R)x[0]; p.y = (R)x[1]; p.z = (R)x[2];
+        }
+        p.w = R(0);
+        P4[slot] = p;
+    }
+}
+
+// Leaf bounding boxes in the halo frame (FP32, rounded outward); one warp per leaf.
+__global__ void k_leaf_bbox(int L, int64_t N, const int32_t* __restrict__ leaf_halo, const int32_t* __restrict__ leaf_off,
+                            const int64_t* __restrict__ halo_off, const HaloFrame* __restrict__ fr,
+                            const double* __restrict__ pos, float4* __restrict__ nlo, float4* __restrict__ nhi)
+{
+    const int lane = threadIdx.x & 31;
+    const int leaf = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (leaf >= L) return;
+    const int h = leaf_halo[leaf];
+    const int64_t b = halo_off[h] + (int64_t)(leaf - leaf_off[h]) * kLeaf;
+    int64_t e = b + kLeaf; if (e > halo_off[h + 1]) e = halo_off[h + 1];
+    const HaloFrame f = fr[h];
+    double mn[3], mx[3];
+    const int64_t s = b + lane < e ? b + lane : b;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { mn[a] = mx[a] = __dsub_rn(pos[a * N + s], f.O[a]); }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[a] = fmin(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+            mx[a] = fmax(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+        }
+    if (lane == 0) {
+        nlo[leaf] = make_float4(__double2float_rd(mn[0]), __double2float_rd(mn[1]), __double2float_rd(mn[2]), 0.f);
+        nhi[leaf] = make_float4(__double2float_ru(mx[0]), __double2float_ru(mx[1]), __double2float_ru(mx[2]), 0.f);
+    }
+}
+
+// Max kernel size per leaf (into lo.w), from the padded h track.
+template <class R>
+__global__ void k_leaf_hmax(int L, int H, const int32_t* __restrict__ leaf_halo, const int32_t* __restrict__ leaf_off,
+                            const int64_t* __restrict__ halo_off, const typename Vec4<R>::T* __restrict__ P4,
+                            float4* __restrict__ nlo)
+{
+    const int lane = threadIdx.x & 31;
+    const int leaf = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (leaf >= L) return;
+    const int h = leaf_halo[leaf];
+    const int64_t local0 = (int64_t)(leaf - leaf_off[h]) * kLeaf;
+    const int cntl = (int)min((int64_t)kLeaf, halo_off[h + 1] - halo_off[h] - local0);
+    float m = 0.f;
+    if (lane < cntl) {
+        const R hv = P4[(int64_t)leaf * kLeaf + lane].w;
+        m = (float)hv;
+        if ((R)m < hv) m = __uint_as_float(__float_as_uint(m) + 1u);   // round up
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) nlo[leaf].w = m;
+}
+
+// One tree level: union of up to 8 children (bbox and max h).
+__global__ void k_tree_level(int lev, int H, const int32_t* __restrict__ lvl_off, float4* __restrict__ nlo,
+                             float4* __restrict__ nhi)
+{
+    const int32_t* off = lvl_off + lev * (H + 1);
+    const int32_t* coff = lvl_off + (lev - 1) * (H + 1);
+    const int total = off[H] - off[0];
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const int node = off[0] + t;
+        const int h = bsearch32(off, H, node);
+        const int local = node - off[h];
+        const int c0 = coff[h] + local * 8;
+        const int c1 = min(c0 + 8, coff[h + 1]);
+        float4 lo = make_float4(INFINITY, INFINITY, INFINITY, 0.f);
+        float4 hi = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
+        for (int c = c0; c < c1; ++c) {
+            float4 a = nlo[c], b = nhi[c];
+            lo.x = fminf(lo.x, a.x); lo.y = fminf(lo.y, a.y); lo.z = fminf(lo.z, a.z); lo.w = fmaxf(lo.w, a.w);
+            hi.x = fmaxf(hi.x, b.x); hi.y = fmaxf(hi.y, b.y); hi.z = fmaxf(hi.z, b.z);
+        }
+        nlo[node] = lo;
+        nhi[node] = hi;
+    }
+}
+
+// ------------------------------------------------------------------ a2 prep
+template <class R>
+__global__ void k_vel_refresh(int64_t N, int H, const int64_t* __restrict__ halo_off, const int64_t* __restrict__ halo_pad,
+                              const R* __restrict__ vel, const uint32_t* __restrict__ ID,
+                              typename Vec4<R>::T* __restrict__ V4)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+        const int h = halo_of(halo_off, H, s);
+        const int64_t slot = halo_pad[h] + (s - halo_off[h]);
+        typename Vec4<R>::T v;
+        v.x = vel[s]; v.y = vel[N + s]; v.z = vel[2 * N + s];
+        if (sizeof(R) == 4) v.w = (R)__uint_as_float(ID[slot]);
+        else v.w = (R)ID[slot];
+        V4[slot] = v;
+    }
+}
+
+// ------------------------------------------------------------------ a4 resolve
+// 128-bit fixed-point accumulation (units of 2^-80) of a double; integer
+// additions commute, so the sum does not depend on the order of the events.
+__device__ __forceinline__ void fx_add(DevCounters* cnt, double v)
+{
+    const double hi_d = floor(ldexp(v, 16));                 // v 2^80 / 2^64
+    const double lo_d = ldexp(v, 80) - ldexp(hi_d, 64);      // in [0, 2^64)
+    unsigned long long lo = lo_d >= 18446744073709551615.0 ? 0xFFFFFFFFFFFFFFFFull : __double2ull_rz(lo_d);
+    unsigned long long hi = (unsigned long long)(long long)hi_d;
+    unsigned long long old = atomicAdd(&cnt->de_lo, lo);
+    if (old + lo < old) hi += 1ull;
+    atomicAdd(&cnt->de_hi, hi);
+}
+
+// Apply scatter events in ascending key order per particle.  One CTA; each
+// round applies every pending event whose key is the smallest pending key at
+// both of its particles (a topological order of the conflict graph, equal to
+// sequential key order because events on disjoint particles commute).
+template <class R>
+__global__ void __launch_bounds__(1024) k_resolve(const sidm_event* __restrict__ ev, int64_t cap, R* vel, int64_t N,
+                                                  const double* __restrict__ mass, unsigned long long* claim,
+                                                  uint32_t* hits, uint8_t* done, DevCounters* cnt,
+                                                  sidm_step_stats* st, int max_rounds, const float* sump, int use_sump)
+{
+    __shared__ unsigned int s_rem;
+    __shared__ unsigned long long s_multi;
+    const unsigned long long n_all = cnt->ev_count;
+    if (threadIdx.x == 0) { s_multi = 0ull; s_rem = 0u; }
+    __syncthreads();
+    unsigned int status = 0u;
+    unsigned int rounds = 0u;
+    if (n_all > (unsigned long long)cap) {
+        status |= SIDM_DEV_EVENT_OVERFLOW;
+    } else if (n_all > 0ull) {
+        const int64_t n = (int64_t)n_all;
+        unsigned long long multi = 0ull;
+        for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+            done[e] = 0;
+            if (atomicAdd(&hits[ev[e].i], 1u) == 1u) ++multi;
+            if (atomicAdd(&hits[ev[e].j], 1u) == 1u) ++multi;
+        }
+        atomicAdd(&s_multi, multi);
+        __syncthreads();
+        R* vx = vel; R* vy = vel + N; R* vz = vel + 2 * N;
+        while (true) {
+            // phase A: claim the smallest pending key at each particle
+            for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+                if (__ldcg(done + e)) continue;
+                atomicMin(&claim[ev[e].i], ev[e].key);
+                atomicMin(&claim[ev[e].j], ev[e].key);
+            }
+            __syncthreads();
+            // phase B: apply events minimal at both particles
+            for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+                if (__ldcg(done + e)) continue;
+                const sidm_event E = ev[e];
+                if (__ldcg(claim + E.i) != E.key || __ldcg(claim + E.j) != E.key) continue;
+                const int h = (int)(E.key >> 54);
+                const double m = mass[h];
+                const R vi[3] = {__ldcg(vx + E.i), __ldcg(vy + E.i), __ldcg(vz + E.i)};
+                const R vj[3] = {__ldcg(vx + E.j), __ldcg(vy + E.j), __ldcg(vz + E.j)};
+                R ct, st_, sp, cp;
+                if (sizeof(R) == 4) {
+                    ct = (R)fmaf((float)E.x1, 0x1p-31f, -1.0f);
+                    st_ = (R)sqrtf(fmaxf(0.f, 1.f - (float)ct * (float)ct));
+                    float s_, c_;
+                    sincospif((float)E.x2 * 0x1p-31f, &s_, &c_);
+                    sp = (R)s_; cp = (R)c_;
+                } else {
+                    ct = (R)(2.0 * ldexp((double)E.x1, -32) - 1.0);
+                    st_ = (R)sqrt(fmax(0.0, 1.0 - (double)ct * (double)ct));
+                    double s_, c_;
+                    sincospi(ldexp((double)E.x2, -31), &s_, &c_);
+                    sp = (R)s_; cp = (R)c_;
+                }
+                const R nh[3] = {st_ * cp, st_ * sp, ct};
+                // equal masses within a halo: v_cm = (v_i + v_j)/2, weights 1/2
+                R dv2 = R(0), vc[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    vc[a] = R(0.5) * (vi[a] + vj[a]);
+                    const R d = vi[a] - vj[a];
+                    dv2 += d * d;
+                }
+                const R hw = R(0.5) * sqrt(dv2);
+                R ni[3], nj[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) { ni[a] = vc[a] + hw * nh[a]; nj[a] = vc[a] - hw * nh[a]; }
+                __stcg(vx + E.i, ni[0]); __stcg(vy + E.i, ni[1]); __stcg(vz + E.i, ni[2]);
+                __stcg(vx + E.j, nj[0]); __stcg(vy + E.j, nj[1]); __stcg(vz + E.j, nj[2]);
+                double e0 = 0.0, e1 = 0.0;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    e0 = __dadd_rn(e0, __dadd_rn(__dmul_rn((double)vi[a], (double)vi[a]), __dmul_rn((double)vj[a], (double)vj[a])));
+                    e1 = __dadd_rn(e1, __dadd_rn(__dmul_rn((double)ni[a], (double)ni[a]), __dmul_rn((double)nj[a], (double)nj[a])));
+                }
+                fx_add(cnt, __dmul_rn(0.5 * m, __dsub_rn(e1, e0)));
+                done[e] = 1;
+            }
+            __syncthreads();
+            // phase C: release claims of everything pending at the start of the round
+            unsigned int rem = 0u;
+            for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+                claim[ev[e].i] = ~0ull;
+                claim[ev[e].j] = ~0ull;
+                if (!__ldcg(done + e)) ++rem;
+            }
+            if (threadIdx.x == 0) s_rem = 0u;
+            __syncthreads();
+            if (rem) atomicAdd(&s_rem, rem);
+            __syncthreads();
+            ++rounds;
+            const unsigned int remaining = s_rem;
+            __syncthreads();
+            if (remaining == 0u) break;
+            if ((int)rounds >= max_rounds) { status |= SIDM_DEV_ROUNDS; break; }
+        }
+        for (int64_t e = threadIdx.x; e < n; e += blockDim.x) { hits[ev[e].i] = 0u; hits[ev[e].j] = 0u; }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (status) raise_status(cnt, status);
+        st->n_events = n_all;
+        st->n_multi = s_multi;
+        st->rounds = rounds;
+        st->status = status;
+        const unsigned long long hi = cnt->de_hi, lo = cnt->de_lo;
+        st->d_energy = ldexp((double)(long long)hi, -16) + ldexp((double)lo, -80);
+    }
+    if (use_sump) {   // max_i sum_j P_ij
+        float m = 0.f;
+        for (int64_t s = threadIdx.x; s < N; s += blockDim.x) m = fmaxf(m, sump[s]);
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((threadIdx.x & 31) == 0) atomicMax((unsigned int*)&st->max_sum_p, __float_as_uint(m));
+    }
+}
+
+// ------------------------------------------------------------------ a5 reduce
+__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e)
+{
+    s = __dadd_rn(a, b);
+    const double bb = __dsub_rn(s, a);
+    e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+}
+
+struct Comp { double s, c; };
+
+__device__ __forceinline__ void comp_add(Comp& x, double v)
+{
+    double s, e;
+    two_sum(x.s, v, s, e);
+    x.s = s;
+    x.c = __dadd_rn(x.c, e);
+}
+
+__device__ __forceinline__ void comp_merge(Comp& x, const Comp& y)
+{
+    double s, e;
+    two_sum(x.s, y.s, s, e);
+    x.s = s;
+    x.c = __dadd_rn(__dadd_rn(x.c, y.c), e);
+}
+
+// Per-chunk compensated partial sums in a fixed order: thread t takes
+// elements t, t+256, ...; then a fixed binary tree over the 256 threads.
+template <class R>
+__global__ void __launch_bounds__(256) k_energy_partial(const R* __restrict__ vel, int64_t N,
+                                                         const int32_t* __restrict__ chunk_halo,
+                                                         const int64_t* __restrict__ chunk_begin,
+                                                         const int64_t* __restrict__ halo_off,
+                                                         const double* __restrict__ mass, double* __restrict__ part)
+{
+    __shared__ Comp sh[4][256];
+    const int c = blockIdx.x;
+    const int h = chunk_halo[c];
+    const int64_t b = chunk_begin[c];
+    int64_t e = b + kChunk; if (e > halo_off[h + 1]) e = halo_off[h + 1];
+    const double m = mass[h];
+    const double hm = __dmul_rn(0.5, m);
+    Comp acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    for (int64_t s = b + threadIdx.x; s < e; s += 256) {
+        const double x = (double)vel[s], y = (double)vel[N + s], z = (double)vel[2 * N + s];
+        double q = __dmul_rn(x, x);
+        q = __dadd_rn(q, __dmul_rn(y, y));
+        q = __dadd_rn(q, __dmul_rn(z, z));
+        comp_add(acc[0], __dmul_rn(hm, q));
+        comp_add(acc[1], __dmul_rn(m, x));
+        comp_add(acc[2], __dmul_rn(m, y));
+        comp_add(acc[3], __dmul_rn(m, z));
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) sh[a][threadIdx.x] = acc[a];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+#pragma unroll
+            for (int a = 0; a < 4; ++a) comp_merge(sh[a][threadIdx.x], sh[a][threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) {
+        part[c * 8 + 2 * threadIdx.x] = sh[threadIdx.x][0].s;
+        part[c * 8 + 2 * threadIdx.x + 1] = sh[threadIdx.x][0].c;
+    }
+}
+
+__global__ void k_energy_final(int H, int nchunk, const int32_t* __restrict__ chunk_halo,
+                               const double* __restrict__ part, double* __restrict__ out, double* __restrict__ comp)
+{
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= H) return;
+    int lo = 0, hi = nchunk;                        // first chunk of halo h
+    while (lo < hi) { int mid = (lo + hi) >> 1; if (chunk_halo[mid] < h) lo = mid + 1; else hi = mid; }
+    Comp acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    for (int c = lo; c < nchunk && chunk_halo[c] == h; ++c)
+        for (int a = 0; a < 4; ++a) comp_merge(acc[a], Comp{part[c * 8 + 2 * a], part[c * 8 + 2 * a + 1]});
+    for (int a = 0; a < 4; ++a) {
+        const double v = __dadd_rn(acc[a].s, acc[a].c);
+        out[h * 4 + a] = v;
+        if (comp) comp[h * 4 + a] = __dsub_rn(acc[a].c, __dsub_rn(v, acc[a].s));
+    }
+}
+
+// ------------------------------------------------------------------ harness
+template <class R>
+__global__ void k_drift(int64_t N, int H, const int64_t* __restrict__ halo_off, const double* __restrict__ dt,
+                        double* __restrict__ pos, const R* __restrict__ vel)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+        const double d = dt[halo_of(halo_off, H, s)];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) pos[a * N + s] = __dadd_rn(pos[a * N + s], __dmul_rn((double)vel[a * N + s], d));
+    }
+}
+
+template <class R>
+__global__ void k_lambda_eval(int64_t n, const double* __restrict__ d, const double* __restrict__ hi,
+                              const double* __restrict__ hj, double* __restrict__ out, const R* __restrict__ T)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        out[t] = (double)lambda_lookup<R>(T, (R)d[t], (R)hi[t], (R)hj[t]);
+}
+
+__global__ void k_fill_u64(unsigned long long* p, int64_t n, unsigned long long v)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) p[t] = v;
+}
+
+// ------------------------------------------------------------------ Lambda table (host)
+// Gauss-Legendre nodes on [-1, 1] by Newton iteration on P_n.
+void gauss_legendre(int n, double* x, double* w)
+{
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) { double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k; p0 = p1; p1 = p2; }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-17) break;
+        }
+        double p0 = 1.0, p1 = z;
+        for (int k = 2; k <= n; ++k) { double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k; p0 = p1; p1 = p2; }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        x[i] = -z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+// Cubic spline of unit support and its first radial moment in closed form:
+// S(t) = int_0^t t' W_1(t') dt'.
+double spline_w1(double t)
+{
+    if (t < 0.0 || t >= 1.0) return 0.0;
+    const double c = 8.0 / M_PI;
+    if (t < 0.5) return c * (1.0 - 6.0 * t * t + 6.0 * t * t * t);
+    const double u = 1.0 - t;
+    return c * 2.0 * u * u * u;
+}
+
+double spline_s1(double t)
+{
+    const double c = 8.0 / M_PI;
+    auto inner = [&](double q) { return c * (0.5 * q * q - 1.5 * q * q * q * q + 1.2 * q * q * q * q * q); };
+    auto outer = [&](double q) { double u = 1.0 - q; return -2.0 * c * (0.25 * u * u * u * u - 0.2 * u * u * u * u * u); };
+    if (t <= 0.0) return 0.0;
+    if (t < 0.5) return inner(t);
+    const double q = t < 1.0 ? t : 1.0;
+    return inner(0.5) + outer(q) - outer(0.5);
+}
+
+// Lambda(d; a, b) for kernels of support a (at the origin) and b (at distance d):
+//   (2 pi / d) int r W_a(r) [S_b(r + d) - S_b(|r - d|)] dr, S_b(s) = S_1(s/b)/b,
+// piecewise Gauss-Legendre between the breakpoints of the polynomial pieces.
+double lambda_host(double d, double a, double b, const double* gx, const double* gw, int ng)
+{
+    if (d >= a + b) return 0.0;
+    auto Sb = [&](double s) { return spline_s1(s / b) / b; };
+    auto Wa = [&](double r) { return spline_w1(r / a) / (a * a * a); };
+    auto Wb = [&](double r) { return spline_w1(r / b) / (b * b * b); };
+    std::vector<double> br;
+    if (d == 0.0) {
+        const double top = std::min(a, b);
+        br = {0.0, top};
+        for (double v : {0.5 * a, 0.5 * b}) if (v > 0.0 && v < top) br.push_back(v);
+        std::sort(br.begin(), br.end());
+        double acc = 0.0;
+        for (size_t p = 0; p + 1 < br.size(); ++p) {
+            const double m = 0.5 * (br[p] + br[p + 1]), hw = 0.5 * (br[p + 1] - br[p]);
+            for (int g = 0; g < ng; ++g) { const double r = m + hw * gx[g]; acc += gw[g] * hw * r * r * Wa(r) * Wb(r); }
+        }
+        return 4.0 * M_PI * acc;
+    }
+    const double lo = std::max(0.0, d - b), hi = std::min(a, d + b);
+    if (hi <= lo) return 0.0;
+    br = {lo, hi};
+    for (double v : {0.5 * a, a, d, d - 0.5 * b, d + 0.5 * b, d - b, d + b, 0.5 * b - d, b - d})
+        if (v > lo && v < hi) br.push_back(v);
+    std::sort(br.begin(), br.end());
+    double acc = 0.0;
+    for (size_t p = 0; p + 1 < br.size(); ++p) {
+        const double m = 0.5 * (br[p] + br[p + 1]), hw = 0.5 * (br[p + 1] - br[p]);
+        if (hw <= 0.0) continue;
+        for (int g = 0; g < ng; ++g) {
+            const double r = m + hw * gx[g];
+            acc += gw[g] * hw * r * Wa(r) * (Sb(r + d) - Sb(std::fabs(r - d)));
+        }
+    }
+    return 2.0 * M_PI * acc / d;
+}
+
+void lambda_table(std::vector<double>& T)
+{
+    const int ng = 10;
+    double gx[16], gw[16];
+    gauss_legendre(ng, gx, gw);
+    T.assign((size_t)kLamNR * kLamNX, 0.0);
+    for (int r = 0; r < kLamNR; ++r) {
+        const double rho = (double)r / (kLamNR - 1);
+        for (int c = 0; c < kLamNX; ++c) {
+            const double x = (double)c / (kLamNX - 1);
+            T[(size_t)r * kLamNX + c] = rho == 0.0 ? spline_w1(x) : lambda_host(x * (1.0 + rho), 1.0, rho, gx, gw, ng);
+        }
+    }
+}
+
+template <class T>
+cudaError_t dev_alloc(T** p, size_t count)
+{
+    return cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(T));
+}
+
+int grid_for(sidm_ctx* c, int64_t n, int threads)
+{
+    int64_t g = cdiv(n, threads);
+    int64_t cap = (int64_t)c->sm_count * 8;
+    return (int)std::max<int64_t>(1, std::min(g, cap));
+}
+
+}  // namespace
+
+// ======================================================================= host
+namespace sidm {
+
+int set_err(sidm_ctx* c, int code, const std::string& msg)
+{
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_check(sidm_ctx* c, cudaError_t e, const char* what)
+{
+    if (e == cudaSuccess) return SIDM_OK;
+    return set_err(c, SIDM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int timer_begin(sidm_ctx* c, int slot, cudaStream_t s)
+{
+    if (!(c->cfg.flags & SIDM_FLAG_TIMING) || c->t_used >= kTimerCap) return -1;
+    const int idx = c->t_used++;
+    c->t_slot[idx] = (int8_t)slot;
+    cudaEventRecord(c->t_ev[2 * idx], s);
+    return idx;
+}
+
+void timer_end(sidm_ctx* c, int idx, cudaStream_t s)
+{
+    if (idx >= 0) cudaEventRecord(c->t_ev[2 * idx + 1], s);
+}
+
+}  // namespace sidm
+
+#define SIDM_LAUNCH(c, ...)                                                     \
+    do {                                                                        \
+        __VA_ARGS__;                                                            \
+        (c)->launches++;                                                        \
+        cudaError_t _e = cudaGetLastError();                                    \
+        if (_e != cudaSuccess) return cuda_check((c), _e, "kernel launch");     \
+    } while (0)
+
+#define SIDM_CUDA(c, call)                                                      \
+    do {                                                                        \
+        cudaError_t _e = (call);                                                \
+        if (_e != cudaSuccess) return cuda_check((c), _e, #call);               \
+    } while (0)
+
+static void free_all(sidm_ctx* c)
+{
+    void* ptrs[] = {c->d_halo_off, c->d_halo_pad, c->d_leaf_off, c->d_lvl_off, c->d_top, c->d_ngb, c->d_leaf_halo,
+                    c->d_chunk_halo, c->d_chunk_begin, c->d_frame, c->d_key, c->d_key2, c->d_val, c->d_val2,
+                    c->d_hist, c->d_P4, c->d_V4, c->d_ID, c->d_cell, c->d_nlo, c->d_nhi, c->d_perm, c->d_tmp_pos,
+                    c->d_tmp_vel, c->d_tmp_id, c->d_claim, c->d_hits, c->d_done, c->d_ev, c->d_sump,
+                    c->d_stats_own, c->d_cnt, c->d_epart, c->d_lam};
+    for (void* p : ptrs) if (p) cudaFree(p);
+    if (c->d_stage) cudaFreeHost(c->d_stage);
+    for (cudaEvent_t e : c->t_ev) if (e) cudaEventDestroy(e);
+    c->t_ev.clear();
+}
+
+extern "C" const char* sidm_create_error(void) { return g_create_err.c_str(); }
+
+extern "C" const char* sidm_last_error(const sidm_ctx* ctx)
+{
+    return ctx ? ctx->err.c_str() : "null context";
+}
+
+extern "C" int64_t sidm_launch_count(const sidm_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+extern "C" int sidm_create(sidm_ctx** out, const sidm_config* cfg)
+{
+    if (!out || !cfg) { g_create_err = "null argument"; return SIDM_EINVAL; }
+    *out = nullptr;
+    if (cfg->n_max < 1 || cfg->n_max >= (1ll << 31)) { g_create_err = "n_max must be in [1, 2^31)"; return SIDM_EINVAL; }
+    if (cfg->halo_max < 1 || cfg->halo_max > kMaxHalos) { g_create_err = "halo_max must be in [1, 1024]"; return SIDM_EINVAL; }
+    if (cfg->ngb_max < 1 || cfg->ngb_max > kMaxNgb) { g_create_err = "ngb_max must be in [1, 128]"; return SIDM_EINVAL; }
+    if (cfg->event_cap < 1) { g_create_err = "event_cap must be >= 1"; return SIDM_EINVAL; }
+    if (cfg->precision != SIDM_MIXED && cfg->precision != SIDM_FP64) { g_create_err = "bad precision"; return SIDM_EINVAL; }
+    if (cfg->knn_warps < 0 || cfg->knn_warps > 16 || cfg->pair_warps < 0 || cfg->pair_warps > 16) {
+        g_create_err = "warps per CTA must be in [0, 16]"; return SIDM_EINVAL;
+    }
+    sidm_ctx* c = new sidm_ctx();
+    c->cfg = *cfg;
+    if (c->cfg.max_rounds <= 0) c->cfg.max_rounds = 256;
+    c->knn_warps = cfg->knn_warps ? cfg->knn_warps : 4;
+    c->pair_warps = cfg->pair_warps ? cfg->pair_warps : 4;
+    auto fail = [&](const std::string& m, cudaError_t e) {
+        g_create_err = m + ": " + cudaGetErrorString(e);
+        free_all(c);
+        delete c;
+        return SIDM_ECUDA;
+    };
+    cudaError_t e = cudaSetDevice(cfg->device);
+    if (e != cudaSuccess) return fail("cudaSetDevice", e);
+    c->dev = cfg->device;
+    e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->dev);
+    if (e != cudaSuccess) return fail("cudaDeviceGetAttribute", e);
+
+    const int64_t N = cfg->n_max, H = cfg->halo_max;
+    const int64_t Lmax = N / kLeaf + H + 1;
+    const int64_t Npad = Lmax * kLeaf;
+    const bool fp64 = cfg->precision == SIDM_FP64;
+    const size_t rs = fp64 ? 8 : 4;
+    c->node_cap = 2 * Lmax + (int64_t)kMaxLevels * (H + 1);
+    c->chunk_cap = N / kChunk + H + 1;
+    c->hist_cap = 256 * cdiv(N, kSortTile);
+    c->stage_bytes = sizeof(int64_t) * (size_t)(8 * (H + 1) + kMaxLevels * (H + 1) + 2 * c->chunk_cap + 64);
+#define ALLOC(p, n) do { e = dev_alloc(&(p), (size_t)(n)); if (e != cudaSuccess) return fail("cudaMalloc " #p, e); } while (0)
+    ALLOC(c->d_halo_off, H + 1);
+    ALLOC(c->d_halo_pad, H + 1);
+    ALLOC(c->d_leaf_off, H + 1);
+    ALLOC(c->d_lvl_off, kMaxLevels * (H + 1));
+    ALLOC(c->d_top, H);
+    ALLOC(c->d_ngb, H);
+    ALLOC(c->d_leaf_halo, Lmax);
+    ALLOC(c->d_chunk_halo, c->chunk_cap);
+    ALLOC(c->d_chunk_begin, c->chunk_cap);
+    ALLOC(c->d_frame, H);
+    ALLOC(c->d_key, N);
+    ALLOC(c->d_key2, N);
+    ALLOC(c->d_val, N);
+    ALLOC(c->d_val2, N);
+    ALLOC(c->d_hist, c->hist_cap);
+    e = cudaMalloc(&c->d_P4, (size_t)Npad * 4 * rs); if (e != cudaSuccess) return fail("cudaMalloc P4", e);
+    e = cudaMalloc(&c->d_V4, (size_t)Npad * 4 * rs); if (e != cudaSuccess) return fail("cudaMalloc V4", e);
+    ALLOC(c->d_ID, Npad);
+    ALLOC(c->d_cell, Lmax);
+    ALLOC(c->d_nlo, c->node_cap);
+    ALLOC(c->d_nhi, c->node_cap);
+    ALLOC(c->d_perm, N);
+    ALLOC(c->d_tmp_pos, 3 * N);
+    e = cudaMalloc(&c->d_tmp_vel, (size_t)3 * N * rs); if (e != cudaSuccess) return fail("cudaMalloc tmp_vel", e);
+    ALLOC(c->d_tmp_id, N);
+    ALLOC(c->d_claim, N);
+    ALLOC(c->d_hits, N);
+    ALLOC(c->d_done, cfg->event_cap);
+    ALLOC(c->d_ev, cfg->event_cap);
+    ALLOC(c->d_sump, (cfg->flags & SIDM_FLAG_SUM_P) ? N : 1);
+    ALLOC(c->d_stats_own, 1);
+    ALLOC(c->d_cnt, 1);
+    ALLOC(c->d_epart, 8 * c->chunk_cap);
+#undef ALLOC
+    e = cudaMallocHost((void**)&c->d_stage, c->stage_bytes);
+    if (e != cudaSuccess) return fail("cudaMallocHost", e);
+    // Lambda table: FP64 quadrature on the host, stored in the form's precision.
+    std::vector<double> T;
+    lambda_table(T);
+    if (fp64) {
+        e = cudaMalloc(&c->d_lam, T.size() * 8); if (e != cudaSuccess) return fail("cudaMalloc lam", e);
+        e = cudaMemcpy(c->d_lam, T.data(), T.size() * 8, cudaMemcpyHostToDevice);
+    } else {
+        std::vector<float> Tf(T.begin(), T.end());
+        e = cudaMalloc(&c->d_lam, Tf.size() * 4); if (e != cudaSuccess) return fail("cudaMalloc lam", e);
+        e = cudaMemcpy(c->d_lam, Tf.data(), Tf.size() * 4, cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) return fail("cudaMemcpy lam", e);
+    e = cudaMemset(c->d_hits, 0, sizeof(uint32_t) * (size_t)N); if (e != cudaSuccess) return fail("memset", e);
+    e = cudaMemset(c->d_cnt, 0, sizeof(DevCounters)); if (e != cudaSuccess) return fail("memset", e);
+    e = cudaMemset(c->d_claim, 0xFF, sizeof(unsigned long long) * (size_t)N); if (e != cudaSuccess) return fail("memset", e);
+    if (cfg->flags & SIDM_FLAG_TIMING) {
+        c->t_ev.assign(2 * kTimerCap, nullptr);
+        c->t_slot.assign(kTimerCap, 0);
+        for (auto& ev : c->t_ev) {
+            e = cudaEventCreate(&ev);
+            if (e != cudaSuccess) return fail("cudaEventCreate", e);
+        }
+    }
+    e = cudaDeviceSynchronize(); if (e != cudaSuccess) return fail("sync", e);
+    *out = c;
+    return SIDM_OK;
+}
+
+extern "C" int sidm_destroy(sidm_ctx* c)
+{
+    if (!c) return SIDM_OK;
+    cudaSetDevice(c->dev);
+    cudaDeviceSynchronize();
+    free_all(c);
+    delete c;
+    return SIDM_OK;
+}
+
+// Host-side layout of a halo set (leaves, tree levels, reduction chunks).
+static int make_layout(sidm_ctx* c, int H, const int64_t* off, LayoutHost& L)
+{
+    L = LayoutHost();
+    L.H = H;
+    L.halo_off.assign(off, off + H + 1);
+    L.N = off[H];
+    L.halo_pad.assign(H + 1, 0);
+    L.leaf_off.assign(H + 1, 0);
+    for (int h = 0; h < H; ++h) {
+        const int64_t n = off[h + 1] - off[h];
+        const int64_t nl = cdiv(n, kLeaf);
+        L.halo_pad[h + 1] = L.halo_pad[h] + nl * kLeaf;
+        L.leaf_off[h + 1] = L.leaf_off[h] + (int32_t)nl;
+    }
+    L.Npad = L.halo_pad[H];
+    L.L = L.leaf_off[H];
+    L.top.assign(H, 0);
+    int maxtop = 0;
+    for (int h = 0; h < H; ++h) {
+        int64_t cnt = L.leaf_off[h + 1] - L.leaf_off[h];
+        int t = 0;
+        while (cnt > 32) { cnt = cdiv(cnt, 8); ++t; }
+        L.top[h] = t;
+        maxtop = std::max(maxtop, t);
+    }
+    L.nlev = maxtop + 1;
+    if (L.nlev > kMaxLevels) return set_err(c, SIDM_ECAPACITY, "too many tree levels");
+    L.lvl_off.assign((size_t)L.nlev * (H + 1), 0);
+    int64_t base = 0;
+    for (int l = 0; l < L.nlev; ++l) {
+        int64_t run = base;
+        for (int h = 0; h < H; ++h) {
+            L.lvl_off[(size_t)l * (H + 1) + h] = (int32_t)run;
+            int64_t cnt = L.leaf_off[h + 1] - L.leaf_off[h];
+            for (int k = 0; k < l; ++k) cnt = cdiv(cnt, 8);
+            run += cnt;
+        }
+        L.lvl_off[(size_t)l * (H + 1) + H] = (int32_t)run;
+        base = run;
+    }
+    if (base > c->node_cap) return set_err(c, SIDM_ECAPACITY, "tree node capacity exceeded");
+    for (int h = 0; h < H; ++h)
+        for (int64_t b = off[h]; b < off[h + 1]; b += kChunk) { L.chunk_halo.push_back(h); L.chunk_begin.push_back(b); }
+    L.nchunk = (int)L.chunk_halo.size();
+    if (L.nchunk > c->chunk_cap) return set_err(c, SIDM_ECAPACITY, "chunk capacity exceeded");
+    int hb = 0;
+    while ((1 << hb) < H) ++hb;
+    L.sort_passes = (int)cdiv(kHaloShift + hb, 8);
+    return SIDM_OK;
+}
+
+static int upload_layout(sidm_ctx* c, cudaStream_t s)
+{
+    const LayoutHost& L = c->lay;
+    const int H = L.H;
+    int64_t* st = c->d_stage;
+    size_t o = 0;
+    auto put = [&](const void* src, size_t bytes, void* dst) -> int {
+        if ((o * 8 + bytes) > c->stage_bytes) return set_err(c, SIDM_ECAPACITY, "staging buffer too small");
+        std::memcpy((char*)st + o * 8, src, bytes);
+        cudaError_t e = cudaMemcpyAsync(dst, (char*)st + o * 8, bytes, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_check(c, e, "layout upload");
+        o += (bytes + 7) / 8;
+        return SIDM_OK;
+    };
+    int rc;
+    if ((rc = put(L.halo_off.data(), 8 * (H + 1), c->d_halo_off))) return rc;
+    if ((rc = put(L.halo_pad.data(), 8 * (H + 1), c->d_halo_pad))) return rc;
+    if ((rc = put(L.leaf_off.data(), 4 * (H + 1), c->d_leaf_off))) return rc;
+    if ((rc = put(L.lvl_off.data(), 4 * L.lvl_off.size(), c->d_lvl_off))) return rc;
+    if ((rc = put(L.top.data(), 4 * H, c->d_top))) return rc;
+    if (L.nchunk) {
+        if ((rc = put(L.chunk_halo.data(), 4 * L.nchunk, c->d_chunk_halo))) return rc;
+        if ((rc = put(L.chunk_begin.data(), 8 * L.nchunk, c->d_chunk_begin))) return rc;
+    }
+    SIDM_CUDA(c, cudaStreamSynchronize(s));   // staging buffer is reused
+    return SIDM_OK;
+}
+
+template <class R>
+static int build_impl(sidm_ctx* c, double* pos, R* vel, uint32_t* id, cudaStream_t s)
+{
+    const LayoutHost& L = c->lay;
+    const int H = L.H;
+    const int64_t N = L.N;
+    if (N == 0) return SIDM_OK;
+    // per-halo bounding box -> frame
+    SIDM_CUDA(c, cudaMemsetAsync(c->d_cnt->bbox, 0xFF, sizeof(unsigned long long) * 3 * H, s));
+    SIDM_CUDA(c, cudaMemsetAsync(c->d_cnt->bbox + 3 * H, 0x00, sizeof(unsigned long long) * 3 * H, s));
+    SIDM_LAUNCH(c, k_bbox<<<L.nchunk, 256, 0, s>>>(pos, N, c->d_chunk_halo, c->d_chunk_begin, c->d_halo_off, H, c->d_cnt->bbox));
+    SIDM_LAUNCH(c, k_frame<<<(H + 127) / 128, 128, 0, s>>>(H, c->d_halo_off, c->d_cnt->bbox, c->d_frame));
+    SIDM_LAUNCH(c, k_keys<<<grid_for(c, N, 256), 256, 0, s>>>(pos, N, c->d_halo_off, H, c->d_frame, c->d_key, c->d_val));
+    // stable LSD radix sort
+    const int nblk = (int)cdiv(N, kSortTile);
+    unsigned long long *ka = c->d_key, *kb = c->d_key2;
+    uint32_t *va = c->d_val, *vb = c->d_val2;
+    for (int p = 0; p < L.sort_passes; ++p) {
+        const int shift = 8 * p;
+        SIDM_LAUNCH(c, k_sort_hist<<<nblk, kSortThreads, 0, s>>>(ka, N, shift, nblk, c->d_hist));
+        SIDM_LAUNCH(c, k_sort_scan<<<1, 1024, 0, s>>>(c->d_hist, (int64_t)256 * nblk));
+        SIDM_LAUNCH(c, k_sort_scatter<<<nblk, kSortThreads, 0, s>>>(ka, va, N, shift, nblk, c->d_hist, kb, vb));
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    // leaves, gather, copy back into the caller's arrays
+    SIDM_LAUNCH(c, k_leaf_fill<<<(L.L + 255) / 256, 256, 0, s>>>(L.L, H, c->d_leaf_off, c->d_halo_off, ka, c->d_frame,
+                                                                  c->d_leaf_halo, c->d_cell));
+    const bool mixed = c->cfg.precision == SIDM_MIXED;
+    using V = typename Vec4<R>::T;
+    if (mixed)
+        SIDM_LAUNCH(c, (k_gather<R, true><<<grid_for(c, N, 256), 256, 0, s>>>(
+            N, H, c->d_halo_off, c->d_halo_pad, c->d_leaf_off, c->d_frame, c->d_cell, ka, va, pos, vel, id,
+            c->d_tmp_pos, (R*)c->d_tmp_vel, c->d_tmp_id, c->d_perm, (V*)c->d_P4, c->d_ID, c->d_cnt)));
+    else
+        SIDM_LAUNCH(c, (k_gather<R, false><<<grid_for(c, N, 256), 256, 0, s>>>(
+            N, H, c->d_halo_off, c->d_halo_pad, c->d_leaf_off, c->d_frame, c->d_cell, ka, va, pos, vel, id,
+            c->d_tmp_pos, (R*)c->d_tmp_vel, c->d_tmp_id, c->d_perm, (V*)c->d_P4, c->d_ID, c->d_cnt)));
+    SIDM_CUDA(c, cudaMemcpyAsync(pos, c->d_tmp_pos, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s));
+    SIDM_CUDA(c, cudaMemcpyAsync(vel, c->d_tmp_vel, sizeof(R) * 3 * N, cudaMemcpyDeviceToDevice, s));
+    SIDM_CUDA(c, cudaMemcpyAsync(id, c->d_tmp_id, sizeof(uint32_t) * N, cudaMemcpyDeviceToDevice, s));
+    SIDM_LAUNCH(c, k_leaf_bbox<<<(L.L * 32 + 255) / 256, 256, 0, s>>>(L.L, N, c->d_leaf_halo, c->d_leaf_off, c->d_halo_off,
+                                                                       c->d_frame, pos, c->d_nlo, c->d_nhi));
+    for (int l = 1; l < L.nlev; ++l) {
+        const int cnt = L.lvl_off[(size_t)l * (H + 1) + H] - L.lvl_off[(size_t)l * (H + 1)];
+        SIDM_LAUNCH(c, k_tree_level<<<std::max(1, (cnt + 255) / 256), 256, 0, s>>>(l, H, c->d_lvl_off, c->d_nlo, c->d_nhi));
+    }
+    return SIDM_OK;
+}
+
+extern "C" int sidm_build_cells(sidm_ctx* c, int32_t n_halos, const int64_t* halo_off, double* pos, void* vel,
+                                uint32_t* id, cudaStream_t s)
+{
+    if (!c) return SIDM_EINVAL;
+    if (n_halos < 1 || n_halos > c->cfg.halo_max || !halo_off) return set_err(c, SIDM_EINVAL, "bad halo count");
+    if (halo_off[0] != 0) return set_err(c, SIDM_EINVAL, "halo_off[0] must be 0");
+    for (int h = 0; h < n_halos; ++h)
+        if (halo_off[h + 1] < halo_off[h]) return set_err(c, SIDM_EINVAL, "halo_off must be non-decreasing");
+    if (halo_off[n_halos] > c->cfg.n_max) return set_err(c, SIDM_ECAPACITY, "more particles than n_max");
+    if (halo_off[n_halos] > 0 && (!pos || !vel || !id)) return set_err(c, SIDM_EINVAL, "null particle array");
+    SIDM_CUDA(c, cudaSetDevice(c->dev));
+    const bool same = c->has_layout && c->lay.H == n_halos &&
+                      std::equal(halo_off, halo_off + n_halos + 1, c->lay.halo_off.begin());
+    if (!same) {
+        LayoutHost L;
+        int rc = make_layout(c, n_halos, halo_off, L);
+        if (rc) return rc;
+        c->lay = L;
+        c->has_layout = true;
+        c->built = c->sized = false;
+        if ((rc = upload_layout(c, s))) { c->has_layout = false; return rc; }
+    }
+    const int tb = timer_begin(c, 0, s);
+    int rc = c->cfg.precision == SIDM_FP64 ? build_impl<double>(c, pos, (double*)vel, id, s)
+                                           : build_impl<float>(c, pos, (float*)vel, id, s);
+    timer_end(c, tb, s);
+    if (rc) return rc;
+    c->built = true;
+    c->sized = false;
+    return SIDM_OK;
+}
+
+extern "C" int sidm_kernel_sizes(sidm_ctx* c, const int32_t* n_ngb, void* h_dev, cudaStream_t s)
+{
+    if (!c) return SIDM_EINVAL;
+    if (!c->built) return set_err(c, SIDM_EINVAL, "sidm_build_cells must come first");
+    if (!n_ngb || (!h_dev && c->lay.N > 0)) return set_err(c, SIDM_EINVAL, "null argument");
+    const LayoutHost& L = c->lay;
+    int kmax = 0;
+    for (int h = 0; h < L.H; ++h) {
+        const int64_t n = L.halo_off[h + 1] - L.halo_off[h];
+        if (n == 0) continue;
+        if (n_ngb[h] < 1 || n_ngb[h] > c->cfg.ngb_max)
+            return set_err(c, SIDM_EINVAL, "n_ngb out of [1, ngb_max] for halo " + std::to_string(h));
+        if (n_ngb[h] >= n)
+            return set_err(c, SIDM_EINVAL, "halo " + std::to_string(h) + " has no more than n_ngb particles");
+        kmax = std::max(kmax, n_ngb[h]);
+    }
+    SIDM_CUDA(c, cudaSetDevice(c->dev));
+    if (c->ngb_host.size() != (size_t)L.H || !std::equal(n_ngb, n_ngb + L.H, c->ngb_host.begin())) {
+        std::memcpy(c->d_stage, n_ngb, sizeof(int32_t) * L.H);
+        SIDM_CUDA(c, cudaMemcpyAsync(c->d_ngb, c->d_stage, sizeof(int32_t) * L.H, cudaMemcpyHostToDevice, s));
+        SIDM_CUDA(c, cudaStreamSynchronize(s));
+        c->ngb_host.assign(n_ngb, n_ngb + L.H);
+    }
+    c->kmax_cur = kmax;
+    if (L.N == 0) { c->sized = true; return SIDM_OK; }
+    int rc = launch_knn(c, h_dev, nullptr, 0, s);
+    if (rc) return rc;
+    if (c->cfg.precision == SIDM_FP64)
+        SIDM_LAUNCH(c, k_leaf_hmax<double><<<(L.L * 32 + 255) / 256, 256, 0, s>>>(L.L, L.H, c->d_leaf_halo, c->d_leaf_off,
+                                                                                 c->d_halo_off, (const double4*)c->d_P4, c->d_nlo));
+    else
+        SIDM_LAUNCH(c, k_leaf_hmax<float><<<(L.L * 32 + 255) / 256, 256, 0, s>>>(L.L, L.H, c->d_leaf_halo, c->d_leaf_off,
+                                                                               c->d_halo_off, (const float4*)c->d_P4, c->d_nlo));
+    for (int l = 1; l < L.nlev; ++l) {
+        const int cnt = L.lvl_off[(size_t)l * (L.H + 1) + L.H] - L.lvl_off[(size_t)l * (L.H + 1)];
+        SIDM_LAUNCH(c, k_tree_level<<<std::max(1, (cnt + 255) / 256), 256, 0, s>>>(l, L.H, c->d_lvl_off, c->d_nlo, c->d_nhi));
+    }
+    c->sized = true;
+    return SIDM_OK;
+}
+
+extern "C" int sidm_neighbours(sidm_ctx* c, const int32_t* n_ngb, int32_t k_stride, uint32_t* nbr, cudaStream_t s)
+{
+    if (!c) return SIDM_EINVAL;
+    if (c->cfg.precision != SIDM_MIXED) return set_err(c, SIDM_EINVAL, "neighbour lists: mixed form only");
+    if (!c->sized) return set_err(c, SIDM_EINVAL, "sidm_kernel_sizes must come first");
+    if (!n_ngb || !nbr) return set_err(c, SIDM_EINVAL, "null argument");
+    for (int h = 0; h < c->lay.H; ++h)
+        if (c->lay.halo_off[h + 1] > c->lay.halo_off[h] && (n_ngb[h] != c->ngb_host[h] || n_ngb[h] > k_stride))
+            return set_err(c, SIDM_EINVAL, "n_ngb must match the kernel-size pass and fit k_stride");
+    SIDM_CUDA(c, cudaSetDevice(c->dev));
+    return launch_knn(c, nullptr, nbr, k_stride, s);
+}
+
+extern "C" int sidm_scatter_step(sidm_ctx* c, uint64_t seed, uint64_t step, const sidm_xs* xs, const double* dt,
+                                 const double* mass, void* vel, sidm_step_stats* stats, cudaStream_t s)
+{
+    if (!c) return SIDM_EINVAL;
+    if (!c->sized) return set_err(c, SIDM_EINVAL, "sidm_kernel_sizes must come first");
+    if (!xs || !dt || !mass || (!vel && c->lay.N > 0)) return set_err(c, SIDM_EINVAL, "null argument");
+    SIDM_CUDA(c, cudaSetDevice(c->dev));
+    const LayoutHost& L = c->lay;
+    sidm_step_stats* st = stats ? stats : c->d_stats_own;
+    SIDM_CUDA(c, cudaMemsetAsync(st, 0, sizeof(sidm_step_stats), s));
+    SIDM_CUDA(c, cudaMemsetAsync(c->d_cnt, 0, offsetof(DevCounters, work), s));
+    if (c->cfg.flags & SIDM_FLAG_SUM_P) SIDM_CUDA(c, cudaMemsetAsync(c->d_sump, 0, sizeof(float) * std::max<int64_t>(L.N, 1), s));
+    c->stepped = true;
+    if (L.N == 0) return SIDM_OK;
+    const bool fp64 = c->cfg.precision == SIDM_FP64;
+    if (fp64)
+        SIDM_LAUNCH(c, k_vel_refresh<double><<<grid_for(c, L.N, 256), 256, 0, s>>>(L.N, L.H, c->d_halo_off, c->d_halo_pad,
+                                                                                  (const double*)vel, c->d_ID, (double4*)c->d_V4));
+    else
+        SIDM_LAUNCH(c, k_vel_refresh<float><<<grid_for(c, L.N, 256), 256, 0, s>>>(L.N, L.H, c->d_halo_off, c->d_halo_pad,
+                                                                                (const float*)vel, c->d_ID, (float4*)c->d_V4));
+    int rc = launch_pairs(c, seed, step, xs, dt, mass, st, s);
+    if (rc) return rc;
+    const int use_sump = (c->cfg.flags & SIDM_FLAG_SUM_P) ? 1 : 0;
+    const int tr = timer_begin(c, 3, s);
+    if (fp64)
+        SIDM_LAUNCH(c, k_resolve<double><<<1, 1024, 0, s>>>(c->d_ev, c->cfg.event_cap, (double*)vel, L.N, mass, c->d_claim,
+                                                          c->d_hits, c->d_done, c->d_cnt, st, c->cfg.max_rounds, c->d_sump, use_sump));
+    else
+        SIDM_LAUNCH(c, k_resolve<float><<<1, 1024, 0, s>>>(c->d_ev, c->cfg.event_cap, (float*)vel, L.N, mass, c->d_claim,
+                                                         c->d_hits, c->d_done, c->d_cnt, st, c->cfg.max_rounds, c->d_sump, use_sump));
+    timer_end(c, tr, s);
+    return SIDM_OK;
+}
+
+extern "C" int sidm_energy_momentum(sidm_ctx* c, const double* mass, const void* vel, double* out, double* comp,
+                                    cudaStream_t s)
+{
+    if (!c) return SIDM_EINVAL;
+    if (!c->has_layout) return set_err(c, SIDM_EINVAL, "sidm_build_cells must come first");
+    if (!mass || !out || (!vel && c->lay.N > 0)) return set_err(c, SIDM_EINVAL, "null argument");
+    SIDM_CUDA(c, cudaSetDevice(c->dev));
+    const LayoutHost& L = c->lay;
+    if (L.nchunk > 0) {
+        if (c->cfg.precision == SIDM_FP64)
+            SIDM_LAUNCH(c, k_energy_partial<double><<<L.nchunk, 256, 0, s>>>((const double*)vel, L.N, c->d_chunk_halo,
+                                                                            c->d_chunk_begin, c->d_halo_off, mass, c->d_epart));
+        else
+            SIDM_LAUNCH(c, k_energy_partial<float><<<L.nchunk, 256, 0, s>>>((const float*)vel, L.N, c->d_chunk_halo,
+                                                                           c->d_chunk_begin, c->d_halo_off, mass, c->d_epart));
+    }
+    SIDM_LAUNCH(c, k_energy_final<<<(L.H + 127) / 128, 128, 0, s>>>(L.H, L.nchunk, c->d_chunk_halo, c->d_epart, out, comp));
+    return SIDM_OK;
+}
+
+extern "C" int sidm_status(sidm_ctx* c, cudaStream_t s, uint32_t* status)
+{
+    if (!c) return SIDM_EINVAL;
+    SIDM_CUDA(c, cudaSetDevice(c->dev));
+    SIDM_CUDA(c, cudaStreamSynchronize(s));
+    unsigned int v = 0;
+    SIDM_CUDA(c, cudaMemcpy(&v, &c->d_cnt->status, sizeof(v), cudaMemcpyDeviceToHost));
+    SIDM_CUDA(c, cudaMemset(&c->d_cnt->status, 0, sizeof(v)));
+    if (status) *status = v;
+    if (v) {
+        std::string m = "device status";
+        if (v & SIDM_DEV_EVENT_OVERFLOW) m += " event-overflow";
+        if (v & SIDM_DEV_ROUNDS) m += " round-limit";
+        if (v & SIDM_DEV_STACK) m += " traversal-stack";
+        if (v & SIDM_DEV_BAD_INPUT) m += " bad-input";
+        if (v & SIDM_DEV_WAIT_TIMEOUT) m += " wait-timeout";
+        return set_err(c, SIDM_EDEVICE, m);
+    }
+    return SIDM_OK;
+}
+
+extern "C" int sidm_get_perm(sidm_ctx* c, uint32_t* perm, cudaStream_t s)
+{
+    if (!c) return SIDM_EINVAL;
+    if (!c->built) return set_err(c, SIDM_EINVAL, "sidm_build_cells must come first");
+    if (!perm) return set_err(c, SIDM_EINVAL, "null argument");
+    SIDM_CUDA(c, cudaSetDevice(c->dev));
+    if (c->lay.N) SIDM_CUDA(c, cudaMemcpyAsync(perm, c->d_perm, sizeof(uint32_t) * c->lay.N, cudaMemcpyDeviceToDevice, s));
+    return SIDM_OK;
+}
+
+extern "C" int sidm_get_events(sidm_ctx* c, int64_t cap, sidm_event* ev, int64_t* n_host, cudaStream_t s)
+{
+    if (!c) return SIDM_EINVAL;
+    if (!c->stepped) return set_err(c, SIDM_EINVAL, "sidm_scatter_step must come first");
+    if (!n_host || (cap > 0 && !ev)) return set_err(c, SIDM_EINVAL, "null argument");
+    SIDM_CUDA(c, cudaSetDevice(c->dev));
+    SIDM_CUDA(c, cudaStreamSynchronize(s));
+    unsigned long long n = 0;
+    SIDM_CUDA(c, cudaMemcpy(&n, &c->d_cnt->ev_count, sizeof(n), cudaMemcpyDeviceToHost));
+    *n_host = (int64_t)n;
+    const int64_t m = std::min<int64_t>({(int64_t)n, cap, c->cfg.event_cap});
+    if (m > 0) SIDM_CUDA(c, cudaMemcpy(ev, c->d_ev, sizeof(sidm_event) * m, cudaMemcpyDeviceToDevice));
+    return SIDM_OK;
+}
+
+extern "C" int sidm_lambda_eval(sidm_ctx* c, int64_t n, const double* d, const double* hi, const double* hj,
+                                double* out, cudaStream_t s)
+{
+    if (!c) return SIDM_EINVAL;
+    if (n < 0 || (n > 0 && (!d || !hi || !hj || !out))) return set_err(c, SIDM_EINVAL, "bad argument");
+    if (n == 0) return SIDM_OK;
+    SIDM_CUDA(c, cudaSetDevice(c->dev));
+    if (c->cfg.precision == SIDM_FP64)
+        SIDM_LAUNCH(c, k_lambda_eval<double><<<grid_for(c, n, 256), 256, 0, s>>>(n, d, hi, hj, out, (const double*)c->d_lam));
+    else
+        SIDM_LAUNCH(c, k_lambda_eval<float><<<grid_for(c, n, 256), 256, 0, s>>>(n, d, hi, hj, out, (const float*)c->d_lam));
+    return SIDM_OK;
+}
+
+extern "C" int sidm_drift(sidm_ctx* c, const double* dt, double* pos, const void* vel, cudaStream_t s)
+{
+    if (!c) return SIDM_EINVAL;
+    if (!c->has_layout) return set_err(c, SIDM_EINVAL, "sidm_build_cells must come first");
+    if (!dt || (c->lay.N > 0 && (!pos || !vel))) return set_err(c, SIDM_EINVAL, "null argument");
+    if (c->lay.N == 0) return SIDM_OK;
+    SIDM_CUDA(c, cudaSetDevice(c->dev));
+    if (c->cfg.precision == SIDM_FP64)
+        SIDM_LAUNCH(c, k_drift<double><<<grid_for(c, c->lay.N, 256), 256, 0, s>>>(c->lay.N, c->lay.H, c->d_halo_off, dt, pos,
+                                                                                (const double*)vel));
+    else
+        SIDM_LAUNCH(c, k_drift<float><<<grid_for(c, c->lay.N, 256), 256, 0, s>>>(c->lay.N, c->lay.H, c->d_halo_off, dt, pos,
+                                                                               (const float*)vel));
+    return SIDM_OK;
+}
+
+extern "C" int sidm_get_sum_p(sidm_ctx* c, float* out, cudaStream_t s)
+{
+    if (!c) return SIDM_EINVAL;
+    if (!(c->cfg.flags & SIDM_FLAG_SUM_P)) return set_err(c, SIDM_EINVAL, "context built without SIDM_FLAG_SUM_P");
+    if (!out) return set_err(c, SIDM_EINVAL, "null argument");
+    SIDM_CUDA(c, cudaSetDevice(c->dev));
+    if (c->lay.N) SIDM_CUDA(c, cudaMemcpyAsync(out, c->d_sump, sizeof(float) * c->lay.N, cudaMemcpyDeviceToDevice, s));
+    return SIDM_OK;
+}
+
+extern "C" int sidm_kernel_times(sidm_ctx* c, double* ms, int64_t* count, int32_t reset)
+{
+    if (!c) return SIDM_EINVAL;
+    if (!(c->cfg.flags & SIDM_FLAG_TIMING)) return set_err(c, SIDM_EINVAL, "context built without SIDM_FLAG_TIMING");
+    if (!ms) return set_err(c, SIDM_EINVAL, "null argument");
+    SIDM_CUDA(c, cudaSetDevice(c->dev));
+    SIDM_CUDA(c, cudaDeviceSynchronize());
+    for (int k = 0; k < 4; ++k) { ms[k] = 0.0; if (count) count[k] = 0; }
+    for (int i = 0; i < c->t_used; ++i) {
+        float t = 0.f;
+        SIDM_CUDA(c, cudaEventElapsedTime(&t, c->t_ev[2 * i], c->t_ev[2 * i + 1]));
+        ms[c->t_slot[i]] += (double)t;
+        if (count) count[c->t_slot[i]] += 1;
+    }
+    if (reset) c->t_used = 0;
+    return SIDM_OK;
+}

@@ -1,0 +1,247 @@
+// sidm_internal.cuh -- context layout and device helpers shared by the CUDA
+// translation units of libsidm (sm_103a).  Nothing here is used by the CPU
+// oracle; the two implementations share no code.
+#pragma once
+
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/sidm.h"
+
+namespace sidm {
+
+constexpr int kLeaf = 32;            // particles per leaf (one warp of queries)
+constexpr int kMortonBits = 17;      // Morton bits per axis
+constexpr int kHaloShift = 51;       // halo index sits above the 51 Morton bits
+constexpr int kMaxHalos = 1024;
+constexpr int kMaxNgb = 128;
+constexpr int kMaxLevels = 12;       // tree levels including the leaf level
+constexpr int kStack = 160;          // traversal stack entries per warp
+constexpr int kLamNX = 257;          // Lambda table: x = d / (h_i + h_j) in [0, 1]
+constexpr int kLamNR = 65;           //               rho = h_min / h_max in [0, 1]
+constexpr uint32_t kIdLimit = 1u << 27;
+
+// Per-halo frame of the canonical geometry: cube [O, O + 2^(E+1))^3,
+// Morton quantisation with 17 bits per axis.
+struct HaloFrame {
+    double O[3];
+    int E;
+    float cube;        // 2^(E+1)
+    float margin;      // pruning margin: 2^(E+1) * 2^-20 (canonical vs exact distance)
+    float fine;        // finest Morton cell edge 2^(E+1-17)
+};
+
+// Internal device counters (one struct, zeroed where each call needs it).
+struct DevCounters {
+    unsigned long long ev_count;     // events drawn this step
+    unsigned long long de_lo;        // 128-bit fixed-point sum of pair dE (2^-80 units)
+    unsigned long long de_hi;
+    unsigned int work[4];            // persistent work-queue counters
+    unsigned int status;             // sticky SIDM_DEV_* bits (cleared by sidm_status)
+    unsigned int pad;
+    unsigned long long bbox[kMaxHalos * 6];   // ordered bits of per-halo min/max
+};
+
+struct LayoutHost {
+    int H = 0;
+    int64_t N = 0, Npad = 0;
+    int L = 0;                                   // leaves
+    int nlev = 1;                                // tree levels incl. leaves
+    std::vector<int64_t> halo_off, halo_pad;
+    std::vector<int32_t> leaf_off;               // [H+1]
+    std::vector<int32_t> lvl_off;                // [nlev][H+1]
+    std::vector<int32_t> top;                    // [H] start level of the traversal
+    std::vector<int32_t> chunk_halo;             // energy reduction chunks
+    std::vector<int64_t> chunk_begin;
+    int nchunk = 0;
+    int sort_passes = 7;
+};
+
+}  // namespace sidm
+
+struct sidm_ctx {
+    sidm_config cfg{};
+    int dev = 0;
+    int sm_count = 0;
+    std::string err;
+    int64_t launches = 0;
+    bool has_layout = false, built = false, sized = false, stepped = false;
+    sidm::LayoutHost lay;
+    std::vector<int32_t> ngb_host;               // cached N_ngb (uploaded when changed)
+    int kmax_cur = 0;
+
+    // layout arrays (device)
+    int64_t* d_halo_off = nullptr;     // [H+1]
+    int64_t* d_halo_pad = nullptr;     // [H+1]
+    int32_t* d_leaf_off = nullptr;     // [H+1]
+    int32_t* d_lvl_off = nullptr;      // [kMaxLevels][H+1]
+    int32_t* d_top = nullptr;          // [H]
+    int32_t* d_ngb = nullptr;          // [H]
+    int32_t* d_leaf_halo = nullptr;    // [Lmax]
+    int32_t* d_chunk_halo = nullptr;   // [chunks]
+    int64_t* d_chunk_begin = nullptr;  // [chunks]
+    sidm::HaloFrame* d_frame = nullptr;  // [H]
+    int64_t* d_stage = nullptr;        // host-pinned staging for layout uploads
+    size_t stage_bytes = 0;
+
+    // sort
+    unsigned long long* d_key = nullptr;
+    unsigned long long* d_key2 = nullptr;
+    uint32_t* d_val = nullptr;
+    uint32_t* d_val2 = nullptr;
+    uint32_t* d_hist = nullptr;
+    int64_t hist_cap = 0;
+
+    // particles (padded per halo to multiples of 32 slots)
+    void* d_P4 = nullptr;              // float4 (ox,oy,oz,h) | double4 (x,y,z,h)
+    void* d_V4 = nullptr;              // float4 (vx,vy,vz,id) | double4
+    uint32_t* d_ID = nullptr;          // ids by slot
+    float4* d_cell = nullptr;          // [Lmax] leaf frame origin relative to O
+    float4* d_nlo = nullptr;           // [nodes] bbox lo (w = max h)
+    float4* d_nhi = nullptr;           // [nodes] bbox hi
+    int64_t node_cap = 0;
+    uint32_t* d_perm = nullptr;        // [N] sorted position -> previous index
+    double* d_tmp_pos = nullptr;       // [3][N]
+    void* d_tmp_vel = nullptr;         // [3][N]
+    uint32_t* d_tmp_id = nullptr;      // [N]
+
+    // scatter
+    unsigned long long* d_claim = nullptr;  // [N] resolve claims (all ones at rest)
+    uint32_t* d_hits = nullptr;             // [N] events per particle (zero at rest)
+    uint8_t* d_done = nullptr;              // [event_cap]
+    sidm_event* d_ev = nullptr;             // [event_cap]
+    float* d_sump = nullptr;                // [N] (SIDM_FLAG_SUM_P)
+    sidm_step_stats* d_stats_own = nullptr; // used when the caller passes NULL
+    sidm::DevCounters* d_cnt = nullptr;
+
+    // energy partials
+    double* d_epart = nullptr;         // [chunks][8]
+    int64_t chunk_cap = 0;
+
+    // Lambda table (float or double [kLamNR][kLamNX])
+    void* d_lam = nullptr;
+
+    int knn_grid = 0, pair_grid = 0, knn_warps = 4, pair_warps = 4;
+
+    // CUDA-event timing of hot kernels (SIDM_FLAG_TIMING): pairs of events
+    std::vector<cudaEvent_t> t_ev;     // [2 * kTimerCap]
+    std::vector<int8_t> t_slot;        // [kTimerCap]
+    int t_used = 0;
+};
+
+namespace sidm {
+
+// ---------------------------------------------------------------- launches
+int set_err(sidm_ctx* c, int code, const std::string& msg);
+int cuda_check(sidm_ctx* c, cudaError_t e, const char* what);
+
+// event timing (no-ops unless SIDM_FLAG_TIMING): slot 0 build, 1 knn, 2 pairs, 3 resolve
+constexpr int kTimerCap = 4096;
+int timer_begin(sidm_ctx* c, int slot, cudaStream_t s);
+void timer_end(sidm_ctx* c, int idx, cudaStream_t s);
+
+// kernel entry points implemented in the other translation units
+int launch_knn(sidm_ctx* c, void* h_out, uint32_t* nbr, int k_stride, cudaStream_t s);
+int launch_pairs(sidm_ctx* c, uint64_t seed, uint64_t step, const sidm_xs* xs, const double* dt,
+                 const double* mass, sidm_step_stats* st, cudaStream_t s);
+
+// ---------------------------------------------------------------- device helpers
+__device__ __forceinline__ void raise_status(DevCounters* cnt, unsigned int bits)
+{
+    atomicOr(&cnt->status, bits);
+}
+
+// Philox4x32-10 block (Salmon et al. 2011): per round the products
+// M0*c0 and M1*c2 are split into high/low words and mixed with c1, c3 and the
+// key; the key advances by the Weyl constants after each round.
+struct Philox4 { uint32_t x[4]; };
+
+__device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                 uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t y0 = hi1 ^ c1 ^ k0;
+        const uint32_t y2 = hi0 ^ c3 ^ k1;
+        c0 = y0; c1 = lo1; c2 = y2; c3 = lo0;
+        k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+    }
+    Philox4 o; o.x[0] = c0; o.x[1] = c1; o.x[2] = c2; o.x[3] = c3;
+    return o;
+}
+
+// Lagrange cubic weights on nodes 0..3 at parameter t.
+template <class R>
+__device__ __forceinline__ void lagrange4(R t, R w[4])
+{
+    const R t1 = t - R(1), t2 = t - R(2), t3 = t - R(3);
+    w[0] = -(t1 * t2 * t3) * (R(1) / R(6));
+    w[1] = (t * t2 * t3) * R(0.5);
+    w[2] = -(t * t1 * t3) * R(0.5);
+    w[3] = (t * t1 * t2) * (R(1) / R(6));
+}
+
+// Lambda(d; h_i, h_j) from the table f(x, rho) = h_max^3 Lambda,
+// x = d / (h_i + h_j), rho = h_min / h_max, Lagrange-bicubic on a
+// uniform 257 x 65 grid.
+template <class R>
+__device__ __forceinline__ R lambda_lookup(const R* __restrict__ T, R d, R hi, R hj)
+{
+    const R hmax = hi > hj ? hi : hj;
+    const R hmin = hi > hj ? hj : hi;
+    R x = d / (hi + hj);
+    if (!(x < R(1))) return R(0);
+    if (x < R(0)) x = R(0);
+    const R rho = hmin / hmax;
+    const R gx = x * R(kLamNX - 1);
+    int ix = (int)floor(gx) - 1;
+    ix = ix < 0 ? 0 : (ix > kLamNX - 4 ? kLamNX - 4 : ix);
+    const R gr = rho * R(kLamNR - 1);
+    int ir = (int)floor(gr) - 1;
+    ir = ir < 0 ? 0 : (ir > kLamNR - 4 ? kLamNR - 4 : ir);
+    R wx[4], wr[4];
+    lagrange4<R>(gx - R(ix), wx);
+    lagrange4<R>(gr - R(ir), wr);
+    R f = R(0);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const R* row = T + (ir + a) * kLamNX + ix;
+        const R s = wx[0] * __ldg(row) + wx[1] * __ldg(row + 1) + wx[2] * __ldg(row + 2) + wx[3] * __ldg(row + 3);
+        f += wr[a] * s;
+    }
+    const R inv = R(1) / hmax;
+    return f * inv * inv * inv;
+}
+
+// Lower bound of the squared gap between two boxes (FP32, rounded down).
+__device__ __forceinline__ float box_gap2_rd(float4 alo, float4 ahi, float4 blo, float4 bhi)
+{
+    float gx = fmaxf(0.f, fmaxf(__fsub_rd(blo.x, ahi.x), __fsub_rd(alo.x, bhi.x)));
+    float gy = fmaxf(0.f, fmaxf(__fsub_rd(blo.y, ahi.y), __fsub_rd(alo.y, bhi.y)));
+    float gz = fmaxf(0.f, fmaxf(__fsub_rd(blo.z, ahi.z), __fsub_rd(alo.z, bhi.z)));
+    return __fadd_rd(__fadd_rd(__fmul_rd(gx, gx), __fmul_rd(gy, gy)), __fmul_rd(gz, gz));
+}
+
+// Order-preserving map of a double to unsigned 64-bit (for atomic min/max).
+__device__ __forceinline__ unsigned long long dbl_to_ord(double v)
+{
+    unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double ord_to_dbl(unsigned long long u)
+{
+    u = (u & 0x8000000000000000ull) ? (u & 0x7FFFFFFFFFFFFFFFull) : ~u;
+    return __longlong_as_double((long long)u);
+}
+
+template <class R> struct Vec4;
+template <> struct Vec4<float> { using T = float4; };
+template <> struct Vec4<double> { using T = double4; };
+
+}  // namespace sidm

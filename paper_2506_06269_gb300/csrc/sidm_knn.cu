@@ -1,0 +1,323 @@
+// sidm_knn.cu -- (a1) kernel sizes: h_i = distance to the N_ngb-th nearest
+// other particle of the halo (Sect. 2: "set by the next N_ngb neighbours";
+// Eq. hDl: h is the radius of the sphere holding N_ngb particles).
+//
+// One warp per leaf of 32 consecutive Morton-ordered particles, one query per
+// lane.  Candidate leaves are staged through shared memory (plain coalesced
+// 128-bit loads, or bulk asynchronous copies with an mbarrier), shifted into
+// the query leaf's frame, and every lane keeps a max-heap of its N_ngb
+// smallest keys in shared memory.  The heap is first filled from the leaves
+// next to the query leaf in Morton order, whose k-th distance bounds the
+// search radius; the bounding-volume tree is then walked with that (shrinking)
+// radius, skipping those leaves.  The result is the exact k-th smallest of the
+// canonical distance, so it does not depend on tile order or launch shape.
+#include <type_traits>
+
+#include "sidm_internal.cuh"
+#include "sidm_tile.cuh"
+
+namespace sidm {
+namespace {
+
+template <class R, bool NBR>
+struct KeyOf {
+    using T = typename std::conditional<(sizeof(R) == 8) || NBR, unsigned long long, uint32_t>::type;
+};
+
+struct KnnParams {
+    int H, L;
+    const int32_t* leaf_halo;
+    const int32_t* leaf_off;
+    const int64_t* halo_off;
+    const int32_t* lvl_off;
+    const int32_t* top;
+    const int32_t* ngb;
+    const HaloFrame* frame;
+    const float4* cell;
+    const float4* nlo;
+    const float4* nhi;
+    void* P4;
+    const uint32_t* ID;
+    void* h_out;
+    uint32_t* nbr;
+    int k_stride;
+    int kcap;
+    DevCounters* cnt;
+    int work_slot;
+};
+
+template <class K> __device__ __forceinline__ K key_max();
+template <> __device__ __forceinline__ uint32_t key_max<uint32_t>() { return 0xFFFFFFFFu; }
+template <> __device__ __forceinline__ unsigned long long key_max<unsigned long long>() { return ~0ull; }
+
+template <class R, bool NBR>
+__device__ __forceinline__ typename KeyOf<R, NBR>::T make_key(R d2, uint32_t id)
+{
+    if constexpr (sizeof(R) == 8) {
+        return (unsigned long long)__double_as_longlong((double)d2);
+    } else if constexpr (NBR) {
+        return ((unsigned long long)__float_as_uint((float)d2) << 32) | id;
+    } else {
+        return __float_as_uint((float)d2);
+    }
+}
+
+template <class R, bool NBR>
+__device__ __forceinline__ R key_d2(typename KeyOf<R, NBR>::T k)
+{
+    if constexpr (sizeof(R) == 8) return (R)__longlong_as_double((long long)k);
+    else if constexpr (NBR) return (R)__uint_as_float((uint32_t)(k >> 32));
+    else return (R)__uint_as_float((uint32_t)k);
+}
+
+// replace the heap root (the largest of the k kept keys) by key and sift down
+template <class K>
+__device__ __forceinline__ void heap_replace(K* heap, int lane, int k, K key)
+{
+    int pos = 0;
+    while (true) {
+        int c = 2 * pos + 1;
+        if (c >= k) break;
+        K cv = heap[c * 32 + lane];
+        if (c + 1 < k) {
+            K c2 = heap[(c + 1) * 32 + lane];
+            if (c2 > cv) { ++c; cv = c2; }
+        }
+        if (!(cv > key)) break;
+        heap[pos * 32 + lane] = cv;
+        pos = c;
+    }
+    heap[pos * 32 + lane] = key;
+}
+
+template <class K>
+__device__ __forceinline__ void heap_sift(K* heap, int lane, int n)
+{
+    int pos = 0;
+    const K key = heap[lane];
+    while (true) {
+        int c = 2 * pos + 1;
+        if (c >= n) break;
+        K cv = heap[c * 32 + lane];
+        if (c + 1 < n) {
+            K c2 = heap[(c + 1) * 32 + lane];
+            if (c2 > cv) { ++c; cv = c2; }
+        }
+        if (!(cv > key)) break;
+        heap[pos * 32 + lane] = cv;
+        pos = c;
+    }
+    heap[pos * 32 + lane] = key;
+}
+
+template <class R>
+__device__ __forceinline__ float to_float_ru(R v)
+{
+    if constexpr (sizeof(R) == 8) return __double2float_ru((double)v);
+    else return (float)v;
+}
+
+template <class R, bool NBR, bool TMA>
+__global__ void k_knn(KnnParams p)
+{
+    using V = typename Vec4<R>::T;
+    using K = typename KeyOf<R, NBR>::T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const size_t per_warp = knn_warp_bytes<R, K>(p.kcap);
+    unsigned char* base = smem + wid * per_warp;
+    TileStageT<R, TMA> stage(base);
+    uint32_t* tids = (uint32_t*)(base + TileStageT<R, TMA>::bytes());
+    int* stack = (int*)(tids + 32);
+    K* heap = (K*)(stack + kStack);
+    stage.init(lane);
+
+    while (true) {
+        int leaf = 0;
+        if (lane == 0) leaf = (int)atomicAdd(&p.cnt->work[p.work_slot], 1u);
+        leaf = __shfl_sync(0xffffffffu, leaf, 0);
+        if (leaf >= p.L) break;
+        const int h = p.leaf_halo[leaf];
+        const int k = p.ngb[h];
+        const int leaf0 = p.leaf_off[h];
+        const int nleaf = p.leaf_off[h + 1] - leaf0;
+        const int64_t hb = p.halo_off[h];
+        const int64_t nh = p.halo_off[h + 1] - hb;
+        const int A = leaf - leaf0;
+        const int countA = (int)min((int64_t)kLeaf, nh - (int64_t)A * kLeaf);
+        const bool active = lane < countA;
+        const HaloFrame fr = p.frame[h];
+        const V q = ((const V*)p.P4)[(int64_t)leaf * kLeaf + lane];
+        const float4 cA = p.cell[leaf];
+        const float4 qlo = p.nlo[leaf], qhi = p.nhi[leaf];
+        const K kmax = key_max<K>();
+        for (int t = 0; t < k; ++t) heap[t * 32 + lane] = kmax;
+        K root = kmax;
+        bool failed = false;
+
+        auto process = [&](int Bl) {
+            const int Bg = leaf0 + Bl;
+            const int countB = (int)min((int64_t)kLeaf, nh - (int64_t)Bl * kLeaf);
+            const V* tile = stage.load((const V*)p.P4 + (int64_t)Bg * kLeaf, lane, p.cnt);
+            // shift the candidates into the query leaf's frame (exact shift)
+            V c = tile[lane];
+            if constexpr (sizeof(R) == 4) {
+                const float4 cB = p.cell[Bg];
+                c.x = __fadd_rn(c.x, __fsub_rn(cB.x, cA.x));
+                c.y = __fadd_rn(c.y, __fsub_rn(cB.y, cA.y));
+                c.z = __fadd_rn(c.z, __fsub_rn(cB.z, cA.z));
+            }
+            __syncwarp();
+            V* sh = stage.shifted();
+            sh[lane] = c;
+            if (NBR) tids[lane] = p.ID[(int64_t)Bg * kLeaf + lane];
+            __syncwarp();
+            if (active) {
+                for (int t = 0; t < countB; ++t) {
+                    if (Bl == A && t == lane) continue;
+                    const V cj = sh[t];
+                    const R dx = sub_rn(cj.x, q.x), dy = sub_rn(cj.y, q.y), dz = sub_rn(cj.z, q.z);
+                    const R d2 = fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
+                    const K key = make_key<R, NBR>(d2, NBR ? tids[t] : 0u);
+                    if (key < root) {
+                        heap_replace<K>(heap, lane, k, key);
+                        root = heap[lane];
+                    }
+                }
+            }
+            __syncwarp();
+        };
+
+        // 1) Morton-window leaves around A holding at least k+1 particles
+        int wlo = A, whi = A;
+        int64_t wcount = countA;
+        while (wcount < k + 1 && (wlo > 0 || whi < nleaf - 1)) {
+            if (whi < nleaf - 1) { ++whi; wcount += min((int64_t)kLeaf, nh - (int64_t)whi * kLeaf); }
+            if (wcount < k + 1 && wlo > 0) { --wlo; wcount += kLeaf; }
+        }
+        for (int Bl = wlo; Bl <= whi; ++Bl) process(Bl);
+
+        // 2) tree walk with the radius bound of the current k-th keys
+        auto bound2 = [&]() -> float {
+            float r = active ? to_float_ru<R>(sqrt_ru(key_d2<R, NBR>(root))) : 0.f;
+            for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
+            r = __fadd_ru(__fmul_ru(r, 1.0f + 0x1p-20f), fr.margin);
+            return __fmul_ru(r, r);
+        };
+        const int top = p.top[h];
+        const int32_t* loff = p.lvl_off;
+        const int Hp = p.H + 1;
+        int sp = 0;
+        {
+            const float R2 = bound2();
+            const int nb = loff[top * Hp + h];
+            const int ntop = loff[top * Hp + h + 1] - nb;
+            bool ok = lane < ntop && box_gap2_rd(qlo, qhi, p.nlo[nb + lane], p.nhi[nb + lane]) <= R2;
+            if (top == 0) ok = ok && (lane < wlo || lane > whi);
+            const uint32_t m = __ballot_sync(0xffffffffu, ok);
+            const int cnt = __popc(m);
+            if (ok) stack[sp + cnt - 1 - __popc(m & ((1u << lane) - 1u))] = (top << 24) | lane;
+            sp += cnt;
+            __syncwarp();
+        }
+        while (sp > 0) {
+            const int e = stack[--sp];
+            __syncwarp();
+            const int lev = e >> 24, idx = e & 0xFFFFFF;
+            const float R2 = bound2();
+            if (lev == 0) {
+                const int g = leaf0 + idx;
+                if (box_gap2_rd(qlo, qhi, p.nlo[g], p.nhi[g]) <= R2) process(idx);
+                continue;
+            }
+            const int cl = lev - 1;
+            const int cb = loff[cl * Hp + h];
+            const int cc = loff[cl * Hp + h + 1] - cb;
+            const int child = idx * 8 + lane;
+            bool ok = lane < 8 && child < cc && box_gap2_rd(qlo, qhi, p.nlo[cb + child], p.nhi[cb + child]) <= R2;
+            if (cl == 0) ok = ok && (child < wlo || child > whi);
+            const uint32_t m = __ballot_sync(0xffffffffu, ok);
+            const int cnt = __popc(m);
+            if (sp + cnt > kStack) { failed = true; break; }
+            if (ok) stack[sp + cnt - 1 - __popc(m & ((1u << lane) - 1u))] = (cl << 24) | child;
+            sp += cnt;
+            __syncwarp();
+        }
+        if (failed && lane == 0) raise_status(p.cnt, SIDM_DEV_STACK);
+
+        // 3) outputs
+        if (active) {
+            const int64_t u = hb + (int64_t)A * kLeaf + lane;
+            const R hval = sqrt_rn(key_d2<R, NBR>(root));
+            if (p.h_out) {
+                ((R*)p.h_out)[u] = hval;
+                ((R*)((V*)p.P4 + (int64_t)leaf * kLeaf + lane))[3] = hval;
+            }
+            if constexpr (NBR) {
+                for (int end = k - 1; end > 0; --end) {       // heap sort: ascending keys
+                    const K t0 = heap[lane];
+                    heap[lane] = heap[end * 32 + lane];
+                    heap[end * 32 + lane] = t0;
+                    heap_sift<K>(heap, lane, end);
+                }
+                for (int t = 0; t < k; ++t) p.nbr[u * p.k_stride + t] = (uint32_t)(heap[t * 32 + lane] & 0xFFFFFFFFull);
+            }
+        }
+        __syncwarp();
+    }
+    stage.finish(lane, p.cnt);
+}
+
+template <class R, bool NBR, bool TMA>
+int launch_t(sidm_ctx* c, void* h_out, uint32_t* nbr, int k_stride, cudaStream_t s)
+{
+    using K = typename KeyOf<R, NBR>::T;
+    KnnParams p;
+    const LayoutHost& L = c->lay;
+    p.H = L.H; p.L = L.L;
+    p.leaf_halo = c->d_leaf_halo; p.leaf_off = c->d_leaf_off; p.halo_off = c->d_halo_off;
+    p.lvl_off = c->d_lvl_off; p.top = c->d_top; p.ngb = c->d_ngb; p.frame = c->d_frame;
+    p.cell = c->d_cell; p.nlo = c->d_nlo; p.nhi = c->d_nhi; p.P4 = c->d_P4; p.ID = c->d_ID;
+    p.h_out = h_out; p.nbr = nbr; p.k_stride = k_stride; p.kcap = c->kmax_cur; p.cnt = c->d_cnt;
+    p.work_slot = 0;
+    const int warps = c->knn_warps;
+    const size_t smem = (size_t)warps * knn_warp_bytes<R, K>(p.kcap);
+    auto kern = k_knn<R, NBR, TMA>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_check(c, e, "knn smem attribute");
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, warps * 32, smem);
+    if (e != cudaSuccess) return cuda_check(c, e, "knn occupancy");
+    if (occ < 1) return set_err(c, SIDM_ECAPACITY, "knn kernel does not fit on an SM (ngb_max too large for knn_warps)");
+    int grid = c->cfg.grid_ctas > 0 ? c->cfg.grid_ctas : c->sm_count * occ;
+    grid = std::max(1, std::min(grid, (L.L + warps - 1) / warps));
+    c->knn_grid = grid;
+    e = cudaMemsetAsync(&c->d_cnt->work[0], 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return cuda_check(c, e, "knn work reset");
+    const int tidx = timer_begin(c, 1, s);
+    kern<<<grid, warps * 32, smem, s>>>(p);
+    timer_end(c, tidx, s);
+    c->launches++;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_check(c, e, "knn launch");
+    return SIDM_OK;
+}
+
+}  // namespace
+
+int launch_knn(sidm_ctx* c, void* h_out, uint32_t* nbr, int k_stride, cudaStream_t s)
+{
+    if (c->lay.L == 0) return SIDM_OK;
+    const bool tma = c->cfg.use_tma != 0;
+    if (c->cfg.precision == SIDM_FP64) {
+        if (nbr) return set_err(c, SIDM_EINVAL, "neighbour lists: mixed form only");
+        return tma ? launch_t<double, false, true>(c, h_out, nullptr, 0, s)
+                   : launch_t<double, false, false>(c, h_out, nullptr, 0, s);
+    }
+    if (nbr) return tma ? launch_t<float, true, true>(c, nullptr, nbr, k_stride, s)
+                        : launch_t<float, true, false>(c, nullptr, nbr, k_stride, s);
+    return tma ? launch_t<float, false, true>(c, h_out, nullptr, 0, s)
+               : launch_t<float, false, false>(c, h_out, nullptr, 0, s);
+}
+
+}  // namespace sidm

@@ -1,0 +1,316 @@
+// sidm_pairs.cu -- (a2, a3) pair interaction probabilities and scatter draws.
+//
+// For every unordered pair of a halo with d_ij < h_i + h_j (Sect. 3.5: the
+// geometric factor Lambda of the interaction probability is the overlap of
+// the two spline kernels):
+//   P_ij = (sigma(v_ij)/m) m_j v_ij Lambda_ij dt,  v_ij = |v_i - v_j|,
+//   sigma/m = s0 or s0 / (1 + (v/w)^2)^2 (Sect. 3.8, Eq. vel_dep),
+// and a counter-based Philox4x32-10 draw keyed by (seed; step, min id,
+// max id, halo), so the draw is independent of thread order.  Event iff
+// u = x0 2^-32 < P (no clamp: P >= 1 always fires).
+//
+// One warp per query leaf A; the tree walk visits leaves B >= A whose boxes
+// are within h_max(A) + h_max(B), so each unordered pair is tested once, in
+// the frame of the lower leaf.  The in-range test runs on a 32 x 32 block;
+// in-range pairs are compacted into a per-warp queue so that the expensive
+// part (Lambda table, sigma, Philox) runs on full warps.
+#include "sidm_internal.cuh"
+#include "sidm_tile.cuh"
+
+namespace sidm {
+namespace {
+
+struct PairParams {
+    int H, L;
+    const int32_t* leaf_halo;
+    const int32_t* leaf_off;
+    const int64_t* halo_off;
+    const int32_t* lvl_off;
+    const int32_t* top;
+    const HaloFrame* frame;
+    const float4* cell;
+    const float4* nlo;
+    const float4* nhi;
+    const void* P4;
+    const void* V4;
+    const void* lam;
+    const sidm_xs* xs;
+    const double* dt;
+    const double* mass;
+    uint32_t seed_lo, seed_hi, step_lo;
+    sidm_event* ev;
+    unsigned long long ev_cap;
+    float* sump;
+    int use_sump;
+    DevCounters* cnt;
+    sidm_step_stats* st;
+};
+
+constexpr int kQueue = 64;
+
+template <class R>
+__device__ __forceinline__ uint32_t id_of(R w)
+{
+    if constexpr (sizeof(R) == 4) return __float_as_uint((float)w);
+    else return (uint32_t)(double)w;
+}
+
+template <class R, bool TMA>
+constexpr size_t pair_warp_bytes()
+{
+    using V = typename Vec4<R>::T;
+    return (TileStageT<R, TMA>::bytes() * 2 + 2 * 32 * sizeof(V) + kQueue * 2 + kStack * 4 + 15) / 16 * 16;
+}
+
+template <class R, bool TMA>
+__global__ void k_pairs(PairParams p)
+{
+    using V = typename Vec4<R>::T;
+    using Stage = TileStageT<R, TMA>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned char* base = smem + wid * pair_warp_bytes<R, TMA>();
+    Stage st_pos(base);
+    Stage st_vel(base + Stage::bytes());
+    V* qp = (V*)(base + 2 * Stage::bytes());
+    V* qv = qp + 32;
+    uint16_t* queue = (uint16_t*)(qv + 32);
+    int* stack = (int*)(queue + kQueue);
+    st_pos.init(lane);
+    st_vel.init(lane);
+    const R* __restrict__ T = (const R*)p.lam;
+    const uint32_t lt = (1u << lane) - 1u;
+
+    unsigned long long n_pairs = 0ull, n_gt1 = 0ull, n_near = 0ull, n_tested = 0ull;
+
+    while (true) {
+        int leaf = 0;
+        if (lane == 0) leaf = (int)atomicAdd(&p.cnt->work[1], 1u);
+        leaf = __shfl_sync(0xffffffffu, leaf, 0);
+        if (leaf >= p.L) break;
+        const int h = p.leaf_halo[leaf];
+        const int leaf0 = p.leaf_off[h];
+        const int64_t hb = p.halo_off[h];
+        const int64_t nh = p.halo_off[h + 1] - hb;
+        const int A = leaf - leaf0;
+        const int countA = (int)min((int64_t)kLeaf, nh - (int64_t)A * kLeaf);
+        const bool active = lane < countA;
+        const HaloFrame fr = p.frame[h];
+        const float4 cA = p.cell[leaf];
+        const float4 qlo = p.nlo[leaf], qhi = p.nhi[leaf];
+        const float hmaxA = qlo.w;
+        const sidm_xs xs = p.xs[h];
+        const int kind = xs.kind;
+        const R pref = (R)xs.s0 * (R)p.mass[h] * (R)p.dt[h];
+        const R inv_w = kind == 1 ? R(1) / (R)xs.w : R(0);
+        const V q = ((const V*)p.P4)[(int64_t)leaf * kLeaf + lane];
+        qp[lane] = q;
+        qv[lane] = ((const V*)p.V4)[(int64_t)leaf * kLeaf + lane];
+        __syncwarp();
+        int qhead = 0, qn = 0;
+
+        // P, draw and event for queue entries qhead .. qhead+nb-1 (one per lane)
+        auto run_batch = [&](int nb, int64_t ubB, const V* tp, const V* tv) {
+            __syncwarp();
+            if (lane < nb) {
+                const uint16_t e = queue[(qhead + lane) & (kQueue - 1)];
+                const int il = e >> 8, t = e & 0xFF;
+                const V pi = qp[il], vi = qv[il], pj = tp[t], vj = tv[t];
+                const R dx = sub_rn(pj.x, pi.x), dy = sub_rn(pj.y, pi.y), dz = sub_rn(pj.z, pi.z);
+                const R d2 = fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
+                const R lamv = lambda_lookup<R>(T, sqrt_rn(d2), pi.w, pj.w);
+                const R ux = vj.x - vi.x, uy = vj.y - vi.y, uz = vj.z - vi.z;
+                const R v = sqrt(ux * ux + uy * uy + uz * uz);
+                R sig = R(1);
+                if (kind == 1) { const R qq = v * inv_w; const R tt = R(1) + qq * qq; sig = R(1) / (tt * tt); }
+                const R P = pref * sig * v * lamv;
+                const uint32_t ida = id_of<R>(vi.w), idb = id_of<R>(vj.w);
+                const uint32_t a = min(ida, idb), b = max(ida, idb);
+                const Philox4 x = philox4x32_10(p.step_lo, a, b, (uint32_t)h, p.seed_lo, p.seed_hi);
+                bool fire;
+                R u;
+                if constexpr (sizeof(R) == 4) {
+                    u = (R)((float)x.x[0] * 0x1p-32f);
+                    fire = P >= R(1) || x.x[0] < (uint32_t)ceilf((float)P * 0x1p32f);
+                } else {
+                    u = (R)ldexp((double)x.x[0], -32);
+                    fire = u < P;
+                }
+                if (P > R(1)) ++n_gt1;
+                if (fabs(P - u) < R(1e-6)) ++n_near;
+                const int64_t ui = hb + (int64_t)A * kLeaf + il;
+                const int64_t uj = ubB + t;
+                if (p.use_sump) {
+                    atomicAdd(p.sump + ui, (float)P);
+                    atomicAdd(p.sump + uj, (float)P);
+                }
+                if (fire) {
+                    const unsigned long long slot = atomicAdd(&p.cnt->ev_count, 1ull);
+                    if (slot < p.ev_cap) {
+                        sidm_event E;
+                        E.key = ((unsigned long long)h << 54) | ((unsigned long long)a << 27) | (unsigned long long)b;
+                        E.i = (uint32_t)(ida < idb ? ui : uj);
+                        E.j = (uint32_t)(ida < idb ? uj : ui);
+                        E.x1 = x.x[1];
+                        E.x2 = x.x[2];
+                        E.P = (float)P;
+                        E.x0 = x.x[0];
+                        p.ev[slot] = E;
+                    }
+                }
+            }
+            qhead = (qhead + nb) & (kQueue - 1);
+            qn -= nb;
+            __syncwarp();
+        };
+
+        auto process = [&](int Bl) {
+            const int Bg = leaf0 + Bl;
+            const int countB = (int)min((int64_t)kLeaf, nh - (int64_t)Bl * kLeaf);
+            const V* rp = st_pos.load((const V*)p.P4 + (int64_t)Bg * kLeaf, lane, p.cnt);
+            const V* rv = st_vel.load((const V*)p.V4 + (int64_t)Bg * kLeaf, lane, p.cnt);
+            V c = rp[lane];
+            if constexpr (sizeof(R) == 4) {
+                const float4 cB = p.cell[Bg];
+                c.x = __fadd_rn(c.x, __fsub_rn(cB.x, cA.x));
+                c.y = __fadd_rn(c.y, __fsub_rn(cB.y, cA.y));
+                c.z = __fadd_rn(c.z, __fsub_rn(cB.z, cA.z));
+            }
+            const V cv = rv[lane];
+            __syncwarp();
+            V* tp = st_pos.shifted();
+            V* tv = st_vel.shifted();
+            tp[lane] = c;
+            tv[lane] = cv;
+            __syncwarp();
+            const int64_t ubB = hb + (int64_t)Bl * kLeaf;
+            n_tested += Bl > A ? (unsigned long long)(countA * countB) : (unsigned long long)(countA * (countA - 1) / 2);
+            for (int t = 0; t < countB; ++t) {
+                bool ok = false;
+                if (active && (Bl > A || t > lane)) {
+                    const V pj = tp[t];
+                    const R dx = sub_rn(pj.x, q.x), dy = sub_rn(pj.y, q.y), dz = sub_rn(pj.z, q.z);
+                    const R d2 = fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
+                    const R hs = add_rn(q.w, pj.w);
+                    ok = d2 < mul_rn(hs, hs);
+                }
+                const uint32_t m = __ballot_sync(0xffffffffu, ok);
+                if (ok) queue[(qhead + qn + __popc(m & lt)) & (kQueue - 1)] = (uint16_t)((lane << 8) | t);
+                const int c2 = __popc(m);
+                qn += c2;
+                n_pairs += (unsigned long long)c2;
+                if (qn >= 32) run_batch(32, ubB, tp, tv);
+            }
+            if (qn > 0) run_batch(qn, ubB, tp, tv);
+            __syncwarp();
+        };
+
+        // tree walk: leaves B >= A with box gap < (hmax_A + hmax_B)(1 + 2^-20) + margin
+        const int top = p.top[h];
+        const int Hp = p.H + 1;
+        auto accept = [&](int lev, int local, int g) -> bool {
+            if (((int64_t)(local + 1) << (3 * lev)) <= A) return false;   // entirely below A
+            const float4 lo = p.nlo[g], hi = p.nhi[g];
+            float r = __fadd_ru(__fmul_ru(__fadd_ru(hmaxA, lo.w), 1.0f + 0x1p-20f), fr.margin);
+            return box_gap2_rd(qlo, qhi, lo, hi) <= __fmul_ru(r, r);
+        };
+        int sp = 0;
+        bool failed = false;
+        {
+            const int nb = p.lvl_off[top * Hp + h];
+            const int ntop = p.lvl_off[top * Hp + h + 1] - nb;
+            const bool ok = lane < ntop && accept(top, lane, nb + lane);
+            const uint32_t m = __ballot_sync(0xffffffffu, ok);
+            const int cnt = __popc(m);
+            if (ok) stack[sp + cnt - 1 - __popc(m & lt)] = (top << 24) | lane;
+            sp += cnt;
+            __syncwarp();
+        }
+        while (sp > 0) {
+            const int e = stack[--sp];
+            __syncwarp();
+            const int lev = e >> 24, idx = e & 0xFFFFFF;
+            if (lev == 0) { process(idx); continue; }
+            const int cl = lev - 1;
+            const int cb = p.lvl_off[cl * Hp + h];
+            const int cc = p.lvl_off[cl * Hp + h + 1] - cb;
+            const int child = idx * 8 + lane;
+            const bool ok = lane < 8 && child < cc && accept(cl, child, cb + child);
+            const uint32_t m = __ballot_sync(0xffffffffu, ok);
+            const int cnt = __popc(m);
+            if (sp + cnt > kStack) { failed = true; break; }
+            if (ok) stack[sp + cnt - 1 - __popc(m & lt)] = (cl << 24) | child;
+            sp += cnt;
+            __syncwarp();
+        }
+        if (failed && lane == 0) raise_status(p.cnt, SIDM_DEV_STACK);
+        (void)cA;
+    }
+    // warp totals -> step statistics
+    for (int o = 16; o > 0; o >>= 1) {
+        n_gt1 += __shfl_xor_sync(0xffffffffu, n_gt1, o);
+        n_near += __shfl_xor_sync(0xffffffffu, n_near, o);
+    }
+    if (lane == 0) {
+        if (n_pairs) atomicAdd(&p.st->n_pairs, n_pairs);
+        if (n_gt1) atomicAdd(&p.st->n_p_gt1, n_gt1);
+        if (n_near) atomicAdd(&p.st->n_near, n_near);
+        if (n_tested) atomicAdd(&p.st->n_tested, n_tested);
+    }
+    st_pos.finish(lane, p.cnt);
+    st_vel.finish(lane, p.cnt);
+}
+
+template <class R, bool TMA>
+int launch_t(sidm_ctx* c, uint64_t seed, uint64_t step, const sidm_xs* xs, const double* dt, const double* mass,
+             sidm_step_stats* st, cudaStream_t s)
+{
+    PairParams p;
+    const LayoutHost& L = c->lay;
+    p.H = L.H; p.L = L.L;
+    p.leaf_halo = c->d_leaf_halo; p.leaf_off = c->d_leaf_off; p.halo_off = c->d_halo_off;
+    p.lvl_off = c->d_lvl_off; p.top = c->d_top; p.frame = c->d_frame; p.cell = c->d_cell;
+    p.nlo = c->d_nlo; p.nhi = c->d_nhi; p.P4 = c->d_P4; p.V4 = c->d_V4; p.lam = c->d_lam;
+    p.xs = xs; p.dt = dt; p.mass = mass;
+    p.seed_lo = (uint32_t)seed; p.seed_hi = (uint32_t)(seed >> 32); p.step_lo = (uint32_t)step;
+    p.ev = c->d_ev; p.ev_cap = (unsigned long long)c->cfg.event_cap;
+    p.sump = c->d_sump; p.use_sump = (c->cfg.flags & SIDM_FLAG_SUM_P) ? 1 : 0;
+    p.cnt = c->d_cnt; p.st = st;
+    const int warps = c->pair_warps;
+    const size_t smem = (size_t)warps * pair_warp_bytes<R, TMA>();
+    auto kern = k_pairs<R, TMA>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_check(c, e, "pair smem attribute");
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, warps * 32, smem);
+    if (e != cudaSuccess) return cuda_check(c, e, "pair occupancy");
+    if (occ < 1) return set_err(c, SIDM_ECAPACITY, "pair kernel does not fit on an SM");
+    int grid = c->cfg.grid_ctas > 0 ? c->cfg.grid_ctas : c->sm_count * occ;
+    grid = std::max(1, std::min(grid, (L.L + warps - 1) / warps));
+    c->pair_grid = grid;
+    e = cudaMemsetAsync(&c->d_cnt->work[1], 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return cuda_check(c, e, "pair work reset");
+    const int tidx = timer_begin(c, 2, s);
+    kern<<<grid, warps * 32, smem, s>>>(p);
+    timer_end(c, tidx, s);
+    c->launches++;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_check(c, e, "pair launch");
+    return SIDM_OK;
+}
+
+}  // namespace
+
+int launch_pairs(sidm_ctx* c, uint64_t seed, uint64_t step, const sidm_xs* xs, const double* dt, const double* mass,
+                 sidm_step_stats* st, cudaStream_t s)
+{
+    if (c->lay.L == 0) return SIDM_OK;
+    const bool tma = c->cfg.use_tma != 0;
+    if (c->cfg.precision == SIDM_FP64)
+        return tma ? launch_t<double, true>(c, seed, step, xs, dt, mass, st, s)
+                   : launch_t<double, false>(c, seed, step, xs, dt, mass, st, s);
+    return tma ? launch_t<float, true>(c, seed, step, xs, dt, mass, st, s)
+               : launch_t<float, false>(c, seed, step, xs, dt, mass, st, s);
+}
+
+}  // namespace sidm

@@ -1,0 +1,243 @@
+"""GPU parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (stated in the spec contract of this build and derived in
+the design doc): kernel sizes and neighbour lists bit-exact (same canonical FP32 /
+FP64 distance); event sets equal except pairs with |P - u| < 1e-6; velocities
+within 1e-5 of the pair's speed scale (mixed form) or 1e-12 (FP64 form);
+untouched particles bit-identical; energy/momentum sums within 1e-14 of the
+exact sums.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2506_06269_gb300 import ics
+
+from gpu_helpers import (compare_events, gpu_step, oracle_step, tainted_particles,
+                         velocity_scale)
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2506_06269_gb300 import build
+    build.build()
+
+
+def _check_velocities(g, o, tol, n):
+    only_o, only_g = compare_events(g["events"], o["events"])
+    bad = tainted_particles(o["events"], g["events"], only_o + only_g, n)
+    scale = velocity_scale(o["events"], g["vel_in"], n)
+    err = np.abs(g["vel"] - o["vel_out"]).max(axis=0)
+    touched = np.zeros(n, bool)
+    if len(o["events"]):
+        touched[o["events"]["i"]] = True
+        touched[o["events"]["j"]] = True
+    ok = ~bad
+    assert np.all(err[ok & touched] <= tol * scale[ok & touched] + 1e-30)
+    assert np.array_equal(g["vel"][:, ok & ~touched], o["vel_out"][:, ok & ~touched])
+    return only_o, only_g, bad
+
+
+# ---------------------------------------------------------------- Lambda table
+@pytest.mark.parametrize("precision,tol", [("mixed", 2e-6), ("fp64", 1e-6)])
+def test_lambda_table_matches_oracle(precision, tol):
+    from paper_2506_06269_gb300 import sidm
+    ctx = sidm.Context(n_max=64, precision=precision)
+    rng = np.random.default_rng(1)
+    n = 3000
+    hi = rng.uniform(0.05, 2.0, n); hj = hi * rng.uniform(0.02, 1.5, n)
+    d = rng.uniform(0, 1.0, n) * (hi + hj)
+    dd = torch.tensor(d, device="cuda"); a = torch.tensor(hi, device="cuda"); b = torch.tensor(hj, device="cuda")
+    got = ctx.lambda_eval(dd, a, b).cpu().numpy()
+    ref = np.array([O.lam(x, y, z) for x, y, z in zip(d, hi, hj)])
+    peak = np.array([O.lam(0.0, y, z) for y, z in zip(hi, hj)])
+    assert np.all(np.abs(got - ref) <= tol * peak)
+    # at the support edge: zero up to the rounding of h_i + h_j in the form's precision
+    z = ctx.lambda_eval(torch.tensor(hi + hj, device="cuda"), a, b).cpu().numpy()
+    assert np.all(np.abs(z) <= 1e-12 * peak)
+    z = ctx.lambda_eval(torch.tensor((hi + hj) * 1.001, device="cuda"), a, b).cpu().numpy()
+    assert np.all(z == 0.0)
+    ctx.close()
+
+
+# ---------------------------------------------------------------- kernel sizes
+def test_knn_parity_hernquist_16384_bit_exact():
+    h = ics.hernquist(16384, 0)
+    b = ics.batch([h])
+    g = gpu_step(b, [32], [(0, 0.0, 1.0)], [1e-3], 0, 0, want_nbrs=True)
+    oh, _, onb = O.knn(h.pos, h.ids, 32, O.MODE_MIXED, want_nbrs=True)
+    assert g["status"] == 0
+    assert np.array_equal(g["h"].astype(np.float32), oh.astype(np.float32))
+    assert np.array_equal(g["nbr"][:, :32], onb)
+
+
+def test_knn_parity_multi_halo_ragged_edges():
+    halos = [ics.hernquist(1000, 3), ics.uniform_box(33, 4), ics.nfw(5017, 5), ics.uniform_box(129, 6)]
+    ks = [16, 32, 64, 128]
+    b = ics.batch(halos)
+    for prec in ("mixed", "fp64"):
+        g = gpu_step(b, ks, [(0, 0.0, 1.0)] * 4, [1e-3] * 4, 0, 0, precision=prec,
+                     want_nbrs=(prec == "mixed"))
+        assert g["status"] == 0
+        for hidx, hh in enumerate(halos):
+            a, e = b.offsets[hidx], b.offsets[hidx + 1]
+            mode = O.MODE_MIXED if prec == "mixed" else O.MODE_FP64
+            oh, _, onb = O.knn(hh.pos, hh.ids, ks[hidx], mode, want_nbrs=(prec == "mixed"))
+            assert np.array_equal(g["h"][a:e], oh), (prec, hidx)
+            if prec == "mixed":
+                assert np.array_equal(g["nbr"][a:e, :ks[hidx]], onb), hidx
+
+
+# ---------------------------------------------------------------- full step
+def test_step_parity_hernquist_config():
+    # Hernquist N=16384, sigma/m=10, N_ngb=32, dt=1e-3, seed 0 (the plain-method case)
+    h = ics.hernquist(16384, 0)
+    b = ics.batch([h])
+    args = ([32], [(0, 10.0, 1.0)], [1e-3], 0, 0)
+    g = gpu_step(b, *args)
+    o = oracle_step(b, *args)
+    assert g["status"] == 0
+    assert g["stats"].n_pairs == o["stats"][0]["n_pairs"]
+    assert np.array_equal(g["h"], o["h"])
+    only_o, only_g, _ = _check_velocities(g, o, 1e-5, b.n)
+    assert len(only_o) + len(only_g) <= max(2, o["stats"][0]["n_near"])
+    assert g["n_events"] == len(g["events"]) and abs(g["n_events"] - len(o["events"])) <= len(only_o) + len(only_g)
+
+
+def test_step_parity_dense_events_multi_hit():
+    # a large dt makes particles scatter several times in one step
+    halos = [ics.hernquist(3000, 7), ics.nfw(2050, 8)]
+    b = ics.batch(halos)
+    args = ([32, 48], [(0, 10.0, 1.0), (1, 100.0, 0.3811)], [0.5, 2.0], 12345, 7)
+    g = gpu_step(b, *args)
+    o = oracle_step(b, *args)
+    assert g["status"] == 0
+    assert g["stats"].n_multi > 10 and g["stats"].rounds >= 2
+    _check_velocities(g, o, 1e-5, b.n)
+    # pair energy and momentum conserved by every event: totals within FP32 rounding
+    m = np.repeat(b.mass, np.diff(b.offsets))
+    e0 = 0.5 * (m * (g["vel_in"] ** 2).sum(0)).sum(); e1 = 0.5 * (m * (g["vel"] ** 2).sum(0)).sum()
+    assert abs(e1 - e0) < 1e-6 * e0
+    assert abs(g["stats"].d_energy - (e1 - e0)) < 1e-9 * e0
+
+
+def test_fp64_form_parity():
+    halos = [ics.hernquist(4000, 9)]
+    b = ics.batch(halos)
+    args = ([32], [(0, 10.0, 1.0)], [0.05], 3, 1)
+    g = gpu_step(b, *args, precision="fp64")
+    o = oracle_step(b, *args, precision="fp64")
+    assert g["status"] == 0
+    assert np.array_equal(g["h"], o["h"])
+    assert g["stats"].n_pairs == o["stats"][0]["n_pairs"]
+    _check_velocities(g, o, 1e-12, b.n)
+
+
+def test_zero_cross_section_is_identity():
+    h = ics.nfw(3000, 10)
+    b = ics.batch([h])
+    g = gpu_step(b, [32], [(0, 0.0, 1.0)], [1e-2], 1, 1)
+    assert g["n_events"] == 0
+    assert np.array_equal(g["vel"], g["vel_in"])
+
+
+def test_launch_shape_invariance():
+    h = ics.nfw(6000, 11)
+    b = ics.batch([h, ics.hernquist(2000, 12)])
+    args = ([64, 32], [(1, 100.0, 0.3811), (0, 10.0, 1.0)], [0.2, 0.05], 99, 5)
+    ref = gpu_step(b, *args)
+    for kw in (dict(knn_warps=1, pair_warps=2), dict(knn_warps=8, pair_warps=8, grid_ctas=3),
+               dict(knn_warps=2, pair_warps=1, grid_ctas=1000)):
+        g = gpu_step(b, *args, ctx_kw=kw)
+        assert np.array_equal(g["h"], ref["h"])
+        assert np.array_equal(g["events"]["key"], ref["events"]["key"])
+        assert np.array_equal(g["vel"], ref["vel"])
+
+
+def test_tma_staging_identical():
+    h = ics.nfw(6000, 13)
+    b = ics.batch([h])
+    args = ([64], [(1, 100.0, 0.3811)], [0.2], 5, 2)
+    ref = gpu_step(b, *args)
+    g = gpu_step(b, *args, ctx_kw=dict(use_tma=1))
+    assert g["status"] == 0
+    assert np.array_equal(g["h"], ref["h"])
+    assert np.array_equal(g["events"]["key"], ref["events"]["key"])
+    assert np.array_equal(g["vel"], ref["vel"])
+
+
+# ---------------------------------------------------------------- a5 reduction
+def test_energy_momentum_exact_and_deterministic():
+    from paper_2506_06269_gb300 import sidm
+    halos = [ics.nfw(40000, 14), ics.hernquist(777, 15)]
+    b = ics.batch(halos)
+    for prec in ("mixed", "fp64"):
+        ctx = sidm.Context(n_max=b.n, halo_max=2, precision=prec)
+        pos = torch.tensor(b.pos, device="cuda")
+        vin = b.vel.astype(np.float32).astype(np.float64) if prec == "mixed" else b.vel
+        vel = torch.tensor(vin, dtype=ctx.vdtype, device="cuda")
+        ids = torch.tensor(b.ids.astype(np.int64), device="cuda").to(torch.int32)
+        ctx.build_cells(b.offsets, pos, vel, ids)
+        mass = ctx.f64(b.mass)
+        out = torch.zeros((2, 4), dtype=torch.float64, device="cuda")
+        out2 = torch.zeros_like(out)
+        ctx.energy_momentum(mass, vel, out)
+        ctx.energy_momentum(mass, vel, out2)
+        assert torch.equal(out, out2)
+        v = vel.cpu().numpy().astype(np.float64)
+        for hidx in range(2):
+            a, e = b.offsets[hidx], b.offsets[hidx + 1]
+            ref = O.energy_momentum(b.mass[hidx], v[:, a:e])
+            got = out[hidx].cpu().numpy()
+            assert abs(got[0] - ref[0]) <= 1e-14 * abs(ref[0])
+            scale = b.mass[hidx] * np.abs(v[:, a:e]).sum()
+            assert np.all(np.abs(got[1:] - ref[1:]) <= 1e-14 * scale)
+        ctx.close()
+
+
+# ---------------------------------------------------------------- failure paths
+def test_event_overflow_leaves_velocities_untouched():
+    h = ics.hernquist(3000, 16)
+    b = ics.batch([h])
+    g = gpu_step(b, [32], [(0, 10.0, 1.0)], [0.5], 1, 1, event_cap=4)
+    assert g["status"] & 1
+    assert g["n_events"] > 4
+    assert np.array_equal(g["vel"], g["vel_in"])
+
+
+def test_round_limit_raises_status():
+    h = ics.hernquist(3000, 16)
+    b = ics.batch([h])
+    g = gpu_step(b, [32], [(0, 10.0, 1.0)], [0.5], 1, 1, ctx_kw=dict(max_rounds=1))
+    assert g["status"] & 2
+    assert g["stats"].rounds == 1
+
+
+def test_bad_arguments_rejected():
+    from paper_2506_06269_gb300 import sidm
+    ctx = sidm.Context(n_max=100, halo_max=2, ngb_max=32)
+    pos = torch.zeros((3, 100), dtype=torch.float64, device="cuda")
+    vel = torch.zeros((3, 100), dtype=torch.float32, device="cuda")
+    ids = torch.arange(100, dtype=torch.int32, device="cuda")
+    h = torch.zeros(100, dtype=torch.float32, device="cuda")
+    with pytest.raises(sidm.SidmError):
+        ctx.kernel_sizes([32], h)                       # before build
+    with pytest.raises(sidm.SidmError):
+        ctx.build_cells([0, 50, 200], pos, vel, ids)    # beyond n_max
+    with pytest.raises(sidm.SidmError):
+        ctx.build_cells([0, 60, 50], pos, vel, ids)     # decreasing
+    pos = torch.rand((3, 100), dtype=torch.float64, device="cuda")
+    ctx.build_cells([0, 30, 100], pos, vel, ids)
+    with pytest.raises(sidm.SidmError):
+        ctx.kernel_sizes([30, 16], h)                   # k >= halo size
+    with pytest.raises(sidm.SidmError):
+        ctx.kernel_sizes([16, 64], h)                   # k > ngb_max
+    ctx.kernel_sizes([16, 32], h)
+    assert ctx.status() == 0
+    ctx.close()
