@@ -244,6 +244,7 @@ def run_ours(args):
         raise RuntimeError(f"device status after warm-up: {ctx.status()}")
     ctx.energy_momentum(mass_t, vel, energy[0])
     ctx.kernel_times(reset=True)
+    ctx.diagnostics(reset=True)
     l0 = ctx.launch_count()
     if ws > 1:
         torch.distributed.barrier()
@@ -254,6 +255,7 @@ def run_ours(args):
     clocks = clk.stop()
     gpu_launches = ctx.launch_count() - l0
     kms, kcnt = ctx.kernel_times(reset=True)
+    diag = ctx.diagnostics(reset=True)
     status = ctx.status()
     total_ms = float(sum(times))
     if ws > 1:
@@ -274,7 +276,8 @@ def run_ours(args):
         "clocks": clocks, "gpu_launches": gpu_launches, "kms": kms, "kcnt": kcnt, "status": status,
         "drift": drift, "book": book, "n_pairs": n_pairs, "n_tested": n_tested, "n_events": n_events,
         "stats": st, "ws": ws, "rank": rank, "local": local, "tensors": (pos, vel, ids, h, xs, dt_t, mass_t),
-        "step": step, "seed": seed,
+        "step": step, "seed": seed, "diag": diag,
+        "knn_candidates_per_step": float(diag[1]) / max(K, 1),
     }
     return res
 
@@ -455,6 +458,10 @@ def main_ours(args):
             "clocks": res["clocks"],
             "gpu_launches": int(res["gpu_launches"]),
             "device_status": res["status"],
+            "work_per_step": {"knn_tiles": float(res["diag"][0]) / K, "knn_candidates": float(res["diag"][1]) / K,
+                              "knn_heap_inserts": float(res["diag"][2]) / K, "knn_max_tiles_one_leaf": int(res["diag"][3]),
+                              "pair_tiles": float(res["diag"][4]) / K, "pair_max_tiles_one_leaf": int(res["diag"][5]),
+                              "pair_tests": res["n_tested"] / K, "pair_evals": res["n_pairs"] / K},
         }
         if fp64:
             line["fp64_form"] = fp64

@@ -239,6 +239,14 @@ int64_t sidm_launch_count(const sidm_ctx* ctx);
  * Synchronises the device. */
 int sidm_kernel_times(sidm_ctx* ctx, double* ms_out, int64_t* count_out, int32_t reset);
 
+/* Work counters of the kernel-size and pair kernels since the last reset
+ * (synchronises the device): out[0] candidate leaves staged by the kernel-size
+ * kernel, out[1] lane-level candidate distances, out[2] heap insertions,
+ * out[3] largest number of leaves staged for one query leaf, out[4] candidate
+ * leaves staged by the pair kernel, out[5] its largest per query leaf,
+ * out[6..7] reserved.  reset != 0 clears them afterwards. */
+int sidm_diagnostics(sidm_ctx* ctx, uint64_t* out, int32_t reset);
+
 #ifdef __cplusplus
 }
 #endif

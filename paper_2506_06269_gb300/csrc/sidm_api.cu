@@ -1304,3 +1304,14 @@ extern "C" int sidm_kernel_times(sidm_ctx* c, double* ms, int64_t* count, int32_
     if (reset) c->t_used = 0;
     return SIDM_OK;
 }
+
+extern "C" int sidm_diagnostics(sidm_ctx* c, uint64_t* out, int32_t reset)
+{
+    if (!c) return SIDM_EINVAL;
+    if (!out) return set_err(c, SIDM_EINVAL, "null argument");
+    SIDM_CUDA(c, cudaSetDevice(c->dev));
+    SIDM_CUDA(c, cudaDeviceSynchronize());
+    SIDM_CUDA(c, cudaMemcpy(out, c->d_cnt->diag, sizeof(unsigned long long) * 8, cudaMemcpyDeviceToHost));
+    if (reset) SIDM_CUDA(c, cudaMemset(c->d_cnt->diag, 0, sizeof(unsigned long long) * 8));
+    return SIDM_OK;
+}

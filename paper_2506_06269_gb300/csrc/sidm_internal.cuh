@@ -43,6 +43,7 @@ struct DevCounters {
     unsigned int work[4];            // persistent work-queue counters
     unsigned int status;             // sticky SIDM_DEV_* bits (cleared by sidm_status)
     unsigned int pad;
+    unsigned long long diag[8];      // diagnostics (sidm_diagnostics)
     unsigned long long bbox[kMaxHalos * 6];   // ordered bits of per-halo min/max
 };
 
@@ -217,6 +218,15 @@ __device__ __forceinline__ R lambda_lookup(const R* __restrict__ T, R d, R hi, R
     }
     const R inv = R(1) / hmax;
     return f * inv * inv * inv;
+}
+
+// Lower bound of the squared distance from a point to a box (FP32, rounded down).
+__device__ __forceinline__ float point_gap2_rd(float3 p, float4 lo, float4 hi)
+{
+    float gx = fmaxf(0.f, fmaxf(__fsub_rd(lo.x, p.x), __fsub_rd(p.x, hi.x)));
+    float gy = fmaxf(0.f, fmaxf(__fsub_rd(lo.y, p.y), __fsub_rd(p.y, hi.y)));
+    float gz = fmaxf(0.f, fmaxf(__fsub_rd(lo.z, p.z), __fsub_rd(p.z, hi.z)));
+    return __fadd_rd(__fadd_rd(__fmul_rd(gx, gx), __fmul_rd(gy, gy)), __fmul_rd(gz, gz));
 }
 
 // Lower bound of the squared gap between two boxes (FP32, rounded down).

@@ -131,6 +131,7 @@ __global__ void k_knn(KnnParams p)
     int* stack = (int*)(tids + 32);
     K* heap = (K*)(stack + kStack);
     stage.init(lane);
+    unsigned long long n_cand = 0ull, n_ins = 0ull, n_tiles_all = 0ull, n_tiles_max = 0ull;
 
     while (true) {
         int leaf = 0;
@@ -149,13 +150,13 @@ __global__ void k_knn(KnnParams p)
         const HaloFrame fr = p.frame[h];
         const V q = ((const V*)p.P4)[(int64_t)leaf * kLeaf + lane];
         const float4 cA = p.cell[leaf];
-        const float4 qlo = p.nlo[leaf], qhi = p.nhi[leaf];
         const K kmax = key_max<K>();
         for (int t = 0; t < k; ++t) heap[t * 32 + lane] = kmax;
         K root = kmax;
         bool failed = false;
+        unsigned long long n_tiles = 0ull;
 
-        auto process = [&](int Bl) {
+        auto process = [&](int Bl, bool mine) {
             const int Bg = leaf0 + Bl;
             const int countB = (int)min((int64_t)kLeaf, nh - (int64_t)Bl * kLeaf);
             const V* tile = stage.load((const V*)p.P4 + (int64_t)Bg * kLeaf, lane, p.cnt);
@@ -172,7 +173,9 @@ __global__ void k_knn(KnnParams p)
             sh[lane] = c;
             if (NBR) tids[lane] = p.ID[(int64_t)Bg * kLeaf + lane];
             __syncwarp();
-            if (active) {
+            ++n_tiles;
+            if (active && mine) {
+                n_cand += (unsigned long long)countB;
                 for (int t = 0; t < countB; ++t) {
                     if (Bl == A && t == lane) continue;
                     const V cj = sh[t];
@@ -180,6 +183,7 @@ __global__ void k_knn(KnnParams p)
                     const R d2 = fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
                     const K key = make_key<R, NBR>(d2, NBR ? tids[t] : 0u);
                     if (key < root) {
+                        ++n_ins;
                         heap_replace<K>(heap, lane, k, key);
                         root = heap[lane];
                     }
@@ -195,55 +199,78 @@ __global__ void k_knn(KnnParams p)
             if (whi < nleaf - 1) { ++whi; wcount += min((int64_t)kLeaf, nh - (int64_t)whi * kLeaf); }
             if (wcount < k + 1 && wlo > 0) { --wlo; wcount += kLeaf; }
         }
-        for (int Bl = wlo; Bl <= whi; ++Bl) process(Bl);
+        for (int Bl = wlo; Bl <= whi; ++Bl) process(Bl, true);
 
-        // 2) tree walk with the radius bound of the current k-th keys
-        auto bound2 = [&]() -> float {
-            float r = active ? to_float_ru<R>(sqrt_ru(key_d2<R, NBR>(root))) : 0.f;
-            for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
+        // 2) tree walk.  A node is visited iff the query point of some lane lies
+        //    within that lane's current k-th distance (+ margin) of the node's box;
+        //    accepted leaves are processed at once so the bound keeps shrinking.
+        float3 pq;                                     // query point in the halo frame
+        if constexpr (sizeof(R) == 4) {
+            pq = make_float3(__fadd_rn(cA.x, (float)q.x), __fadd_rn(cA.y, (float)q.y), __fadd_rn(cA.z, (float)q.z));
+        } else {
+            pq = make_float3(__double2float_rn((double)q.x - fr.O[0]), __double2float_rn((double)q.y - fr.O[1]),
+                             __double2float_rn((double)q.z - fr.O[2]));
+        }
+        auto my_r2 = [&]() -> float {
+            if (!active) return -1.0f;
+            float r = to_float_ru<R>(sqrt_ru(key_d2<R, NBR>(root)));
             r = __fadd_ru(__fmul_ru(r, 1.0f + 0x1p-20f), fr.margin);
             return __fmul_ru(r, r);
+        };
+        auto near = [&](int g, float r2) -> bool {
+            return r2 >= 0.f && point_gap2_rd(pq, p.nlo[g], p.nhi[g]) <= r2;
+        };
+        auto visit_leaf = [&](int Bl) {
+            const bool mine = near(leaf0 + Bl, my_r2());
+            if (__any_sync(0xffffffffu, mine)) process(Bl, mine);
         };
         const int top = p.top[h];
         const int32_t* loff = p.lvl_off;
         const int Hp = p.H + 1;
         int sp = 0;
         {
-            const float R2 = bound2();
             const int nb = loff[top * Hp + h];
             const int ntop = loff[top * Hp + h + 1] - nb;
-            bool ok = lane < ntop && box_gap2_rd(qlo, qhi, p.nlo[nb + lane], p.nhi[nb + lane]) <= R2;
-            if (top == 0) ok = ok && (lane < wlo || lane > whi);
-            const uint32_t m = __ballot_sync(0xffffffffu, ok);
-            const int cnt = __popc(m);
-            if (ok) stack[sp + cnt - 1 - __popc(m & ((1u << lane) - 1u))] = (top << 24) | lane;
-            sp += cnt;
-            __syncwarp();
+            if (top == 0) {
+                for (int c = 0; c < ntop; ++c)
+                    if (c < wlo || c > whi) visit_leaf(c);
+            } else {
+                const float r2 = my_r2();
+                uint32_t acc = 0u;
+                for (int c = 0; c < ntop; ++c)
+                    if (__any_sync(0xffffffffu, near(nb + c, r2))) acc |= 1u << c;
+                for (int c = ntop - 1; c >= 0; --c)
+                    if ((acc >> c) & 1u) { if (lane == 0) stack[sp] = (top << 24) | c; ++sp; }
+                __syncwarp();
+            }
         }
         while (sp > 0) {
             const int e = stack[--sp];
             __syncwarp();
             const int lev = e >> 24, idx = e & 0xFFFFFF;
-            const float R2 = bound2();
-            if (lev == 0) {
-                const int g = leaf0 + idx;
-                if (box_gap2_rd(qlo, qhi, p.nlo[g], p.nhi[g]) <= R2) process(idx);
-                continue;
-            }
             const int cl = lev - 1;
             const int cb = loff[cl * Hp + h];
             const int cc = loff[cl * Hp + h + 1] - cb;
-            const int child = idx * 8 + lane;
-            bool ok = lane < 8 && child < cc && box_gap2_rd(qlo, qhi, p.nlo[cb + child], p.nhi[cb + child]) <= R2;
-            if (cl == 0) ok = ok && (child < wlo || child > whi);
-            const uint32_t m = __ballot_sync(0xffffffffu, ok);
-            const int cnt = __popc(m);
+            const int first = idx * 8;
+            const int nch = min(8, cc - first);
+            if (cl == 0) {
+                for (int c = 0; c < nch; ++c)
+                    if (first + c < wlo || first + c > whi) visit_leaf(first + c);
+                continue;
+            }
+            const float r2 = my_r2();
+            uint32_t acc = 0u;
+            for (int c = 0; c < nch; ++c)
+                if (__any_sync(0xffffffffu, near(cb + first + c, r2))) acc |= 1u << c;
+            const int cnt = __popc(acc);
             if (sp + cnt > kStack) { failed = true; break; }
-            if (ok) stack[sp + cnt - 1 - __popc(m & ((1u << lane) - 1u))] = (cl << 24) | child;
-            sp += cnt;
+            for (int c = nch - 1; c >= 0; --c)
+                if ((acc >> c) & 1u) { if (lane == 0) stack[sp] = (cl << 24) | (first + c); ++sp; }
             __syncwarp();
         }
         if (failed && lane == 0) raise_status(p.cnt, SIDM_DEV_STACK);
+        n_tiles_all += n_tiles;
+        n_tiles_max = n_tiles > n_tiles_max ? n_tiles : n_tiles_max;
 
         // 3) outputs
         if (active) {
@@ -264,6 +291,17 @@ __global__ void k_knn(KnnParams p)
             }
         }
         __syncwarp();
+    }
+    // diagnostics: tiles, lane-level candidates, heap insertions, worst leaf
+    for (int o = 16; o > 0; o >>= 1) {
+        n_cand += __shfl_xor_sync(0xffffffffu, n_cand, o);
+        n_ins += __shfl_xor_sync(0xffffffffu, n_ins, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&p.cnt->diag[0], n_tiles_all);
+        atomicAdd(&p.cnt->diag[1], n_cand);
+        atomicAdd(&p.cnt->diag[2], n_ins);
+        atomicMax(&p.cnt->diag[3], n_tiles_max);
     }
     stage.finish(lane, p.cnt);
 }

@@ -55,6 +55,13 @@ __device__ __forceinline__ uint32_t id_of(R w)
     else return (uint32_t)(double)w;
 }
 
+template <class R>
+__device__ __forceinline__ float to_float_ru_p(R v)
+{
+    if constexpr (sizeof(R) == 8) return __double2float_ru((double)v);
+    else return (float)v;
+}
+
 template <class R, bool TMA>
 constexpr size_t pair_warp_bytes()
 {
@@ -82,6 +89,7 @@ __global__ void k_pairs(PairParams p)
     const uint32_t lt = (1u << lane) - 1u;
 
     unsigned long long n_pairs = 0ull, n_gt1 = 0ull, n_near = 0ull, n_tested = 0ull;
+    unsigned long long n_tiles_all = 0ull, n_tiles_max = 0ull;
 
     while (true) {
         int leaf = 0;
@@ -97,8 +105,6 @@ __global__ void k_pairs(PairParams p)
         const bool active = lane < countA;
         const HaloFrame fr = p.frame[h];
         const float4 cA = p.cell[leaf];
-        const float4 qlo = p.nlo[leaf], qhi = p.nhi[leaf];
-        const float hmaxA = qlo.w;
         const sidm_xs xs = p.xs[h];
         const int kind = xs.kind;
         const R pref = (R)xs.s0 * (R)p.mass[h] * (R)p.dt[h];
@@ -108,6 +114,7 @@ __global__ void k_pairs(PairParams p)
         qv[lane] = ((const V*)p.V4)[(int64_t)leaf * kLeaf + lane];
         __syncwarp();
         int qhead = 0, qn = 0;
+        unsigned long long n_tiles = 0ull;
 
         // P, draw and event for queue entries qhead .. qhead+nb-1 (one per lane)
         auto run_batch = [&](int nb, int64_t ubB, const V* tp, const V* tv) {
@@ -164,8 +171,9 @@ __global__ void k_pairs(PairParams p)
             __syncwarp();
         };
 
-        auto process = [&](int Bl) {
+        auto process = [&](int Bl, bool mine) {
             const int Bg = leaf0 + Bl;
+            ++n_tiles;
             const int countB = (int)min((int64_t)kLeaf, nh - (int64_t)Bl * kLeaf);
             const V* rp = st_pos.load((const V*)p.P4 + (int64_t)Bg * kLeaf, lane, p.cnt);
             const V* rv = st_vel.load((const V*)p.V4 + (int64_t)Bg * kLeaf, lane, p.cnt);
@@ -187,7 +195,7 @@ __global__ void k_pairs(PairParams p)
             n_tested += Bl > A ? (unsigned long long)(countA * countB) : (unsigned long long)(countA * (countA - 1) / 2);
             for (int t = 0; t < countB; ++t) {
                 bool ok = false;
-                if (active && (Bl > A || t > lane)) {
+                if (mine && (Bl > A || t > lane)) {
                     const V pj = tp[t];
                     const R dx = sub_rn(pj.x, q.x), dy = sub_rn(pj.y, q.y), dz = sub_rn(pj.z, q.z);
                     const R d2 = fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
@@ -205,46 +213,70 @@ __global__ void k_pairs(PairParams p)
             __syncwarp();
         };
 
-        // tree walk: leaves B >= A with box gap < (hmax_A + hmax_B)(1 + 2^-20) + margin
+        // tree walk over leaves B >= A.  A node is visited iff some lane's point
+        // lies within (h_i + hmax_node)(1 + 2^-20) + margin of the node's box.
+        float3 pq;                                     // query point in the halo frame
+        if constexpr (sizeof(R) == 4) {
+            pq = make_float3(__fadd_rn(cA.x, (float)q.x), __fadd_rn(cA.y, (float)q.y), __fadd_rn(cA.z, (float)q.z));
+        } else {
+            pq = make_float3(__double2float_rn((double)q.x - fr.O[0]), __double2float_rn((double)q.y - fr.O[1]),
+                             __double2float_rn((double)q.z - fr.O[2]));
+        }
+        const float hq = active ? to_float_ru_p<R>(q.w) : -INFINITY;
+        auto near = [&](int g) -> bool {
+            const float4 lo = p.nlo[g], hi = p.nhi[g];
+            const float r = __fadd_ru(__fmul_ru(__fadd_ru(hq, lo.w), 1.0f + 0x1p-20f), fr.margin);
+            return active && point_gap2_rd(pq, lo, hi) <= __fmul_ru(r, r);
+        };
         const int top = p.top[h];
         const int Hp = p.H + 1;
-        auto accept = [&](int lev, int local, int g) -> bool {
-            if (((int64_t)(local + 1) << (3 * lev)) <= A) return false;   // entirely below A
-            const float4 lo = p.nlo[g], hi = p.nhi[g];
-            float r = __fadd_ru(__fmul_ru(__fadd_ru(hmaxA, lo.w), 1.0f + 0x1p-20f), fr.margin);
-            return box_gap2_rd(qlo, qhi, lo, hi) <= __fmul_ru(r, r);
-        };
         int sp = 0;
         bool failed = false;
+        auto visit_leaf = [&](int Bl) {
+            if (Bl < A) return;
+            const bool mine = near(leaf0 + Bl);
+            if (__any_sync(0xffffffffu, mine)) process(Bl, mine);
+        };
         {
             const int nb = p.lvl_off[top * Hp + h];
             const int ntop = p.lvl_off[top * Hp + h + 1] - nb;
-            const bool ok = lane < ntop && accept(top, lane, nb + lane);
-            const uint32_t m = __ballot_sync(0xffffffffu, ok);
-            const int cnt = __popc(m);
-            if (ok) stack[sp + cnt - 1 - __popc(m & lt)] = (top << 24) | lane;
-            sp += cnt;
-            __syncwarp();
+            if (top == 0) {
+                for (int c = 0; c < ntop; ++c) visit_leaf(c);
+            } else {
+                uint32_t acc = 0u;
+                for (int c = 0; c < ntop; ++c)
+                    if (((int64_t)(c + 1) << (3 * top)) > A && __any_sync(0xffffffffu, near(nb + c))) acc |= 1u << c;
+                for (int c = ntop - 1; c >= 0; --c)
+                    if ((acc >> c) & 1u) { if (lane == 0) stack[sp] = (top << 24) | c; ++sp; }
+                __syncwarp();
+            }
         }
         while (sp > 0) {
             const int e = stack[--sp];
             __syncwarp();
             const int lev = e >> 24, idx = e & 0xFFFFFF;
-            if (lev == 0) { process(idx); continue; }
             const int cl = lev - 1;
             const int cb = p.lvl_off[cl * Hp + h];
             const int cc = p.lvl_off[cl * Hp + h + 1] - cb;
-            const int child = idx * 8 + lane;
-            const bool ok = lane < 8 && child < cc && accept(cl, child, cb + child);
-            const uint32_t m = __ballot_sync(0xffffffffu, ok);
-            const int cnt = __popc(m);
+            const int first = idx * 8;
+            const int nch = min(8, cc - first);
+            if (cl == 0) {
+                for (int c = 0; c < nch; ++c) visit_leaf(first + c);
+                continue;
+            }
+            uint32_t acc = 0u;
+            for (int c = 0; c < nch; ++c)
+                if (((int64_t)(first + c + 1) << (3 * cl)) > A && __any_sync(0xffffffffu, near(cb + first + c)))
+                    acc |= 1u << c;
+            const int cnt = __popc(acc);
             if (sp + cnt > kStack) { failed = true; break; }
-            if (ok) stack[sp + cnt - 1 - __popc(m & lt)] = (cl << 24) | child;
-            sp += cnt;
+            for (int c = nch - 1; c >= 0; --c)
+                if ((acc >> c) & 1u) { if (lane == 0) stack[sp] = (cl << 24) | (first + c); ++sp; }
             __syncwarp();
         }
         if (failed && lane == 0) raise_status(p.cnt, SIDM_DEV_STACK);
-        (void)cA;
+        n_tiles_all += n_tiles;
+        n_tiles_max = n_tiles > n_tiles_max ? n_tiles : n_tiles_max;
     }
     // warp totals -> step statistics
     for (int o = 16; o > 0; o >>= 1) {
@@ -256,6 +288,8 @@ __global__ void k_pairs(PairParams p)
         if (n_gt1) atomicAdd(&p.st->n_p_gt1, n_gt1);
         if (n_near) atomicAdd(&p.st->n_near, n_near);
         if (n_tested) atomicAdd(&p.st->n_tested, n_tested);
+        atomicAdd(&p.cnt->diag[4], n_tiles_all);
+        atomicMax(&p.cnt->diag[5], n_tiles_max);
     }
     st_pos.finish(lane, p.cnt);
     st_vel.finish(lane, p.cnt);

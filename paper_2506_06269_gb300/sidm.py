@@ -76,9 +76,10 @@ def load_library():
     L.sidm_get_sum_p.argtypes = [vp, vp, vp]
     L.sidm_launch_count.argtypes = [vp]; L.sidm_launch_count.restype = i64
     L.sidm_kernel_times.argtypes = [vp, vp, vp, i32]
+    L.sidm_diagnostics.argtypes = [vp, vp, i32]
     for f in ("sidm_create", "sidm_destroy", "sidm_build_cells", "sidm_kernel_sizes", "sidm_scatter_step",
               "sidm_energy_momentum", "sidm_status", "sidm_get_perm", "sidm_neighbours", "sidm_get_events",
-              "sidm_lambda_eval", "sidm_drift", "sidm_get_sum_p", "sidm_kernel_times"):
+              "sidm_lambda_eval", "sidm_drift", "sidm_get_sum_p", "sidm_kernel_times", "sidm_diagnostics"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -87,7 +88,7 @@ def load_library():
 EXPORTED = ["sidm_create", "sidm_destroy", "sidm_last_error", "sidm_create_error", "sidm_build_cells",
             "sidm_kernel_sizes", "sidm_scatter_step", "sidm_energy_momentum", "sidm_status", "sidm_get_perm",
             "sidm_neighbours", "sidm_get_events", "sidm_lambda_eval", "sidm_drift", "sidm_get_sum_p",
-            "sidm_launch_count", "sidm_kernel_times"]
+            "sidm_launch_count", "sidm_kernel_times", "sidm_diagnostics"]
 
 
 def _torch():
@@ -185,6 +186,13 @@ def sidm_get_sum_p(ctx, out, stream=None):
 
 def sidm_launch_count(ctx) -> int:
     return int(load_library().sidm_launch_count(ctx))
+
+
+def sidm_diagnostics(ctx, reset=True):
+    """Work counters of the kernel-size and pair kernels (see include/sidm.h)."""
+    out = np.zeros(8, np.uint64)
+    _check(ctx, load_library().sidm_diagnostics(ctx, out.ctypes.data_as(C.c_void_p), 1 if reset else 0))
+    return out
 
 
 def sidm_kernel_times(ctx, reset=True):
@@ -310,3 +318,6 @@ class Context:
 
     def kernel_times(self, reset=True):
         return sidm_kernel_times(self.handle, reset)
+
+    def diagnostics(self, reset=True):
+        return sidm_diagnostics(self.handle, reset)
