@@ -247,6 +247,50 @@ int sidm_kernel_times(sidm_ctx* ctx, double* ms_out, int64_t* count_out, int32_t
  * out[6..7] reserved.  reset != 0 clears them afterwards. */
 int sidm_diagnostics(sidm_ctx* ctx, uint64_t* out, int32_t reset);
 
+
+/* ---- allocation-free variant -------------------------------------------- */
+
+/* Limits of sidm_energy_momentum_static. */
+#define SIDM_STATIC_MAX_HALOS   64     /* halos per call                                */
+#define SIDM_STATIC_MAX_CHUNKS  4096   /* chunks of 16384 particles per call (~67 M)    */
+
+/* Per-halo kinetic energy and momentum, like sidm_energy_momentum, for callers
+ * that must not allocate device memory.  (The paper has no counterpart: this
+ * is a deployment variant, not a step of the method.)
+ *
+ * Who needs it: code running inside a host application that owns all device
+ * memory of the process -- a framework with its own caching allocator, or a
+ * fixed memory budget -- where a library may not call cudaMalloc/cudaFree.
+ * This call needs no context and allocates nothing: it calls no cudaMalloc,
+ * cudaFree or allocating library routine.  Its scratch (two FP64 words per
+ * quantity per chunk, 256 KiB in all) is a fixed file-scope device array,
+ * which every GPU that loads libsidm holds until the process exits.
+ *
+ * The first call on a device, with that device current, looks up the device
+ * address of the scratch array (cudaGetSymbolAddress) and caches it; make that
+ * first call before any stream capture.  Every call shares the same scratch
+ * and overwrites what it uses (nothing has to start at zero), so calls that
+ * overlap on the GPU -- on different streams, or from different threads --
+ * race and must be serialised by the caller.
+ *
+ * The arithmetic and its order are those of sidm_energy_momentum, so both give
+ * the same bits on the same inputs.
+ *   n_halos   : 1..SIDM_STATIC_MAX_HALOS
+ *   halo_off  : host int64[n_halos+1], halo_off[0] == 0, non-decreasing; the
+ *               halos may hold at most SIDM_STATIC_MAX_CHUNKS chunks of 16384
+ *               particles together (SIDM_ECAPACITY otherwise)
+ *   precision : SIDM_MIXED (vel f32) or SIDM_FP64 (vel f64)
+ *   mass_dev  : device f64[n_halos]
+ *   vel_dev   : device [3][N] velocities, N = halo_off[n_halos]
+ *   out_dev   : device f64[n_halos][4] = (E, px, py, pz)
+ *   comp_dev  : device f64[n_halos][4] residual compensation terms, or NULL
+ * Returns SIDM_OK, SIDM_EINVAL (bad argument), SIDM_ECAPACITY (too many
+ * chunks) or SIDM_ECUDA (device lookup or launch failed).  Asynchronous on
+ * the stream. */
+int sidm_energy_momentum_static(int32_t n_halos, const int64_t* halo_off, int32_t precision,
+                                const double* mass_dev, const void* vel_dev, double* out_dev,
+                                double* comp_dev, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -77,9 +77,11 @@ def load_library():
     L.sidm_launch_count.argtypes = [vp]; L.sidm_launch_count.restype = i64
     L.sidm_kernel_times.argtypes = [vp, vp, vp, i32]
     L.sidm_diagnostics.argtypes = [vp, vp, i32]
+    L.sidm_energy_momentum_static.argtypes = [i32, vp, i32, vp, vp, vp, vp, vp]
     for f in ("sidm_create", "sidm_destroy", "sidm_build_cells", "sidm_kernel_sizes", "sidm_scatter_step",
               "sidm_energy_momentum", "sidm_status", "sidm_get_perm", "sidm_neighbours", "sidm_get_events",
-              "sidm_lambda_eval", "sidm_drift", "sidm_get_sum_p", "sidm_kernel_times", "sidm_diagnostics"):
+              "sidm_lambda_eval", "sidm_drift", "sidm_get_sum_p", "sidm_kernel_times", "sidm_diagnostics",
+              "sidm_energy_momentum_static"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -88,7 +90,7 @@ def load_library():
 EXPORTED = ["sidm_create", "sidm_destroy", "sidm_last_error", "sidm_create_error", "sidm_build_cells",
             "sidm_kernel_sizes", "sidm_scatter_step", "sidm_energy_momentum", "sidm_status", "sidm_get_perm",
             "sidm_neighbours", "sidm_get_events", "sidm_lambda_eval", "sidm_drift", "sidm_get_sum_p",
-            "sidm_launch_count", "sidm_kernel_times", "sidm_diagnostics"]
+            "sidm_launch_count", "sidm_kernel_times", "sidm_diagnostics", "sidm_energy_momentum_static"]
 
 
 def _torch():
@@ -186,6 +188,17 @@ def sidm_get_sum_p(ctx, out, stream=None):
 
 def sidm_launch_count(ctx) -> int:
     return int(load_library().sidm_launch_count(ctx))
+
+
+def sidm_energy_momentum_static(halo_off, precision, mass, vel, out, comp=None, stream=None):
+    """Allocation-free per-halo energy and momentum (no context; see include/sidm.h)."""
+    off = np.ascontiguousarray(halo_off, dtype=np.int64)
+    prec = SIDM_FP64 if precision in ("fp64", SIDM_FP64) else SIDM_MIXED
+    rc = load_library().sidm_energy_momentum_static(len(off) - 1, off.ctypes.data_as(C.c_void_p), prec, _ptr(mass),
+                                                    _ptr(vel), _ptr(out), _ptr(comp), _stream(stream))
+    if rc != SIDM_OK:
+        raise SidmError(rc, {SIDM_EINVAL: "bad argument", SIDM_ECAPACITY: "more chunks than the static scratch holds",
+                             SIDM_ECUDA: "CUDA call failed"}.get(rc, "error"))
 
 
 def sidm_diagnostics(ctx, reset=True):
