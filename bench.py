@@ -185,6 +185,20 @@ def dt_rule(ctx_cls, halo, vmax, device):
     return TAU / q, q
 
 
+def max_over_ranks(value, device):
+    """MAX of a per-rank scalar over the process group (timing only)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(n_per_rank, world, steps, max_ms):
+    """Whole-job particle-steps/s: every rank advances its own halo."""
+    return world * n_per_rank * steps / (max_ms * 1e-3)
+
+
 def time_steps(ctx, step_fn, k, flush, first_step):
     import torch
     s = torch.cuda.current_stream()
@@ -257,11 +271,7 @@ def run_ours(args):
     kms, kcnt = ctx.kernel_times(reset=True)
     diag = ctx.diagnostics(reset=True)
     status = ctx.status()
-    total_ms = float(sum(times))
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(sum(times)), dev) if ws > 1 else float(sum(times))
     st = [sidm.parse_stats(stats[i]) for i in range(K)]
     E = energy.cpu().numpy()
     e0 = E[0, 0]
@@ -431,7 +441,7 @@ def main_ours(args):
     K, W = args.steps, args.warmup
     n = res["halo"].n
     total_ms = res["total_ms"]
-    value = ws * n * K / (total_ms * 1e-3)
+    value = job_throughput(n, ws, K, total_ms)
     peaks, peak_src = load_peaks()
     line = None
     if rank == 0:

@@ -765,6 +765,28 @@ int cuda_check(sidm_ctx* c, cudaError_t e, const char* what)
     return set_err(c, SIDM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+cudaError_t ensure_device(sidm_ctx* c)
+{
+    int cur = -1;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e != cudaSuccess) return e;
+    return cur == c->dev ? cudaSuccess : cudaSetDevice(c->dev);
+}
+
+int occupancy(sidm_ctx* c, const void* fn, int threads, size_t smem, int* occ)
+{
+    for (const auto& e : c->launch_cache)
+        if (e.fn == fn && e.smem == smem) { *occ = e.occ; return SIDM_OK; }
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_check(c, e, "shared-memory attribute");
+    int o = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, threads, smem);
+    if (e != cudaSuccess) return cuda_check(c, e, "occupancy");
+    c->launch_cache.push_back({fn, smem, o});
+    *occ = o;
+    return SIDM_OK;
+}
+
 int timer_begin(sidm_ctx* c, int slot, cudaStream_t s)
 {
     if (!(c->cfg.flags & SIDM_FLAG_TIMING) || c->t_used >= kTimerCap) return -1;
@@ -1070,7 +1092,7 @@ extern "C" int sidm_build_cells(sidm_ctx* c, int32_t n_halos, const int64_t* hal
         if (halo_off[h + 1] < halo_off[h]) return set_err(c, SIDM_EINVAL, "halo_off must be non-decreasing");
     if (halo_off[n_halos] > c->cfg.n_max) return set_err(c, SIDM_ECAPACITY, "more particles than n_max");
     if (halo_off[n_halos] > 0 && (!pos || !vel || !id)) return set_err(c, SIDM_EINVAL, "null particle array");
-    SIDM_CUDA(c, cudaSetDevice(c->dev));
+    SIDM_CUDA(c, ensure_device(c));
     const bool same = c->has_layout && c->lay.H == n_halos &&
                       std::equal(halo_off, halo_off + n_halos + 1, c->lay.halo_off.begin());
     if (!same) {
@@ -1108,7 +1130,7 @@ extern "C" int sidm_kernel_sizes(sidm_ctx* c, const int32_t* n_ngb, void* h_dev,
             return set_err(c, SIDM_EINVAL, "halo " + std::to_string(h) + " has no more than n_ngb particles");
         kmax = std::max(kmax, n_ngb[h]);
     }
-    SIDM_CUDA(c, cudaSetDevice(c->dev));
+    SIDM_CUDA(c, ensure_device(c));
     if (c->ngb_host.size() != (size_t)L.H || !std::equal(n_ngb, n_ngb + L.H, c->ngb_host.begin())) {
         std::memcpy(c->d_stage, n_ngb, sizeof(int32_t) * L.H);
         SIDM_CUDA(c, cudaMemcpyAsync(c->d_ngb, c->d_stage, sizeof(int32_t) * L.H, cudaMemcpyHostToDevice, s));
@@ -1142,7 +1164,7 @@ extern "C" int sidm_neighbours(sidm_ctx* c, const int32_t* n_ngb, int32_t k_stri
     for (int h = 0; h < c->lay.H; ++h)
         if (c->lay.halo_off[h + 1] > c->lay.halo_off[h] && (n_ngb[h] != c->ngb_host[h] || n_ngb[h] > k_stride))
             return set_err(c, SIDM_EINVAL, "n_ngb must match the kernel-size pass and fit k_stride");
-    SIDM_CUDA(c, cudaSetDevice(c->dev));
+    SIDM_CUDA(c, ensure_device(c));
     return launch_knn(c, nullptr, nbr, k_stride, s);
 }
 
@@ -1152,7 +1174,7 @@ extern "C" int sidm_scatter_step(sidm_ctx* c, uint64_t seed, uint64_t step, cons
     if (!c) return SIDM_EINVAL;
     if (!c->sized) return set_err(c, SIDM_EINVAL, "sidm_kernel_sizes must come first");
     if (!xs || !dt || !mass || (!vel && c->lay.N > 0)) return set_err(c, SIDM_EINVAL, "null argument");
-    SIDM_CUDA(c, cudaSetDevice(c->dev));
+    SIDM_CUDA(c, ensure_device(c));
     const LayoutHost& L = c->lay;
     sidm_step_stats* st = stats ? stats : c->d_stats_own;
     SIDM_CUDA(c, cudaMemsetAsync(st, 0, sizeof(sidm_step_stats), s));
@@ -1187,7 +1209,7 @@ extern "C" int sidm_energy_momentum(sidm_ctx* c, const double* mass, const void*
     if (!c) return SIDM_EINVAL;
     if (!c->has_layout) return set_err(c, SIDM_EINVAL, "sidm_build_cells must come first");
     if (!mass || !out || (!vel && c->lay.N > 0)) return set_err(c, SIDM_EINVAL, "null argument");
-    SIDM_CUDA(c, cudaSetDevice(c->dev));
+    SIDM_CUDA(c, ensure_device(c));
     const LayoutHost& L = c->lay;
     if (L.nchunk > 0) {
         if (c->cfg.precision == SIDM_FP64)
@@ -1204,7 +1226,7 @@ extern "C" int sidm_energy_momentum(sidm_ctx* c, const double* mass, const void*
 extern "C" int sidm_status(sidm_ctx* c, cudaStream_t s, uint32_t* status)
 {
     if (!c) return SIDM_EINVAL;
-    SIDM_CUDA(c, cudaSetDevice(c->dev));
+    SIDM_CUDA(c, ensure_device(c));
     SIDM_CUDA(c, cudaStreamSynchronize(s));
     unsigned int v = 0;
     SIDM_CUDA(c, cudaMemcpy(&v, &c->d_cnt->status, sizeof(v), cudaMemcpyDeviceToHost));
@@ -1227,7 +1249,7 @@ extern "C" int sidm_get_perm(sidm_ctx* c, uint32_t* perm, cudaStream_t s)
     if (!c) return SIDM_EINVAL;
     if (!c->built) return set_err(c, SIDM_EINVAL, "sidm_build_cells must come first");
     if (!perm) return set_err(c, SIDM_EINVAL, "null argument");
-    SIDM_CUDA(c, cudaSetDevice(c->dev));
+    SIDM_CUDA(c, ensure_device(c));
     if (c->lay.N) SIDM_CUDA(c, cudaMemcpyAsync(perm, c->d_perm, sizeof(uint32_t) * c->lay.N, cudaMemcpyDeviceToDevice, s));
     return SIDM_OK;
 }
@@ -1237,7 +1259,7 @@ extern "C" int sidm_get_events(sidm_ctx* c, int64_t cap, sidm_event* ev, int64_t
     if (!c) return SIDM_EINVAL;
     if (!c->stepped) return set_err(c, SIDM_EINVAL, "sidm_scatter_step must come first");
     if (!n_host || (cap > 0 && !ev)) return set_err(c, SIDM_EINVAL, "null argument");
-    SIDM_CUDA(c, cudaSetDevice(c->dev));
+    SIDM_CUDA(c, ensure_device(c));
     SIDM_CUDA(c, cudaStreamSynchronize(s));
     unsigned long long n = 0;
     SIDM_CUDA(c, cudaMemcpy(&n, &c->d_cnt->ev_count, sizeof(n), cudaMemcpyDeviceToHost));
@@ -1253,7 +1275,7 @@ extern "C" int sidm_lambda_eval(sidm_ctx* c, int64_t n, const double* d, const d
     if (!c) return SIDM_EINVAL;
     if (n < 0 || (n > 0 && (!d || !hi || !hj || !out))) return set_err(c, SIDM_EINVAL, "bad argument");
     if (n == 0) return SIDM_OK;
-    SIDM_CUDA(c, cudaSetDevice(c->dev));
+    SIDM_CUDA(c, ensure_device(c));
     if (c->cfg.precision == SIDM_FP64)
         SIDM_LAUNCH(c, k_lambda_eval<double><<<grid_for(c, n, 256), 256, 0, s>>>(n, d, hi, hj, out, (const double*)c->d_lam));
     else
@@ -1267,7 +1289,7 @@ extern "C" int sidm_drift(sidm_ctx* c, const double* dt, double* pos, const void
     if (!c->has_layout) return set_err(c, SIDM_EINVAL, "sidm_build_cells must come first");
     if (!dt || (c->lay.N > 0 && (!pos || !vel))) return set_err(c, SIDM_EINVAL, "null argument");
     if (c->lay.N == 0) return SIDM_OK;
-    SIDM_CUDA(c, cudaSetDevice(c->dev));
+    SIDM_CUDA(c, ensure_device(c));
     if (c->cfg.precision == SIDM_FP64)
         SIDM_LAUNCH(c, k_drift<double><<<grid_for(c, c->lay.N, 256), 256, 0, s>>>(c->lay.N, c->lay.H, c->d_halo_off, dt, pos,
                                                                                 (const double*)vel));
@@ -1282,7 +1304,7 @@ extern "C" int sidm_get_sum_p(sidm_ctx* c, float* out, cudaStream_t s)
     if (!c) return SIDM_EINVAL;
     if (!(c->cfg.flags & SIDM_FLAG_SUM_P)) return set_err(c, SIDM_EINVAL, "context built without SIDM_FLAG_SUM_P");
     if (!out) return set_err(c, SIDM_EINVAL, "null argument");
-    SIDM_CUDA(c, cudaSetDevice(c->dev));
+    SIDM_CUDA(c, ensure_device(c));
     if (c->lay.N) SIDM_CUDA(c, cudaMemcpyAsync(out, c->d_sump, sizeof(float) * c->lay.N, cudaMemcpyDeviceToDevice, s));
     return SIDM_OK;
 }
@@ -1292,7 +1314,7 @@ extern "C" int sidm_kernel_times(sidm_ctx* c, double* ms, int64_t* count, int32_
     if (!c) return SIDM_EINVAL;
     if (!(c->cfg.flags & SIDM_FLAG_TIMING)) return set_err(c, SIDM_EINVAL, "context built without SIDM_FLAG_TIMING");
     if (!ms) return set_err(c, SIDM_EINVAL, "null argument");
-    SIDM_CUDA(c, cudaSetDevice(c->dev));
+    SIDM_CUDA(c, ensure_device(c));
     SIDM_CUDA(c, cudaDeviceSynchronize());
     for (int k = 0; k < 4; ++k) { ms[k] = 0.0; if (count) count[k] = 0; }
     for (int i = 0; i < c->t_used; ++i) {
@@ -1309,7 +1331,7 @@ extern "C" int sidm_diagnostics(sidm_ctx* c, uint64_t* out, int32_t reset)
 {
     if (!c) return SIDM_EINVAL;
     if (!out) return set_err(c, SIDM_EINVAL, "null argument");
-    SIDM_CUDA(c, cudaSetDevice(c->dev));
+    SIDM_CUDA(c, ensure_device(c));
     SIDM_CUDA(c, cudaDeviceSynchronize());
     SIDM_CUDA(c, cudaMemcpy(out, c->d_cnt->diag, sizeof(unsigned long long) * 8, cudaMemcpyDeviceToHost));
     if (reset) SIDM_CUDA(c, cudaMemset(c->d_cnt->diag, 0, sizeof(unsigned long long) * 8));

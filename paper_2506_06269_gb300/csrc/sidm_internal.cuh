@@ -128,6 +128,11 @@ struct sidm_ctx {
 
     int knn_grid = 0, pair_grid = 0, knn_warps = 4, pair_warps = 4;
 
+    // launch configuration cache: (kernel, dynamic smem) -> CTAs per SM, so
+    // that repeated calls issue stream operations only
+    struct LaunchCfg { const void* fn; size_t smem; int occ; };
+    std::vector<LaunchCfg> launch_cache;
+
     // CUDA-event timing of hot kernels (SIDM_FLAG_TIMING): pairs of events
     std::vector<cudaEvent_t> t_ev;     // [2 * kTimerCap]
     std::vector<int8_t> t_slot;        // [kTimerCap]
@@ -144,6 +149,13 @@ int cuda_check(sidm_ctx* c, cudaError_t e, const char* what);
 constexpr int kTimerCap = 4096;
 int timer_begin(sidm_ctx* c, int slot, cudaStream_t s);
 void timer_end(sidm_ctx* c, int idx, cudaStream_t s);
+
+// make the context's device current (no call if it already is)
+cudaError_t ensure_device(sidm_ctx* c);
+
+// CTAs per SM of a kernel at a dynamic shared-memory size (cached per context;
+// sets the kernel's dynamic shared-memory limit on first use)
+int occupancy(sidm_ctx* c, const void* fn, int threads, size_t smem, int* occ);
 
 // kernel entry points implemented in the other translation units
 int launch_knn(sidm_ctx* c, void* h_out, uint32_t* nbr, int k_stride, cudaStream_t s);
@@ -217,6 +229,34 @@ __device__ __forceinline__ R lambda_lookup(const R* __restrict__ T, R d, R hi, R
         f += wr[a] * s;
     }
     const R inv = R(1) / hmax;
+    return f * inv * inv * inv;
+}
+
+// FP32 variant of lambda_lookup with approximate reciprocals (relative error
+// ~1e-7, far below the table's own 1e-6 of the peak).
+__device__ __forceinline__ float lambda_lookup_fast(const float* __restrict__ T, float d, float hi, float hj)
+{
+    const float hmax = fmaxf(hi, hj), hmin = fminf(hi, hj);
+    float x = __fdividef(d, hi + hj);
+    if (!(x < 1.f)) return 0.f;
+    x = fmaxf(x, 0.f);
+    const float inv = __fdividef(1.f, hmax);
+    const float rho = hmin * inv;
+    const float gx = x * (float)(kLamNX - 1);
+    int ix = (int)floorf(gx) - 1;
+    ix = ix < 0 ? 0 : (ix > kLamNX - 4 ? kLamNX - 4 : ix);
+    const float gr = rho * (float)(kLamNR - 1);
+    int ir = (int)floorf(gr) - 1;
+    ir = ir < 0 ? 0 : (ir > kLamNR - 4 ? kLamNR - 4 : ir);
+    float wx[4], wr[4];
+    lagrange4<float>(gx - (float)ix, wx);
+    lagrange4<float>(gr - (float)ir, wr);
+    float f = 0.f;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const float* row = T + (ir + a) * kLamNX + ix;
+        f = fmaf(wr[a], wx[0] * __ldg(row) + wx[1] * __ldg(row + 1) + wx[2] * __ldg(row + 2) + wx[3] * __ldg(row + 3), f);
+    }
     return f * inv * inv * inv;
 }
 

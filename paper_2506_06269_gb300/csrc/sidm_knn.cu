@@ -150,6 +150,7 @@ __global__ void k_knn(KnnParams p)
         const HaloFrame fr = p.frame[h];
         const V q = ((const V*)p.P4)[(int64_t)leaf * kLeaf + lane];
         const float4 cA = p.cell[leaf];
+        const float4 qlo = p.nlo[leaf], qhi = p.nhi[leaf];
         const K kmax = key_max<K>();
         for (int t = 0; t < k; ++t) heap[t * 32 + lane] = kmax;
         K root = kmax;
@@ -227,24 +228,49 @@ __global__ void k_knn(KnnParams p)
         const int top = p.top[h];
         const int32_t* loff = p.lvl_off;
         const int Hp = p.H + 1;
+        // Accepted nodes are visited nearest first (box gap to the query leaf),
+        // so the k-th bound shrinks early.  rank = position among the accepted.
+        auto order_rank = [&](uint32_t acc, int n, int g0) -> int {
+            const bool mine_acc = lane < n && ((acc >> lane) & 1u);
+            const float pr = mine_acc ? box_gap2_rd(qlo, qhi, p.nlo[g0 + lane], p.nhi[g0 + lane]) : INFINITY;
+            int rank = 0;
+            for (int j = 0; j < n; ++j) {
+                const float pj = __shfl_sync(0xffffffffu, pr, j);
+                if ((acc >> j) & 1u) rank += (pj < pr || (pj == pr && j < lane)) ? 1 : 0;
+            }
+            return rank;
+        };
+        auto visit_leaves_in_order = [&](uint32_t acc, int n, int first_local, int g0) {
+            const int rank = order_rank(acc, n, g0);
+            const int cnt = __popc(acc);
+            for (int r = 0; r < cnt; ++r) {
+                const uint32_t m = __ballot_sync(0xffffffffu, lane < n && ((acc >> lane) & 1u) && rank == r);
+                visit_leaf(first_local + __ffs(m) - 1);
+            }
+        };
+        auto push_in_order = [&](uint32_t acc, int n, int lev, int first_local, int g0, int& sp) -> bool {
+            const int rank = order_rank(acc, n, g0);
+            const int cnt = __popc(acc);
+            if (sp + cnt > kStack) return false;
+            if (lane < n && ((acc >> lane) & 1u)) stack[sp + cnt - 1 - rank] = (lev << 24) | (first_local + lane);
+            sp += cnt;
+            __syncwarp();
+            return true;
+        };
         int sp = 0;
         {
             const int nb = loff[top * Hp + h];
             const int ntop = loff[top * Hp + h + 1] - nb;
-            if (top == 0) {
-                for (int c = 0; c < ntop; ++c)
-                    if (c < wlo || c > whi) visit_leaf(c);
-            } else {
-                const float r2 = my_r2();
-                uint32_t acc = 0u;
-                for (int c = 0; c < ntop; ++c)
-                    if (__any_sync(0xffffffffu, near(nb + c, r2))) acc |= 1u << c;
-                for (int c = ntop - 1; c >= 0; --c)
-                    if ((acc >> c) & 1u) { if (lane == 0) stack[sp] = (top << 24) | c; ++sp; }
-                __syncwarp();
+            const float r2 = my_r2();
+            uint32_t acc = 0u;
+            for (int c = 0; c < ntop; ++c) {
+                if (top == 0 && c >= wlo && c <= whi) continue;
+                if (__any_sync(0xffffffffu, near(nb + c, r2))) acc |= 1u << c;
             }
+            if (top == 0) visit_leaves_in_order(acc, ntop, 0, nb);
+            else if (!push_in_order(acc, ntop, top, 0, nb, sp)) failed = true;
         }
-        while (sp > 0) {
+        while (sp > 0 && !failed) {
             const int e = stack[--sp];
             __syncwarp();
             const int lev = e >> 24, idx = e & 0xFFFFFF;
@@ -253,20 +279,14 @@ __global__ void k_knn(KnnParams p)
             const int cc = loff[cl * Hp + h + 1] - cb;
             const int first = idx * 8;
             const int nch = min(8, cc - first);
-            if (cl == 0) {
-                for (int c = 0; c < nch; ++c)
-                    if (first + c < wlo || first + c > whi) visit_leaf(first + c);
-                continue;
-            }
             const float r2 = my_r2();
             uint32_t acc = 0u;
-            for (int c = 0; c < nch; ++c)
+            for (int c = 0; c < nch; ++c) {
+                if (cl == 0 && first + c >= wlo && first + c <= whi) continue;
                 if (__any_sync(0xffffffffu, near(cb + first + c, r2))) acc |= 1u << c;
-            const int cnt = __popc(acc);
-            if (sp + cnt > kStack) { failed = true; break; }
-            for (int c = nch - 1; c >= 0; --c)
-                if ((acc >> c) & 1u) { if (lane == 0) stack[sp] = (cl << 24) | (first + c); ++sp; }
-            __syncwarp();
+            }
+            if (cl == 0) visit_leaves_in_order(acc, nch, first, cb + first);
+            else if (!push_in_order(acc, nch, cl, first, cb + first, sp)) failed = true;
         }
         if (failed && lane == 0) raise_status(p.cnt, SIDM_DEV_STACK);
         n_tiles_all += n_tiles;
@@ -321,11 +341,10 @@ int launch_t(sidm_ctx* c, void* h_out, uint32_t* nbr, int k_stride, cudaStream_t
     const int warps = c->knn_warps;
     const size_t smem = (size_t)warps * knn_warp_bytes<R, K>(p.kcap);
     auto kern = k_knn<R, NBR, TMA>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_check(c, e, "knn smem attribute");
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, warps * 32, smem);
-    if (e != cudaSuccess) return cuda_check(c, e, "knn occupancy");
+    int rc = occupancy(c, (const void*)kern, warps * 32, smem, &occ);
+    if (rc) return rc;
+    cudaError_t e;
     if (occ < 1) return set_err(c, SIDM_ECAPACITY, "knn kernel does not fit on an SM (ngb_max too large for knn_warps)");
     int grid = c->cfg.grid_ctas > 0 ? c->cfg.grid_ctas : c->sm_count * occ;
     grid = std::max(1, std::min(grid, (L.L + warps - 1) / warps));

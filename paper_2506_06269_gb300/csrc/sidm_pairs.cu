@@ -109,6 +109,8 @@ __global__ void k_pairs(PairParams p)
         const int kind = xs.kind;
         const R pref = (R)xs.s0 * (R)p.mass[h] * (R)p.dt[h];
         const R inv_w = kind == 1 ? R(1) / (R)xs.w : R(0);
+        const float4 qlo = p.nlo[leaf], qhi = p.nhi[leaf];
+        const float hmaxA = qlo.w;
         const V q = ((const V*)p.P4)[(int64_t)leaf * kLeaf + lane];
         qp[lane] = q;
         qv[lane] = ((const V*)p.V4)[(int64_t)leaf * kLeaf + lane];
@@ -125,12 +127,26 @@ __global__ void k_pairs(PairParams p)
                 const V pi = qp[il], vi = qv[il], pj = tp[t], vj = tv[t];
                 const R dx = sub_rn(pj.x, pi.x), dy = sub_rn(pj.y, pi.y), dz = sub_rn(pj.z, pi.z);
                 const R d2 = fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
-                const R lamv = lambda_lookup<R>(T, sqrt_rn(d2), pi.w, pj.w);
                 const R ux = vj.x - vi.x, uy = vj.y - vi.y, uz = vj.z - vi.z;
-                const R v = sqrt(ux * ux + uy * uy + uz * uz);
-                R sig = R(1);
-                if (kind == 1) { const R qq = v * inv_w; const R tt = R(1) + qq * qq; sig = R(1) / (tt * tt); }
-                const R P = pref * sig * v * lamv;
+                const R v2 = ux * ux + uy * uy + uz * uz;
+                R P;
+                if constexpr (sizeof(R) == 4) {
+                    // P needs ~1e-6 relative accuracy only (the event decision below is
+                    // exact for the P computed here): reciprocal square roots and
+                    // approximate divisions are enough.
+                    const float d = d2 > 0.f ? d2 * rsqrtf(d2) : 0.f;
+                    const float lamv = lambda_lookup_fast(T, d, pi.w, pj.w);
+                    const float v = v2 > 0.f ? v2 * rsqrtf(v2) : 0.f;
+                    float sig = 1.f;
+                    if (kind == 1) { const float qq = v * inv_w; const float tt = 1.f + qq * qq; sig = __fdividef(1.f, tt * tt); }
+                    P = pref * sig * v * lamv;
+                } else {
+                    const R lamv = lambda_lookup<R>(T, sqrt_rn(d2), pi.w, pj.w);
+                    const R v = sqrt(v2);
+                    R sig = R(1);
+                    if (kind == 1) { const R qq = v * inv_w; const R tt = R(1) + qq * qq; sig = R(1) / (tt * tt); }
+                    P = pref * sig * v * lamv;
+                }
                 const uint32_t ida = id_of<R>(vi.w), idb = id_of<R>(vj.w);
                 const uint32_t a = min(ida, idb), b = max(ida, idb);
                 const Philox4 x = philox4x32_10(p.step_lo, a, b, (uint32_t)h, p.seed_lo, p.seed_hi);
@@ -192,10 +208,22 @@ __global__ void k_pairs(PairParams p)
             tv[lane] = cv;
             __syncwarp();
             const int64_t ubB = hb + (int64_t)Bl * kLeaf;
-            n_tested += Bl > A ? (unsigned long long)(countA * countB) : (unsigned long long)(countA * (countA - 1) / 2);
-            for (int t = 0; t < countB; ++t) {
+            // candidates that cannot reach any query of A (box gap > h_t + hmax_A) are skipped
+            float3 pc;
+            if constexpr (sizeof(R) == 4) {
+                pc = make_float3(__fadd_rn(cA.x, c.x), __fadd_rn(cA.y, c.y), __fadd_rn(cA.z, c.z));
+            } else {
+                pc = make_float3(__double2float_rn((double)c.x - fr.O[0]), __double2float_rn((double)c.y - fr.O[1]),
+                                 __double2float_rn((double)c.z - fr.O[2]));
+            }
+            const float rc = __fadd_ru(__fmul_ru(__fadd_ru(to_float_ru_p<R>(c.w), hmaxA), 1.0f + 0x1p-20f), fr.margin);
+            uint32_t cmask = __ballot_sync(0xffffffffu, lane < countB && point_gap2_rd(pc, qlo, qhi) <= __fmul_ru(rc, rc));
+            while (cmask) {
+                const int t = __ffs(cmask) - 1;
+                cmask &= cmask - 1u;
                 bool ok = false;
                 if (mine && (Bl > A || t > lane)) {
+                    ++n_tested;
                     const V pj = tp[t];
                     const R dx = sub_rn(pj.x, q.x), dy = sub_rn(pj.y, q.y), dz = sub_rn(pj.z, q.z);
                     const R d2 = fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
@@ -282,6 +310,7 @@ __global__ void k_pairs(PairParams p)
     for (int o = 16; o > 0; o >>= 1) {
         n_gt1 += __shfl_xor_sync(0xffffffffu, n_gt1, o);
         n_near += __shfl_xor_sync(0xffffffffu, n_near, o);
+        n_tested += __shfl_xor_sync(0xffffffffu, n_tested, o);
     }
     if (lane == 0) {
         if (n_pairs) atomicAdd(&p.st->n_pairs, n_pairs);
@@ -313,11 +342,10 @@ int launch_t(sidm_ctx* c, uint64_t seed, uint64_t step, const sidm_xs* xs, const
     const int warps = c->pair_warps;
     const size_t smem = (size_t)warps * pair_warp_bytes<R, TMA>();
     auto kern = k_pairs<R, TMA>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_check(c, e, "pair smem attribute");
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, warps * 32, smem);
-    if (e != cudaSuccess) return cuda_check(c, e, "pair occupancy");
+    int rc = occupancy(c, (const void*)kern, warps * 32, smem, &occ);
+    if (rc) return rc;
+    cudaError_t e;
     if (occ < 1) return set_err(c, SIDM_ECAPACITY, "pair kernel does not fit on an SM");
     int grid = c->cfg.grid_ctas > 0 ? c->cfg.grid_ctas : c->sm_count * occ;
     grid = std::max(1, std::min(grid, (L.L + warps - 1) / warps));

@@ -29,6 +29,7 @@ array positions.
 from __future__ import annotations
 
 from dataclasses import dataclass, field
+import functools
 import math
 
 import numpy as np
@@ -144,16 +145,25 @@ def _sample_table(rng, n, r_grid, m_grid):
     return np.interp(u, m_grid, r_grid)
 
 
+@functools.lru_cache(maxsize=None)
+def _nfw_tables(r_cut: float):
+    """Inverse-CDF table and Jeans dispersion table of the NFW profile (cached)."""
+    r_grid = np.concatenate([[0.0], np.geomspace(1e-7, r_cut, 200001)])
+    m_grid = _nfw_mass(r_grid)
+    rho = lambda s: NFW_RHO_S / (s * (1.0 + s) ** 2)
+    mass = lambda s: float(_nfw_mass(np.array(s)))
+    r_sig = np.geomspace(1e-7, r_cut, 4001)
+    sig = _jeans_sigma(rho, mass, r_sig)
+    return r_grid, m_grid, r_sig, sig
+
+
 def nfw(n: int, seed: int, r_cut: float = 10.0) -> Halo:
     """NFW halo, r_s = 1, truncated at r_cut, total sampled mass rescaled to 1."""
     rng = np.random.default_rng(seed)
-    r_grid = np.concatenate([[0.0], np.geomspace(1e-7, r_cut, 200001)])
-    m_grid = _nfw_mass(r_grid)
+    r_grid, m_grid, r_sig, sig = _nfw_tables(float(r_cut))
     r = _sample_table(rng, n, r_grid, m_grid)
     r = np.maximum(r, 1e-7)
-    rho = lambda s: NFW_RHO_S / (s * (1.0 + s) ** 2)
-    mass = lambda s: float(_nfw_mass(np.array(s)))
-    sigma = _jeans_sigma(rho, mass, r)
+    sigma = np.exp(np.interp(np.log(r), np.log(r_sig), np.log(sig)))
     return _finish(rng, r, sigma, "nfw", {"r_cut": r_cut})
 
 

@@ -241,3 +241,38 @@ def test_bad_arguments_rejected():
     ctx.kernel_sizes([16, 32], h)
     assert ctx.status() == 0
     ctx.close()
+
+
+# ---------------------------------------------------------------- long runs
+def test_energy_drift_1000_steps_below_1e4():
+    # drift + full rebuild + kernel sizes + scatter every step, velocity-
+    # dependent cross-section; FP64 compensated totals every step
+    from paper_2506_06269_gb300 import sidm
+    h = ics.nfw(1 << 15, 41)
+    n = h.n
+    ctx = sidm.Context(n_max=n, halo_max=1, ngb_max=64, event_cap=1 << 16)
+    pos = torch.tensor(h.pos, device="cuda")
+    vel = torch.tensor(h.vel.astype(np.float32), device="cuda")
+    ids = torch.tensor(h.ids.astype(np.int64), device="cuda").to(torch.int32)
+    hh = torch.zeros(n, dtype=torch.float32, device="cuda")
+    xs = ctx.xs_tensor([(1, 100.0, 0.3811)]); dt = ctx.f64([2e-2]); mass = ctx.f64([h.mass])
+    E = torch.zeros((1001, 4), dtype=torch.float64, device="cuda")
+    ctx.build_cells([0, n], pos, vel, ids)
+    ctx.energy_momentum(mass, vel, E[0])
+    events = 0
+    for s in range(1000):
+        ctx.drift(dt, pos, vel)
+        ctx.build_cells([0, n], pos, vel, ids)
+        ctx.kernel_sizes([64], hh)
+        ctx.scatter_step(7, s, xs, dt, mass, vel)
+        ctx.energy_momentum(mass, vel, E[s + 1])
+        if s % 100 == 0:
+            events += ctx.stats().n_events
+    assert ctx.status() == 0
+    e = E[:, 0].cpu().numpy()
+    drift = np.max(np.abs(e - e[0])) / abs(e[0])
+    assert events > 50
+    assert drift < 1e-4, drift
+    p = E[:, 1:].cpu().numpy()
+    assert np.max(np.abs(p - p[0])) < 1e-5 * (h.mass * np.abs(h.vel).sum())
+    ctx.close()
