@@ -38,6 +38,7 @@ N_NGB = 64
 S0 = 100.0
 SEED_IC = 1
 TAU = 0.04
+DT_PROBE = 1e-6            # probe time step of the dt rule (sum_j P_ij / dt is dt-independent)
 METRIC = "SIDM particle-steps/s"
 UNIT = "particle-steps/s"
 WORKLOAD = "nfw_rcut10_N1048576_ngb64_veldep_s0_100_w_vmax"
@@ -60,6 +61,7 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--use-tma", type=int, default=0)
+    ap.add_argument("--no-batched", action="store_true")
     return ap.parse_args()
 
 
@@ -177,9 +179,11 @@ def dt_rule(ctx_cls, halo, vmax, device):
     h = torch.zeros(n, dtype=torch.float32, device=dev)
     c.build_cells([0, n], pos, vel, ids)
     c.kernel_sizes([N_NGB], h)
-    c.scatter_step(0, 0, c.xs_tensor([(1, S0, vmax)]), c.f64([1.0]), c.f64([halo.mass]), vel)
-    c.status()                        # event overflow is expected here (dt = 1)
-    sp = c.sum_p(n).cpu().numpy().astype(np.float64)
+    # sum_j P_ij / dt does not depend on dt: probe with a tiny dt so that
+    # (almost) no event fires
+    c.scatter_step(0, 0, c.xs_tensor([(1, S0, vmax)]), c.f64([DT_PROBE]), c.f64([halo.mass]), vel)
+    c.status()
+    sp = c.sum_p(n).cpu().numpy().astype(np.float64) / DT_PROBE
     c.close()
     q = float(np.quantile(sp, 0.999))
     return TAU / q, q
@@ -389,6 +393,116 @@ def cpu_baseline(dt, vmax, threads=None):
                       f"{sec:.2f} s", "seconds": sec, "pairs": int(r["stats"][0]["n_pairs"])}
 
 
+def run_batched(local, graph_steps=50, seq_steps=2):
+    """64 independent NFW halos in one persistent launch per kernel, 50 steps
+    captured in one CUDA graph, against 64 sequential single-halo contexts."""
+    import torch
+    from paper_2506_06269_gb300 import ics, sidm, tune
+    rng = np.random.default_rng(3)
+    H = 64
+    sizes = np.round(10.0 ** rng.uniform(4.0, math.log10(2e6), H)).astype(np.int64)
+    halos = [ics.nfw(int(sizes[h]), 3 * 1000 + h) for h in range(H)]
+    b = ics.batch(halos)
+    n = b.n
+    ks = [[16, 32, 64, 128][h % 4] for h in range(H)]
+    xs_list = [(0, 10.0, 1.0)] * H
+    dev = torch.device("cuda", local)
+    # Δt per halo by the same rule (q99.9 of sum_j P_ij/Δt on the initial state)
+    c = sidm.Context(n_max=n, halo_max=H, ngb_max=128, event_cap=16, device=local, flags=sidm.SIDM_FLAG_SUM_P)
+    pos = torch.tensor(b.pos, device=dev); vel = torch.tensor(b.vel.astype(np.float32), device=dev)
+    ids = torch.tensor(b.ids.astype(np.int64), device=dev).to(torch.int32)
+    hbuf = torch.zeros(n, dtype=torch.float32, device=dev)
+    c.build_cells(b.offsets, pos, vel, ids); c.kernel_sizes(ks, hbuf)
+    c.scatter_step(0, 0, c.xs_tensor(xs_list), c.f64([DT_PROBE] * H), c.f64(b.mass), vel)
+    c.status()
+    sp = c.sum_p(n).cpu().numpy().astype(np.float64) / DT_PROBE
+    c.close()
+    dts = [TAU / float(np.quantile(sp[b.offsets[h]:b.offsets[h + 1]], 0.999)) for h in range(H)]
+
+    def make_inputs(ctx):
+        return (torch.tensor(b.pos, device=dev), torch.tensor(b.vel.astype(np.float32), device=dev),
+                torch.tensor(b.ids.astype(np.int64), device=dev).to(torch.int32))
+
+    choice, table = tune.autotune(make_inputs, ks, xs_list, dts, b.mass, b.offsets)
+    ctx = sidm.Context(n_max=n, halo_max=H, ngb_max=128, event_cap=max(1 << 16, n // 8), device=local, **choice)
+    pos, vel, ids = make_inputs(ctx)
+    xs = ctx.xs_tensor(xs_list); dt_t = ctx.f64(dts); mass_t = ctx.f64(b.mass)
+    E = torch.zeros((graph_steps + 1, H, 4), dtype=torch.float64, device=dev)
+
+    def step(i, slot):
+        ctx.drift(dt_t, pos, vel)
+        ctx.build_cells(b.offsets, pos, vel, ids)
+        ctx.kernel_sizes(ks, hbuf)
+        ctx.scatter_step(777, i, xs, dt_t, mass_t, vel)
+        ctx.energy_momentum(mass_t, vel, E[slot])
+
+    ctx.build_cells(b.offsets, pos, vel, ids)
+    s = torch.cuda.Stream(device=dev)
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for i in range(2):                         # warm-up outside the graph
+            step(i, 0)
+        ctx.energy_momentum(mass_t, vel, E[0])
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    lc0 = ctx.launch_count()
+    with torch.cuda.graph(g, stream=s):
+        for i in range(graph_steps):
+            step(2 + i, i + 1)
+    per_step_launches = (ctx.launch_count() - lc0) / graph_steps   # kernels captured per step
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms_graph = e0.elapsed_time(e1)
+    status = ctx.status()
+    Eh = E[:, :, 0].cpu().numpy()
+    drift = float(np.max(np.abs(Eh[1:] - Eh[0]) / np.abs(Eh[0])))
+    ctx.close()
+    del g
+    # 64 sequential single-halo contexts, eager launches
+    ctxs = []
+    for hh, halo in enumerate(halos):
+        cc = sidm.Context(n_max=halo.n, halo_max=1, ngb_max=ks[hh], event_cap=max(4096, halo.n // 8), device=local,
+                          knn_warps=choice["knn_warps"], pair_warps=choice["pair_warps"], use_tma=choice["use_tma"])
+        t = (torch.tensor(halo.pos, device=dev), torch.tensor(halo.vel.astype(np.float32), device=dev),
+             torch.tensor(halo.ids.astype(np.int64), device=dev).to(torch.int32),
+             torch.zeros(halo.n, dtype=torch.float32, device=dev), cc.xs_tensor([xs_list[hh]]), cc.f64([dts[hh]]),
+             cc.f64([halo.mass]), torch.zeros(4, dtype=torch.float64, device=dev))
+        cc.build_cells([0, halo.n], t[0], t[1], t[2])
+        ctxs.append((cc, t, halo.n, ks[hh]))
+
+    def seq_step(i):
+        for cc, t, nh, kh in ctxs:
+            cc.drift(t[5], t[0], t[1])
+            cc.build_cells([0, nh], t[0], t[1], t[2])
+            cc.kernel_sizes([kh], t[3])
+            cc.scatter_step(777, i, t[4], t[5], t[6], t[1])
+            cc.energy_momentum(t[6], t[1], t[7])
+
+    seq_step(0)
+    torch.cuda.synchronize()
+    e0.record()
+    for i in range(seq_steps):
+        seq_step(1 + i)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1) / seq_steps
+    for cc, *_ in ctxs:
+        cc.close()
+    return {"workload": "64 NFW halos, N log-uniform in [1e4, 2e6] (seed 3), N_ngb 16/32/64/128 round-robin, "
+                        "sigma/m = 10, 50 steps in one CUDA graph",
+            "n_particles": int(n), "halos": H, "graph_steps": graph_steps,
+            "value": n * graph_steps / (ms_graph * 1e-3), "unit": UNIT, "ms_per_step": ms_graph / graph_steps,
+            "sequential_single_halo": {"value": n / (ms_seq * 1e-3), "ms_per_step": ms_seq},
+            "batched_over_sequential": (ms_seq) / (ms_graph / graph_steps),
+            "energy_drift_max_halo": drift, "device_status": status, "tuned": choice, "tuning": table,
+            "kernels_per_step_in_graph": per_step_launches,
+            "gpu_launches": int(round(per_step_launches * graph_steps))}
+
+
 def roofline(res, peaks, peak_src):
     """Roofline of the dominant hot kernel (by measured event time)."""
     kms, kcnt = res["kms"], res["kcnt"]
@@ -476,6 +590,10 @@ def main_ours(args):
         if fp64:
             line["fp64_form"] = fp64
             line["mixed_over_fp64"] = value / ws / fp64["value"]
+        if not args.no_batched:
+            line["batched"] = run_batched(res["local"])
+            if fp64:
+                line["batched_over_fp64_single_halo"] = line["batched"]["value"] / fp64["value"]
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline(res["dt"], res["vmax"])
         emit(line)
@@ -502,9 +620,9 @@ def main_reference(args):
     # dt of the same rule, evaluated on the oracle's own sample
     h, _, _ = O.knn(halo.pos, halo.ids, N_NGB, O.MODE_MIXED)
     vel = halo.vel.astype(np.float32).astype(np.float64)
-    _, _, sump = O.pairs(halo.pos, vel, halo.ids, h, O.MODE_MIXED, (1, S0, vmax), halo.mass, 1.0, 0, 0, 0,
-                         ev_cap=1 << 22)
-    dt = TAU / float(np.quantile(sump, 0.999))
+    _, _, sump = O.pairs(halo.pos, vel, halo.ids, h, O.MODE_MIXED, (1, S0, vmax), halo.mass, DT_PROBE, 0, 0, 0,
+                         ev_cap=1 << 16)
+    dt = TAU / float(np.quantile(sump / DT_PROBE, 0.999))
     pos = halo.pos.copy()
 
     def one(step_no):

@@ -168,25 +168,41 @@ __global__ void k_sort_hist(const unsigned long long* __restrict__ key, int64_t 
     hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = cnt[threadIdx.x];
 }
 
-// exclusive scan of hist[0..len) by one CTA of 1024 threads (contiguous segments)
-__global__ void k_sort_scan(uint32_t* __restrict__ hist, int64_t len)
+// exclusive scan of hist[0..len) in one CTA of 1024 threads: coalesced tiles
+// of 1024 entries, warp-shuffle scans, a running carry between tiles
+__global__ void __launch_bounds__(1024) k_sort_scan(uint32_t* __restrict__ hist, int64_t len)
 {
-    __shared__ uint32_t part[1024];
-    const int64_t seg = (len + 1023) / 1024;
-    const int64_t b = threadIdx.x * seg;
-    int64_t e = b + seg; if (e > len) e = len;
-    uint32_t sum = 0;
-    for (int64_t i = b; i < e; ++i) sum += hist[i];
-    part[threadIdx.x] = sum;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        uint32_t v = threadIdx.x >= o ? part[threadIdx.x - o] : 0u;
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t carry_sh;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t carry = 0;
+    for (int64_t base = 0; base < len; base += 1024) {
+        const int64_t i = base + threadIdx.x;
+        const uint32_t v = i < len ? hist[i] : 0u;
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
         __syncthreads();
-        part[threadIdx.x] += v;
+        if (warp == 0) {
+            const uint32_t w = wsum[lane];
+            uint32_t z = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
+                if (lane >= o) z += y;
+            }
+            wsum[lane] = z - w;                 // exclusive warp offsets
+            if (lane == 31) carry_sh = z;       // tile total
+        }
+        __syncthreads();
+        if (i < len) hist[i] = carry + wsum[warp] + x - v;
+        carry += carry_sh;
         __syncthreads();
     }
-    uint32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
-    for (int64_t i = b; i < e; ++i) { uint32_t v = hist[i]; hist[i] = run; run += v; }
 }
 
 // Scatter of one tile in 16 rounds of 256 consecutive keys; the rank of a key
