@@ -243,7 +243,7 @@ def run_ours(args):
     mass_t = ctx.f64([halo.mass])
     K, W = args.steps, args.warmup
     stats = torch.zeros((max(K, W, 1), sidm.STATS_DTYPE.itemsize), dtype=torch.uint8, device=dev)
-    energy = torch.zeros((max(K, 1) + 1, 4), dtype=torch.float64, device=dev)
+    energy = torch.zeros((max(K, W, 1) + 1, 4), dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     seed = 20250617 + rank
 

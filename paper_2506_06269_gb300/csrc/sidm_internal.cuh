@@ -202,11 +202,18 @@ __device__ __forceinline__ void lagrange4(R t, R w[4])
     w[3] = (t * t1 * t2) * (R(1) / R(6));
 }
 
+// Upper bound of the interpolated table value f = h_max^3 Lambda: the exact
+// overlap obeys Lambda <= W(0, h_max) and the largest tabulated value is
+// h^3 Lambda(0; h, h) = 0.9923; a 4 x 4-point Lagrange interpolant can exceed
+// the largest node value by at most the square of the cubic Lebesgue constant
+// (1.631^2 = 2.66), so no interpolated f exceeds 2.64 < 4.
+constexpr float kLamFUp = 4.0f;
+
 // Lambda(d; h_i, h_j) from the table f(x, rho) = h_max^3 Lambda,
 // x = d / (h_i + h_j), rho = h_min / h_max, Lagrange-bicubic on a
 // uniform 257 x 65 grid.
 template <class R>
-__device__ __forceinline__ R lambda_lookup(const R* __restrict__ T, R d, R hi, R hj)
+__device__ __forceinline__ R lambda_f(const R* __restrict__ T, R d, R hi, R hj)
 {
     const R hmax = hi > hj ? hi : hj;
     const R hmin = hi > hj ? hj : hi;
@@ -230,19 +237,26 @@ __device__ __forceinline__ R lambda_lookup(const R* __restrict__ T, R d, R hi, R
         const R s = wx[0] * __ldg(row) + wx[1] * __ldg(row + 1) + wx[2] * __ldg(row + 2) + wx[3] * __ldg(row + 3);
         f += wr[a] * s;
     }
-    const R inv = R(1) / hmax;
-    return f * inv * inv * inv;
+    return f;
 }
 
-// FP32 variant of lambda_lookup with approximate reciprocals (relative error
-// ~1e-7, far below the table's own 1e-6 of the peak).
-__device__ __forceinline__ float lambda_lookup_fast(const float* __restrict__ T, float d, float hi, float hj)
+// Lambda(d; h_i, h_j) = f(x, rho) / h_max^3.
+template <class R>
+__device__ __forceinline__ R lambda_lookup(const R* __restrict__ T, R d, R hi, R hj)
 {
-    const float hmax = fmaxf(hi, hj), hmin = fminf(hi, hj);
+    const R hmax = hi > hj ? hi : hj;
+    const R inv = R(1) / hmax;
+    return lambda_f<R>(T, d, hi, hj) * inv * inv * inv;
+}
+
+// FP32 interpolated f with approximate reciprocals (relative error ~1e-7,
+// far below the table's own 1e-6 of the peak); inv = 1/h_max from the caller.
+__device__ __forceinline__ float lambda_f_fast(const float* __restrict__ T, float d, float hi, float hj, float inv)
+{
+    const float hmin = fminf(hi, hj);
     float x = __fdividef(d, hi + hj);
     if (!(x < 1.f)) return 0.f;
     x = fmaxf(x, 0.f);
-    const float inv = __fdividef(1.f, hmax);
     const float rho = hmin * inv;
     const float gx = x * (float)(kLamNX - 1);
     int ix = (int)floorf(gx) - 1;
@@ -259,7 +273,13 @@ __device__ __forceinline__ float lambda_lookup_fast(const float* __restrict__ T,
         const float* row = T + (ir + a) * kLamNX + ix;
         f = fmaf(wr[a], wx[0] * __ldg(row) + wx[1] * __ldg(row + 1) + wx[2] * __ldg(row + 2) + wx[3] * __ldg(row + 3), f);
     }
-    return f * inv * inv * inv;
+    return f;
+}
+
+__device__ __forceinline__ float lambda_lookup_fast(const float* __restrict__ T, float d, float hi, float hj)
+{
+    const float inv = __fdividef(1.f, fmaxf(hi, hj));
+    return lambda_f_fast(T, d, hi, hj, inv) * inv * inv * inv;
 }
 
 // Lower bound of the squared distance from a point to a box (FP32, rounded down).

@@ -5,12 +5,17 @@
 // One warp per leaf of 32 consecutive Morton-ordered particles, one query per
 // lane.  Candidate leaves are staged through shared memory (plain coalesced
 // 128-bit loads, or bulk asynchronous copies with an mbarrier), shifted into
-// the query leaf's frame, and every lane keeps a max-heap of its N_ngb
-// smallest keys in shared memory.  The heap is first filled from the leaves
-// next to the query leaf in Morton order, whose k-th distance bounds the
-// search radius; the bounding-volume tree is then walked with that (shrinking)
-// radius, skipping those leaves.  The result is the exact k-th smallest of the
-// canonical distance, so it does not depend on tile order or launch shape.
+// the query leaf's frame, and every lane keeps a 4-ary max-heap of its N_ngb
+// smallest keys in shared memory (one 128-bit load per heap level).  The heap
+// is first filled from the leaves next to the query leaf in Morton order
+// (stored unsorted, then heapified once), whose k-th distance bounds the
+// search radius; the bounding-volume tree is then walked with that
+// (shrinking) radius, nearest children first, skipping those leaves.  Inside
+// a tile a lane only appends keys below its current bound to a short pending
+// list; the lists are merged into the heaps in batches, so the divergent heap
+// sift runs with every lane busy instead of once per candidate.  The result
+// is the exact k-th smallest of the canonical distance, so it does not depend
+// on tile order, flush points or launch shape.
 #include <type_traits>
 
 #include "sidm_internal.cuh"
@@ -46,10 +51,6 @@ struct KnnParams {
     int work_slot;
 };
 
-template <class K> __device__ __forceinline__ K key_max();
-template <> __device__ __forceinline__ uint32_t key_max<uint32_t>() { return 0xFFFFFFFFu; }
-template <> __device__ __forceinline__ unsigned long long key_max<unsigned long long>() { return ~0ull; }
-
 template <class R, bool NBR>
 __device__ __forceinline__ typename KeyOf<R, NBR>::T make_key(R d2, uint32_t id)
 {
@@ -70,51 +71,99 @@ __device__ __forceinline__ R key_d2(typename KeyOf<R, NBR>::T k)
     else return (R)__uint_as_float((uint32_t)k);
 }
 
-// replace the heap root (the largest of the k kept keys) by key and sift down
+// Per-lane 4-ary max-heaps of keys (all keys are >= 0 as unsigned integers).
+// Node t (0-based) sits at position t + 3, so the children 4t+1 .. 4t+4 of
+// node t fill the aligned group t + 1.  Group g of lane l is stored at
+// [g][l][0..3]: a lane reads all four children with one vector load and the
+// 32 lanes of a warp hit distinct banks.  Positions past the last node read
+// as 0, which never exceeds a key, so a missing child is never promoted.
 template <class K>
-__device__ __forceinline__ void heap_replace(K* heap, int lane, int k, K key)
-{
-    int pos = 0;
-    while (true) {
-        int c = 2 * pos + 1;
-        if (c >= k) break;
-        K cv = heap[c * 32 + lane];
-        if (c + 1 < k) {
-            K c2 = heap[(c + 1) * 32 + lane];
-            if (c2 > cv) { ++c; cv = c2; }
+struct Heap4 {
+    K* g;        // [groups][32][4]
+    int lane;
+    __device__ K& at(int t) const { const int pos = t + 3; return g[((pos >> 2) * 32 + lane) * 4 + (pos & 3)]; }
+    __device__ void children(int t, K c[4]) const
+    {
+        const K* src = g + ((t + 1) * 32 + lane) * 4;
+        if constexpr (sizeof(K) == 4) {
+            const uint4 v = *(const uint4*)src;
+            c[0] = v.x; c[1] = v.y; c[2] = v.z; c[3] = v.w;
+        } else {
+            const ulonglong2 a = *(const ulonglong2*)src, b = *(const ulonglong2*)(src + 2);
+            c[0] = a.x; c[1] = a.y; c[2] = b.x; c[3] = b.y;
         }
-        if (!(cv > key)) break;
-        heap[pos * 32 + lane] = cv;
-        pos = c;
     }
-    heap[pos * 32 + lane] = key;
-}
+    // zero the positions after node n-1 up to the end of its group
+    __device__ void clear_tail(int n) const
+    {
+        for (int pos = n + 3; pos <= ((n + 2) | 3); ++pos) g[((pos >> 2) * 32 + lane) * 4 + (pos & 3)] = K(0);
+    }
+    // sift key down from node t of a heap of n nodes
+    __device__ void sift(int t, int n, K key) const
+    {
+        while (4 * t + 1 < n) {
+            K c[4];
+            children(t, c);
+            K m = c[0];
+            int j = 0;
+            if (c[1] > m) { m = c[1]; j = 1; }
+            if (c[2] > m) { m = c[2]; j = 2; }
+            if (c[3] > m) { m = c[3]; j = 3; }
+            if (!(m > key)) break;
+            at(t) = m;
+            t = 4 * t + 1 + j;
+        }
+        at(t) = key;
+    }
+    // as sift, for a heap whose storage past node n-1 holds stale keys
+    __device__ void sift_masked(int t, int n, K key) const
+    {
+        while (4 * t + 1 < n) {
+            K c[4];
+            children(t, c);
+            if (4 * t + 2 >= n) c[1] = K(0);
+            if (4 * t + 3 >= n) c[2] = K(0);
+            if (4 * t + 4 >= n) c[3] = K(0);
+            K m = c[0];
+            int j = 0;
+            if (c[1] > m) { m = c[1]; j = 1; }
+            if (c[2] > m) { m = c[2]; j = 2; }
+            if (c[3] > m) { m = c[3]; j = 3; }
+            if (!(m > key)) break;
+            at(t) = m;
+            t = 4 * t + 1 + j;
+        }
+        at(t) = key;
+    }
+    __device__ void heapify(int n) const
+    {
+        for (int t = (n - 2) / 4; t >= 0; --t) sift(t, n, at(t));
+    }
+};
 
 template <class K>
-__device__ __forceinline__ void heap_sift(K* heap, int lane, int n)
-{
-    int pos = 0;
-    const K key = heap[lane];
-    while (true) {
-        int c = 2 * pos + 1;
-        if (c >= n) break;
-        K cv = heap[c * 32 + lane];
-        if (c + 1 < n) {
-            K c2 = heap[(c + 1) * 32 + lane];
-            if (c2 > cv) { ++c; cv = c2; }
-        }
-        if (!(cv > key)) break;
-        heap[pos * 32 + lane] = cv;
-        pos = c;
-    }
-    heap[pos * 32 + lane] = key;
-}
+__host__ __device__ constexpr int heap4_groups(int kcap) { return (kcap + 2) / 4 + 1; }
+
+// pending heap insertions per lane (a tile adds at most 32, so the lists are
+// merged whenever one holds more than kPend - 32 keys), and the pending count
+// at which the lists are merged before a tree node's tests
+constexpr int kPend = 48;
+constexpr int kFlushNode = 8;
 
 template <class R>
 __device__ __forceinline__ float to_float_ru(R v)
 {
     if constexpr (sizeof(R) == 8) return __double2float_ru((double)v);
     else return (float)v;
+}
+
+// shared memory of one warp: staged tile | ids | traversal stack | node boxes
+// (32 lo + 32 hi) | heap groups | pending keys
+template <class R, class K>
+__host__ __device__ constexpr size_t knn_warp_bytes_t(int kcap)
+{
+    return (TileStageT<R, false>::bytes() + 32 * 4 + kStack * 4 + 64 * 16 +
+            (size_t)heap4_groups<K>(kcap) * 32 * 4 * sizeof(K) + (size_t)kPend * 32 * sizeof(K) + 15) / 16 * 16;
 }
 
 template <class R, bool NBR, bool TMA>
@@ -124,12 +173,15 @@ __global__ void k_knn(KnnParams p)
     using K = typename KeyOf<R, NBR>::T;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const size_t per_warp = knn_warp_bytes<R, K>(p.kcap);
-    unsigned char* base = smem + wid * per_warp;
+    unsigned char* base = smem + wid * knn_warp_bytes_t<R, K>(p.kcap);
     TileStageT<R, TMA> stage(base);
     uint32_t* tids = (uint32_t*)(base + TileStageT<R, TMA>::bytes());
     int* stack = (int*)(tids + 32);
-    K* heap = (K*)(stack + kStack);
+    float4* blo = (float4*)(stack + kStack);       // [32] boxes of the children being tested
+    float4* bhi = blo + 32;
+    K* heapg = (K*)(bhi + 32);
+    K* pend = heapg + (size_t)heap4_groups<K>(p.kcap) * 32 * 4;   // [kPend][32]
+    const Heap4<K> hp{heapg, lane};
     stage.init(lane);
     unsigned long long n_cand = 0ull, n_ins = 0ull, n_tiles_all = 0ull, n_tiles_max = 0ull;
 
@@ -151,11 +203,25 @@ __global__ void k_knn(KnnParams p)
         const V q = ((const V*)p.P4)[(int64_t)leaf * kLeaf + lane];
         const float4 cA = p.cell[leaf];
         const float4 qlo = p.nlo[leaf], qhi = p.nhi[leaf];
-        const K kmax = key_max<K>();
-        for (int t = 0; t < k; ++t) heap[t * 32 + lane] = kmax;
-        K root = kmax;
+        hp.clear_tail(k);
+        K root = ~K(0);
+        int nfill = 0, np = 0;                         // heap fill level, pending keys
         bool failed = false;
         unsigned long long n_tiles = 0ull;
+
+        // merge the pending keys of every lane into its heap (each lane works
+        // on its own heap column; no lane reads another's)
+        auto flush = [&]() {
+            for (int i = 0; i < np; ++i) {
+                const K key = pend[i * 32 + lane];
+                if (key < root) {
+                    ++n_ins;
+                    hp.sift(0, k, key);
+                    root = hp.at(0);
+                }
+            }
+            np = 0;
+        };
 
         auto process = [&](int Bl, bool mine) {
             const int Bg = leaf0 + Bl;
@@ -177,16 +243,26 @@ __global__ void k_knn(KnnParams p)
             ++n_tiles;
             if (active && mine) {
                 n_cand += (unsigned long long)countB;
-                for (int t = 0; t < countB; ++t) {
-                    if (Bl == A && t == lane) continue;
-                    const V cj = sh[t];
-                    const R dx = sub_rn(cj.x, q.x), dy = sub_rn(cj.y, q.y), dz = sub_rn(cj.z, q.z);
-                    const R d2 = fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
-                    const K key = make_key<R, NBR>(d2, NBR ? tids[t] : 0u);
-                    if (key < root) {
-                        ++n_ins;
-                        heap_replace<K>(heap, lane, k, key);
-                        root = heap[lane];
+                if (nfill < k) {
+                    // window fill: the first k keys go into the heap array unsorted
+                    for (int t = 0; t < countB; ++t) {
+                        if (Bl == A && t == lane) continue;
+                        const V cj = sh[t];
+                        const R dx = sub_rn(cj.x, q.x), dy = sub_rn(cj.y, q.y), dz = sub_rn(cj.z, q.z);
+                        const R d2 = fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
+                        const K key = make_key<R, NBR>(d2, NBR ? tids[t] : 0u);
+                        if (nfill < k) hp.at(nfill++) = key;
+                        else pend[(np++) * 32 + lane] = key;
+                    }
+                } else {
+                    // at most 32 appends per tile: np stays below kPend
+#pragma unroll 4
+                    for (int t = 0; t < countB; ++t) {
+                        const V cj = sh[t];
+                        const R dx = sub_rn(cj.x, q.x), dy = sub_rn(cj.y, q.y), dz = sub_rn(cj.z, q.z);
+                        const R d2 = fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
+                        const K key = make_key<R, NBR>(d2, NBR ? tids[t] : 0u);
+                        if (key < root && !(Bl == A && t == lane)) pend[(np++) * 32 + lane] = key;
                     }
                 }
             }
@@ -201,6 +277,13 @@ __global__ void k_knn(KnnParams p)
             if (wcount < k + 1 && wlo > 0) { --wlo; wcount += kLeaf; }
         }
         for (int Bl = wlo; Bl <= whi; ++Bl) process(Bl, true);
+        // the window holds at least k other particles: heapify once, then merge
+        // the window's keys beyond the first k (fewer than kLeaf of them)
+        if (active && nfill == k) {
+            hp.heapify(k);
+            root = hp.at(0);
+        }
+        flush();
 
         // 2) tree walk.  A node is visited iff the query point of some lane lies
         //    within that lane's current k-th distance (+ margin) of the node's box;
@@ -218,21 +301,39 @@ __global__ void k_knn(KnnParams p)
             r = __fadd_ru(__fmul_ru(r, 1.0f + 0x1p-20f), fr.margin);
             return __fmul_ru(r, r);
         };
-        auto near = [&](int g, float r2) -> bool {
-            return r2 >= 0.f && point_gap2_rd(pq, p.nlo[g], p.nhi[g]) <= r2;
+        // boxes of nodes g0 .. g0+n-1 (n <= 32) into the warp's box buffer, one per lane
+        auto load_boxes = [&](int g0, int n) {
+            __syncwarp();
+            if (lane < n) { blo[lane] = p.nlo[g0 + lane]; bhi[lane] = p.nhi[g0 + lane]; }
+            __syncwarp();
         };
-        auto visit_leaf = [&](int Bl) {
-            const bool mine = near(leaf0 + Bl, my_r2());
-            if (__any_sync(0xffffffffu, mine)) process(Bl, mine);
+        // bit c: the query of some lane lies within its bound of box c
+        auto accept = [&](int n, float r2, uint32_t skip) -> uint32_t {
+            uint32_t bits = 0u;
+            if (r2 >= 0.f)
+                for (int c = 0; c < n; ++c)
+                    if (point_gap2_rd(pq, blo[c], bhi[c]) <= r2) bits |= 1u << c;
+            return __reduce_or_sync(0xffffffffu, bits) & ~skip;
         };
-        const int top = p.top[h];
-        const int32_t* loff = p.lvl_off;
-        const int Hp = p.H + 1;
-        // Accepted nodes are visited nearest first (box gap to the query leaf),
+        // leaves of the Morton window among local leaves first .. first+n-1
+        auto window_mask = [&](int first, int n) -> uint32_t {
+            const int lo = max(wlo - first, 0), hi = min(whi - first, n - 1);
+            if (lo > hi) return 0u;
+            return ((2u << hi) - 1u) & ~((1u << lo) - 1u);
+        };
+        auto visit_leaf = [&](int Bl, int c) {
+            const float r2 = my_r2();
+            const bool mine = r2 >= 0.f && point_gap2_rd(pq, blo[c], bhi[c]) <= r2;
+            if (__any_sync(0xffffffffu, mine)) {
+                if (__any_sync(0xffffffffu, np > kPend - kLeaf)) flush();   // room for one tile
+                process(Bl, mine);
+            }
+        };
+        // Accepted children are visited nearest first (box gap to the query leaf),
         // so the k-th bound shrinks early.  rank = position among the accepted.
-        auto order_rank = [&](uint32_t acc, int n, int g0) -> int {
+        auto order_rank = [&](uint32_t acc, int n) -> int {
             const bool mine_acc = lane < n && ((acc >> lane) & 1u);
-            const float pr = mine_acc ? box_gap2_rd(qlo, qhi, p.nlo[g0 + lane], p.nhi[g0 + lane]) : INFINITY;
+            const float pr = mine_acc ? box_gap2_rd(qlo, qhi, blo[lane], bhi[lane]) : INFINITY;
             int rank = 0;
             for (int j = 0; j < n; ++j) {
                 const float pj = __shfl_sync(0xffffffffu, pr, j);
@@ -240,16 +341,17 @@ __global__ void k_knn(KnnParams p)
             }
             return rank;
         };
-        auto visit_leaves_in_order = [&](uint32_t acc, int n, int first_local, int g0) {
-            const int rank = order_rank(acc, n, g0);
+        auto visit_leaves_in_order = [&](uint32_t acc, int n, int first_local) {
+            const int rank = order_rank(acc, n);
             const int cnt = __popc(acc);
             for (int r = 0; r < cnt; ++r) {
                 const uint32_t m = __ballot_sync(0xffffffffu, lane < n && ((acc >> lane) & 1u) && rank == r);
-                visit_leaf(first_local + __ffs(m) - 1);
+                const int c = __ffs(m) - 1;
+                visit_leaf(first_local + c, c);
             }
         };
-        auto push_in_order = [&](uint32_t acc, int n, int lev, int first_local, int g0, int& sp) -> bool {
-            const int rank = order_rank(acc, n, g0);
+        auto push_in_order = [&](uint32_t acc, int n, int lev, int first_local, int& sp) -> bool {
+            const int rank = order_rank(acc, n);
             const int cnt = __popc(acc);
             if (sp + cnt > kStack) return false;
             if (lane < n && ((acc >> lane) & 1u)) stack[sp + cnt - 1 - rank] = (lev << 24) | (first_local + lane);
@@ -257,18 +359,17 @@ __global__ void k_knn(KnnParams p)
             __syncwarp();
             return true;
         };
+        const int top = p.top[h];
+        const int32_t* loff = p.lvl_off;
+        const int Hp = p.H + 1;
         int sp = 0;
         {
             const int nb = loff[top * Hp + h];
             const int ntop = loff[top * Hp + h + 1] - nb;
-            const float r2 = my_r2();
-            uint32_t acc = 0u;
-            for (int c = 0; c < ntop; ++c) {
-                if (top == 0 && c >= wlo && c <= whi) continue;
-                if (__any_sync(0xffffffffu, near(nb + c, r2))) acc |= 1u << c;
-            }
-            if (top == 0) visit_leaves_in_order(acc, ntop, 0, nb);
-            else if (!push_in_order(acc, ntop, top, 0, nb, sp)) failed = true;
+            load_boxes(nb, ntop);
+            const uint32_t acc = accept(ntop, my_r2(), top == 0 ? window_mask(0, ntop) : 0u);
+            if (top == 0) visit_leaves_in_order(acc, ntop, 0);
+            else if (!push_in_order(acc, ntop, top, 0, sp)) failed = true;
         }
         while (sp > 0 && !failed) {
             const int e = stack[--sp];
@@ -279,15 +380,14 @@ __global__ void k_knn(KnnParams p)
             const int cc = loff[cl * Hp + h + 1] - cb;
             const int first = idx * 8;
             const int nch = min(8, cc - first);
-            const float r2 = my_r2();
-            uint32_t acc = 0u;
-            for (int c = 0; c < nch; ++c) {
-                if (cl == 0 && first + c >= wlo && first + c <= whi) continue;
-                if (__any_sync(0xffffffffu, near(cb + first + c, r2))) acc |= 1u << c;
-            }
-            if (cl == 0) visit_leaves_in_order(acc, nch, first, cb + first);
-            else if (!push_in_order(acc, nch, cl, first, cb + first, sp)) failed = true;
+            // tighten the bounds before the node tests once enough keys wait
+            if (__any_sync(0xffffffffu, np >= kFlushNode)) flush();
+            load_boxes(cb + first, nch);
+            const uint32_t acc = accept(nch, my_r2(), cl == 0 ? window_mask(first, nch) : 0u);
+            if (cl == 0) visit_leaves_in_order(acc, nch, first);
+            else if (!push_in_order(acc, nch, cl, first, sp)) failed = true;
         }
+        flush();
         if (failed && lane == 0) raise_status(p.cnt, SIDM_DEV_STACK);
         n_tiles_all += n_tiles;
         n_tiles_max = n_tiles > n_tiles_max ? n_tiles : n_tiles_max;
@@ -301,13 +401,14 @@ __global__ void k_knn(KnnParams p)
                 ((R*)((V*)p.P4 + (int64_t)leaf * kLeaf + lane))[3] = hval;
             }
             if constexpr (NBR) {
-                for (int end = k - 1; end > 0; --end) {       // heap sort: ascending keys
-                    const K t0 = heap[lane];
-                    heap[lane] = heap[end * 32 + lane];
-                    heap[end * 32 + lane] = t0;
-                    heap_sift<K>(heap, lane, end);
+                // heap sort: repeatedly move the maximum behind the shrinking heap
+                for (int end = k - 1; end > 0; --end) {
+                    const K top_key = hp.at(0);
+                    const K last = hp.at(end);
+                    hp.at(end) = top_key;
+                    hp.sift_masked(0, end, last);
                 }
-                for (int t = 0; t < k; ++t) p.nbr[u * p.k_stride + t] = (uint32_t)(heap[t * 32 + lane] & 0xFFFFFFFFull);
+                for (int t = 0; t < k; ++t) p.nbr[u * p.k_stride + t] = (uint32_t)(hp.at(t) & 0xFFFFFFFFull);
             }
         }
         __syncwarp();
@@ -339,7 +440,7 @@ int launch_t(sidm_ctx* c, void* h_out, uint32_t* nbr, int k_stride, cudaStream_t
     p.h_out = h_out; p.nbr = nbr; p.k_stride = k_stride; p.kcap = c->kmax_cur; p.cnt = c->d_cnt;
     p.work_slot = 0;
     const int warps = c->knn_warps;
-    const size_t smem = (size_t)warps * knn_warp_bytes<R, K>(p.kcap);
+    const size_t smem = (size_t)warps * knn_warp_bytes_t<R, K>(p.kcap);
     auto kern = k_knn<R, NBR, TMA>;
     int occ = 0;
     int rc = occupancy(c, (const void*)kern, warps * 32, smem, &occ);

@@ -12,8 +12,10 @@
 // One warp per query leaf A; the tree walk visits leaves B >= A whose boxes
 // are within h_max(A) + h_max(B), so each unordered pair is tested once, in
 // the frame of the lower leaf.  The in-range test runs on a 32 x 32 block;
-// in-range pairs are compacted into a per-warp queue so that the expensive
-// part (Lambda table, sigma, Philox) runs on full warps.
+// in-range pairs are compacted into a per-warp queue of (slot i, slot j, d^2)
+// that persists across candidate leaves, so the expensive part (sigma,
+// Philox, Lambda) runs on full warps.  The Lambda table is read only for the
+// pairs whose draw falls below an upper bound of P (see k_pairs).
 #include "sidm_internal.cuh"
 #include "sidm_tile.cuh"
 
@@ -62,15 +64,22 @@ __device__ __forceinline__ float to_float_ru_p(R v)
     else return (float)v;
 }
 
+// per warp: staged candidate leaf, queue of in-range pairs (slot i, slot j,
+// d^2), traversal stack
 template <class R, bool TMA>
 constexpr size_t pair_warp_bytes()
 {
-    using V = typename Vec4<R>::T;
-    return (TileStageT<R, TMA>::bytes() * 2 + 2 * 32 * sizeof(V) + kQueue * 2 + kStack * 4 + 15) / 16 * 16;
+    return (TileStageT<R, TMA>::bytes() + kQueue * (8 + sizeof(R)) + kStack * 4 + 15) / 16 * 16;
 }
 
-template <class R, bool TMA>
-__global__ void k_pairs(PairParams p)
+// EXACT: form P (and so Lambda) for every in-range pair (per-particle sums of
+// P requested).  Otherwise Lambda is looked up only when the draw lies below
+// an upper bound of P: P_up uses kLamFUp in place of the interpolated table
+// value, and since FP32/FP64 products round monotonically P <= P_up for the P
+// that would have been formed, so a draw u >= P_up + 2e-6 decides "no event"
+// and "not within 1e-6 of P" exactly as the full evaluation would.
+template <class R, bool TMA, bool EXACT>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParams p)
 {
     using V = typename Vec4<R>::T;
     using Stage = TileStageT<R, TMA>;
@@ -78,17 +87,17 @@ __global__ void k_pairs(PairParams p)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned char* base = smem + wid * pair_warp_bytes<R, TMA>();
     Stage st_pos(base);
-    Stage st_vel(base + Stage::bytes());
-    V* qp = (V*)(base + 2 * Stage::bytes());
-    V* qv = qp + 32;
-    uint16_t* queue = (uint16_t*)(qv + 32);
-    int* stack = (int*)(queue + kQueue);
+    uint32_t* q_si = (uint32_t*)(base + Stage::bytes());
+    uint32_t* q_sj = q_si + kQueue;
+    R* q_d2 = (R*)(q_sj + kQueue);
+    int* stack = (int*)(q_d2 + kQueue);
     st_pos.init(lane);
-    st_vel.init(lane);
     const R* __restrict__ T = (const R*)p.lam;
+    const V* __restrict__ P4 = (const V*)p.P4;
+    const V* __restrict__ V4 = (const V*)p.V4;
     const uint32_t lt = (1u << lane) - 1u;
 
-    unsigned long long n_pairs = 0ull, n_gt1 = 0ull, n_near = 0ull, n_tested = 0ull;
+    unsigned long long n_pairs = 0ull, n_gt1 = 0ull, n_near = 0ull, n_tested = 0ull, n_lam = 0ull;
     unsigned long long n_tiles_all = 0ull, n_tiles_max = 0ull;
 
     while (true) {
@@ -100,6 +109,7 @@ __global__ void k_pairs(PairParams p)
         const int leaf0 = p.leaf_off[h];
         const int64_t hb = p.halo_off[h];
         const int64_t nh = p.halo_off[h + 1] - hb;
+        const int64_t slot2u = hb - (int64_t)leaf0 * kLeaf;   // padded slot -> particle index
         const int A = leaf - leaf0;
         const int countA = (int)min((int64_t)kLeaf, nh - (int64_t)A * kLeaf);
         const bool active = lane < countA;
@@ -111,61 +121,74 @@ __global__ void k_pairs(PairParams p)
         const R inv_w = kind == 1 ? R(1) / (R)xs.w : R(0);
         const float4 qlo = p.nlo[leaf], qhi = p.nhi[leaf];
         const float hmaxA = qlo.w;
-        const V q = ((const V*)p.P4)[(int64_t)leaf * kLeaf + lane];
-        qp[lane] = q;
-        qv[lane] = ((const V*)p.V4)[(int64_t)leaf * kLeaf + lane];
-        __syncwarp();
+        const uint32_t slotA = (uint32_t)leaf * kLeaf + lane;
+        const V q = P4[slotA];
         int qhead = 0, qn = 0;
         unsigned long long n_tiles = 0ull;
 
         // P, draw and event for queue entries qhead .. qhead+nb-1 (one per lane)
-        auto run_batch = [&](int nb, int64_t ubB, const V* tp, const V* tv) {
+        auto run_batch = [&](int nb) {
             __syncwarp();
             if (lane < nb) {
-                const uint16_t e = queue[(qhead + lane) & (kQueue - 1)];
-                const int il = e >> 8, t = e & 0xFF;
-                const V pi = qp[il], vi = qv[il], pj = tp[t], vj = tv[t];
-                const R dx = sub_rn(pj.x, pi.x), dy = sub_rn(pj.y, pi.y), dz = sub_rn(pj.z, pi.z);
-                const R d2 = fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
+                const int e = (qhead + lane) & (kQueue - 1);
+                const uint32_t si = q_si[e], sj = q_sj[e];
+                const R d2 = q_d2[e];
+                const V vi = V4[si], vj = V4[sj];
+                const R hi = ((const R*)(P4 + si))[3], hj = ((const R*)(P4 + sj))[3];
                 const R ux = vj.x - vi.x, uy = vj.y - vi.y, uz = vj.z - vi.z;
                 const R v2 = ux * ux + uy * uy + uz * uz;
-                R P;
+                const uint32_t ida = id_of<R>(vi.w), idb = id_of<R>(vj.w);
+                const uint32_t a = min(ida, idb), b = max(ida, idb);
+                const Philox4 x = philox4x32_10(p.step_lo, a, b, (uint32_t)h, p.seed_lo, p.seed_hi);
+                R P, pre, inv, u;
+                bool need;
                 if constexpr (sizeof(R) == 4) {
                     // P needs ~1e-6 relative accuracy only (the event decision below is
                     // exact for the P computed here): reciprocal square roots and
                     // approximate divisions are enough.
-                    const float d = d2 > 0.f ? d2 * rsqrtf(d2) : 0.f;
-                    const float lamv = lambda_lookup_fast(T, d, pi.w, pj.w);
                     const float v = v2 > 0.f ? v2 * rsqrtf(v2) : 0.f;
                     float sig = 1.f;
                     if (kind == 1) { const float qq = v * inv_w; const float tt = 1.f + qq * qq; sig = __fdividef(1.f, tt * tt); }
-                    P = pref * sig * v * lamv;
+                    pre = pref * sig * v;
+                    inv = __fdividef(1.f, fmaxf(hi, hj));
+                    u = (R)((float)x.x[0] * 0x1p-32f);
                 } else {
-                    const R lamv = lambda_lookup<R>(T, sqrt_rn(d2), pi.w, pj.w);
                     const R v = sqrt(v2);
                     R sig = R(1);
                     if (kind == 1) { const R qq = v * inv_w; const R tt = R(1) + qq * qq; sig = R(1) / (tt * tt); }
-                    P = pref * sig * v * lamv;
-                }
-                const uint32_t ida = id_of<R>(vi.w), idb = id_of<R>(vj.w);
-                const uint32_t a = min(ida, idb), b = max(ida, idb);
-                const Philox4 x = philox4x32_10(p.step_lo, a, b, (uint32_t)h, p.seed_lo, p.seed_hi);
-                bool fire;
-                R u;
-                if constexpr (sizeof(R) == 4) {
-                    u = (R)((float)x.x[0] * 0x1p-32f);
-                    fire = P >= R(1) || x.x[0] < (uint32_t)ceilf((float)P * 0x1p32f);
-                } else {
+                    pre = pref * sig * v;
+                    inv = R(1) / (hi > hj ? hi : hj);
                     u = (R)ldexp((double)x.x[0], -32);
-                    fire = u < P;
                 }
-                if (P > R(1)) ++n_gt1;
-                if (fabs(P - u) < R(1e-6)) ++n_near;
-                const int64_t ui = hb + (int64_t)A * kLeaf + il;
-                const int64_t uj = ubB + t;
-                if (p.use_sump) {
-                    atomicAdd(p.sump + ui, (float)P);
-                    atomicAdd(p.sump + uj, (float)P);
+                if constexpr (EXACT) {
+                    need = true;
+                } else {
+                    const R P_up = pre * (R(kLamFUp) * inv * inv * inv);
+                    need = !(u >= P_up + R(2e-6));
+                }
+                P = R(0);
+                bool fire = false;
+                if (need) {
+                    ++n_lam;
+                    R f;
+                    if constexpr (sizeof(R) == 4) {
+                        const float d = d2 > 0.f ? d2 * rsqrtf(d2) : 0.f;
+                        f = lambda_f_fast(T, d, hi, hj, inv);
+                    } else {
+                        f = lambda_f<R>(T, sqrt_rn(d2), hi, hj);
+                    }
+                    P = pre * (f * inv * inv * inv);
+                    if constexpr (sizeof(R) == 4) fire = P >= R(1) || x.x[0] < (uint32_t)ceilf((float)P * 0x1p32f);
+                    else fire = u < P;
+                    if (P > R(1)) ++n_gt1;
+                    if (fabs(P - u) < R(1e-6)) ++n_near;
+                }
+                const int64_t ui = slot2u + si, uj = slot2u + sj;
+                if constexpr (EXACT) {
+                    if (p.use_sump) {
+                        atomicAdd(p.sump + ui, (float)P);
+                        atomicAdd(p.sump + uj, (float)P);
+                    }
                 }
                 if (fire) {
                     const unsigned long long slot = atomicAdd(&p.cnt->ev_count, 1ull);
@@ -191,8 +214,7 @@ __global__ void k_pairs(PairParams p)
             const int Bg = leaf0 + Bl;
             ++n_tiles;
             const int countB = (int)min((int64_t)kLeaf, nh - (int64_t)Bl * kLeaf);
-            const V* rp = st_pos.load((const V*)p.P4 + (int64_t)Bg * kLeaf, lane, p.cnt);
-            const V* rv = st_vel.load((const V*)p.V4 + (int64_t)Bg * kLeaf, lane, p.cnt);
+            const V* rp = st_pos.load(P4 + (int64_t)Bg * kLeaf, lane, p.cnt);
             V c = rp[lane];
             if constexpr (sizeof(R) == 4) {
                 const float4 cB = p.cell[Bg];
@@ -200,14 +222,11 @@ __global__ void k_pairs(PairParams p)
                 c.y = __fadd_rn(c.y, __fsub_rn(cB.y, cA.y));
                 c.z = __fadd_rn(c.z, __fsub_rn(cB.z, cA.z));
             }
-            const V cv = rv[lane];
             __syncwarp();
             V* tp = st_pos.shifted();
-            V* tv = st_vel.shifted();
             tp[lane] = c;
-            tv[lane] = cv;
             __syncwarp();
-            const int64_t ubB = hb + (int64_t)Bl * kLeaf;
+            const uint32_t slotB = (uint32_t)Bg * kLeaf;
             // candidates that cannot reach any query of A (box gap > h_t + hmax_A) are skipped
             float3 pc;
             if constexpr (sizeof(R) == 4) {
@@ -222,22 +241,27 @@ __global__ void k_pairs(PairParams p)
                 const int t = __ffs(cmask) - 1;
                 cmask &= cmask - 1u;
                 bool ok = false;
+                R d2 = R(0);
                 if (mine && (Bl > A || t > lane)) {
                     ++n_tested;
                     const V pj = tp[t];
                     const R dx = sub_rn(pj.x, q.x), dy = sub_rn(pj.y, q.y), dz = sub_rn(pj.z, q.z);
-                    const R d2 = fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
+                    d2 = fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
                     const R hs = add_rn(q.w, pj.w);
                     ok = d2 < mul_rn(hs, hs);
                 }
                 const uint32_t m = __ballot_sync(0xffffffffu, ok);
-                if (ok) queue[(qhead + qn + __popc(m & lt)) & (kQueue - 1)] = (uint16_t)((lane << 8) | t);
+                if (ok) {
+                    const int e = (qhead + qn + __popc(m & lt)) & (kQueue - 1);
+                    q_si[e] = slotA;
+                    q_sj[e] = slotB + t;
+                    q_d2[e] = d2;
+                }
                 const int c2 = __popc(m);
                 qn += c2;
                 n_pairs += (unsigned long long)c2;
-                if (qn >= 32) run_batch(32, ubB, tp, tv);
+                if (qn >= 32) run_batch(32);
             }
-            if (qn > 0) run_batch(qn, ubB, tp, tv);
             __syncwarp();
         };
 
@@ -302,6 +326,9 @@ __global__ void k_pairs(PairParams p)
                 if ((acc >> c) & 1u) { if (lane == 0) stack[sp] = (cl << 24) | (first + c); ++sp; }
             __syncwarp();
         }
+        // the queue outlives the staged tiles (entries are slots), so one partial
+        // batch per query leaf remains
+        if (qn > 0) run_batch(qn);
         if (failed && lane == 0) raise_status(p.cnt, SIDM_DEV_STACK);
         n_tiles_all += n_tiles;
         n_tiles_max = n_tiles > n_tiles_max ? n_tiles : n_tiles_max;
@@ -311,6 +338,7 @@ __global__ void k_pairs(PairParams p)
         n_gt1 += __shfl_xor_sync(0xffffffffu, n_gt1, o);
         n_near += __shfl_xor_sync(0xffffffffu, n_near, o);
         n_tested += __shfl_xor_sync(0xffffffffu, n_tested, o);
+        n_lam += __shfl_xor_sync(0xffffffffu, n_lam, o);
     }
     if (lane == 0) {
         if (n_pairs) atomicAdd(&p.st->n_pairs, n_pairs);
@@ -319,12 +347,12 @@ __global__ void k_pairs(PairParams p)
         if (n_tested) atomicAdd(&p.st->n_tested, n_tested);
         atomicAdd(&p.cnt->diag[4], n_tiles_all);
         atomicMax(&p.cnt->diag[5], n_tiles_max);
+        if (n_lam) atomicAdd(&p.cnt->diag[6], n_lam);
     }
     st_pos.finish(lane, p.cnt);
-    st_vel.finish(lane, p.cnt);
 }
 
-template <class R, bool TMA>
+template <class R, bool TMA, bool EXACT>
 int launch_t(sidm_ctx* c, uint64_t seed, uint64_t step, const sidm_xs* xs, const double* dt, const double* mass,
              sidm_step_stats* st, cudaStream_t s)
 {
@@ -341,7 +369,7 @@ int launch_t(sidm_ctx* c, uint64_t seed, uint64_t step, const sidm_xs* xs, const
     p.cnt = c->d_cnt; p.st = st;
     const int warps = c->pair_warps;
     const size_t smem = (size_t)warps * pair_warp_bytes<R, TMA>();
-    auto kern = k_pairs<R, TMA>;
+    auto kern = k_pairs<R, TMA, EXACT>;
     int occ = 0;
     int rc = occupancy(c, (const void*)kern, warps * 32, smem, &occ);
     if (rc) return rc;
@@ -368,11 +396,15 @@ int launch_pairs(sidm_ctx* c, uint64_t seed, uint64_t step, const sidm_xs* xs, c
 {
     if (c->lay.L == 0) return SIDM_OK;
     const bool tma = c->cfg.use_tma != 0;
-    if (c->cfg.precision == SIDM_FP64)
-        return tma ? launch_t<double, true>(c, seed, step, xs, dt, mass, st, s)
-                   : launch_t<double, false>(c, seed, step, xs, dt, mass, st, s);
-    return tma ? launch_t<float, true>(c, seed, step, xs, dt, mass, st, s)
-               : launch_t<float, false>(c, seed, step, xs, dt, mass, st, s);
+    const bool exact = (c->cfg.flags & SIDM_FLAG_SUM_P) != 0;
+#define SIDM_PAIRS_DISPATCH(R)                                                                   \
+    if (exact) return tma ? launch_t<R, true, true>(c, seed, step, xs, dt, mass, st, s)          \
+                          : launch_t<R, false, true>(c, seed, step, xs, dt, mass, st, s);        \
+    return tma ? launch_t<R, true, false>(c, seed, step, xs, dt, mass, st, s)                    \
+               : launch_t<R, false, false>(c, seed, step, xs, dt, mass, st, s);
+    if (c->cfg.precision == SIDM_FP64) { SIDM_PAIRS_DISPATCH(double) }
+    SIDM_PAIRS_DISPATCH(float)
+#undef SIDM_PAIRS_DISPATCH
 }
 
 }  // namespace sidm

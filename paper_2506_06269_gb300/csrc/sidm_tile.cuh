@@ -110,13 +110,4 @@ struct TileStageT {
 template <class R>
 using TileStage = TileStageT<R, false>;
 
-constexpr int kPend = 8;   // deferred heap insertions per lane in the kernel-size kernel
-
-template <class R, class K>
-__host__ __device__ constexpr size_t knn_warp_bytes(int kcap)
-{
-    return (TileStageT<R, false>::bytes() + 32 * 4 + kStack * 4 + ((size_t)kcap + kPend) * 32 * sizeof(K) + 15) /
-           16 * 16;
-}
-
 }  // namespace sidm
