@@ -47,7 +47,8 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 N_SM, LANES_PER_SM = 152, 128
 # algorithmic lane operations per unit of the two ALU-bound kernels (derived in the design doc)
 OPS_PER_TEST = 10          # canonical d^2 (3 sub, 1 mul, 2 fma), sum, square, compare, ballot
-OPS_PER_PAIR = 170         # d^2 + sqrt + Lambda table + |v_ij| + sigma(v) + P + Philox4x32-10 + draw
+OPS_PER_PAIR = 121         # |v_ij| + sigma(v) + Philox4x32-10 + upper bound of P + draw decision + bookkeeping
+OPS_PER_LAMBDA = 50        # sqrt(d^2) + Lambda table (bicubic, 16 loads) + P + exact decision, when looked up
 OPS_PER_KNN_CAND = 8       # canonical d^2 (6) + key compare (2)
 
 
@@ -275,6 +276,16 @@ def run_ours(args):
     kms, kcnt = ctx.kernel_times(reset=True)
     diag = ctx.diagnostics(reset=True)
     status = ctx.status()
+    # the kernel-size search from scratch (no previous h), same particles
+    ctx.warm_start(False)
+    ctx.build_cells(off, pos, vel, ids)
+    for _ in range(3):
+        ctx.kernel_sizes([N_NGB], h)
+    torch.cuda.synchronize()
+    kms_cold, kcnt_cold = ctx.kernel_times(reset=True)
+    ctx.diagnostics(reset=True)
+    ctx.warm_start(True)
+    knn_cold_ms = float(kms_cold[1] / max(kcnt_cold[1], 1))
     total_ms = max_over_ranks(float(sum(times)), dev) if ws > 1 else float(sum(times))
     st = [sidm.parse_stats(stats[i]) for i in range(K)]
     E = energy.cpu().numpy()
@@ -290,7 +301,7 @@ def run_ours(args):
         "clocks": clocks, "gpu_launches": gpu_launches, "kms": kms, "kcnt": kcnt, "status": status,
         "drift": drift, "book": book, "n_pairs": n_pairs, "n_tested": n_tested, "n_events": n_events,
         "stats": st, "ws": ws, "rank": rank, "local": local, "tensors": (pos, vel, ids, h, xs, dt_t, mass_t),
-        "step": step, "seed": seed, "diag": diag,
+        "step": step, "seed": seed, "diag": diag, "knn_cold_ms": knn_cold_ms,
         "knn_candidates_per_step": float(diag[1]) / max(K, 1),
     }
     return res
@@ -305,10 +316,11 @@ def run_e2e(res, steps):
     halo = res["halo"]
     n = halo.n
     pos, vel, ids, h, xs, dt_t, mass_t = res["tensors"]
-    hp = torch.tensor(halo.pos).pin_memory()
-    hv = torch.tensor(halo.vel.astype(np.float32)).pin_memory()
-    hi = torch.tensor(halo.ids.astype(np.int64)).to(torch.int32).pin_memory()
-    out_v = torch.empty_like(hv).pin_memory()
+    # the particle state lives on the host: every step uploads it, runs the
+    # pass and downloads the evolved (reordered) state and the energy
+    hp = torch.tensor(pos.cpu().numpy()).pin_memory()
+    hv = torch.tensor(vel.cpu().numpy()).pin_memory()
+    hi = torch.tensor(ids.cpu().numpy()).pin_memory()
     out_e = torch.empty((steps, 4), dtype=torch.float64).pin_memory()
     energy = torch.zeros(4, dtype=torch.float64, device=ctx.device)
     s = torch.cuda.current_stream()
@@ -324,13 +336,15 @@ def run_e2e(res, steps):
         ctx.kernel_sizes([N_NGB], h)
         ctx.scatter_step(res["seed"], 10_000 + i, xs, dt_t, mass_t, vel)
         ctx.energy_momentum(mass_t, vel, energy)
-        out_v.copy_(vel, non_blocking=True)
+        hp.copy_(pos, non_blocking=True)
+        hv.copy_(vel, non_blocking=True)
+        hi.copy_(ids, non_blocking=True)
         out_e[i].copy_(energy, non_blocking=True)
     e1.record(s)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     h2d = hp.numel() * 8 + hv.numel() * 4 + hi.numel() * 4
-    d2h = out_v.numel() * 4 + 4 * 8
+    d2h = hp.numel() * 8 + hv.numel() * 4 + hi.numel() * 4 + 4 * 8
     return {"value": n * steps / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "steps": steps}
 
@@ -517,14 +531,15 @@ def roofline(res, peaks, peak_src):
     per_launch_ms = kms[dom] / launches
     n = res["halo"].n
     if name == "pairs":
-        ops = (res["n_tested"] * OPS_PER_TEST + res["n_pairs"] * OPS_PER_PAIR) / K
+        ops = (res["n_tested"] * OPS_PER_TEST + res["n_pairs"] * OPS_PER_PAIR + res["diag"][6] * OPS_PER_LAMBDA) / K
         achieved = ops / (per_launch_ms * 1e-3) / 1e12
         tr = traffic.get("pairs")
         return {"kernel": "k_pairs", "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
                 "frac": achieved / alu_peak, "traffic": (tr["bytes_per_launch"] * n / tr["units_per_launch"]) if tr else None,
                 "peak_source": f"derived: {N_SM} SMs x {LANES_PER_SM} FP32/INT32 lanes x {clock_mhz:.0f} MHz "
                                f"({peak_src} sm_max_mhz)",
-                "ops_per_unit": {"candidate_test": OPS_PER_TEST, "pair_eval": OPS_PER_PAIR},
+                "ops_per_unit": {"candidate_test": OPS_PER_TEST, "pair_eval": OPS_PER_PAIR,
+                                 "lambda_lookup": OPS_PER_LAMBDA},
                 "ms_per_launch": per_launch_ms}
     if name == "knn":
         cand = res.get("knn_candidates_per_step")
@@ -585,7 +600,13 @@ def main_ours(args):
             "work_per_step": {"knn_tiles": float(res["diag"][0]) / K, "knn_candidates": float(res["diag"][1]) / K,
                               "knn_heap_inserts": float(res["diag"][2]) / K, "knn_max_tiles_one_leaf": int(res["diag"][3]),
                               "pair_tiles": float(res["diag"][4]) / K, "pair_max_tiles_one_leaf": int(res["diag"][5]),
-                              "pair_tests": res["n_tested"] / K, "pair_evals": res["n_pairs"] / K},
+                              "pair_tests": res["n_tested"] / K, "pair_evals": res["n_pairs"] / K,
+                              "pair_lambda_lookups": float(res["diag"][6]) / K,
+                              "knn_redone_cold": float(res["diag"][7]) / K},
+            "knn_warm_start": {"ms_per_launch_warm": kms[1] / K, "ms_per_launch_cold": res["knn_cold_ms"],
+                               "note": "kernel sizes start from the previous step's h (bound 1.0625 h_prev); "
+                                       "particles with fewer than N_ngb candidates inside are redone cold; "
+                                       "results bit-identical to the cold search"},
         }
         if fp64:
             line["fp64_form"] = fp64

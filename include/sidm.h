@@ -244,8 +244,26 @@ int sidm_kernel_times(sidm_ctx* ctx, double* ms_out, int64_t* count_out, int32_t
  * kernel, out[1] lane-level candidate distances, out[2] heap insertions,
  * out[3] largest number of leaves staged for one query leaf, out[4] candidate
  * leaves staged by the pair kernel, out[5] its largest per query leaf,
- * out[6..7] reserved.  reset != 0 clears them afterwards. */
+ * out[6] in-range pairs whose Lambda was looked up (all of them under
+ * SIDM_FLAG_SUM_P; otherwise only those whose draw fell below the upper bound
+ * of P), out[7] particles whose warm-started kernel-size search found fewer
+ * than N_ngb candidates inside the guessed bound and was redone cold.
+ * reset != 0 clears them afterwards. */
 int sidm_diagnostics(sidm_ctx* ctx, uint64_t* out, int32_t reset);
+
+/* Warm start of the kernel-size search (enabled by default).  When enabled,
+ * sidm_build_cells seeds every particle's search with its kernel size from the
+ * last sidm_kernel_sizes call (carried through the permutation, so the
+ * caller's arrays must still be in the order that call left them, with the
+ * same halo layout and N_ngb).  The search then only admits candidates within
+ * 1.0625 times that size; a particle with fewer than N_ngb of them is redone
+ * from scratch in the same launch.  The result is the exact k-th distance in
+ * every case -- a stale or wrong guess costs time, never accuracy -- so this
+ * is the usual SPH practice of starting from the previous smoothing length
+ * (Sect. 2: h follows the N_ngb nearest neighbours as particles move).
+ *   enable : 0 disables it (every search starts cold), non-zero enables it
+ * Host-only; takes effect at the next sidm_build_cells. */
+int sidm_warm_start(sidm_ctx* ctx, int32_t enable);
 
 
 /* ---- allocation-free variant -------------------------------------------- */

@@ -277,7 +277,8 @@ __global__ void k_gather(int64_t N, int H, const int64_t* __restrict__ halo_off,
                          const uint32_t* __restrict__ sval, const double* __restrict__ pos, const R* __restrict__ vel,
                          const uint32_t* __restrict__ id, double* __restrict__ tpos, R* __restrict__ tvel,
                          uint32_t* __restrict__ tid, uint32_t* __restrict__ perm,
-                         typename Vec4<R>::T* __restrict__ P4, uint32_t* __restrict__ ID, DevCounters* cnt)
+                         typename Vec4<R>::T* __restrict__ P4, uint32_t* __restrict__ ID, DevCounters* cnt,
+                         const R* __restrict__ hprev)
 {
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t src = sval[s];
@@ -308,7 +309,7 @@ __global__ void k_gather(int64_t N, int H, const int64_t* __restrict__ halo_off,
         } else {
             p.x = (R)x[0]; p.y = (R)x[1]; p.z = (R)x[2];
         }
-        p.w = R(0);
+        p.w = hprev ? hprev[src] : R(0);   // previous kernel size: a guess for the search
         P4[slot] = p;
     }
 }
@@ -839,7 +840,7 @@ static void free_all(sidm_ctx* c)
                     c->d_chunk_halo, c->d_chunk_begin, c->d_frame, c->d_key, c->d_key2, c->d_val, c->d_val2,
                     c->d_hist, c->d_P4, c->d_V4, c->d_ID, c->d_cell, c->d_nlo, c->d_nhi, c->d_perm, c->d_tmp_pos,
                     c->d_tmp_vel, c->d_tmp_id, c->d_claim, c->d_hits, c->d_done, c->d_ev, c->d_sump,
-                    c->d_stats_own, c->d_cnt, c->d_epart, c->d_lam};
+                    c->d_stats_own, c->d_cnt, c->d_epart, c->d_lam, c->d_hprev};
     for (void* p : ptrs) if (p) cudaFree(p);
     if (c->d_stage) cudaFreeHost(c->d_stage);
     for (cudaEvent_t e : c->t_ev) if (e) cudaEventDestroy(e);
@@ -916,6 +917,7 @@ extern "C" int sidm_create(sidm_ctx** out, const sidm_config* cfg)
     ALLOC(c->d_nlo, c->node_cap);
     ALLOC(c->d_nhi, c->node_cap);
     ALLOC(c->d_perm, N);
+    e = cudaMalloc(&c->d_hprev, (size_t)N * rs); if (e != cudaSuccess) return fail("cudaMalloc hprev", e);
     ALLOC(c->d_tmp_pos, 3 * N);
     e = cudaMalloc(&c->d_tmp_vel, (size_t)3 * N * rs); if (e != cudaSuccess) return fail("cudaMalloc tmp_vel", e);
     ALLOC(c->d_tmp_id, N);
@@ -1078,14 +1080,19 @@ static int build_impl(sidm_ctx* c, double* pos, R* vel, uint32_t* id, cudaStream
                                                                   c->d_leaf_halo, c->d_cell));
     const bool mixed = c->cfg.precision == SIDM_MIXED;
     using V = typename Vec4<R>::T;
+    // the last kernel sizes, in the order the caller's arrays had after that
+    // call, seed the next search (only a guess: the search stays exact)
+    const R* hprev = (c->warm_enabled && c->hprev_valid) ? (const R*)c->d_hprev : nullptr;
+    c->guess_in_p4 = hprev != nullptr;
+    c->hprev_valid = false;
     if (mixed)
         SIDM_LAUNCH(c, (k_gather<R, true><<<grid_for(c, N, 256), 256, 0, s>>>(
             N, H, c->d_halo_off, c->d_halo_pad, c->d_leaf_off, c->d_frame, c->d_cell, ka, va, pos, vel, id,
-            c->d_tmp_pos, (R*)c->d_tmp_vel, c->d_tmp_id, c->d_perm, (V*)c->d_P4, c->d_ID, c->d_cnt)));
+            c->d_tmp_pos, (R*)c->d_tmp_vel, c->d_tmp_id, c->d_perm, (V*)c->d_P4, c->d_ID, c->d_cnt, hprev)));
     else
         SIDM_LAUNCH(c, (k_gather<R, false><<<grid_for(c, N, 256), 256, 0, s>>>(
             N, H, c->d_halo_off, c->d_halo_pad, c->d_leaf_off, c->d_frame, c->d_cell, ka, va, pos, vel, id,
-            c->d_tmp_pos, (R*)c->d_tmp_vel, c->d_tmp_id, c->d_perm, (V*)c->d_P4, c->d_ID, c->d_cnt)));
+            c->d_tmp_pos, (R*)c->d_tmp_vel, c->d_tmp_id, c->d_perm, (V*)c->d_P4, c->d_ID, c->d_cnt, hprev)));
     SIDM_CUDA(c, cudaMemcpyAsync(pos, c->d_tmp_pos, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s));
     SIDM_CUDA(c, cudaMemcpyAsync(vel, c->d_tmp_vel, sizeof(R) * 3 * N, cudaMemcpyDeviceToDevice, s));
     SIDM_CUDA(c, cudaMemcpyAsync(id, c->d_tmp_id, sizeof(uint32_t) * N, cudaMemcpyDeviceToDevice, s));
@@ -1118,6 +1125,7 @@ extern "C" int sidm_build_cells(sidm_ctx* c, int32_t n_halos, const int64_t* hal
         c->lay = L;
         c->has_layout = true;
         c->built = c->sized = false;
+        c->hprev_valid = false;
         if ((rc = upload_layout(c, s))) { c->has_layout = false; return rc; }
     }
     const int tb = timer_begin(c, 0, s);
@@ -1155,8 +1163,12 @@ extern "C" int sidm_kernel_sizes(sidm_ctx* c, const int32_t* n_ngb, void* h_dev,
     }
     c->kmax_cur = kmax;
     if (L.N == 0) { c->sized = true; return SIDM_OK; }
-    int rc = launch_knn(c, h_dev, nullptr, 0, s);
+    const bool use_guess = c->guess_in_p4 && c->ngb_prev == c->ngb_host;
+    c->guess_in_p4 = false;
+    int rc = launch_knn(c, h_dev, nullptr, 0, use_guess, s);
     if (rc) return rc;
+    c->hprev_valid = true;
+    c->ngb_prev = c->ngb_host;
     if (c->cfg.precision == SIDM_FP64)
         SIDM_LAUNCH(c, k_leaf_hmax<double><<<(L.L * 32 + 255) / 256, 256, 0, s>>>(L.L, L.H, c->d_leaf_halo, c->d_leaf_off,
                                                                                  c->d_halo_off, (const double4*)c->d_P4, c->d_nlo));
@@ -1181,7 +1193,7 @@ extern "C" int sidm_neighbours(sidm_ctx* c, const int32_t* n_ngb, int32_t k_stri
         if (c->lay.halo_off[h + 1] > c->lay.halo_off[h] && (n_ngb[h] != c->ngb_host[h] || n_ngb[h] > k_stride))
             return set_err(c, SIDM_EINVAL, "n_ngb must match the kernel-size pass and fit k_stride");
     SIDM_CUDA(c, ensure_device(c));
-    return launch_knn(c, nullptr, nbr, k_stride, s);
+    return launch_knn(c, nullptr, nbr, k_stride, false, s);
 }
 
 extern "C" int sidm_scatter_step(sidm_ctx* c, uint64_t seed, uint64_t step, const sidm_xs* xs, const double* dt,
@@ -1340,6 +1352,14 @@ extern "C" int sidm_kernel_times(sidm_ctx* c, double* ms, int64_t* count, int32_
         if (count) count[c->t_slot[i]] += 1;
     }
     if (reset) c->t_used = 0;
+    return SIDM_OK;
+}
+
+extern "C" int sidm_warm_start(sidm_ctx* c, int32_t enable)
+{
+    if (!c) return SIDM_EINVAL;
+    c->warm_enabled = enable != 0;
+    if (!c->warm_enabled) c->hprev_valid = false;
     return SIDM_OK;
 }
 

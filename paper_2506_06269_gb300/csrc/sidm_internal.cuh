@@ -75,6 +75,15 @@ struct sidm_ctx {
     std::vector<int32_t> ngb_host;               // cached N_ngb (uploaded when changed)
     int kmax_cur = 0;
 
+    // warm start of the kernel-size search: the last h per particle (in the
+    // order of the caller's arrays after that call), and whether the next
+    // build may seed P4.w with it / the last build did
+    void* d_hprev = nullptr;           // f32|f64 [N]
+    bool warm_enabled = true;
+    bool hprev_valid = false;
+    bool guess_in_p4 = false;
+    std::vector<int32_t> ngb_prev;     // N_ngb of the call that wrote d_hprev
+
     // layout arrays (device)
     int64_t* d_halo_off = nullptr;     // [H+1]
     int64_t* d_halo_pad = nullptr;     // [H+1]
@@ -158,7 +167,7 @@ cudaError_t ensure_device(sidm_ctx* c);
 int occupancy(sidm_ctx* c, const void* fn, int threads, size_t smem, int* occ);
 
 // kernel entry points implemented in the other translation units
-int launch_knn(sidm_ctx* c, void* h_out, uint32_t* nbr, int k_stride, cudaStream_t s);
+int launch_knn(sidm_ctx* c, void* h_out, uint32_t* nbr, int k_stride, bool use_guess, cudaStream_t s);
 int launch_pairs(sidm_ctx* c, uint64_t seed, uint64_t step, const sidm_xs* xs, const double* dt,
                  const double* mass, sidm_step_stats* st, cudaStream_t s);
 

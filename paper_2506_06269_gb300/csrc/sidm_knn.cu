@@ -49,6 +49,9 @@ struct KnnParams {
     int kcap;
     DevCounters* cnt;
     int work_slot;
+    void* hprev;        // out: h per particle (next call's guess), NULL for neighbour lists
+    int use_guess;      // P4.w holds each particle's previous kernel size
+    float slack;        // guess bound = previous h * slack
 };
 
 template <class R, bool NBR>
@@ -149,6 +152,8 @@ __host__ __device__ constexpr int heap4_groups(int kcap) { return (kcap + 2) / 4
 // at which the lists are merged before a tree node's tests
 constexpr int kPend = 48;
 constexpr int kFlushNode = 8;
+// warm start: the search bound is the previous kernel size times this factor
+constexpr float kGuessSlack = 1.0625f;
 
 template <class R>
 __device__ __forceinline__ float to_float_ru(R v)
@@ -183,7 +188,7 @@ __global__ void k_knn(KnnParams p)
     K* pend = heapg + (size_t)heap4_groups<K>(p.kcap) * 32 * 4;   // [kPend][32]
     const Heap4<K> hp{heapg, lane};
     stage.init(lane);
-    unsigned long long n_cand = 0ull, n_ins = 0ull, n_tiles_all = 0ull, n_tiles_max = 0ull;
+    unsigned long long n_cand = 0ull, n_ins = 0ull, n_tiles_all = 0ull, n_tiles_max = 0ull, n_redo = 0ull;
 
     while (true) {
         int leaf = 0;
@@ -203,11 +208,34 @@ __global__ void k_knn(KnnParams p)
         const V q = ((const V*)p.P4)[(int64_t)leaf * kLeaf + lane];
         const float4 cA = p.cell[leaf];
         const float4 qlo = p.nlo[leaf], qhi = p.nhi[leaf];
+        unsigned long long n_tiles = 0ull;
+        bool failed = false;
+        // Warm start: q.w holds the particle's kernel size of the previous call.
+        // Pass 0 fills the heap with k copies of the key of (h_prev * slack)^2, so
+        // only candidates inside that bound enter; a lane that ends with a copy
+        // still in its heap had fewer than k such candidates and is redone by
+        // the cold pass 1 (Morton-window fill, unbounded start).
+        const bool guess = p.use_guess && active && q.w > R(0);
+        K sentinel = ~K(0);
+        if (guess) {
+            R r;
+            if constexpr (sizeof(R) == 4) r = __fmul_ru((float)q.w, p.slack);
+            else r = __dmul_ru((double)q.w, (double)p.slack);
+            sentinel = make_key<R, NBR>(mul_ru(r, r), 0xFFFFFFFFu);
+        }
+        K result = K(0);
+        bool todo = active;
+        for (int pass = __any_sync(0xffffffffu, guess) ? 0 : 1; pass < 2; ++pass) {
+        const bool act = pass == 0 ? guess : todo;
+        if (!__any_sync(0xffffffffu, act)) break;
         hp.clear_tail(k);
         K root = ~K(0);
         int nfill = 0, np = 0;                         // heap fill level, pending keys
-        bool failed = false;
-        unsigned long long n_tiles = 0ull;
+        if (pass == 0 && act) {
+            for (int t = 0; t < k; ++t) hp.at(t) = sentinel;
+            root = sentinel;
+            nfill = k;
+        }
 
         // merge the pending keys of every lane into its heap (each lane works
         // on its own heap column; no lane reads another's)
@@ -241,7 +269,7 @@ __global__ void k_knn(KnnParams p)
             if (NBR) tids[lane] = p.ID[(int64_t)Bg * kLeaf + lane];
             __syncwarp();
             ++n_tiles;
-            if (active && mine) {
+            if (act && mine) {
                 n_cand += (unsigned long long)countB;
                 if (nfill < k) {
                     // window fill: the first k keys go into the heap array unsorted
@@ -269,21 +297,24 @@ __global__ void k_knn(KnnParams p)
             __syncwarp();
         };
 
-        // 1) Morton-window leaves around A holding at least k+1 particles
-        int wlo = A, whi = A;
-        int64_t wcount = countA;
-        while (wcount < k + 1 && (wlo > 0 || whi < nleaf - 1)) {
-            if (whi < nleaf - 1) { ++whi; wcount += min((int64_t)kLeaf, nh - (int64_t)whi * kLeaf); }
-            if (wcount < k + 1 && wlo > 0) { --wlo; wcount += kLeaf; }
+        // 1) cold pass: Morton-window leaves around A holding at least k+1 particles
+        int wlo = 0, whi = -1;
+        if (pass == 1) {
+            wlo = A; whi = A;
+            int64_t wcount = countA;
+            while (wcount < k + 1 && (wlo > 0 || whi < nleaf - 1)) {
+                if (whi < nleaf - 1) { ++whi; wcount += min((int64_t)kLeaf, nh - (int64_t)whi * kLeaf); }
+                if (wcount < k + 1 && wlo > 0) { --wlo; wcount += kLeaf; }
+            }
+            for (int Bl = wlo; Bl <= whi; ++Bl) process(Bl, true);
+            // the window holds at least k other particles: heapify once, then merge
+            // the window's keys beyond the first k (fewer than kLeaf of them)
+            if (act && nfill == k) {
+                hp.heapify(k);
+                root = hp.at(0);
+            }
+            flush();
         }
-        for (int Bl = wlo; Bl <= whi; ++Bl) process(Bl, true);
-        // the window holds at least k other particles: heapify once, then merge
-        // the window's keys beyond the first k (fewer than kLeaf of them)
-        if (active && nfill == k) {
-            hp.heapify(k);
-            root = hp.at(0);
-        }
-        flush();
 
         // 2) tree walk.  A node is visited iff the query point of some lane lies
         //    within that lane's current k-th distance (+ margin) of the node's box;
@@ -296,7 +327,7 @@ __global__ void k_knn(KnnParams p)
                              __double2float_rn((double)q.z - fr.O[2]));
         }
         auto my_r2 = [&]() -> float {
-            if (!active) return -1.0f;
+            if (!act) return -1.0f;
             float r = to_float_ru<R>(sqrt_ru(key_d2<R, NBR>(root)));
             r = __fadd_ru(__fmul_ru(r, 1.0f + 0x1p-20f), fr.margin);
             return __fmul_ru(r, r);
@@ -388,6 +419,9 @@ __global__ void k_knn(KnnParams p)
             else if (!push_in_order(acc, nch, cl, first, sp)) failed = true;
         }
         flush();
+        if (act && (pass == 1 || root != sentinel)) { result = root; todo = false; }
+        if (pass == 0 && act && todo) ++n_redo;
+        }   // passes
         if (failed && lane == 0) raise_status(p.cnt, SIDM_DEV_STACK);
         n_tiles_all += n_tiles;
         n_tiles_max = n_tiles > n_tiles_max ? n_tiles : n_tiles_max;
@@ -395,10 +429,11 @@ __global__ void k_knn(KnnParams p)
         // 3) outputs
         if (active) {
             const int64_t u = hb + (int64_t)A * kLeaf + lane;
-            const R hval = sqrt_rn(key_d2<R, NBR>(root));
+            const R hval = sqrt_rn(key_d2<R, NBR>(result));
             if (p.h_out) {
                 ((R*)p.h_out)[u] = hval;
                 ((R*)((V*)p.P4 + (int64_t)leaf * kLeaf + lane))[3] = hval;
+                if (p.hprev) ((R*)p.hprev)[u] = hval;
             }
             if constexpr (NBR) {
                 // heap sort: repeatedly move the maximum behind the shrinking heap
@@ -417,18 +452,20 @@ __global__ void k_knn(KnnParams p)
     for (int o = 16; o > 0; o >>= 1) {
         n_cand += __shfl_xor_sync(0xffffffffu, n_cand, o);
         n_ins += __shfl_xor_sync(0xffffffffu, n_ins, o);
+        n_redo += __shfl_xor_sync(0xffffffffu, n_redo, o);
     }
     if (lane == 0) {
         atomicAdd(&p.cnt->diag[0], n_tiles_all);
         atomicAdd(&p.cnt->diag[1], n_cand);
         atomicAdd(&p.cnt->diag[2], n_ins);
         atomicMax(&p.cnt->diag[3], n_tiles_max);
+        if (n_redo) atomicAdd(&p.cnt->diag[7], n_redo);
     }
     stage.finish(lane, p.cnt);
 }
 
 template <class R, bool NBR, bool TMA>
-int launch_t(sidm_ctx* c, void* h_out, uint32_t* nbr, int k_stride, cudaStream_t s)
+int launch_t(sidm_ctx* c, void* h_out, uint32_t* nbr, int k_stride, bool use_guess, cudaStream_t s)
 {
     using K = typename KeyOf<R, NBR>::T;
     KnnParams p;
@@ -439,6 +476,9 @@ int launch_t(sidm_ctx* c, void* h_out, uint32_t* nbr, int k_stride, cudaStream_t
     p.cell = c->d_cell; p.nlo = c->d_nlo; p.nhi = c->d_nhi; p.P4 = c->d_P4; p.ID = c->d_ID;
     p.h_out = h_out; p.nbr = nbr; p.k_stride = k_stride; p.kcap = c->kmax_cur; p.cnt = c->d_cnt;
     p.work_slot = 0;
+    p.hprev = NBR ? nullptr : c->d_hprev;
+    p.use_guess = use_guess ? 1 : 0;
+    p.slack = kGuessSlack;
     const int warps = c->knn_warps;
     const size_t smem = (size_t)warps * knn_warp_bytes_t<R, K>(p.kcap);
     auto kern = k_knn<R, NBR, TMA>;
@@ -463,19 +503,19 @@ int launch_t(sidm_ctx* c, void* h_out, uint32_t* nbr, int k_stride, cudaStream_t
 
 }  // namespace
 
-int launch_knn(sidm_ctx* c, void* h_out, uint32_t* nbr, int k_stride, cudaStream_t s)
+int launch_knn(sidm_ctx* c, void* h_out, uint32_t* nbr, int k_stride, bool use_guess, cudaStream_t s)
 {
     if (c->lay.L == 0) return SIDM_OK;
     const bool tma = c->cfg.use_tma != 0;
     if (c->cfg.precision == SIDM_FP64) {
         if (nbr) return set_err(c, SIDM_EINVAL, "neighbour lists: mixed form only");
-        return tma ? launch_t<double, false, true>(c, h_out, nullptr, 0, s)
-                   : launch_t<double, false, false>(c, h_out, nullptr, 0, s);
+        return tma ? launch_t<double, false, true>(c, h_out, nullptr, 0, use_guess, s)
+                   : launch_t<double, false, false>(c, h_out, nullptr, 0, use_guess, s);
     }
-    if (nbr) return tma ? launch_t<float, true, true>(c, nullptr, nbr, k_stride, s)
-                        : launch_t<float, true, false>(c, nullptr, nbr, k_stride, s);
-    return tma ? launch_t<float, false, true>(c, h_out, nullptr, 0, s)
-               : launch_t<float, false, false>(c, h_out, nullptr, 0, s);
+    if (nbr) return tma ? launch_t<float, true, true>(c, nullptr, nbr, k_stride, false, s)
+                        : launch_t<float, true, false>(c, nullptr, nbr, k_stride, false, s);
+    return tma ? launch_t<float, false, true>(c, h_out, nullptr, 0, use_guess, s)
+               : launch_t<float, false, false>(c, h_out, nullptr, 0, use_guess, s);
 }
 
 }  // namespace sidm

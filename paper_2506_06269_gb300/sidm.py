@@ -77,11 +77,12 @@ def load_library():
     L.sidm_launch_count.argtypes = [vp]; L.sidm_launch_count.restype = i64
     L.sidm_kernel_times.argtypes = [vp, vp, vp, i32]
     L.sidm_diagnostics.argtypes = [vp, vp, i32]
+    L.sidm_warm_start.argtypes = [vp, i32]
     L.sidm_energy_momentum_static.argtypes = [i32, vp, i32, vp, vp, vp, vp, vp]
     for f in ("sidm_create", "sidm_destroy", "sidm_build_cells", "sidm_kernel_sizes", "sidm_scatter_step",
               "sidm_energy_momentum", "sidm_status", "sidm_get_perm", "sidm_neighbours", "sidm_get_events",
               "sidm_lambda_eval", "sidm_drift", "sidm_get_sum_p", "sidm_kernel_times", "sidm_diagnostics",
-              "sidm_energy_momentum_static"):
+              "sidm_energy_momentum_static", "sidm_warm_start"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -90,7 +91,8 @@ def load_library():
 EXPORTED = ["sidm_create", "sidm_destroy", "sidm_last_error", "sidm_create_error", "sidm_build_cells",
             "sidm_kernel_sizes", "sidm_scatter_step", "sidm_energy_momentum", "sidm_status", "sidm_get_perm",
             "sidm_neighbours", "sidm_get_events", "sidm_lambda_eval", "sidm_drift", "sidm_get_sum_p",
-            "sidm_launch_count", "sidm_kernel_times", "sidm_diagnostics", "sidm_energy_momentum_static"]
+            "sidm_launch_count", "sidm_kernel_times", "sidm_diagnostics", "sidm_energy_momentum_static",
+            "sidm_warm_start"]
 
 
 def _torch():
@@ -199,6 +201,11 @@ def sidm_energy_momentum_static(halo_off, precision, mass, vel, out, comp=None, 
     if rc != SIDM_OK:
         raise SidmError(rc, {SIDM_EINVAL: "bad argument", SIDM_ECAPACITY: "more chunks than the static scratch holds",
                              SIDM_ECUDA: "CUDA call failed"}.get(rc, "error"))
+
+
+def sidm_warm_start(ctx, enable=True):
+    """Enable/disable seeding the kernel-size search with the last kernel sizes."""
+    _check(ctx, load_library().sidm_warm_start(ctx, 1 if enable else 0))
 
 
 def sidm_diagnostics(ctx, reset=True):
@@ -334,3 +341,6 @@ class Context:
 
     def diagnostics(self, reset=True):
         return sidm_diagnostics(self.handle, reset)
+
+    def warm_start(self, enable=True):
+        sidm_warm_start(self.handle, enable)
