@@ -211,17 +211,18 @@ __global__ void k_knn(KnnParams p)
         unsigned long long n_tiles = 0ull;
         bool failed = false;
         // Warm start: q.w holds the particle's kernel size of the previous call.
-        // Pass 0 fills the heap with k copies of the key of (h_prev * slack)^2, so
-        // only candidates inside that bound enter; a lane that ends with a copy
-        // still in its heap had fewer than k such candidates and is redone by
-        // the cold pass 1 (Morton-window fill, unbounded start).
+        // Pass 0 starts with the bound key of (h_prev * slack)^2, so only
+        // candidates inside that bound enter; a lane that collects fewer than k
+        // of them is redone by the cold pass 1 (Morton-window fill, unbounded
+        // start).  In both passes the first k admitted keys are stored unsorted
+        // and heapified once.
         const bool guess = p.use_guess && active && q.w > R(0);
-        K sentinel = ~K(0);
+        K bound_key = ~K(0);
         if (guess) {
             R r;
             if constexpr (sizeof(R) == 4) r = __fmul_ru((float)q.w, p.slack);
             else r = __dmul_ru((double)q.w, (double)p.slack);
-            sentinel = make_key<R, NBR>(mul_ru(r, r), 0xFFFFFFFFu);
+            bound_key = make_key<R, NBR>(mul_ru(r, r), 0xFFFFFFFFu);
         }
         K result = K(0);
         bool todo = active;
@@ -229,17 +230,18 @@ __global__ void k_knn(KnnParams p)
         const bool act = pass == 0 ? guess : todo;
         if (!__any_sync(0xffffffffu, act)) break;
         hp.clear_tail(k);
-        K root = ~K(0);
+        K root = (pass == 0 && act) ? bound_key : ~K(0);
         int nfill = 0, np = 0;                         // heap fill level, pending keys
-        if (pass == 0 && act) {
-            for (int t = 0; t < k; ++t) hp.at(t) = sentinel;
-            root = sentinel;
-            nfill = k;
-        }
+        bool heaped = false;
 
         // merge the pending keys of every lane into its heap (each lane works
         // on its own heap column; no lane reads another's)
         auto flush = [&]() {
+            if (!heaped && nfill == k) {               // the heap array is full: order it once
+                hp.heapify(k);
+                root = hp.at(0);
+                heaped = true;
+            }
             for (int i = 0; i < np; ++i) {
                 const K key = pend[i * 32 + lane];
                 if (key < root) {
@@ -272,15 +274,18 @@ __global__ void k_knn(KnnParams p)
             if (act && mine) {
                 n_cand += (unsigned long long)countB;
                 if (nfill < k) {
-                    // window fill: the first k keys go into the heap array unsorted
+                    // fill: the first k admitted keys go into the heap array unsorted
+                    // (heapified at the next merge; later keys wait in the pending list)
+#pragma unroll 4
                     for (int t = 0; t < countB; ++t) {
-                        if (Bl == A && t == lane) continue;
                         const V cj = sh[t];
                         const R dx = sub_rn(cj.x, q.x), dy = sub_rn(cj.y, q.y), dz = sub_rn(cj.z, q.z);
                         const R d2 = fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
                         const K key = make_key<R, NBR>(d2, NBR ? tids[t] : 0u);
-                        if (nfill < k) hp.at(nfill++) = key;
-                        else pend[(np++) * 32 + lane] = key;
+                        if (key < root && !(Bl == A && t == lane)) {
+                            if (nfill < k) hp.at(nfill++) = key;
+                            else pend[(np++) * 32 + lane] = key;
+                        }
                     }
                 } else {
                     // at most 32 appends per tile: np stays below kPend
@@ -306,13 +311,9 @@ __global__ void k_knn(KnnParams p)
                 if (whi < nleaf - 1) { ++whi; wcount += min((int64_t)kLeaf, nh - (int64_t)whi * kLeaf); }
                 if (wcount < k + 1 && wlo > 0) { --wlo; wcount += kLeaf; }
             }
+            // the window holds at least k other particles, so every lane's heap is
+            // full after it: order it and merge the window's keys beyond the first k
             for (int Bl = wlo; Bl <= whi; ++Bl) process(Bl, true);
-            // the window holds at least k other particles: heapify once, then merge
-            // the window's keys beyond the first k (fewer than kLeaf of them)
-            if (act && nfill == k) {
-                hp.heapify(k);
-                root = hp.at(0);
-            }
             flush();
         }
 
@@ -419,7 +420,7 @@ __global__ void k_knn(KnnParams p)
             else if (!push_in_order(acc, nch, cl, first, sp)) failed = true;
         }
         flush();
-        if (act && (pass == 1 || root != sentinel)) { result = root; todo = false; }
+        if (act && heaped) { result = root; todo = false; }
         if (pass == 0 && act && todo) ++n_redo;
         }   // passes
         if (failed && lane == 0) raise_status(p.cnt, SIDM_DEV_STACK);

@@ -64,12 +64,12 @@ __device__ __forceinline__ float to_float_ru_p(R v)
     else return (float)v;
 }
 
-// per warp: staged candidate leaf, queue of in-range pairs (slot i, slot j,
-// d^2), traversal stack
+// per warp: staged candidate leaf, queue of in-range pairs (slot i, slot j),
+// traversal stack
 template <class R, bool TMA>
 constexpr size_t pair_warp_bytes()
 {
-    return (TileStageT<R, TMA>::bytes() + kQueue * (8 + sizeof(R)) + kStack * 4 + 15) / 16 * 16;
+    return (TileStageT<R, TMA>::bytes() + kQueue * 8 + kStack * 4 + 15) / 16 * 16;
 }
 
 // EXACT: form P (and so Lambda) for every in-range pair (per-particle sums of
@@ -89,8 +89,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
     Stage st_pos(base);
     uint32_t* q_si = (uint32_t*)(base + Stage::bytes());
     uint32_t* q_sj = q_si + kQueue;
-    R* q_d2 = (R*)(q_sj + kQueue);
-    int* stack = (int*)(q_d2 + kQueue);
+    int* stack = (int*)(q_sj + kQueue);
     st_pos.init(lane);
     const R* __restrict__ T = (const R*)p.lam;
     const V* __restrict__ P4 = (const V*)p.P4;
@@ -132,9 +131,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
             if (lane < nb) {
                 const int e = (qhead + lane) & (kQueue - 1);
                 const uint32_t si = q_si[e], sj = q_sj[e];
-                const R d2 = q_d2[e];
                 const V vi = V4[si], vj = V4[sj];
-                const R hi = ((const R*)(P4 + si))[3], hj = ((const R*)(P4 + sj))[3];
+                const V pi = P4[si], pj = P4[sj];
+                const R hi = pi.w, hj = pj.w;
                 const R ux = vj.x - vi.x, uy = vj.y - vi.y, uz = vj.z - vi.z;
                 const R v2 = ux * ux + uy * uy + uz * uz;
                 const uint32_t ida = id_of<R>(vi.w), idb = id_of<R>(vj.w);
@@ -170,6 +169,17 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
                 bool fire = false;
                 if (need) {
                     ++n_lam;
+                    // d^2 of the pair, recomputed exactly as in the in-range test
+                    // (candidate shifted into the frame of the query's leaf)
+                    R cx = pj.x, cy = pj.y, cz = pj.z;
+                    if constexpr (sizeof(R) == 4) {
+                        const float4 ci = p.cell[si / kLeaf], cj = p.cell[sj / kLeaf];
+                        cx = __fadd_rn(cx, __fsub_rn(cj.x, ci.x));
+                        cy = __fadd_rn(cy, __fsub_rn(cj.y, ci.y));
+                        cz = __fadd_rn(cz, __fsub_rn(cj.z, ci.z));
+                    }
+                    const R dx = sub_rn(cx, pi.x), dy = sub_rn(cy, pi.y), dz = sub_rn(cz, pi.z);
+                    const R d2 = fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
                     R f;
                     if constexpr (sizeof(R) == 4) {
                         const float d = d2 > 0.f ? d2 * rsqrtf(d2) : 0.f;
@@ -236,26 +246,31 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
                                  __double2float_rn((double)c.z - fr.O[2]));
             }
             const float rc = __fadd_ru(__fmul_ru(__fadd_ru(to_float_ru_p<R>(c.w), hmaxA), 1.0f + 0x1p-20f), fr.margin);
-            uint32_t cmask = __ballot_sync(0xffffffffu, lane < countB && point_gap2_rd(pc, qlo, qhi) <= __fmul_ru(rc, rc));
-            while (cmask) {
-                const int t = __ffs(cmask) - 1;
-                cmask &= cmask - 1u;
-                bool ok = false;
-                R d2 = R(0);
-                if (mine && (Bl > A || t > lane)) {
-                    ++n_tested;
-                    const V pj = tp[t];
-                    const R dx = sub_rn(pj.x, q.x), dy = sub_rn(pj.y, q.y), dz = sub_rn(pj.z, q.z);
-                    d2 = fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
-                    const R hs = add_rn(q.w, pj.w);
-                    ok = d2 < mul_rn(hs, hs);
-                }
-                const uint32_t m = __ballot_sync(0xffffffffu, ok);
-                if (ok) {
+            const uint32_t cmask = __ballot_sync(0xffffffffu, lane < countB && point_gap2_rd(pc, qlo, qhi) <= __fmul_ru(rc, rc));
+            // (i) in-range bits of this lane's query against every candidate of the
+            //     warp-uniform mask: straight-line arithmetic, no vote per candidate
+            uint32_t okm = 0u;
+            for (uint32_t mm = cmask; mm; mm &= mm - 1u) {
+                const int t = __ffs(mm) - 1;
+                const V pj = tp[t];
+                const R dx = sub_rn(pj.x, q.x), dy = sub_rn(pj.y, q.y), dz = sub_rn(pj.z, q.z);
+                const R d2 = fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
+                const R hs = add_rn(q.w, pj.w);
+                okm |= (d2 < mul_rn(hs, hs) ? 1u : 0u) << t;
+            }
+            // pairs this lane owns: its query reaches B, and inside A only t > lane
+            uint32_t allow = mine ? cmask : 0u;
+            if (Bl == A) allow &= 0xFFFFFFFEu << lane;
+            n_tested += (unsigned long long)__popc(allow);
+            okm &= allow;
+            // (ii) queue the pairs in rounds: every lane with pairs left adds one
+            for (uint32_t m = __ballot_sync(0xffffffffu, okm != 0u); m; m = __ballot_sync(0xffffffffu, okm != 0u)) {
+                if (okm) {
+                    const int t = __ffs(okm) - 1;
+                    okm &= okm - 1u;
                     const int e = (qhead + qn + __popc(m & lt)) & (kQueue - 1);
                     q_si[e] = slotA;
                     q_sj[e] = slotB + t;
-                    q_d2[e] = d2;
                 }
                 const int c2 = __popc(m);
                 qn += c2;
