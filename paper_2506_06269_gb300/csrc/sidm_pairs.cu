@@ -57,6 +57,18 @@ __device__ __forceinline__ uint32_t id_of(R w)
     else return (uint32_t)(double)w;
 }
 
+// position of the r-th (0-based) set bit of m (m has more than r set bits)
+__device__ __forceinline__ int nth_set_bit(uint32_t m, int r)
+{
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) {
+        const int c = __popc(m & ((1u << w) - 1u));
+        if (r >= c) { r -= c; m >>= w; pos += w; }
+    }
+    return pos;
+}
+
 template <class R>
 __device__ __forceinline__ float to_float_ru_p(R v)
 {
@@ -65,11 +77,11 @@ __device__ __forceinline__ float to_float_ru_p(R v)
 }
 
 // per warp: staged candidate leaf, queue of in-range pairs (slot i, slot j),
-// traversal stack
+// traversal stack, boxes of the nodes under test (32 lo + 32 hi)
 template <class R, bool TMA>
 constexpr size_t pair_warp_bytes()
 {
-    return (TileStageT<R, TMA>::bytes() + kQueue * 8 + kStack * 4 + 15) / 16 * 16;
+    return (TileStageT<R, TMA>::bytes() + kQueue * 8 + kStack * 4 + 64 * 16 + 15) / 16 * 16;
 }
 
 // EXACT: form P (and so Lambda) for every in-range pair (per-particle sums of
@@ -90,6 +102,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
     uint32_t* q_si = (uint32_t*)(base + Stage::bytes());
     uint32_t* q_sj = q_si + kQueue;
     int* stack = (int*)(q_sj + kQueue);
+    float4* blo = (float4*)(stack + kStack);
+    float4* bhi = blo + 32;
     st_pos.init(lane);
     const R* __restrict__ T = (const R*)p.lam;
     const V* __restrict__ P4 = (const V*)p.P4;
@@ -290,35 +304,61 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
                              __double2float_rn((double)q.z - fr.O[2]));
         }
         const float hq = active ? to_float_ru_p<R>(q.w) : -INFINITY;
-        auto near = [&](int g) -> bool {
-            const float4 lo = p.nlo[g], hi = p.nhi[g];
+        // this lane's query reaches box c: within (h_i + hmax_node)(1 + 2^-20) + margin
+        auto near_box = [&](int c) -> bool {
+            const float4 lo = blo[c], hi = bhi[c];
             const float r = __fadd_ru(__fmul_ru(__fadd_ru(hq, lo.w), 1.0f + 0x1p-20f), fr.margin);
             return active && point_gap2_rd(pq, lo, hi) <= __fmul_ru(r, r);
+        };
+        // boxes of nodes g0 .. g0+n-1 (n <= 32), one per lane
+        auto load_boxes = [&](int g0, int n) {
+            __syncwarp();
+            if (lane < n) { blo[lane] = p.nlo[g0 + lane]; bhi[lane] = p.nhi[g0 + lane]; }
+            __syncwarp();
+        };
+        // bit c: some lane's query reaches box c
+        auto accept = [&](int n, uint32_t eligible) -> uint32_t {
+            uint32_t bits = 0u;
+            if (active)
+                for (int c = 0; c < n; ++c)
+                    if ((eligible >> c) & 1u) bits |= (near_box(c) ? 1u : 0u) << c;
+            return __reduce_or_sync(0xffffffffu, bits);
+        };
+        // nodes whose subtree holds a leaf >= A (level lev, local indices first ..)
+        auto eligible_mask = [&](int lev, int first, int n) -> uint32_t {
+            uint32_t m = 0u;
+            for (int c = 0; c < n; ++c)
+                if (((int64_t)(first + c + 1) << (3 * lev)) > A) m |= 1u << c;
+            return m;
+        };
+        auto visit_leaves = [&](uint32_t acc, int first) {
+            for (; acc; acc &= acc - 1u) {
+                const int c = __ffs(acc) - 1;
+                process(first + c, near_box(c));
+            }
+        };
+        auto push = [&](uint32_t acc, int lev, int first, int& sp) -> bool {
+            const int cnt = __popc(acc);
+            if (sp + cnt > kStack) return false;
+            // descending local index on the stack, so the lowest is visited first
+            if ((acc >> lane) & 1u) stack[sp + cnt - 1 - __popc(acc & lt)] = (lev << 24) | (first + lane);
+            sp += cnt;
+            __syncwarp();
+            return true;
         };
         const int top = p.top[h];
         const int Hp = p.H + 1;
         int sp = 0;
         bool failed = false;
-        auto visit_leaf = [&](int Bl) {
-            if (Bl < A) return;
-            const bool mine = near(leaf0 + Bl);
-            if (__any_sync(0xffffffffu, mine)) process(Bl, mine);
-        };
         {
             const int nb = p.lvl_off[top * Hp + h];
             const int ntop = p.lvl_off[top * Hp + h + 1] - nb;
-            if (top == 0) {
-                for (int c = 0; c < ntop; ++c) visit_leaf(c);
-            } else {
-                uint32_t acc = 0u;
-                for (int c = 0; c < ntop; ++c)
-                    if (((int64_t)(c + 1) << (3 * top)) > A && __any_sync(0xffffffffu, near(nb + c))) acc |= 1u << c;
-                for (int c = ntop - 1; c >= 0; --c)
-                    if ((acc >> c) & 1u) { if (lane == 0) stack[sp] = (top << 24) | c; ++sp; }
-                __syncwarp();
-            }
+            load_boxes(nb, ntop);
+            const uint32_t acc = accept(ntop, eligible_mask(top, 0, ntop));
+            if (top == 0) visit_leaves(acc, 0);
+            else if (!push(acc, top, 0, sp)) failed = true;
         }
-        while (sp > 0) {
+        while (sp > 0 && !failed) {
             const int e = stack[--sp];
             __syncwarp();
             const int lev = e >> 24, idx = e & 0xFFFFFF;
@@ -327,19 +367,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
             const int cc = p.lvl_off[cl * Hp + h + 1] - cb;
             const int first = idx * 8;
             const int nch = min(8, cc - first);
-            if (cl == 0) {
-                for (int c = 0; c < nch; ++c) visit_leaf(first + c);
-                continue;
-            }
-            uint32_t acc = 0u;
-            for (int c = 0; c < nch; ++c)
-                if (((int64_t)(first + c + 1) << (3 * cl)) > A && __any_sync(0xffffffffu, near(cb + first + c)))
-                    acc |= 1u << c;
-            const int cnt = __popc(acc);
-            if (sp + cnt > kStack) { failed = true; break; }
-            for (int c = nch - 1; c >= 0; --c)
-                if ((acc >> c) & 1u) { if (lane == 0) stack[sp] = (cl << 24) | (first + c); ++sp; }
-            __syncwarp();
+            load_boxes(cb + first, nch);
+            const uint32_t acc = accept(nch, eligible_mask(cl, first, nch));
+            if (cl == 0) visit_leaves(acc, first);
+            else if (!push(acc, cl, first, sp)) failed = true;
         }
         // the queue outlives the staged tiles (entries are slots), so one partial
         // batch per query leaf remains
