@@ -70,7 +70,7 @@ def lib():
             L.orc_knn_halo.argtypes = [i32, vp, vp, vp, vp, i32, i32, i32, vp, vp, vp, vp]
             L.orc_knn_halo.restype = i32
             L.orc_pairs_halo.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, i32, i32, d, d, d, d,
-                                         u64, u64, u32, vp, i64, P(_PairStats), vp]
+                                         u64, u64, u32, vp, i64, P(_PairStats), vp, vp]
             L.orc_pairs_halo.restype = i32
             L.orc_sort_events.argtypes = [vp, i64]
             L.orc_apply_events.argtypes = [vp, i64, vp, vp, vp, vp, vp]
@@ -182,22 +182,26 @@ def knn(pos: np.ndarray, ids: np.ndarray, k: int, mode: int = MODE_MIXED, brute:
     return h, d2k, nb
 
 
-def pairs(pos, vel, ids, h, mode, xs, mass, dt, seed, step, halo, ev_cap=None):
+def pairs(pos, vel, ids, h, mode, xs, mass, dt, seed, step, halo, ev_cap=None, mask=None):
     """Pair probabilities and draws of one halo.
 
     xs = (kind, s0, w).  Returns (events [EVENT_DTYPE], stats dict, sum_p[n]).
     Event indices are local (halo) input indices; i has the smaller id.
+    mask (bool [n], optional): only pairs with a masked endpoint are evaluated
+    (stats and sum_p then cover those pairs only).
     """
     p = _c(pos, np.float64); v = _c(vel, np.float64); n = p.shape[1]
     idv = _c(ids, np.uint32); hh = _c(h, np.float64)
     cap = int(ev_cap if ev_cap is not None else max(1024, n))
     ev = np.zeros(cap, EVENT_DTYPE)
     st = _PairStats(); sump = np.zeros(n)
+    pm = None if mask is None else _c(mask, np.uint8)
     kind, s0, w = xs
     rc = lib().orc_pairs_halo(n, _p(p[0]), _p(p[1]), _p(p[2]), _p(v[0]), _p(v[1]), _p(v[2]),
                               _p(idv), _p(hh), int(mode), int(kind), float(s0), float(w),
                               float(mass), float(dt), C.c_uint64(int(seed)), C.c_uint64(int(step)),
-                              C.c_uint32(int(halo)), _p(ev), cap, C.byref(st), _p(sump))
+                              C.c_uint32(int(halo)), _p(ev), cap, C.byref(st), _p(sump),
+                              _p(pm))
     if rc != 0:
         raise RuntimeError(f"oracle pair pass failed ({rc}): event buffer too small")
     ne = int(st.n_events)

@@ -499,6 +499,9 @@ int orc_knn_halo(int n, const double* px, const double* py, const double* pz, co
 /* (h_i == h_j and i < j).  Mixed: range test d2 < RN32(RN32(h_i+h_j)^2) on  */
 /* the canonical FP32 d2 in the lower leaf's frame; FP64: d2 < (h_i+h_j)^2.  */
 /* Lambda uses the FP64 distance of the FP64 positions.                      */
+/* pair_mask (may be NULL): evaluate only the pairs with an endpoint i whose  */
+/* pair_mask[i] is non-zero (test sampling at full size; the arithmetic of   */
+/* every evaluated pair is unchanged).                                        */
 /* ------------------------------------------------------------------------- */
 typedef struct {
     uint64_t key;     /* halo<<54 | min id<<27 | max id                       */
@@ -517,7 +520,8 @@ int orc_pairs_halo(int n, const double* px, const double* py, const double* pz,
                    const uint32_t* ids, const double* h, int mode,
                    int xs_kind, double s0, double w, double mass, double dt,
                    uint64_t seed, uint64_t step, uint32_t halo,
-                   orc_event* ev_out, int64_t ev_cap, orc_pair_stats* st, double* sum_p_out)
+                   orc_event* ev_out, int64_t ev_cap, orc_pair_stats* st, double* sum_p_out,
+                   const uint8_t* pair_mask)
 {
     orc_geom g; memset(&g, 0, sizeof(g));
     if (mode == 0) geom_build(&g, n, px, py, pz);
@@ -548,6 +552,7 @@ int orc_pairs_halo(int n, const double* px, const double* py, const double* pz,
                     int j = G.items[t];
                     if (j == i) continue;
                     if (!(h[i] > h[j] || (h[i] == h[j] && i < j))) continue;
+                    if (pair_mask && !pair_mask[i] && !pair_mask[j]) continue;
                     int inr;
                     if (mode == 0) {
                         int Ai = (int)(g.rank[i] / ORC_LEAF), Aj = (int)(g.rank[j] / ORC_LEAF);

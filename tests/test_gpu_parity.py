@@ -275,3 +275,36 @@ def test_energy_drift_1000_steps_below_1e4():
     p = E[:, 1:].cpu().numpy()
     assert np.max(np.abs(p - p[0])) < 1e-5 * (h.mass * np.abs(h.vel).sum())
     ctx.close()
+
+
+# ---------------------------------------------------------------- batched workload
+def test_batched_64_halos_four_smallest_match_oracle():
+    # the 64-halo convergence batch of the benchmark (N log-uniform in [1e4, 2e6],
+    # seed 3, N_ngb 16/32/64/128 round-robin, sigma/m = 10) in one context;
+    # the four smallest halos are checked against the oracle
+    import math as _m
+    rng = np.random.default_rng(3)
+    H = 64
+    sizes = np.round(10.0 ** rng.uniform(4.0, _m.log10(2e6), H)).astype(np.int64)
+    halos = [ics.nfw(int(sizes[h]), 3 * 1000 + h) for h in range(H)]
+    b = ics.batch(halos)
+    ks = [[16, 32, 64, 128][h % 4] for h in range(H)]
+    xs = [(0, 10.0, 1.0)] * H
+    dts = [0.01] * H
+    g = gpu_step(b, ks, xs, dts, 4, 1, event_cap=1 << 22)
+    assert g["status"] == 0
+    small = np.argsort(sizes)[:4]
+    for hidx in small:
+        a, e = int(b.offsets[hidx]), int(b.offsets[hidx + 1])
+        hh = halos[hidx]
+        vin = hh.vel.astype(np.float32).astype(np.float64)
+        oh, _, _ = O.knn(hh.pos, hh.ids, ks[hidx], O.MODE_MIXED)
+        oev, _, _ = O.pairs(hh.pos, vin, hh.ids, oh, O.MODE_MIXED, xs[hidx], hh.mass, dts[hidx], 4, 1, int(hidx))
+        oev = np.sort(oev, order="key")
+        vout, _ = O.apply_events(oev, np.full(hh.n, hh.mass), vin)
+        o = {"h": oh, "events": oev, "vel_out": vout}
+        assert np.array_equal(g["h"][a:e].astype(np.float32), oh.astype(np.float32)), hidx
+        ge = g["events"][(g["events"]["i"] >= a) & (g["events"]["i"] < e)].copy()
+        ge["i"] -= a; ge["j"] -= a
+        sub_g = {"events": ge, "vel_in": g["vel_in"][:, a:e], "vel": g["vel"][:, a:e]}
+        _check_velocities(sub_g, o, 1e-5, e - a)

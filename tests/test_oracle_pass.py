@@ -164,6 +164,21 @@ def test_event_keys_sorted_unique_and_draws_below_p():
         assert e["u"] == x[0] * 2.0 ** -32 and e["x1"] == x[1] and e["x2"] == x[2]
 
 
+def test_pair_mask_selects_exactly_the_masked_pairs():
+    # the sampled pair pass used at full size evaluates the same pairs, with the
+    # same draws and probabilities, as the full pass restricted to the sample
+    h = ics.hernquist(4000, 9)
+    vel = h.vel.astype(np.float32).astype(np.float64)
+    hh, _, _ = O.knn(h.pos, h.ids, 32, O.MODE_MIXED)
+    full, _, _ = O.pairs(h.pos, vel, h.ids, hh, O.MODE_MIXED, (0, 10.0, 1.0), h.mass, 0.25, 1, 3, 0)
+    mask = np.zeros(h.n, bool)
+    mask[np.random.default_rng(2).choice(h.n, 600, replace=False)] = True
+    part, _, _ = O.pairs(h.pos, vel, h.ids, hh, O.MODE_MIXED, (0, 10.0, 1.0), h.mass, 0.25, 1, 3, 0, mask=mask)
+    want = full[mask[full["i"]] | mask[full["j"]]]
+    assert want.size > 10 and want.size < full.size
+    assert np.array_equal(part, want)
+
+
 # ---------------------------------------------------------------- scatter
 def _random_events(n_part, n_ev, seed, chain=False):
     rng = np.random.default_rng(seed)
