@@ -69,6 +69,8 @@ def lib():
             L.orc_sigma.argtypes = [i32, d, d, d]; L.orc_sigma.restype = d
             L.orc_knn_halo.argtypes = [i32, vp, vp, vp, vp, i32, i32, i32, vp, vp, vp, vp]
             L.orc_knn_halo.restype = i32
+            L.orc_knn_sample.argtypes = [i32, vp, vp, vp, vp, i32, i32, i64, vp, vp]
+            L.orc_knn_sample.restype = i32
             L.orc_pairs_halo.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, i32, i32, d, d, d, d,
                                          u64, u64, u32, vp, i64, P(_PairStats), vp, vp]
             L.orc_pairs_halo.restype = i32
@@ -180,6 +182,20 @@ def knn(pos: np.ndarray, ids: np.ndarray, k: int, mode: int = MODE_MIXED, brute:
     if rc != 0:
         raise ValueError(f"oracle kNN failed ({rc}): need 1 <= k <= n-1 (k={k}, n={n})")
     return h, d2k, nb
+
+
+def knn_sample(pos: np.ndarray, ids: np.ndarray, k: int, qidx, mode: int = MODE_MIXED):
+    """Kernel sizes of the listed particles for every N_ngb = 1..k: returns
+    h[len(qidx), k] with h[t, r] the distance to the (r+1)-th nearest other
+    particle of particle qidx[t] (the same definition as knn)."""
+    p = _c(pos, np.float64); n = p.shape[1]
+    idv = _c(ids, np.uint32)
+    q = _c(qidx, np.int64)
+    h = np.full((q.size, k), np.nan)
+    rc = lib().orc_knn_sample(n, _p(p[0]), _p(p[1]), _p(p[2]), _p(idv), int(k), int(mode), q.size, _p(q), _p(h))
+    if rc != 0:
+        raise ValueError(f"oracle kNN failed ({rc}): need 1 <= k <= n-1 (k={k}, n={n})")
+    return h
 
 
 def pairs(pos, vel, ids, h, mode, xs, mass, dt, seed, step, halo, ev_cap=None, mask=None):

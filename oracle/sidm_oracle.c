@@ -401,6 +401,65 @@ static void topk_insert(knn_ent* list, int* cnt, int k, knn_ent e)
     list[pos] = e;
 }
 
+/* The k nearest other particles of particle i, sorted by (d^2, id), into
+ * list[0..k); returns how many were found (k unless the halo is too small). */
+static int knn_one(int i, int n, const double* px, const double* py, const double* pz, const uint32_t* ids,
+                   int k, int mode, int brute, const orc_geom* g, const orc_grid* G, double absmargin,
+                   knn_ent* list)
+{
+    int cnt = 0;
+    if (brute) {
+        for (int j = 0; j < n; ++j) {
+            if (j == i) continue;
+            knn_ent e;
+            e.d = mode == 0 ? (uint64_t)fbits(d2_mixed(g, (uint32_t)i, (uint32_t)j))
+                            : dbits(d2_fp64(px, py, pz, (uint32_t)i, (uint32_t)j));
+            e.id = ids[j]; e.idx = (uint32_t)j;
+            topk_insert(list, &cnt, k, e);
+        }
+        return cnt;
+    }
+    double xi[3] = {px[i], py[i], pz[i]};
+    int ci[3]; grid_cell_of(G, xi, ci);
+    int maxs = G->dim[0] > G->dim[1] ? G->dim[0] : G->dim[1];
+    if (G->dim[2] > maxs) maxs = G->dim[2];
+    for (int s = 0; s <= maxs; ++s) {
+        for (int cz = ci[2] - s; cz <= ci[2] + s; ++cz) {
+            if (cz < 0 || cz >= G->dim[2]) continue;
+            for (int cy = ci[1] - s; cy <= ci[1] + s; ++cy) {
+                if (cy < 0 || cy >= G->dim[1]) continue;
+                for (int cx = ci[0] - s; cx <= ci[0] + s; ++cx) {
+                    if (cx < 0 || cx >= G->dim[0]) continue;
+                    int cheb = abs(cx - ci[0]);
+                    if (abs(cy - ci[1]) > cheb) cheb = abs(cy - ci[1]);
+                    if (abs(cz - ci[2]) > cheb) cheb = abs(cz - ci[2]);
+                    if (cheb != s) continue;
+                    long c = ((long)cz * G->dim[1] + cy) * G->dim[0] + cx;
+                    for (int t = G->start[c]; t < G->start[c + 1]; ++t) {
+                        int j = G->items[t];
+                        if (j == i) continue;
+                        knn_ent e;
+                        e.d = mode == 0 ? (uint64_t)fbits(d2_mixed(g, (uint32_t)i, (uint32_t)j))
+                                        : dbits(d2_fp64(px, py, pz, (uint32_t)i, (uint32_t)j));
+                        e.id = ids[j]; e.idx = (uint32_t)j;
+                        topk_insert(list, &cnt, k, e);
+                    }
+                }
+            }
+        }
+        if (cnt == k) {
+            /* every unvisited particle lies at exact distance >= s*cs;
+             * the canonical distance differs from the exact one by far
+             * less than the 1e-5 relative margin used here.           */
+            double kth;
+            if (mode == 0) { float f; uint32_t u = (uint32_t)list[k - 1].d; memcpy(&f, &u, 4); kth = sqrt((double)f); }
+            else { double f; uint64_t u = list[k - 1].d; memcpy(&f, &u, 8); kth = sqrt(f); }
+            if ((double)s * G->cs > kth * (1.0 + 1e-5) + absmargin) break;
+        }
+    }
+    return cnt;
+}
+
 int orc_knn_halo(int n, const double* px, const double* py, const double* pz, const uint32_t* ids,
                  int k, int mode, int brute, const uint8_t* query_mask,
                  double* h_out, uint64_t* d2k_bits_out, uint32_t* nbr_ids_out)
@@ -419,56 +478,7 @@ int orc_knn_halo(int n, const double* px, const double* py, const double* pz, co
         #pragma omp for schedule(dynamic, 64)
         for (int i = 0; i < n; ++i) {
             if (query_mask && !query_mask[i]) continue;
-            int cnt = 0;
-            if (brute) {
-                for (int j = 0; j < n; ++j) {
-                    if (j == i) continue;
-                    knn_ent e;
-                    e.d = mode == 0 ? (uint64_t)fbits(d2_mixed(&g, (uint32_t)i, (uint32_t)j))
-                                    : dbits(d2_fp64(px, py, pz, (uint32_t)i, (uint32_t)j));
-                    e.id = ids[j]; e.idx = (uint32_t)j;
-                    topk_insert(list, &cnt, k, e);
-                }
-            } else {
-                double xi[3] = {px[i], py[i], pz[i]};
-                int ci[3]; grid_cell_of(&G, xi, ci);
-                int maxs = G.dim[0] > G.dim[1] ? G.dim[0] : G.dim[1];
-                if (G.dim[2] > maxs) maxs = G.dim[2];
-                for (int s = 0; s <= maxs; ++s) {
-                    for (int cz = ci[2] - s; cz <= ci[2] + s; ++cz) {
-                        if (cz < 0 || cz >= G.dim[2]) continue;
-                        for (int cy = ci[1] - s; cy <= ci[1] + s; ++cy) {
-                            if (cy < 0 || cy >= G.dim[1]) continue;
-                            for (int cx = ci[0] - s; cx <= ci[0] + s; ++cx) {
-                                if (cx < 0 || cx >= G.dim[0]) continue;
-                                int cheb = abs(cx - ci[0]);
-                                if (abs(cy - ci[1]) > cheb) cheb = abs(cy - ci[1]);
-                                if (abs(cz - ci[2]) > cheb) cheb = abs(cz - ci[2]);
-                                if (cheb != s) continue;
-                                long c = ((long)cz * G.dim[1] + cy) * G.dim[0] + cx;
-                                for (int t = G.start[c]; t < G.start[c + 1]; ++t) {
-                                    int j = G.items[t];
-                                    if (j == i) continue;
-                                    knn_ent e;
-                                    e.d = mode == 0 ? (uint64_t)fbits(d2_mixed(&g, (uint32_t)i, (uint32_t)j))
-                                                    : dbits(d2_fp64(px, py, pz, (uint32_t)i, (uint32_t)j));
-                                    e.id = ids[j]; e.idx = (uint32_t)j;
-                                    topk_insert(list, &cnt, k, e);
-                                }
-                            }
-                        }
-                    }
-                    if (cnt == k) {
-                        /* every unvisited particle lies at exact distance >= s*cs;
-                         * the canonical distance differs from the exact one by far
-                         * less than the 1e-5 relative margin used here.           */
-                        double kth;
-                        if (mode == 0) { float f; uint32_t u = (uint32_t)list[k - 1].d; memcpy(&f, &u, 4); kth = sqrt((double)f); }
-                        else { double f; uint64_t u = list[k - 1].d; memcpy(&f, &u, 8); kth = sqrt(f); }
-                        if ((double)s * G.cs > kth * (1.0 + 1e-5) + absmargin) break;
-                    }
-                }
-            }
+            int cnt = knn_one(i, n, px, py, pz, ids, k, mode, brute, &g, &G, absmargin, list);
             if (cnt < k) {
                 #pragma omp atomic write
                 err = -2;
@@ -488,6 +498,49 @@ int orc_knn_halo(int n, const double* px, const double* py, const double* pz, co
         free(list);
     }
     if (!brute) grid_free(&G);
+    if (mode == 0) geom_free(&g);
+    return err;
+}
+
+/* Kernel sizes of a list of particles for every N_ngb = 1..k at once: for the
+ * t-th listed particle i = qidx[t], h_out[t*k + r] is the distance to its
+ * (r+1)-th nearest other particle (same distance and order as orc_knn_halo),
+ * from one geometry and grid build (test sampling of very large halos). */
+int orc_knn_sample(int n, const double* px, const double* py, const double* pz, const uint32_t* ids,
+                   int k, int mode, int64_t nq, const int64_t* qidx, double* h_out)
+{
+    if (k < 1 || k > n - 1) return -1;
+    orc_geom g; memset(&g, 0, sizeof(g));
+    if (mode == 0) geom_build(&g, n, px, py, pz);
+    orc_grid G; memset(&G, 0, sizeof(G));
+    grid_build(&G, n, px, py, pz, 8.0);
+    int err = 0;
+    const double absmargin = mode == 0 ? ldexp(1.0, g.E + 1 - 20) : 0.0;
+    #pragma omp parallel
+    {
+        knn_ent* list = (knn_ent*)malloc(sizeof(knn_ent) * (size_t)k);
+        #pragma omp for schedule(dynamic, 1)
+        for (int64_t t = 0; t < nq; ++t) {
+            const int i = (int)qidx[t];
+            int cnt = knn_one(i, n, px, py, pz, ids, k, mode, 0, &g, &G, absmargin, list);
+            if (cnt < k) {
+                #pragma omp atomic write
+                err = -2;
+                continue;
+            }
+            for (int r = 0; r < k; ++r) {
+                if (mode == 0) {
+                    float f; uint32_t u = (uint32_t)list[r].d; memcpy(&f, &u, 4);
+                    h_out[t * k + r] = (double)sqrtf(f);
+                } else {
+                    double f; uint64_t u = list[r].d; memcpy(&f, &u, 8);
+                    h_out[t * k + r] = sqrt(f);
+                }
+            }
+        }
+        free(list);
+    }
+    grid_free(&G);
     if (mode == 0) geom_free(&g);
     return err;
 }

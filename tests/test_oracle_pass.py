@@ -25,6 +25,17 @@ def test_knn_grid_equals_brute_force(k):
         assert np.array_equal(hb, hg) and np.array_equal(db, dg) and np.array_equal(nb, ng)
 
 
+def test_knn_sample_equals_knn_for_every_k():
+    # the sampled entry (all N_ngb up to k from one search) against separate calls
+    h = ics.nfw(5000, 4)
+    q = np.random.default_rng(3).choice(h.n, 200, replace=False)
+    for mode in (O.MODE_MIXED, O.MODE_FP64):
+        hs = O.knn_sample(h.pos, h.ids, 64, q, mode)
+        for k in (1, 16, 33, 64):
+            hk, _, _ = O.knn(h.pos, h.ids, k, mode)
+            assert np.array_equal(hs[:, k - 1], hk[q]), (mode, k)
+
+
 def test_knn_matches_library_kdtree():
     # exact FP64 kNN distances from scipy's kd-tree (its own arithmetic)
     h = ics.nfw(6000, 2)
