@@ -8,7 +8,9 @@ generators in ``paper_2506_06269_gb300.ics`` or from literal test values.
 Functions follow the paper (Fischer, Yu & Dolag 2025): Sect. 2 (spline kernel,
 N_ngb-adaptive size, energy/momentum conserving scatter), Sect. 3.5 (geometric
 factor Lambda of the interaction probability, Eq. hDl), Sect. 3.8 (Eq. vel_dep),
-Sect. 5 (conservation independent of the kernel).  The readings where the paper
+Sect. 5 (conservation independent of the kernel); local diagnostics: Eq. hDl
+(Sect. 3.5), Eq. knudsen_number (Sect. 3.6), Eq. effective_cross_section
+(App. C).  The readings where the paper
 is silent are documented in the C source header.
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test
@@ -71,6 +73,9 @@ def lib():
             L.orc_knn_halo.restype = i32
             L.orc_knn_sample.argtypes = [i32, vp, vp, vp, vp, i32, i32, i64, vp, vp]
             L.orc_knn_sample.restype = i32
+            L.orc_sigma_eff.argtypes = [i32, d, d, d]; L.orc_sigma_eff.restype = d
+            L.orc_local_diag.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, d, i32, i32, d, d, d, vp]
+            L.orc_local_diag.restype = i32
             L.orc_pairs_halo.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, i32, i32, d, d, d, d,
                                          u64, u64, u32, vp, i64, P(_PairStats), vp, vp]
             L.orc_pairs_halo.restype = i32
@@ -196,6 +201,21 @@ def knn_sample(pos: np.ndarray, ids: np.ndarray, k: int, qidx, mode: int = MODE_
     if rc != 0:
         raise ValueError(f"oracle kNN failed ({rc}): need 1 <= k <= n-1 (k={k}, n={n})")
     return h
+
+
+def sigma_eff(kind: int, s0: float, w: float, nu: float) -> float:
+    """Effective cross-section per mass at 1-D velocity dispersion nu."""
+    return float(lib().orc_sigma_eff(int(kind), float(s0), float(w), float(nu)))
+
+
+def local_diag(pos, vel, h, mass: float, nngb: int, xs, G: float = 1.0) -> dict:
+    """Per-particle rho, nu, sigma_eff/m, h/l (Eq. hDl) and Kn of one halo (FP64)."""
+    p = _c(pos, np.float64); v = _c(vel, np.float64); hh = _c(h, np.float64); n = p.shape[1]
+    out = np.zeros((5, n))
+    kind, s0, w = xs
+    lib().orc_local_diag(n, _p(p[0]), _p(p[1]), _p(p[2]), _p(v[0]), _p(v[1]), _p(v[2]), _p(hh), float(mass),
+                         int(nngb), int(kind), float(s0), float(w), float(G), _p(out))
+    return {"rho": out[0], "nu": out[1], "sigma_eff": out[2], "h_over_l": out[3], "kn": out[4]}
 
 
 def pairs(pos, vel, ids, h, mode, xs, mass, dt, seed, step, halo, ev_cap=None, mask=None):

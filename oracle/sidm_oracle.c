@@ -18,6 +18,10 @@
  *               the kernel ("by construction").
  *   App. A    : viscosity cross-section normalised to the total one for
  *               isotropic scattering (so sigma_V = sigma here).
+ *   Sect. 3.5, Sect. 3.6, App. C : local diagnostics -- SPH density and
+ *               velocity dispersion over the particle's kernel, the effective
+ *               cross-section (Eq. effective_cross_section), h/l (Eq. hDl) and
+ *               the Knudsen number (Eq. knudsen_number).
  * Readings where the paper is silent (all listed in the design doc):
  *   h_i      = distance to the N_ngb-th nearest *other* particle of the halo,
  *              ties broken by id; the kernel support radius is h_i.
@@ -721,6 +725,91 @@ void orc_apply_events(const orc_event* ev, int64_t n_ev, const double* m,
 /* Each term is formed in FP64 as term = (0.5*m) * (vx*vx + vy*vy + vz*vz)   */
 /* (left to right, no FMA) and p = m*v; only the summation is exact.          */
 /* ------------------------------------------------------------------------- */
+/* ------------------------------------------------------------------------- */
+/* Local diagnostics (Sect. 3.5 Eq. hDl, Sect. 3.6 Eq. knudsen_number, and    */
+/* the effective cross-section of App. C, Eq. effective_cross_section).       */
+/* Readings: the density is the SPH sum rho_i = m sum_{|x_j-x_i| < h_i}       */
+/* W(|x_j - x_i|, h_i) over the particle's own kernel, itself included; the    */
+/* 1-D velocity dispersion nu_i comes from the same kernel-weighted moments,   */
+/* nu_i^2 = (<|v|^2> - |<v>|^2)/3; sigma_eff averages v^5 sigma_V(v) over the  */
+/* relative-speed Maxwellian of two particles of 1-D dispersion nu,           */
+/* f(v) ~ v^2 exp(-v^2/(4 nu^2)); sigma_V = sigma for isotropic scattering.    */
+/* ------------------------------------------------------------------------- */
+double orc_sigma_eff(int kind, double s0, double w, double nu)
+{
+    if (kind == 0) return s0;
+    if (!(nu > 0.0)) return s0;
+    /* num / den = int v^7 sigma(v) e^{-v^2/(4nu^2)} dv / int v^7 e^{-v^2/(4nu^2)} dv,
+     * composite 8-point Gauss-Legendre on [0, 40 nu] (the tail beyond is e^{-400}) */
+    const int panels = 400;
+    const double L = 40.0 * nu, hp = L / panels;
+    double num = 0.0, den = 0.0;
+    for (int k = 0; k < panels; ++k) {
+        const double a = k * hp, c = a + 0.5 * hp;
+        for (int g = 0; g < 8; ++g) {
+            const double v = c + 0.5 * hp * GL8_X[g];
+            const double v2 = v * v;
+            const double base = GL8_W[g] * v2 * v2 * v2 * v * exp(-v2 / (4.0 * nu * nu));
+            num += base * orc_sigma(kind, s0, w, v);
+            den += base;
+        }
+    }
+    return num / den;
+}
+
+/* Per particle (local input order), FP64 distances of the FP64 positions:
+ * out[0][i] rho_i, out[1][i] nu_i, out[2][i] sigma_eff/m at nu_i,
+ * out[3][i] h/l by Eq. hDl with N_ngb and the particle mass m,
+ * out[4][i] Kn by Eq. knudsen_number with gravitational constant G. */
+int orc_local_diag(int n, const double* px, const double* py, const double* pz,
+                   const double* vx, const double* vy, const double* vz, const double* h,
+                   double m, int nngb, int kind, double s0, double w, double G, double* out)
+{
+    orc_grid Gr; memset(&Gr, 0, sizeof(Gr));
+    grid_build(&Gr, n, px, py, pz, 8.0);
+    #pragma omp parallel for schedule(dynamic, 64)
+    for (int i = 0; i < n; ++i) {
+        double sw = 0.0, sv[3] = {0.0, 0.0, 0.0}, sv2 = 0.0;
+        const double hi = h[i];
+        int lo[3], hc[3];
+        const double xi[3] = {px[i], py[i], pz[i]};
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = (int)floor((xi[a] - hi - Gr.lo[a]) / Gr.cs);
+            hc[a] = (int)floor((xi[a] + hi - Gr.lo[a]) / Gr.cs);
+            if (lo[a] < 0) lo[a] = 0;
+            if (hc[a] >= Gr.dim[a]) hc[a] = Gr.dim[a] - 1;
+        }
+        for (int cz = lo[2]; cz <= hc[2]; ++cz)
+        for (int cy = lo[1]; cy <= hc[1]; ++cy)
+        for (int cx = lo[0]; cx <= hc[0]; ++cx) {
+            long c = ((long)cz * Gr.dim[1] + cy) * Gr.dim[0] + cx;
+            for (int t = Gr.start[c]; t < Gr.start[c + 1]; ++t) {
+                const int j = Gr.items[t];
+                const double dx = px[j] - px[i], dy = py[j] - py[i], dz = pz[j] - pz[i];
+                const double d = sqrt(dx * dx + dy * dy + dz * dz);
+                if (!(d < hi)) continue;          /* j == i contributes W(0, h_i) */
+                const double wt = m * orc_kernel_w(d, hi);
+                sw += wt;
+                sv[0] += wt * vx[j]; sv[1] += wt * vy[j]; sv[2] += wt * vz[j];
+                sv2 += wt * (vx[j] * vx[j] + vy[j] * vy[j] + vz[j] * vz[j]);
+            }
+        }
+        const double rho = sw;
+        const double mx = sv[0] / sw, my = sv[1] / sw, mz = sv[2] / sw;
+        double var = (sv2 / sw - (mx * mx + my * my + mz * mz)) / 3.0;
+        if (var < 0.0) var = 0.0;
+        const double nu = sqrt(var);
+        const double se = orc_sigma_eff(kind, s0, w, nu);
+        out[i] = rho;
+        out[(size_t)n + i] = nu;
+        out[2 * (size_t)n + i] = se;
+        out[3 * (size_t)n + i] = se * pow(rho, 2.0 / 3.0) * cbrt(3.0 * m * nngb / (ORC_PI * sqrt(2.0)));
+        out[4 * (size_t)n + i] = sqrt(4.0 * ORC_PI * G / (rho * nu * nu)) / se;
+    }
+    grid_free(&Gr);
+    return 0;
+}
+
 typedef struct { double* p; int n, cap; } orc_xsum;
 
 static void xsum_add(orc_xsum* s, double x)

@@ -134,3 +134,22 @@ def test_exact_sum_matches_fsum():
     assert em[0] == math.fsum(terms)
     for a in range(3):
         assert em[1 + a] == math.fsum(m * vel[a])
+
+
+def test_sigma_eff_matches_its_definition():
+    # App. C: <v^5 sigma_V(v)> / <v^5> over the relative-speed Maxwellian of two
+    # particles of 1-D dispersion nu; evaluated here by scipy's adaptive
+    # quadrature in the substituted variable t = v^2 / (4 nu^2)
+    from scipy import integrate
+    s0, w = 100.0, 0.3811
+    assert O.sigma_eff(0, 7.5, w, 0.2) == 7.5
+    for nu in (0.01, 0.1, 0.3811, 1.0, 3.0):
+        a = 4.0 * nu * nu
+        num = integrate.quad(lambda t: t ** 3 * math.exp(-t) / (1.0 + a * t / w ** 2) ** 2, 0, math.inf,
+                             epsabs=0, epsrel=1e-13, limit=400)[0]
+        want = s0 * num / 6.0
+        assert O.sigma_eff(1, s0, w, nu) == pytest.approx(want, rel=1e-10), nu
+    # limits: nu -> 0 recovers sigma(0) = s0; large nu falls like (w / 2nu)^4 * 2 / 6
+    assert O.sigma_eff(1, s0, w, 1e-4) == pytest.approx(s0, rel=1e-5)
+    nu = 200.0
+    assert O.sigma_eff(1, s0, w, nu) == pytest.approx(s0 * (w * w / (4 * nu * nu)) ** 2 * 1.0 / 6.0, rel=1e-3)

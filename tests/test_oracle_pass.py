@@ -255,3 +255,62 @@ def test_isotropy_chi_square():
     inc = (vel[:, ev["i"]] - vel[:, ev["j"]])
     inc /= np.linalg.norm(inc, axis=0)
     assert abs(np.mean((inc * nh).sum(0))) < 5 / math.sqrt(n_ev)
+
+
+# ---------------------------------------------------------------- local diagnostics
+def test_local_density_dispersion_and_ratios_in_a_uniform_box():
+    # Sums over each particle's own kernel (itself included), recomputed from a
+    # library neighbour search (scipy kd-tree) and numpy; the kernel W itself is
+    # pinned in test_oracle_math.
+    n = 20000
+    b = ics.uniform_box(n, 31)
+    rng = np.random.default_rng(4)
+    hh = rng.uniform(0.06, 0.12, n)
+    d = O.local_diag(b.pos, b.vel, hh, b.mass, 64, (1, 100.0, 0.3811))
+    tree = spatial.cKDTree(b.pos.T)
+    for i in rng.choice(n, 200, replace=False):
+        nb = np.array(tree.query_ball_point(b.pos[:, i], hh[i]))
+        r = np.linalg.norm(b.pos[:, nb] - b.pos[:, [i]], axis=0)
+        nb, r = nb[r < hh[i]], r[r < hh[i]]
+        wt = b.mass * np.array([O.kernel_w(x, hh[i]) for x in r])
+        rho = wt.sum()
+        mean = (wt * b.vel[:, nb]).sum(1) / rho
+        nu = math.sqrt(max(((wt * (b.vel[:, nb] ** 2).sum(0)).sum() / rho - (mean ** 2).sum()) / 3.0, 0.0))
+        assert d["rho"][i] == pytest.approx(rho, rel=1e-12)
+        assert d["nu"][i] == pytest.approx(nu, rel=1e-9)
+        assert d["sigma_eff"][i] == pytest.approx(O.sigma_eff(1, 100.0, 0.3811, nu), rel=1e-12)
+    # statistics of a unit-density Maxwellian box (1-D dispersion 1): the interior
+    # density is ~ 1 + m W(0, h) up to the ~1 % count fluctuation of the region;
+    # a weighted variance of independent velocities has expectation
+    # 1 - sum w^2 / (sum w)^2 per component
+    inner = np.all((b.pos > 0.12) & (b.pos < 0.88), axis=0)
+    self_term = b.mass * 8.0 / (math.pi * hh ** 3)
+    assert abs((d["rho"] - self_term)[inner].mean() - 1.0) < 0.03
+    pick = rng.choice(np.where(inner)[0], 2000, replace=False)
+    expect = []
+    for i in pick:
+        nb = np.array(tree.query_ball_point(b.pos[:, i], hh[i]))
+        r = np.linalg.norm(b.pos[:, nb] - b.pos[:, [i]], axis=0)
+        wt = np.array([O.kernel_w(x, hh[i]) for x in r[r < hh[i]]])
+        expect.append(1.0 - (wt ** 2).sum() / wt.sum() ** 2)
+    assert (d["nu"][pick] ** 2).mean() == pytest.approx(np.mean(expect), rel=0.03)
+    # h/l (Eq. hDl) is sqrt(2) rho sigma_eff/m times the kernel size of a sphere
+    # holding N_ngb particles at density rho; Kn (Eq. knudsen_number) is the mean
+    # free path 1/(rho sigma_eff/m) over the Jeans length nu / sqrt(4 pi G rho)
+    r = d["rho"]; se = d["sigma_eff"]
+    h_est = (3.0 * b.mass * 64 / (4.0 * math.pi * r)) ** (1.0 / 3.0)
+    assert np.allclose(d["h_over_l"], math.sqrt(2.0) * r * se * h_est, rtol=1e-12)
+    lam = 1.0 / (r * se)
+    jeans = d["nu"] / np.sqrt(4.0 * math.pi * r)
+    assert np.allclose(d["kn"], lam / jeans, rtol=1e-12)
+
+
+def test_local_dispersion_vanishes_for_equal_velocities():
+    b = ics.uniform_box(3000, 32)
+    vel = np.tile(np.array([[0.3], [-1.2], [2.0]]), (1, b.n))
+    d = O.local_diag(b.pos, vel, np.full(b.n, 0.2), b.mass, 32, (1, 100.0, 0.38))
+    assert np.all(d["nu"] < 1e-7)
+    # a particle alone in its kernel has the self term only
+    lone = O.local_diag(np.array([[0.0, 5.0], [0.0, 5.0], [0.0, 5.0]]), np.zeros((3, 2)), np.array([1.0, 1.0]),
+                        0.5, 1, (0, 1.0, 1.0))
+    assert lone["rho"][0] == 0.5 * O.kernel_w(0.0, 1.0)
