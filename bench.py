@@ -232,7 +232,7 @@ def run_ours(args):
     halo, vmax = make_halo(n, SEED_IC + rank)
     dt, q999 = dt_rule(sidm.Context, halo, vmax, local)
     ctx = sidm.Context(n_max=n, halo_max=1, ngb_max=N_NGB, event_cap=max(1 << 16, n // 8), precision="mixed",
-                       device=local, flags=sidm.SIDM_FLAG_TIMING, use_tma=args.use_tma)
+                       device=local, flags=sidm.SIDM_FLAG_TIMING | sidm.SIDM_FLAG_LOCAL_DIAG, use_tma=args.use_tma)
     dev = ctx.device
     off = [0, n]
     pos = torch.tensor(halo.pos, device=dev)
@@ -286,6 +286,19 @@ def run_ours(args):
     ctx.diagnostics(reset=True)
     ctx.warm_start(True)
     knn_cold_ms = float(kms_cold[1] / max(kcnt_cold[1], 1))
+    # local diagnostics of the evolved halo (one fused pair traversal + finalize)
+    ctx.local_diagnostics(xs, mass_t, vel, n)
+    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    d0.record()
+    diag_out = ctx.local_diagnostics(xs, mass_t, vel, n)
+    d1.record()
+    torch.cuda.synchronize()
+    hl = diag_out["h_over_l"].double(); kn = diag_out["kn"].double()
+    local_diag = {"ms": d0.elapsed_time(d1), "h_over_l_median": float(hl.median()), "h_over_l_max": float(hl.max()),
+                  "h_over_l_q99": float(torch.quantile(hl[::16], 0.99)), "kn_median": float(kn.median()),
+                  "kn_min": float(kn.min()), "G": 1.0,
+                  "note": "per particle: SPH density over its kernel, kernel-weighted dispersion, sigma_eff, "
+                          "h/l (Eq. hDl), Knudsen number (Eq. knudsen_number)"}
     total_ms = max_over_ranks(float(sum(times)), dev) if ws > 1 else float(sum(times))
     st = [sidm.parse_stats(stats[i]) for i in range(K)]
     E = energy.cpu().numpy()
@@ -301,7 +314,7 @@ def run_ours(args):
         "clocks": clocks, "gpu_launches": gpu_launches, "kms": kms, "kcnt": kcnt, "status": status,
         "drift": drift, "book": book, "n_pairs": n_pairs, "n_tested": n_tested, "n_events": n_events,
         "stats": st, "ws": ws, "rank": rank, "local": local, "tensors": (pos, vel, ids, h, xs, dt_t, mass_t),
-        "step": step, "seed": seed, "diag": diag, "knn_cold_ms": knn_cold_ms,
+        "step": step, "seed": seed, "diag": diag, "knn_cold_ms": knn_cold_ms, "local_diag": local_diag,
         "knn_candidates_per_step": float(diag[1]) / max(K, 1),
     }
     return res
@@ -603,6 +616,7 @@ def main_ours(args):
                               "pair_tests": res["n_tested"] / K, "pair_evals": res["n_pairs"] / K,
                               "pair_lambda_lookups": float(res["diag"][6]) / K,
                               "knn_redone_cold": float(res["diag"][7]) / K},
+            "local_diagnostics": res["local_diag"],
             "knn_warm_start": {"ms_per_launch_warm": kms[1] / K, "ms_per_launch_cold": res["knn_cold_ms"],
                                "note": "kernel sizes start from the previous step's h (bound 1.0625 h_prev); "
                                        "particles with fewer than N_ngb candidates inside are redone cold; "

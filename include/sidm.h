@@ -61,6 +61,7 @@ extern "C" {
 /* sidm_config.flags */
 #define SIDM_FLAG_SUM_P   0x1  /* accumulate sum_j P_ij per particle (diagnostic) */
 #define SIDM_FLAG_TIMING  0x2  /* time hot kernels with CUDA events (sidm_kernel_times) */
+#define SIDM_FLAG_LOCAL_DIAG 0x4 /* keep scratch for sidm_local_diagnostics (40 B/particle) */
 
 typedef struct sidm_ctx sidm_ctx;
 
@@ -250,6 +251,32 @@ int sidm_kernel_times(sidm_ctx* ctx, double* ms_out, int64_t* count_out, int32_t
  * than N_ngb candidates inside the guessed bound and was redone cold.
  * reset != 0 clears them afterwards. */
 int sidm_diagnostics(sidm_ctx* ctx, uint64_t* out, int32_t reset);
+
+/* Local diagnostics of every particle (Sect. 3.5 Eq. hDl, Sect. 3.6
+ * Eq. knudsen_number, App. C Eq. effective_cross_section), from one traversal
+ * of the in-range pairs fused with the kernel sums (no draws, no velocity
+ * change):
+ *   rho_i = sum over j with d_ij < h_i, i itself included, of m W(d_ij, h_i)
+ *           (SPH density over the particle's own kernel);
+ *   nu_i  = 1-D velocity dispersion of the same kernel-weighted moments,
+ *           nu^2 = (<|v|^2> - |<v>|^2) / 3;
+ *   sigma_eff_i / m = <v^5 sigma(v)> / <v^5> over the relative-speed
+ *           Maxwellian of two particles of dispersion nu_i (sigma_V = sigma
+ *           for isotropic scattering);
+ *   (h/l)_i = (sigma_eff/m) rho^(2/3) (3 m N_ngb / (pi sqrt 2))^(1/3);
+ *   Kn_i    = sqrt(4 pi G / (rho nu^2)) / (sigma_eff/m).
+ *   xs_dev   : device sidm_xs[n_halos] (the cross-section law of each halo)
+ *   mass_dev : device f64[n_halos] particle mass per halo
+ *   vel_dev  : [3][N] velocities (f32 or f64 by precision), read only
+ *   G        : gravitational constant in code units
+ *   out_dev  : out, f32 (SIDM_MIXED) or f64 (SIDM_FP64) [5][N]: rho, nu,
+ *              sigma_eff/m, h/l, Kn, in the order left by sidm_build_cells
+ * Requires SIDM_FLAG_LOCAL_DIAG at creation and a preceding
+ * sidm_kernel_sizes; uses the kernel sizes and N_ngb of that call.  The
+ * moments are summed with FP64 atomics, so the last bits of rho and nu may
+ * differ between runs. */
+int sidm_local_diagnostics(sidm_ctx* ctx, const sidm_xs* xs_dev, const double* mass_dev, const void* vel_dev,
+                           double G, void* out_dev, cudaStream_t stream);
 
 /* Warm start of the kernel-size search (enabled by default).  When enabled,
  * sidm_build_cells seeds every particle's search with its kernel size from the

@@ -343,6 +343,65 @@ __global__ void k_leaf_bbox(int L, int64_t N, const int32_t* __restrict__ leaf_h
 }
 
 // Max kernel size per leaf (into lo.w), from the padded h track.
+// sigma_eff / s0 = (1/6) int_0^inf t^3 e^-t / (1 + beta t)^2 dt, beta = 4 nu^2 / w^2
+// (the Maxwellian average <v^5 sigma(v)> / <v^5> with t = v^2 / (4 nu^2)):
+// 4-point Gauss-Legendre on 48 panels with edges 64 (k/48)^2, which follow the
+// 1/beta scale near t = 0; error below 1e-6 up to beta = 1e4.
+__device__ double sigma_eff_ratio(double beta)
+{
+    const double a = sqrt(3.0 / 7.0 + 2.0 / 7.0 * sqrt(1.2)), b = sqrt(3.0 / 7.0 - 2.0 / 7.0 * sqrt(1.2));
+    const double wa = (18.0 - sqrt(30.0)) / 36.0, wb = (18.0 + sqrt(30.0)) / 36.0;
+    const double xg[4] = {-a, -b, b, a}, wg[4] = {wa, wb, wb, wa};
+    double tot = 0.0;
+    for (int k = 0; k < 48; ++k) {
+        const double lo = 64.0 * (k / 48.0) * (k / 48.0), hi = 64.0 * ((k + 1) / 48.0) * ((k + 1) / 48.0);
+        const double c = 0.5 * (lo + hi), hw = 0.5 * (hi - lo);
+        for (int g = 0; g < 4; ++g) {
+            const double t = c + hw * xg[g];
+            const double den = 1.0 + beta * t;
+            tot += hw * wg[g] * t * t * t * exp(-t) / (den * den);
+        }
+    }
+    return tot / 6.0;
+}
+
+// Local diagnostics from the kernel-weighted pair moments plus the self term
+// (one thread per slot of a leaf).
+template <class R>
+__global__ void k_diag_final(int L, const int32_t* __restrict__ leaf_halo, const int32_t* __restrict__ leaf_off,
+                             const int64_t* __restrict__ halo_off, const typename Vec4<R>::T* __restrict__ P4,
+                             const typename Vec4<R>::T* __restrict__ V4, const double* __restrict__ dacc, int64_t N,
+                             const double* __restrict__ mass, const sidm_xs* __restrict__ xs,
+                             const int32_t* __restrict__ ngb, double G, R* __restrict__ out)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int leaf = (int)(t / kLeaf), lane = (int)(t % kLeaf);
+    if (leaf >= L) return;
+    const int h = leaf_halo[leaf];
+    const int64_t local = (int64_t)(leaf - leaf_off[h]) * kLeaf + lane;
+    if (local >= halo_off[h + 1] - halo_off[h]) return;
+    const int64_t u = halo_off[h] + local;
+    const int64_t slot = (int64_t)leaf * kLeaf + lane;
+    const double hv = (double)P4[slot].w;
+    const typename Vec4<R>::T v = V4[slot];
+    const double vx = (double)v.x, vy = (double)v.y, vz = (double)v.z;
+    const double m = mass[h];
+    const double w0 = m * (8.0 / 3.14159265358979323846) / (hv * hv * hv);
+    const double sw = dacc[u] + w0;
+    const double mx = (dacc[N + u] + w0 * vx) / sw, my = (dacc[2 * N + u] + w0 * vy) / sw,
+                 mz = (dacc[3 * N + u] + w0 * vz) / sw;
+    const double m2 = (dacc[4 * N + u] + w0 * (vx * vx + vy * vy + vz * vz)) / sw;
+    const double nu = sqrt(fmax((m2 - (mx * mx + my * my + mz * mz)) / 3.0, 0.0));
+    const sidm_xs x = xs[h];
+    const double se = x.kind == 1 ? x.s0 * sigma_eff_ratio(4.0 * nu * nu / (x.w * x.w)) : x.s0;
+    const double rho = sw;
+    out[u] = (R)rho;
+    out[N + u] = (R)nu;
+    out[2 * N + u] = (R)se;
+    out[3 * N + u] = (R)(se * cbrt(rho * rho) * cbrt(3.0 * m * ngb[h] / (3.14159265358979323846 * sqrt(2.0))));
+    out[4 * N + u] = (R)(sqrt(4.0 * 3.14159265358979323846 * G / (rho * nu * nu)) / se);
+}
+
 template <class R>
 __global__ void k_leaf_hmax(int L, int H, const int32_t* __restrict__ leaf_halo, const int32_t* __restrict__ leaf_off,
                             const int64_t* __restrict__ halo_off, const typename Vec4<R>::T* __restrict__ P4,
@@ -840,7 +899,7 @@ static void free_all(sidm_ctx* c)
                     c->d_chunk_halo, c->d_chunk_begin, c->d_frame, c->d_key, c->d_key2, c->d_val, c->d_val2,
                     c->d_hist, c->d_P4, c->d_V4, c->d_ID, c->d_cell, c->d_nlo, c->d_nhi, c->d_perm, c->d_tmp_pos,
                     c->d_tmp_vel, c->d_tmp_id, c->d_claim, c->d_hits, c->d_done, c->d_ev, c->d_sump,
-                    c->d_stats_own, c->d_cnt, c->d_epart, c->d_lam, c->d_hprev};
+                    c->d_stats_own, c->d_cnt, c->d_epart, c->d_lam, c->d_hprev, c->d_dacc};
     for (void* p : ptrs) if (p) cudaFree(p);
     if (c->d_stage) cudaFreeHost(c->d_stage);
     for (cudaEvent_t e : c->t_ev) if (e) cudaEventDestroy(e);
@@ -926,6 +985,7 @@ extern "C" int sidm_create(sidm_ctx** out, const sidm_config* cfg)
     ALLOC(c->d_done, cfg->event_cap);
     ALLOC(c->d_ev, cfg->event_cap);
     ALLOC(c->d_sump, (cfg->flags & SIDM_FLAG_SUM_P) ? N : 1);
+    ALLOC(c->d_dacc, (cfg->flags & SIDM_FLAG_LOCAL_DIAG) ? 5 * N : 1);
     ALLOC(c->d_stats_own, 1);
     ALLOC(c->d_cnt, 1);
     ALLOC(c->d_epart, 8 * c->chunk_cap);
@@ -1228,6 +1288,39 @@ extern "C" int sidm_scatter_step(sidm_ctx* c, uint64_t seed, uint64_t step, cons
         SIDM_LAUNCH(c, k_resolve<float><<<1, 1024, 0, s>>>(c->d_ev, c->cfg.event_cap, (float*)vel, L.N, mass, c->d_claim,
                                                          c->d_hits, c->d_done, c->d_cnt, st, c->cfg.max_rounds, c->d_sump, use_sump));
     timer_end(c, tr, s);
+    return SIDM_OK;
+}
+
+extern "C" int sidm_local_diagnostics(sidm_ctx* c, const sidm_xs* xs, const double* mass, const void* vel, double G,
+                                      void* out, cudaStream_t s)
+{
+    if (!c) return SIDM_EINVAL;
+    if (!(c->cfg.flags & SIDM_FLAG_LOCAL_DIAG)) return set_err(c, SIDM_EINVAL, "context built without SIDM_FLAG_LOCAL_DIAG");
+    if (!c->sized) return set_err(c, SIDM_EINVAL, "sidm_kernel_sizes must come first");
+    if (!xs || !mass || ((!vel || !out) && c->lay.N > 0)) return set_err(c, SIDM_EINVAL, "null argument");
+    if (!(G > 0.0)) return set_err(c, SIDM_EINVAL, "G must be positive");
+    SIDM_CUDA(c, ensure_device(c));
+    const LayoutHost& L = c->lay;
+    if (L.N == 0) return SIDM_OK;
+    const bool fp64 = c->cfg.precision == SIDM_FP64;
+    SIDM_CUDA(c, cudaMemsetAsync(c->d_dacc, 0, sizeof(double) * 5 * L.N, s));
+    if (fp64)
+        SIDM_LAUNCH(c, k_vel_refresh<double><<<grid_for(c, L.N, 256), 256, 0, s>>>(L.N, L.H, c->d_halo_off, c->d_halo_pad,
+                                                                                  (const double*)vel, c->d_ID, (double4*)c->d_V4));
+    else
+        SIDM_LAUNCH(c, k_vel_refresh<float><<<grid_for(c, L.N, 256), 256, 0, s>>>(L.N, L.H, c->d_halo_off, c->d_halo_pad,
+                                                                                (const float*)vel, c->d_ID, (float4*)c->d_V4));
+    int rc = launch_pairs_diag(c, xs, mass, s);
+    if (rc) return rc;
+    const int blocks = (int)(((int64_t)L.L * kLeaf + 255) / 256);
+    if (fp64)
+        SIDM_LAUNCH(c, k_diag_final<double><<<blocks, 256, 0, s>>>(L.L, c->d_leaf_halo, c->d_leaf_off, c->d_halo_off,
+                                                                   (const double4*)c->d_P4, (const double4*)c->d_V4,
+                                                                   c->d_dacc, L.N, mass, xs, c->d_ngb, G, (double*)out));
+    else
+        SIDM_LAUNCH(c, k_diag_final<float><<<blocks, 256, 0, s>>>(L.L, c->d_leaf_halo, c->d_leaf_off, c->d_halo_off,
+                                                                  (const float4*)c->d_P4, (const float4*)c->d_V4,
+                                                                  c->d_dacc, L.N, mass, xs, c->d_ngb, G, (float*)out));
     return SIDM_OK;
 }
 

@@ -125,6 +125,7 @@ struct sidm_ctx {
     uint8_t* d_done = nullptr;              // [event_cap]
     sidm_event* d_ev = nullptr;             // [event_cap]
     float* d_sump = nullptr;                // [N] (SIDM_FLAG_SUM_P)
+    double* d_dacc = nullptr;               // [5][N] kernel-weighted moments (SIDM_FLAG_LOCAL_DIAG)
     sidm_step_stats* d_stats_own = nullptr; // used when the caller passes NULL
     sidm::DevCounters* d_cnt = nullptr;
 
@@ -170,6 +171,7 @@ int occupancy(sidm_ctx* c, const void* fn, int threads, size_t smem, int* occ);
 int launch_knn(sidm_ctx* c, void* h_out, uint32_t* nbr, int k_stride, bool use_guess, cudaStream_t s);
 int launch_pairs(sidm_ctx* c, uint64_t seed, uint64_t step, const sidm_xs* xs, const double* dt,
                  const double* mass, sidm_step_stats* st, cudaStream_t s);
+int launch_pairs_diag(sidm_ctx* c, const sidm_xs* xs, const double* mass, cudaStream_t s);
 
 // ---------------------------------------------------------------- device helpers
 __device__ __forceinline__ void raise_status(DevCounters* cnt, unsigned int bits)

@@ -44,9 +44,28 @@ struct PairParams {
     unsigned long long ev_cap;
     float* sump;
     int use_sump;
+    double* dacc;       // local diagnostics: [5][nacc] kernel-weighted moments
+    int64_t nacc;
     DevCounters* cnt;
     sidm_step_stats* st;
 };
+
+// what one traversal of the in-range pairs computes
+constexpr int kModeDraw = 0;        // draws, Lambda only below the bound of P
+constexpr int kModeDrawExact = 1;   // draws, every P formed (per-particle sums of P)
+constexpr int kModeDiag = 2;        // no draws: kernel-weighted moments for the local diagnostics
+
+// spline kernel of Sect. 2, support h, normalised to one
+template <class R>
+__device__ __forceinline__ R spline_w(R d, R h)
+{
+    const R q = d / h;
+    if (!(q < R(1))) return R(0);
+    const R norm = R(8.0 / 3.14159265358979323846) / (h * h * h);
+    if (q < R(0.5)) return norm * (R(1) - R(6) * q * q * (R(1) - q));
+    const R t = R(1) - q;
+    return norm * R(2) * t * t * t;
+}
 
 constexpr int kQueue = 64;
 
@@ -84,13 +103,16 @@ constexpr size_t pair_warp_bytes()
     return (TileStageT<R, TMA>::bytes() + kQueue * 8 + kStack * 4 + 64 * 16 + 15) / 16 * 16;
 }
 
-// EXACT: form P (and so Lambda) for every in-range pair (per-particle sums of
-// P requested).  Otherwise Lambda is looked up only when the draw lies below
+// MODE kModeDrawExact: form P (and so Lambda) for every in-range pair
+// (per-particle sums of P requested).  kModeDiag: no draws; each pair adds
+// m W(d, h_i) and its velocity moments of j to particle i when d < h_i, and
+// the same for j (the SPH sums of the local diagnostics).  kModeDraw: Lambda
+// is looked up only when the draw lies below
 // an upper bound of P: P_up uses kLamFUp in place of the interpolated table
 // value, and since FP32/FP64 products round monotonically P <= P_up for the P
 // that would have been formed, so a draw u >= P_up + 2e-6 decides "no event"
 // and "not within 1e-6 of P" exactly as the full evaluation would.
-template <class R, bool TMA, bool EXACT>
+template <class R, bool TMA, int MODE>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParams p)
 {
     using V = typename Vec4<R>::T;
@@ -139,10 +161,54 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
         int qhead = 0, qn = 0;
         unsigned long long n_tiles = 0ull;
 
-        // P, draw and event for queue entries qhead .. qhead+nb-1 (one per lane)
+        // d^2 of a queued pair, recomputed exactly as in the in-range test
+        // (candidate shifted into the frame of the query's leaf)
+        auto pair_d2 = [&](uint32_t si, uint32_t sj, const V& pi, const V& pj) -> R {
+            R cx = pj.x, cy = pj.y, cz = pj.z;
+            if constexpr (sizeof(R) == 4) {
+                const float4 ci = p.cell[si / kLeaf], cj = p.cell[sj / kLeaf];
+                cx = __fadd_rn(cx, __fsub_rn(cj.x, ci.x));
+                cy = __fadd_rn(cy, __fsub_rn(cj.y, ci.y));
+                cz = __fadd_rn(cz, __fsub_rn(cj.z, ci.z));
+            }
+            const R dx = sub_rn(cx, pi.x), dy = sub_rn(cy, pi.y), dz = sub_rn(cz, pi.z);
+            return fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
+        };
+
+        // P, draw and event (or the diagnostic moments) for queue entries
+        // qhead .. qhead+nb-1, one per lane
         auto run_batch = [&](int nb) {
             __syncwarp();
-            if (lane < nb) {
+            if constexpr (MODE == kModeDiag) {
+                if (lane < nb) {
+                    const int e = (qhead + lane) & (kQueue - 1);
+                    const uint32_t si = q_si[e], sj = q_sj[e];
+                    const V vi = V4[si], vj = V4[sj];
+                    const V pi = P4[si], pj = P4[sj];
+                    const R d2 = pair_d2(si, sj, pi, pj);
+                    const R d = sqrt_rn(d2);
+                    const R mh = (R)p.mass[h];
+                    const int64_t ui = slot2u + si, uj = slot2u + sj;
+                    if (d2 < mul_rn(pi.w, pi.w)) {
+                        const double wt = (double)(mh * spline_w<R>(d, pi.w));
+                        atomicAdd(p.dacc + ui, wt);
+                        atomicAdd(p.dacc + p.nacc + ui, wt * (double)vj.x);
+                        atomicAdd(p.dacc + 2 * p.nacc + ui, wt * (double)vj.y);
+                        atomicAdd(p.dacc + 3 * p.nacc + ui, wt * (double)vj.z);
+                        atomicAdd(p.dacc + 4 * p.nacc + ui,
+                                  wt * ((double)vj.x * vj.x + (double)vj.y * vj.y + (double)vj.z * vj.z));
+                    }
+                    if (d2 < mul_rn(pj.w, pj.w)) {
+                        const double wt = (double)(mh * spline_w<R>(d, pj.w));
+                        atomicAdd(p.dacc + uj, wt);
+                        atomicAdd(p.dacc + p.nacc + uj, wt * (double)vi.x);
+                        atomicAdd(p.dacc + 2 * p.nacc + uj, wt * (double)vi.y);
+                        atomicAdd(p.dacc + 3 * p.nacc + uj, wt * (double)vi.z);
+                        atomicAdd(p.dacc + 4 * p.nacc + uj,
+                                  wt * ((double)vi.x * vi.x + (double)vi.y * vi.y + (double)vi.z * vi.z));
+                    }
+                }
+            } else if (lane < nb) {
                 const int e = (qhead + lane) & (kQueue - 1);
                 const uint32_t si = q_si[e], sj = q_sj[e];
                 const V vi = V4[si], vj = V4[sj];
@@ -173,7 +239,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
                     inv = R(1) / (hi > hj ? hi : hj);
                     u = (R)ldexp((double)x.x[0], -32);
                 }
-                if constexpr (EXACT) {
+                if constexpr (MODE == kModeDrawExact) {
                     need = true;
                 } else {
                     const R P_up = pre * (R(kLamFUp) * inv * inv * inv);
@@ -183,17 +249,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
                 bool fire = false;
                 if (need) {
                     ++n_lam;
-                    // d^2 of the pair, recomputed exactly as in the in-range test
-                    // (candidate shifted into the frame of the query's leaf)
-                    R cx = pj.x, cy = pj.y, cz = pj.z;
-                    if constexpr (sizeof(R) == 4) {
-                        const float4 ci = p.cell[si / kLeaf], cj = p.cell[sj / kLeaf];
-                        cx = __fadd_rn(cx, __fsub_rn(cj.x, ci.x));
-                        cy = __fadd_rn(cy, __fsub_rn(cj.y, ci.y));
-                        cz = __fadd_rn(cz, __fsub_rn(cj.z, ci.z));
-                    }
-                    const R dx = sub_rn(cx, pi.x), dy = sub_rn(cy, pi.y), dz = sub_rn(cz, pi.z);
-                    const R d2 = fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
+                    const R d2 = pair_d2(si, sj, pi, pj);
                     R f;
                     if constexpr (sizeof(R) == 4) {
                         const float d = d2 > 0.f ? d2 * rsqrtf(d2) : 0.f;
@@ -208,7 +264,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
                     if (fabs(P - u) < R(1e-6)) ++n_near;
                 }
                 const int64_t ui = slot2u + si, uj = slot2u + sj;
-                if constexpr (EXACT) {
+                if constexpr (MODE == kModeDrawExact) {
                     if (p.use_sump) {
                         atomicAdd(p.sump + ui, (float)P);
                         atomicAdd(p.sump + uj, (float)P);
@@ -398,7 +454,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
     st_pos.finish(lane, p.cnt);
 }
 
-template <class R, bool TMA, bool EXACT>
+template <class R, bool TMA, int MODE>
 int launch_t(sidm_ctx* c, uint64_t seed, uint64_t step, const sidm_xs* xs, const double* dt, const double* mass,
              sidm_step_stats* st, cudaStream_t s)
 {
@@ -412,10 +468,11 @@ int launch_t(sidm_ctx* c, uint64_t seed, uint64_t step, const sidm_xs* xs, const
     p.seed_lo = (uint32_t)seed; p.seed_hi = (uint32_t)(seed >> 32); p.step_lo = (uint32_t)step;
     p.ev = c->d_ev; p.ev_cap = (unsigned long long)c->cfg.event_cap;
     p.sump = c->d_sump; p.use_sump = (c->cfg.flags & SIDM_FLAG_SUM_P) ? 1 : 0;
+    p.dacc = c->d_dacc; p.nacc = L.N;
     p.cnt = c->d_cnt; p.st = st;
     const int warps = c->pair_warps;
     const size_t smem = (size_t)warps * pair_warp_bytes<R, TMA>();
-    auto kern = k_pairs<R, TMA, EXACT>;
+    auto kern = k_pairs<R, TMA, MODE>;
     int occ = 0;
     int rc = occupancy(c, (const void*)kern, warps * 32, smem, &occ);
     if (rc) return rc;
@@ -426,9 +483,9 @@ int launch_t(sidm_ctx* c, uint64_t seed, uint64_t step, const sidm_xs* xs, const
     c->pair_grid = grid;
     e = cudaMemsetAsync(&c->d_cnt->work[1], 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return cuda_check(c, e, "pair work reset");
-    const int tidx = timer_begin(c, 2, s);
+    const int tidx = MODE == kModeDiag ? -1 : timer_begin(c, 2, s);
     kern<<<grid, warps * 32, smem, s>>>(p);
-    timer_end(c, tidx, s);
+    if (tidx >= 0) timer_end(c, tidx, s);
     c->launches++;
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_check(c, e, "pair launch");
@@ -443,14 +500,22 @@ int launch_pairs(sidm_ctx* c, uint64_t seed, uint64_t step, const sidm_xs* xs, c
     if (c->lay.L == 0) return SIDM_OK;
     const bool tma = c->cfg.use_tma != 0;
     const bool exact = (c->cfg.flags & SIDM_FLAG_SUM_P) != 0;
-#define SIDM_PAIRS_DISPATCH(R)                                                                   \
-    if (exact) return tma ? launch_t<R, true, true>(c, seed, step, xs, dt, mass, st, s)          \
-                          : launch_t<R, false, true>(c, seed, step, xs, dt, mass, st, s);        \
-    return tma ? launch_t<R, true, false>(c, seed, step, xs, dt, mass, st, s)                    \
-               : launch_t<R, false, false>(c, seed, step, xs, dt, mass, st, s);
+#define SIDM_PAIRS_DISPATCH(R)                                                                                   \
+    if (exact) return tma ? launch_t<R, true, kModeDrawExact>(c, seed, step, xs, dt, mass, st, s)                \
+                          : launch_t<R, false, kModeDrawExact>(c, seed, step, xs, dt, mass, st, s);              \
+    return tma ? launch_t<R, true, kModeDraw>(c, seed, step, xs, dt, mass, st, s)                                \
+               : launch_t<R, false, kModeDraw>(c, seed, step, xs, dt, mass, st, s);
     if (c->cfg.precision == SIDM_FP64) { SIDM_PAIRS_DISPATCH(double) }
     SIDM_PAIRS_DISPATCH(float)
 #undef SIDM_PAIRS_DISPATCH
+}
+
+int launch_pairs_diag(sidm_ctx* c, const sidm_xs* xs, const double* mass, cudaStream_t s)
+{
+    if (c->lay.L == 0) return SIDM_OK;
+    if (c->cfg.precision == SIDM_FP64)
+        return launch_t<double, false, kModeDiag>(c, 0, 0, xs, nullptr, mass, c->d_stats_own, s);
+    return launch_t<float, false, kModeDiag>(c, 0, 0, xs, nullptr, mass, c->d_stats_own, s);
 }
 
 }  // namespace sidm

@@ -23,6 +23,7 @@ SIDM_OK, SIDM_EINVAL, SIDM_ECAPACITY, SIDM_ECUDA, SIDM_EROUNDS, SIDM_EDEVICE = 0
 SIDM_DEV_EVENT_OVERFLOW, SIDM_DEV_ROUNDS, SIDM_DEV_STACK, SIDM_DEV_BAD_INPUT, SIDM_DEV_WAIT_TIMEOUT = 1, 2, 4, 8, 16
 SIDM_MIXED, SIDM_FP64 = 0, 1
 SIDM_FLAG_SUM_P = 1
+SIDM_FLAG_LOCAL_DIAG = 4
 SIDM_FLAG_TIMING = 2
 
 XS_DTYPE = np.dtype([("kind", "<i4"), ("pad", "<i4"), ("s0", "<f8"), ("w", "<f8")])
@@ -78,11 +79,12 @@ def load_library():
     L.sidm_kernel_times.argtypes = [vp, vp, vp, i32]
     L.sidm_diagnostics.argtypes = [vp, vp, i32]
     L.sidm_warm_start.argtypes = [vp, i32]
+    L.sidm_local_diagnostics.argtypes = [vp, vp, vp, vp, C.c_double, vp, vp]
     L.sidm_energy_momentum_static.argtypes = [i32, vp, i32, vp, vp, vp, vp, vp]
     for f in ("sidm_create", "sidm_destroy", "sidm_build_cells", "sidm_kernel_sizes", "sidm_scatter_step",
               "sidm_energy_momentum", "sidm_status", "sidm_get_perm", "sidm_neighbours", "sidm_get_events",
               "sidm_lambda_eval", "sidm_drift", "sidm_get_sum_p", "sidm_kernel_times", "sidm_diagnostics",
-              "sidm_energy_momentum_static", "sidm_warm_start"):
+              "sidm_energy_momentum_static", "sidm_warm_start", "sidm_local_diagnostics"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -92,7 +94,7 @@ EXPORTED = ["sidm_create", "sidm_destroy", "sidm_last_error", "sidm_create_error
             "sidm_kernel_sizes", "sidm_scatter_step", "sidm_energy_momentum", "sidm_status", "sidm_get_perm",
             "sidm_neighbours", "sidm_get_events", "sidm_lambda_eval", "sidm_drift", "sidm_get_sum_p",
             "sidm_launch_count", "sidm_kernel_times", "sidm_diagnostics", "sidm_energy_momentum_static",
-            "sidm_warm_start"]
+            "sidm_warm_start", "sidm_local_diagnostics"]
 
 
 def _torch():
@@ -201,6 +203,12 @@ def sidm_energy_momentum_static(halo_off, precision, mass, vel, out, comp=None, 
     if rc != SIDM_OK:
         raise SidmError(rc, {SIDM_EINVAL: "bad argument", SIDM_ECAPACITY: "more chunks than the static scratch holds",
                              SIDM_ECUDA: "CUDA call failed"}.get(rc, "error"))
+
+
+def sidm_local_diagnostics(ctx, xs, mass, vel, G, out, stream=None):
+    """Per-particle rho, nu, sigma_eff/m, h/l, Kn into out ([5][N], f32 or f64 by precision)."""
+    _check(ctx, load_library().sidm_local_diagnostics(ctx, _ptr(xs), _ptr(mass), _ptr(vel), float(G), _ptr(out),
+                                                      _stream(stream)))
 
 
 def sidm_warm_start(ctx, enable=True):
@@ -344,3 +352,9 @@ class Context:
 
     def warm_start(self, enable=True):
         sidm_warm_start(self.handle, enable)
+
+    def local_diagnostics(self, xs, mass, vel, n, G=1.0, stream=None):
+        """dict of per-particle rho, nu, sigma_eff, h_over_l, kn (tensors of the form's precision, current order)."""
+        out = self.torch.empty((5, n), dtype=self.vdtype, device=self.device)
+        sidm_local_diagnostics(self.handle, xs, mass, vel, G, out, stream)
+        return {"rho": out[0], "nu": out[1], "sigma_eff": out[2], "h_over_l": out[3], "kn": out[4]}
