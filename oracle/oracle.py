@@ -76,6 +76,7 @@ def lib():
             L.orc_sigma_eff.argtypes = [i32, d, d, d]; L.orc_sigma_eff.restype = d
             L.orc_local_diag.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, d, i32, i32, d, d, d, vp]
             L.orc_local_diag.restype = i32
+            L.orc_timestep.argtypes = [i32, vp, d, d, d, d, i32, vp, vp]
             L.orc_pairs_halo.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, i32, i32, d, d, d, d,
                                          u64, u64, u32, vp, i64, P(_PairStats), vp, vp]
             L.orc_pairs_halo.restype = i32
@@ -216,6 +217,15 @@ def local_diag(pos, vel, h, mass: float, nngb: int, xs, G: float = 1.0) -> dict:
     lib().orc_local_diag(n, _p(p[0]), _p(p[1]), _p(p[2]), _p(v[0]), _p(v[1]), _p(v[2]), _p(hh), float(mass),
                          int(nngb), int(kind), float(s0), float(w), float(G), _p(out))
     return {"rho": out[0], "nu": out[1], "sigma_eff": out[2], "h_over_l": out[3], "kn": out[4]}
+
+
+def timestep(sum_p, tau: float, dt: float, dt_min: float, dt_max: float, n_bins: int):
+    """SIDM time step per particle from its summed pair probabilities, and its
+    power-of-two bin (see orc_timestep)."""
+    sp = _c(sum_p, np.float64); n = sp.size
+    dto = np.zeros(n); bo = np.zeros(n, np.int32)
+    lib().orc_timestep(n, _p(sp), float(tau), float(dt), float(dt_min), float(dt_max), int(n_bins), _p(dto), _p(bo))
+    return dto, bo
 
 
 def pairs(pos, vel, ids, h, mode, xs, mass, dt, seed, step, halo, ev_cap=None, mask=None):

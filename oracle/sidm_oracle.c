@@ -810,6 +810,30 @@ int orc_local_diag(int n, const double* px, const double* py, const double* pz,
     return 0;
 }
 
+/* ------------------------------------------------------------------------- */
+/* SIDM time-step criterion (Sect. 2: a separate criterion for the self-      */
+/* interactions; tau of the simulation table; Sect. 3.6: a minimum allowed    */
+/* step).  Reading: the step on which the particle's expected number of       */
+/* scatterings, sum_j P_ij for the step dt the sums were formed with, equals  */
+/* tau: dt_i = tau dt / sum_j P_ij, raised to dt_min, capped at dt_max (a     */
+/* particle without partners gets dt_max).  Power-of-two bins: the particle   */
+/* takes the largest step dt_max / 2^b that does not exceed dt_i, b in        */
+/* [0, n_bins - 1] (the smallest bin if even that is too long).               */
+/* ------------------------------------------------------------------------- */
+void orc_timestep(int n, const double* sum_p, double tau, double dt, double dt_min, double dt_max, int n_bins,
+                  double* dt_out, int* bin_out)
+{
+    for (int i = 0; i < n; ++i) {
+        double di = sum_p[i] > 0.0 ? tau * dt / sum_p[i] : dt_max;
+        if (di < dt_min) di = dt_min;
+        if (di > dt_max) di = dt_max;
+        dt_out[i] = di;
+        int b = 0;
+        while (b < n_bins - 1 && ldexp(dt_max, -b) > di) ++b;
+        bin_out[i] = b;
+    }
+}
+
 typedef struct { double* p; int n, cap; } orc_xsum;
 
 static void xsum_add(orc_xsum* s, double x)

@@ -153,3 +153,22 @@ def test_sigma_eff_matches_its_definition():
     assert O.sigma_eff(1, s0, w, 1e-4) == pytest.approx(s0, rel=1e-5)
     nu = 200.0
     assert O.sigma_eff(1, s0, w, nu) == pytest.approx(s0 * (w * w / (4 * nu * nu)) ** 2 * 1.0 / 6.0, rel=1e-3)
+
+
+def test_timestep_criterion_and_bins():
+    # dt_i = tau dt / sum_j P_ij (expected scatterings per step = tau), bounded by
+    # [dt_min, dt_max]; bin b: the largest dt_max / 2^b not above dt_i
+    rng = np.random.default_rng(8)
+    sp = 10.0 ** rng.uniform(-6, 1, 5000)
+    sp[:7] = 0.0
+    tau, dt, dmin, dmax, nb = 0.04, 1e-3, 1e-6, 4e-3, 4
+    dto, bo = O.timestep(sp, tau, dt, dmin, dmax, nb)
+    safe = np.where(sp > 0, sp, 1.0)
+    free = (sp > 0) & (tau * dt / safe > dmin) & (tau * dt / safe < dmax)
+    assert np.all(dto[free] * sp[free] == pytest.approx(tau * dt, rel=1e-14))
+    assert np.all(dto[:7] == dmax) and dto.min() >= dmin and dto.max() <= dmax
+    step = dmax / 2.0 ** bo
+    top = bo < nb - 1
+    assert np.all(step[top] <= dto[top]) and np.all((bo == 0) | (2 * step > dto))
+    # a step longer than the criterion only where no smaller bin exists
+    assert np.all(bo[step > dto] == nb - 1) and np.any(step > dto)
