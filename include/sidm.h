@@ -278,6 +278,28 @@ int sidm_diagnostics(sidm_ctx* ctx, uint64_t* out, int32_t reset);
 int sidm_local_diagnostics(sidm_ctx* ctx, const sidm_xs* xs_dev, const double* mass_dev, const void* vel_dev,
                            double G, void* out_dev, cudaStream_t stream);
 
+/* SIDM time-step criterion (Sect. 2: a separate time-step criterion for the
+ * self-interactions; tau = 0.04 in every SIDM run of the simulation table;
+ * Sect. 3.6: a minimum allowed time step).  From the per-particle sums of the
+ * last sidm_scatter_step (SIDM_FLAG_SUM_P), the step on which the particle
+ * expects tau scatterings:
+ *   dt_i = tau * dt_h / sum_j P_ij, raised to dt_min and capped at dt_max
+ *          (dt_max for a particle without partners),
+ * and its power-of-two bin: the largest dt_max / 2^b not above dt_i,
+ * b in [0, n_bins - 1] (the smallest bin if even that is too long).
+ *   tau, dt_min, dt_max : 0 < tau, 0 <= dt_min <= dt_max, dt_max > 0
+ *   n_bins              : 1..32
+ *   dt_dev              : device f64[n_halos], the dt the sums were formed with
+ *   dt_out_dev          : out, device f64[N] (may be NULL)
+ *   bin_out_dev         : out, device int32[N] (may be NULL)
+ *   dt_halo_min_dev     : out, device f64[n_halos], the smallest dt_i of each
+ *                         halo (dt_max for an empty halo; may be NULL)
+ * Outputs follow the order left by sidm_build_cells.  Requires
+ * SIDM_FLAG_SUM_P at creation and a preceding sidm_scatter_step. */
+int sidm_timestep_criterion(sidm_ctx* ctx, double tau, double dt_min, double dt_max, int32_t n_bins,
+                            const double* dt_dev, double* dt_out_dev, int32_t* bin_out_dev,
+                            double* dt_halo_min_dev, cudaStream_t stream);
+
 /* Warm start of the kernel-size search (enabled by default).  When enabled,
  * sidm_build_cells seeds every particle's search with its kernel size from the
  * last sidm_kernel_sizes call (carried through the permutation, so the

@@ -343,6 +343,36 @@ __global__ void k_leaf_bbox(int L, int64_t N, const int32_t* __restrict__ leaf_h
 }
 
 // Max kernel size per leaf (into lo.w), from the padded h track.
+// SIDM time step and power-of-two bin of every particle from its summed pair
+// probabilities; the halo minimum by an atomic min on order-preserving bits.
+__global__ void k_timestep(int64_t N, int H, const int64_t* __restrict__ halo_off, const float* __restrict__ sump,
+                           const double* __restrict__ dt, double tau, double dt_min, double dt_max, int n_bins,
+                           double* __restrict__ dt_out, int32_t* __restrict__ bin_out,
+                           unsigned long long* __restrict__ halo_min)
+{
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < N; u += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = H - 1;                    // halo of particle u: last h with halo_off[h] <= u
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (halo_off[mid] <= u) lo = mid; else hi = mid - 1;
+        }
+        const double sp = (double)sump[u];
+        double di = sp > 0.0 ? tau * dt[lo] / sp : dt_max;
+        di = fmin(fmax(di, dt_min), dt_max);
+        int b = 0;
+        while (b < n_bins - 1 && ldexp(dt_max, -b) > di) ++b;
+        if (dt_out) dt_out[u] = di;
+        if (bin_out) bin_out[u] = b;
+        if (halo_min) atomicMin(halo_min + lo, dbl_to_ord(di));
+    }
+}
+
+__global__ void k_halo_min_final(int H, const unsigned long long* __restrict__ ord, double dt_max, double* __restrict__ out)
+{
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h < H) out[h] = ord[h] == ~0ull ? dt_max : ord_to_dbl(ord[h]);
+}
+
 // sigma_eff / s0 = (1/6) int_0^inf t^3 e^-t / (1 + beta t)^2 dt, beta = 4 nu^2 / w^2
 // (the Maxwellian average <v^5 sigma(v)> / <v^5> with t = v^2 / (4 nu^2)):
 // 4-point Gauss-Legendre on 48 panels with edges 64 (k/48)^2, which follow the
@@ -899,7 +929,7 @@ static void free_all(sidm_ctx* c)
                     c->d_chunk_halo, c->d_chunk_begin, c->d_frame, c->d_key, c->d_key2, c->d_val, c->d_val2,
                     c->d_hist, c->d_P4, c->d_V4, c->d_ID, c->d_cell, c->d_nlo, c->d_nhi, c->d_perm, c->d_tmp_pos,
                     c->d_tmp_vel, c->d_tmp_id, c->d_claim, c->d_hits, c->d_done, c->d_ev, c->d_sump,
-                    c->d_stats_own, c->d_cnt, c->d_epart, c->d_lam, c->d_hprev, c->d_dacc};
+                    c->d_stats_own, c->d_cnt, c->d_epart, c->d_lam, c->d_hprev, c->d_dacc, c->d_halo_ord};
     for (void* p : ptrs) if (p) cudaFree(p);
     if (c->d_stage) cudaFreeHost(c->d_stage);
     for (cudaEvent_t e : c->t_ev) if (e) cudaEventDestroy(e);
@@ -989,6 +1019,7 @@ extern "C" int sidm_create(sidm_ctx** out, const sidm_config* cfg)
     ALLOC(c->d_stats_own, 1);
     ALLOC(c->d_cnt, 1);
     ALLOC(c->d_epart, 8 * c->chunk_cap);
+    ALLOC(c->d_halo_ord, H);
 #undef ALLOC
     e = cudaMallocHost((void**)&c->d_stage, c->stage_bytes);
     if (e != cudaSuccess) return fail("cudaMallocHost", e);
@@ -1288,6 +1319,30 @@ extern "C" int sidm_scatter_step(sidm_ctx* c, uint64_t seed, uint64_t step, cons
         SIDM_LAUNCH(c, k_resolve<float><<<1, 1024, 0, s>>>(c->d_ev, c->cfg.event_cap, (float*)vel, L.N, mass, c->d_claim,
                                                          c->d_hits, c->d_done, c->d_cnt, st, c->cfg.max_rounds, c->d_sump, use_sump));
     timer_end(c, tr, s);
+    return SIDM_OK;
+}
+
+extern "C" int sidm_timestep_criterion(sidm_ctx* c, double tau, double dt_min, double dt_max, int32_t n_bins,
+                                       const double* dt, double* dt_out, int32_t* bin_out, double* dt_halo_min,
+                                       cudaStream_t s)
+{
+    if (!c) return SIDM_EINVAL;
+    if (!(c->cfg.flags & SIDM_FLAG_SUM_P)) return set_err(c, SIDM_EINVAL, "context built without SIDM_FLAG_SUM_P");
+    if (!c->stepped) return set_err(c, SIDM_EINVAL, "sidm_scatter_step must come first");
+    if (!(tau > 0.0) || !(dt_min >= 0.0) || !(dt_max >= dt_min) || !(dt_max > 0.0))
+        return set_err(c, SIDM_EINVAL, "need 0 < tau and 0 <= dt_min <= dt_max, dt_max > 0");
+    if (n_bins < 1 || n_bins > 32) return set_err(c, SIDM_EINVAL, "n_bins must be in 1..32");
+    if (!dt) return set_err(c, SIDM_EINVAL, "null dt");
+    SIDM_CUDA(c, ensure_device(c));
+    const LayoutHost& L = c->lay;
+    unsigned long long* ord = c->d_halo_ord;
+    if (dt_halo_min) SIDM_CUDA(c, cudaMemsetAsync(ord, 0xFF, sizeof(unsigned long long) * L.H, s));
+    if (L.N > 0)
+        SIDM_LAUNCH(c, k_timestep<<<grid_for(c, L.N, 256), 256, 0, s>>>(L.N, L.H, c->d_halo_off, c->d_sump, dt, tau, dt_min,
+                                                                      dt_max, n_bins, dt_out, bin_out,
+                                                                      dt_halo_min ? ord : nullptr));
+    if (dt_halo_min)
+        SIDM_LAUNCH(c, k_halo_min_final<<<(L.H + 127) / 128, 128, 0, s>>>(L.H, ord, dt_max, dt_halo_min));
     return SIDM_OK;
 }
 

@@ -126,6 +126,7 @@ struct sidm_ctx {
     sidm_event* d_ev = nullptr;             // [event_cap]
     float* d_sump = nullptr;                // [N] (SIDM_FLAG_SUM_P)
     double* d_dacc = nullptr;               // [5][N] kernel-weighted moments (SIDM_FLAG_LOCAL_DIAG)
+    unsigned long long* d_halo_ord = nullptr;  // [H] per-halo minima (order-preserving bits)
     sidm_step_stats* d_stats_own = nullptr; // used when the caller passes NULL
     sidm::DevCounters* d_cnt = nullptr;
 

@@ -80,11 +80,12 @@ def load_library():
     L.sidm_diagnostics.argtypes = [vp, vp, i32]
     L.sidm_warm_start.argtypes = [vp, i32]
     L.sidm_local_diagnostics.argtypes = [vp, vp, vp, vp, C.c_double, vp, vp]
+    L.sidm_timestep_criterion.argtypes = [vp, C.c_double, C.c_double, C.c_double, i32, vp, vp, vp, vp, vp]
     L.sidm_energy_momentum_static.argtypes = [i32, vp, i32, vp, vp, vp, vp, vp]
     for f in ("sidm_create", "sidm_destroy", "sidm_build_cells", "sidm_kernel_sizes", "sidm_scatter_step",
               "sidm_energy_momentum", "sidm_status", "sidm_get_perm", "sidm_neighbours", "sidm_get_events",
               "sidm_lambda_eval", "sidm_drift", "sidm_get_sum_p", "sidm_kernel_times", "sidm_diagnostics",
-              "sidm_energy_momentum_static", "sidm_warm_start", "sidm_local_diagnostics"):
+              "sidm_energy_momentum_static", "sidm_warm_start", "sidm_local_diagnostics", "sidm_timestep_criterion"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -94,7 +95,7 @@ EXPORTED = ["sidm_create", "sidm_destroy", "sidm_last_error", "sidm_create_error
             "sidm_kernel_sizes", "sidm_scatter_step", "sidm_energy_momentum", "sidm_status", "sidm_get_perm",
             "sidm_neighbours", "sidm_get_events", "sidm_lambda_eval", "sidm_drift", "sidm_get_sum_p",
             "sidm_launch_count", "sidm_kernel_times", "sidm_diagnostics", "sidm_energy_momentum_static",
-            "sidm_warm_start", "sidm_local_diagnostics"]
+            "sidm_warm_start", "sidm_local_diagnostics", "sidm_timestep_criterion"]
 
 
 def _torch():
@@ -209,6 +210,14 @@ def sidm_local_diagnostics(ctx, xs, mass, vel, G, out, stream=None):
     """Per-particle rho, nu, sigma_eff/m, h/l, Kn into out ([5][N], f32 or f64 by precision)."""
     _check(ctx, load_library().sidm_local_diagnostics(ctx, _ptr(xs), _ptr(mass), _ptr(vel), float(G), _ptr(out),
                                                       _stream(stream)))
+
+
+def sidm_timestep_criterion(ctx, tau, dt_min, dt_max, n_bins, dt, dt_out=None, bin_out=None, dt_halo_min=None,
+                            stream=None):
+    """SIDM time step and power-of-two bin per particle, smallest step per halo."""
+    _check(ctx, load_library().sidm_timestep_criterion(ctx, float(tau), float(dt_min), float(dt_max), int(n_bins),
+                                                       _ptr(dt), _ptr(dt_out), _ptr(bin_out), _ptr(dt_halo_min),
+                                                       _stream(stream)))
 
 
 def sidm_warm_start(ctx, enable=True):
@@ -352,6 +361,15 @@ class Context:
 
     def warm_start(self, enable=True):
         sidm_warm_start(self.handle, enable)
+
+    def timestep_criterion(self, tau, dt_min, dt_max, n_bins, dt, n, n_halos, stream=None):
+        """(dt f64[n], bin int32[n], smallest dt per halo f64[n_halos]) in the current order."""
+        torch = self.torch
+        dto = torch.empty(n, dtype=torch.float64, device=self.device)
+        bo = torch.empty(n, dtype=torch.int32, device=self.device)
+        hm = torch.empty(n_halos, dtype=torch.float64, device=self.device)
+        sidm_timestep_criterion(self.handle, tau, dt_min, dt_max, n_bins, dt, dto, bo, hm, stream)
+        return dto, bo, hm
 
     def local_diagnostics(self, xs, mass, vel, n, G=1.0, stream=None):
         """dict of per-particle rho, nu, sigma_eff, h_over_l, kn (tensors of the form's precision, current order)."""
