@@ -960,7 +960,7 @@ extern "C" int sidm_create(sidm_ctx** out, const sidm_config* cfg)
     sidm_ctx* c = new sidm_ctx();
     c->cfg = *cfg;
     if (c->cfg.max_rounds <= 0) c->cfg.max_rounds = 256;
-    c->knn_warps = cfg->knn_warps ? cfg->knn_warps : 4;
+    c->knn_warps = cfg->knn_warps ? cfg->knn_warps : 8;
     c->pair_warps = cfg->pair_warps ? cfg->pair_warps : 4;
     auto fail = [&](const std::string& m, cudaError_t e) {
         g_create_err = m + ": " + cudaGetErrorString(e);

@@ -148,10 +148,12 @@ template <class K>
 __host__ __device__ constexpr int heap4_groups(int kcap) { return (kcap + 2) / 4 + 1; }
 
 // pending heap insertions per lane (a tile adds at most 32, so the lists are
-// merged whenever one holds more than kPend - 32 keys), and the pending count
-// at which the lists are merged before a tree node's tests
-constexpr int kPend = 48;
+// merged whenever one holds more than kPend - 32 keys), the pending count at
+// which the lists are merged before a tree node's tests, and the node boxes
+// tested at once (the children of one node; a wider top level in chunks)
+constexpr int kPend = 32;
 constexpr int kFlushNode = 8;
+constexpr int kBoxes = 8;
 // warm start: the search bound is the previous kernel size times this factor
 constexpr float kGuessSlack = 1.0625f;
 
@@ -162,12 +164,13 @@ __device__ __forceinline__ float to_float_ru(R v)
     else return (float)v;
 }
 
-// shared memory of one warp: staged tile | ids | traversal stack | node boxes
-// (32 lo + 32 hi) | heap groups | pending keys
+// shared memory of one warp: staged tile (shifted in place) | ids | traversal
+// stack | node boxes (kBoxes lo + kBoxes hi) | heap groups | pending keys;
+// 14.3 KB at N_ngb = 64 in the mixed form, so 16 warps fit on an SM
 template <class R, class K>
 __host__ __device__ constexpr size_t knn_warp_bytes_t(int kcap)
 {
-    return (TileStageT<R, false>::bytes() + 32 * 4 + kStack * 4 + 64 * 16 +
+    return (TileStageT<R, false, 1>::bytes() + 32 * 4 + kStack * 4 + 2 * kBoxes * 16 +
             (size_t)heap4_groups<K>(kcap) * 32 * 4 * sizeof(K) + (size_t)kPend * 32 * sizeof(K) + 15) / 16 * 16;
 }
 
@@ -179,12 +182,12 @@ __global__ void k_knn(KnnParams p)
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned char* base = smem + wid * knn_warp_bytes_t<R, K>(p.kcap);
-    TileStageT<R, TMA> stage(base);
-    uint32_t* tids = (uint32_t*)(base + TileStageT<R, TMA>::bytes());
+    TileStageT<R, TMA, 1> stage(base);
+    uint32_t* tids = (uint32_t*)(base + TileStageT<R, TMA, 1>::bytes());
     int* stack = (int*)(tids + 32);
-    float4* blo = (float4*)(stack + kStack);       // [32] boxes of the children being tested
-    float4* bhi = blo + 32;
-    K* heapg = (K*)(bhi + 32);
+    float4* blo = (float4*)(stack + kStack);       // [kBoxes] boxes of the children being tested
+    float4* bhi = blo + kBoxes;
+    K* heapg = (K*)(bhi + kBoxes);
     K* pend = heapg + (size_t)heap4_groups<K>(p.kcap) * 32 * 4;   // [kPend][32]
     const Heap4<K> hp{heapg, lane};
     stage.init(lane);
@@ -333,7 +336,7 @@ __global__ void k_knn(KnnParams p)
             r = __fadd_ru(__fmul_ru(r, 1.0f + 0x1p-20f), fr.margin);
             return __fmul_ru(r, r);
         };
-        // boxes of nodes g0 .. g0+n-1 (n <= 32) into the warp's box buffer, one per lane
+        // boxes of nodes g0 .. g0+n-1 (n <= kBoxes) into the warp's box buffer, one per lane
         auto load_boxes = [&](int g0, int n) {
             __syncwarp();
             if (lane < n) { blo[lane] = p.nlo[g0 + lane]; bhi[lane] = p.nhi[g0 + lane]; }
@@ -373,8 +376,10 @@ __global__ void k_knn(KnnParams p)
             }
             return rank;
         };
+        // the warm pass starts from a tight bound, so it takes the accepted
+        // children in index order; the cold pass visits the nearest first
         auto visit_leaves_in_order = [&](uint32_t acc, int n, int first_local) {
-            const int rank = order_rank(acc, n);
+            const int rank = pass == 0 ? __popc(acc & ((1u << lane) - 1u)) : order_rank(acc, n);
             const int cnt = __popc(acc);
             for (int r = 0; r < cnt; ++r) {
                 const uint32_t m = __ballot_sync(0xffffffffu, lane < n && ((acc >> lane) & 1u) && rank == r);
@@ -383,7 +388,7 @@ __global__ void k_knn(KnnParams p)
             }
         };
         auto push_in_order = [&](uint32_t acc, int n, int lev, int first_local, int& sp) -> bool {
-            const int rank = order_rank(acc, n);
+            const int rank = pass == 0 ? __popc(acc & ((1u << lane) - 1u)) : order_rank(acc, n);
             const int cnt = __popc(acc);
             if (sp + cnt > kStack) return false;
             if (lane < n && ((acc >> lane) & 1u)) stack[sp + cnt - 1 - rank] = (lev << 24) | (first_local + lane);
@@ -397,11 +402,14 @@ __global__ void k_knn(KnnParams p)
         int sp = 0;
         {
             const int nb = loff[top * Hp + h];
-            const int ntop = loff[top * Hp + h + 1] - nb;
-            load_boxes(nb, ntop);
-            const uint32_t acc = accept(ntop, my_r2(), top == 0 ? window_mask(0, ntop) : 0u);
-            if (top == 0) visit_leaves_in_order(acc, ntop, 0);
-            else if (!push_in_order(acc, ntop, top, 0, sp)) failed = true;
+            const int ntop = loff[top * Hp + h + 1] - nb;   // at most 32
+            for (int c0 = 0; c0 < ntop && !failed; c0 += kBoxes) {
+                const int n = min(kBoxes, ntop - c0);
+                load_boxes(nb + c0, n);
+                const uint32_t acc = accept(n, my_r2(), top == 0 ? window_mask(c0, n) : 0u);
+                if (top == 0) visit_leaves_in_order(acc, n, c0);
+                else if (!push_in_order(acc, n, top, c0, sp)) failed = true;
+            }
         }
         while (sp > 0 && !failed) {
             const int e = stack[--sp];
@@ -480,7 +488,10 @@ int launch_t(sidm_ctx* c, void* h_out, uint32_t* nbr, int k_stride, bool use_gue
     p.hprev = NBR ? nullptr : c->d_hprev;
     p.use_guess = use_guess ? 1 : 0;
     p.slack = kGuessSlack;
-    const int warps = c->knn_warps;
+    // the configured warps per CTA, halved while a CTA would exceed the 227 KB
+    // of shared memory one block may use (large N_ngb in the FP64 form)
+    int warps = c->knn_warps;
+    while (warps > 1 && (size_t)warps * knn_warp_bytes_t<R, K>(p.kcap) > (size_t)227 * 1024) warps /= 2;
     const size_t smem = (size_t)warps * knn_warp_bytes_t<R, K>(p.kcap);
     auto kern = k_knn<R, NBR, TMA>;
     int occ = 0;

@@ -36,17 +36,19 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p)
 
 constexpr unsigned kWaitLimit = 1u << 22;
 
-template <class R, bool TMA>
+// NBUF = 2: the staged tile and a second buffer for its shifted copy;
+// NBUF = 1: the caller shifts the tile in place (each lane its own entry).
+template <class R, bool TMA, int NBUF = 2>
 struct TileStageT {
     using V = typename Vec4<R>::T;
-    static constexpr size_t bytes() { return 2 * 32 * sizeof(V) + 16; }
+    static constexpr size_t bytes() { return NBUF * 32 * sizeof(V) + 16; }
     unsigned char* base;
     uint32_t phase;
     bool timed_out;
     __device__ explicit TileStageT(unsigned char* b) : base(b), phase(0u), timed_out(false) {}
     __device__ V* raw() const { return (V*)base; }
-    __device__ V* shifted() const { return (V*)(base + 32 * sizeof(V)); }
-    __device__ unsigned long long* bar() const { return (unsigned long long*)(base + 2 * 32 * sizeof(V)); }
+    __device__ V* shifted() const { return (V*)(base + (NBUF - 1) * 32 * sizeof(V)); }
+    __device__ unsigned long long* bar() const { return (unsigned long long*)(base + NBUF * 32 * sizeof(V)); }
 
     __device__ void init(int lane)
     {
