@@ -203,6 +203,26 @@ __device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint3
     return o;
 }
 
+// The same block with the round keys given (rk[2r], rk[2r+1] = key + r * Weyl
+// pair, mod 2^32); a launch passes them as kernel parameters, so a round is the
+// two products and two three-way xors.
+__device__ __forceinline__ Philox4 philox4x32_10_rk(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                    const uint32_t* rk)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c0;
+        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c2;
+        const uint32_t lo0 = (uint32_t)p0, hi0 = (uint32_t)(p0 >> 32);
+        const uint32_t lo1 = (uint32_t)p1, hi1 = (uint32_t)(p1 >> 32);
+        const uint32_t y0 = hi1 ^ c1 ^ rk[2 * r];
+        const uint32_t y2 = hi0 ^ c3 ^ rk[2 * r + 1];
+        c0 = y0; c1 = lo1; c2 = y2; c3 = lo0;
+    }
+    Philox4 o; o.x[0] = c0; o.x[1] = c1; o.x[2] = c2; o.x[3] = c3;
+    return o;
+}
+
 // Lagrange cubic weights on nodes 0..3 at parameter t.
 template <class R>
 __device__ __forceinline__ void lagrange4(R t, R w[4])

@@ -40,6 +40,7 @@ struct PairParams {
     const double* dt;
     const double* mass;
     uint32_t seed_lo, seed_hi, step_lo;
+    uint32_t rk[20];    // Philox round keys of the seed
     sidm_event* ev;
     unsigned long long ev_cap;
     float* sump;
@@ -212,13 +213,12 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
                 const int e = (qhead + lane) & (kQueue - 1);
                 const uint32_t si = q_si[e], sj = q_sj[e];
                 const V vi = V4[si], vj = V4[sj];
-                const V pi = P4[si], pj = P4[sj];
-                const R hi = pi.w, hj = pj.w;
+                const R hi = ((const R*)(P4 + si))[3], hj = ((const R*)(P4 + sj))[3];
                 const R ux = vj.x - vi.x, uy = vj.y - vi.y, uz = vj.z - vi.z;
                 const R v2 = ux * ux + uy * uy + uz * uz;
                 const uint32_t ida = id_of<R>(vi.w), idb = id_of<R>(vj.w);
                 const uint32_t a = min(ida, idb), b = max(ida, idb);
-                const Philox4 x = philox4x32_10(p.step_lo, a, b, (uint32_t)h, p.seed_lo, p.seed_hi);
+                const Philox4 x = philox4x32_10_rk(p.step_lo, a, b, (uint32_t)h, p.rk);
                 R P, pre, inv, u;
                 bool need;
                 if constexpr (sizeof(R) == 4) {
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
                 bool fire = false;
                 if (need) {
                     ++n_lam;
-                    const R d2 = pair_d2(si, sj, pi, pj);
+                    const R d2 = pair_d2(si, sj, P4[si], P4[sj]);
                     R f;
                     if constexpr (sizeof(R) == 4) {
                         const float d = d2 > 0.f ? d2 * rsqrtf(d2) : 0.f;
@@ -466,6 +466,10 @@ int launch_t(sidm_ctx* c, uint64_t seed, uint64_t step, const sidm_xs* xs, const
     p.nlo = c->d_nlo; p.nhi = c->d_nhi; p.P4 = c->d_P4; p.V4 = c->d_V4; p.lam = c->d_lam;
     p.xs = xs; p.dt = dt; p.mass = mass;
     p.seed_lo = (uint32_t)seed; p.seed_hi = (uint32_t)(seed >> 32); p.step_lo = (uint32_t)step;
+    for (int r = 0; r < 10; ++r) {
+        p.rk[2 * r] = p.seed_lo + (uint32_t)r * 0x9E3779B9u;
+        p.rk[2 * r + 1] = p.seed_hi + (uint32_t)r * 0xBB67AE85u;
+    }
     p.ev = c->d_ev; p.ev_cap = (unsigned long long)c->cfg.event_cap;
     p.sump = c->d_sump; p.use_sump = (c->cfg.flags & SIDM_FLAG_SUM_P) ? 1 : 0;
     p.dacc = c->d_dacc; p.nacc = L.N;
