@@ -78,7 +78,10 @@ def lib():
             L.orc_local_diag.restype = i32
             L.orc_timestep.argtypes = [i32, vp, d, d, d, d, i32, vp, vp]
             L.orc_pairs_halo.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, i32, i32, d, d, d, d,
-                                         u64, u64, u32, vp, i64, P(_PairStats), vp, vp]
+                                         u64, u64, u32, vp, i64, P(_PairStats), vp, vp, vp, i32, i32, d]
+            L.orc_host_mass.argtypes = [d, d, d]; L.orc_host_mass.restype = d
+            L.orc_host_phi.argtypes = [d, d, d, d]; L.orc_host_phi.restype = d
+            L.orc_host_kick.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, i32, d, d, d, d, d, d, d]
             L.orc_pairs_halo.restype = i32
             L.orc_sort_events.argtypes = [vp, i64]
             L.orc_apply_events.argtypes = [vp, i64, vp, vp, vp, vp, vp]
@@ -228,8 +231,35 @@ def timestep(sum_p, tau: float, dt: float, dt_min: float, dt_max: float, n_bins:
     return dto, bo
 
 
-def pairs(pos, vel, ids, h, mode, xs, mass, dt, seed, step, halo, ev_cap=None, mask=None):
+def host_mass(r, Mn, Rs):
+    return float(lib().orc_host_mass(float(r), float(Mn), float(Rs)))
+
+
+def host_phi(r, G, Mn, Rs):
+    return float(lib().orc_host_phi(float(r), float(G), float(Mn), float(Rs)))
+
+
+def host_kick(pos, vel, host, dt_max, bins=None, n_bins=1, substep=0, phase=0):
+    """Half kick of the particles due at this sub-step (see orc_host_kick); returns new vel.
+
+    host = (G, M_n, R_s, (cx, cy, cz))."""
+    p = _c(pos, np.float64); v = np.array(vel, dtype=np.float64, copy=True, order="C"); n = p.shape[1]
+    bn = None if bins is None else _c(bins, np.int32)
+    G, Mn, Rs, c = host
+    lib().orc_host_kick(n, _p(p[0]), _p(p[1]), _p(p[2]), _p(v[0]), _p(v[1]), _p(v[2]), _p(bn), int(n_bins),
+                        int(substep), int(phase), float(dt_max), float(G), float(Mn), float(Rs),
+                        float(c[0]), float(c[1]), float(c[2]))
+    return v
+
+
+def pairs(pos, vel, ids, h, mode, xs, mass, dt, seed, step, halo, ev_cap=None, mask=None, bins=None,
+          n_bins=1, substep=0, dt_max=0.0):
     """Pair probabilities and draws of one halo.
+
+    bins (int [n], optional): individual power-of-two steps; only pairs whose
+    particles both open a step at `substep` are evaluated, on the longer step
+    dt_max / 2^min(b_i, b_j) (dt is then unused); sum_p then holds the sums of
+    P scaled to dt_max.
 
     xs = (kind, s0, w).  Returns (events [EVENT_DTYPE], stats dict, sum_p[n]).
     Event indices are local (halo) input indices; i has the smaller id.
@@ -242,12 +272,13 @@ def pairs(pos, vel, ids, h, mode, xs, mass, dt, seed, step, halo, ev_cap=None, m
     ev = np.zeros(cap, EVENT_DTYPE)
     st = _PairStats(); sump = np.zeros(n)
     pm = None if mask is None else _c(mask, np.uint8)
+    bn = None if bins is None else _c(bins, np.int32)
     kind, s0, w = xs
     rc = lib().orc_pairs_halo(n, _p(p[0]), _p(p[1]), _p(p[2]), _p(v[0]), _p(v[1]), _p(v[2]),
                               _p(idv), _p(hh), int(mode), int(kind), float(s0), float(w),
                               float(mass), float(dt), C.c_uint64(int(seed)), C.c_uint64(int(step)),
                               C.c_uint32(int(halo)), _p(ev), cap, C.byref(st), _p(sump),
-                              _p(pm))
+                              _p(pm), _p(bn), int(n_bins), int(substep), float(dt_max))
     if rc != 0:
         raise RuntimeError(f"oracle pair pass failed ({rc}): event buffer too small")
     ne = int(st.n_events)

@@ -572,13 +572,18 @@ typedef struct {
     double max_sum_p;
 } orc_pair_stats;
 
+/* Individual power-of-two time steps: a particle in bin b (step dt_max / 2^b)
+ * opens a step at sub-step s (of 2^(n_bins-1) sub-steps of the smallest bin)
+ * iff s is a multiple of 2^(n_bins-1-b). */
+static int orc_step_opens(int b, int n_bins, int s) { return (s % (1 << (n_bins - 1 - b))) == 0; }
+
 int orc_pairs_halo(int n, const double* px, const double* py, const double* pz,
                    const double* vx, const double* vy, const double* vz,
                    const uint32_t* ids, const double* h, int mode,
                    int xs_kind, double s0, double w, double mass, double dt,
                    uint64_t seed, uint64_t step, uint32_t halo,
                    orc_event* ev_out, int64_t ev_cap, orc_pair_stats* st, double* sum_p_out,
-                   const uint8_t* pair_mask)
+                   const uint8_t* pair_mask, const int* bins, int n_bins, int substep, double dt_max)
 {
     orc_geom g; memset(&g, 0, sizeof(g));
     if (mode == 0) geom_build(&g, n, px, py, pz);
@@ -610,6 +615,14 @@ int orc_pairs_halo(int n, const double* px, const double* py, const double* pz,
                     if (j == i) continue;
                     if (!(h[i] > h[j] || (h[i] == h[j] && i < j))) continue;
                     if (pair_mask && !pair_mask[i] && !pair_mask[j]) continue;
+                    /* individual steps: only pairs whose particles both start a step at
+                     * this sub-step, on the longer of the two steps */
+                    double dtp = dt;
+                    if (bins) {
+                        if (!orc_step_opens(bins[i], n_bins, substep) || !orc_step_opens(bins[j], n_bins, substep))
+                            continue;
+                        dtp = ldexp(dt_max, -(bins[i] < bins[j] ? bins[i] : bins[j]));
+                    }
                     int inr;
                     if (mode == 0) {
                         int Ai = (int)(g.rank[i] / ORC_LEAF), Aj = (int)(g.rank[j] / ORC_LEAF);
@@ -629,7 +642,9 @@ int orc_pairs_halo(int n, const double* px, const double* py, const double* pz,
                     double lam = orc_lambda(d, h[i], h[j]);
                     double ux = vx[i] - vx[j], uy = vy[i] - vy[j], uz = vz[i] - vz[j];
                     double v = sqrt(ux * ux + uy * uy + uz * uz);
-                    double P = orc_sigma(xs_kind, s0, w, v) * mass * v * lam * dt;
+                    double P = orc_sigma(xs_kind, s0, w, v) * mass * v * lam * dtp;
+                    /* sums of P per particle, on individual steps scaled to dt_max (a rate) */
+                    const double Psum = bins ? P * (dt_max / dtp) : P;
                     uint32_t a = ids[i] < ids[j] ? ids[i] : ids[j];
                     uint32_t b = ids[i] < ids[j] ? ids[j] : ids[i];
                     uint32_t ctr[4] = {(uint32_t)step, a, b, halo}, x[4];
@@ -638,9 +653,9 @@ int orc_pairs_halo(int n, const double* px, const double* py, const double* pz,
                     if (P > 1.0) n_gt1++;
                     if (fabs(P - u) < 1e-6) n_near++;
                     #pragma omp atomic
-                    sump[i] += P;
+                    sump[i] += Psum;
                     #pragma omp atomic
-                    sump[j] += P;
+                    sump[j] += Psum;
                     if (u < P) {
                         int64_t slot;
                         #pragma omp atomic capture
@@ -831,6 +846,45 @@ void orc_timestep(int n, const double* sum_p, double tau, double dt, double dt_m
         int b = 0;
         while (b < n_bins - 1 && ldexp(dt_max, -b) > di) ++b;
         bin_out[i] = b;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Satellite in a fixed analytic host (Sect. 4.1 evolves the satellite in an  */
+/* external potential; here an NFW host, reading of the set-up):             */
+/*   M(<r) = M_n [ln(1 + x) - x / (1 + x)], x = r / R_s,                      */
+/*   Phi(r) = -G M_n ln(1 + x) / r,  a = -G M(<r) (x_vec - c) / r^3.          */
+/* Kick-drift-kick with individual power-of-two steps: at sub-step s a        */
+/* particle of bin b gets the opening half kick dt_b / 2 when its step opens  */
+/* at s (phase 0), the closing half kick after the drift of s when its step   */
+/* closes at s + 1 (phase 1); dt_b = dt_max / 2^b.                            */
+/* ------------------------------------------------------------------------- */
+double orc_host_mass(double r, double Mn, double Rs)
+{
+    const double x = r / Rs;
+    return Mn * (log1p(x) - x / (1.0 + x));
+}
+
+double orc_host_phi(double r, double G, double Mn, double Rs)
+{
+    if (r == 0.0) return -G * Mn / Rs;
+    return -G * Mn * log1p(r / Rs) / r;
+}
+
+void orc_host_kick(int n, const double* px, const double* py, const double* pz, double* vx, double* vy, double* vz,
+                   const int* bins, int n_bins, int substep, int phase, double dt_max,
+                   double G, double Mn, double Rs, double cx, double cy, double cz)
+{
+    for (int i = 0; i < n; ++i) {
+        const int b = bins ? bins[i] : 0;
+        const int period = 1 << (n_bins - 1 - b);
+        const int due = phase == 0 ? (substep % period == 0) : ((substep + 1) % period == 0);
+        if (!due) continue;
+        const double dx = px[i] - cx, dy = py[i] - cy, dz = pz[i] - cz;
+        const double r = sqrt(dx * dx + dy * dy + dz * dz);
+        if (r == 0.0) continue;
+        const double f = -G * orc_host_mass(r, Mn, Rs) / (r * r * r) * (0.5 * ldexp(dt_max, -b));
+        vx[i] += f * dx; vy[i] += f * dy; vz[i] += f * dz;
     }
 }
 
