@@ -92,6 +92,16 @@ typedef struct {
     double w;
 } sidm_xs;
 
+/* A fixed analytic NFW host (Sect. 4.1 evolves the satellite in an external
+ * potential): M(<r) = M_n [ln(1 + r/R_s) - (r/R_s)/(1 + r/R_s)] about center,
+ * acceleration -G M(<r) (x - center) / r^3.  Code units. */
+typedef struct {
+    double G;
+    double M_n;
+    double R_s;
+    double center[3];
+} sidm_host;
+
 /* Per-step statistics, written by sidm_scatter_step (device memory). */
 typedef struct {
     unsigned long long n_pairs;   /* in-range pairs whose P was formed            */
@@ -277,6 +287,37 @@ int sidm_diagnostics(sidm_ctx* ctx, uint64_t* out, int32_t reset);
  * differ between runs. */
 int sidm_local_diagnostics(sidm_ctx* ctx, const sidm_xs* xs_dev, const double* mass_dev, const void* vel_dev,
                            double G, void* out_dev, cudaStream_t stream);
+
+/* Scatter step on individual power-of-two time steps (the individual time
+ * steps of Sect. 3.1).  Particle u of bin b = bin_dev[u] has the step
+ * dt_max / 2^b; the 2^(n_bins-1) sub-steps of a big step dt_max are numbered
+ * 0 .., and bin b opens a step at sub-step s iff s is a multiple of
+ * 2^(n_bins-1-b).  At sub-step `substep` only pairs whose particles both open
+ * a step are tested, with P formed on the longer of the two steps,
+ * dt_max / 2^min(b_i, b_j); everything else is sidm_scatter_step.  Under
+ * SIDM_FLAG_SUM_P the per-particle sums hold P scaled to dt_max (a rate times
+ * dt_max), so sidm_timestep_criterion takes dt_max as the step of every halo.
+ *   dt_max    : the longest step (bin 0), > 0
+ *   n_bins    : 1..16;  substep : 0 .. 2^(n_bins-1) - 1
+ *   bin_dev   : device int32[N], bins in 0 .. n_bins-1, in the order left by
+ *               sidm_build_cells (the caller permutes its bins with the
+ *               particles, e.g. through sidm_get_perm)
+ * Other arguments and behaviour as sidm_scatter_step. */
+int sidm_scatter_step_binned(sidm_ctx* ctx, uint64_t seed, uint64_t step, const sidm_xs* xs_dev, double dt_max,
+                             int32_t n_bins, int32_t substep, const int32_t* bin_dev, const double* mass_dev,
+                             void* vel_dev, sidm_step_stats* stats_dev, cudaStream_t stream);
+
+/* Kick by the analytic host (kick-drift-kick on individual steps): every
+ * particle whose step opens at sub-step `substep` (phase 0, before the drift)
+ * or closes after it (phase 1, after the drift of that sub-step) gets
+ * v += a(x) dt_b / 2, dt_b = dt_max / 2^b, with the acceleration of `host`
+ * evaluated in FP64 at its FP64 position.
+ *   host      : host-memory sidm_host
+ *   bin_dev   : device int32[N] or NULL (every particle in bin 0)
+ *   pos_dev   : f64 [3][N];  vel_dev : [3][N] f32 or f64 by precision, updated
+ * Arrays in the order left by sidm_build_cells (which must come first). */
+int sidm_host_kick(sidm_ctx* ctx, const sidm_host* host, double dt_max, int32_t n_bins, int32_t substep,
+                   int32_t phase, const int32_t* bin_dev, const double* pos_dev, void* vel_dev, cudaStream_t stream);
 
 /* SIDM time-step criterion (Sect. 2: a separate time-step criterion for the
  * self-interactions; tau = 0.04 in every SIDM run of the simulation table;

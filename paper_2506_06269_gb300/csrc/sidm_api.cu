@@ -1287,12 +1287,9 @@ extern "C" int sidm_neighbours(sidm_ctx* c, const int32_t* n_ngb, int32_t k_stri
     return launch_knn(c, nullptr, nbr, k_stride, false, s);
 }
 
-extern "C" int sidm_scatter_step(sidm_ctx* c, uint64_t seed, uint64_t step, const sidm_xs* xs, const double* dt,
-                                 const double* mass, void* vel, sidm_step_stats* stats, cudaStream_t s)
+static int scatter_impl(sidm_ctx* c, uint64_t seed, uint64_t step, const sidm_xs* xs, const double* dt,
+                        const double* mass, void* vel, sidm_step_stats* stats, cudaStream_t s)
 {
-    if (!c) return SIDM_EINVAL;
-    if (!c->sized) return set_err(c, SIDM_EINVAL, "sidm_kernel_sizes must come first");
-    if (!xs || !dt || !mass || (!vel && c->lay.N > 0)) return set_err(c, SIDM_EINVAL, "null argument");
     SIDM_CUDA(c, ensure_device(c));
     const LayoutHost& L = c->lay;
     sidm_step_stats* st = stats ? stats : c->d_stats_own;
@@ -1376,6 +1373,83 @@ extern "C" int sidm_local_diagnostics(sidm_ctx* c, const sidm_xs* xs, const doub
         SIDM_LAUNCH(c, k_diag_final<float><<<blocks, 256, 0, s>>>(L.L, c->d_leaf_halo, c->d_leaf_off, c->d_halo_off,
                                                                   (const float4*)c->d_P4, (const float4*)c->d_V4,
                                                                   c->d_dacc, L.N, mass, xs, c->d_ngb, G, (float*)out));
+    return SIDM_OK;
+}
+
+extern "C" int sidm_scatter_step(sidm_ctx* c, uint64_t seed, uint64_t step, const sidm_xs* xs, const double* dt,
+                                 const double* mass, void* vel, sidm_step_stats* stats, cudaStream_t s)
+{
+    if (!c) return SIDM_EINVAL;
+    if (!c->sized) return set_err(c, SIDM_EINVAL, "sidm_kernel_sizes must come first");
+    if (!xs || !dt || !mass || (!vel && c->lay.N > 0)) return set_err(c, SIDM_EINVAL, "null argument");
+    c->step_bins = nullptr;
+    return scatter_impl(c, seed, step, xs, dt, mass, vel, stats, s);
+}
+
+extern "C" int sidm_scatter_step_binned(sidm_ctx* c, uint64_t seed, uint64_t step, const sidm_xs* xs, double dt_max,
+                                        int32_t n_bins, int32_t substep, const int32_t* bins, const double* mass,
+                                        void* vel, sidm_step_stats* stats, cudaStream_t s)
+{
+    if (!c) return SIDM_EINVAL;
+    if (!c->sized) return set_err(c, SIDM_EINVAL, "sidm_kernel_sizes must come first");
+    if (!xs || !mass || ((!vel || !bins) && c->lay.N > 0)) return set_err(c, SIDM_EINVAL, "null argument");
+    if (n_bins < 1 || n_bins > 16) return set_err(c, SIDM_EINVAL, "n_bins must be in 1..16");
+    if (substep < 0 || substep >= (1 << (n_bins - 1))) return set_err(c, SIDM_EINVAL, "substep out of range");
+    if (!(dt_max > 0.0)) return set_err(c, SIDM_EINVAL, "dt_max must be positive");
+    c->step_bins = bins;
+    c->step_nbins = n_bins;
+    c->step_sub = substep;
+    c->step_dtmax = dt_max;
+    const int rc = scatter_impl(c, seed, step, xs, nullptr, mass, vel, stats, s);
+    c->step_bins = nullptr;
+    return rc;
+}
+
+// Half kick by the analytic NFW host for the particles whose individual step
+// opens (phase 0) or closes (phase 1) at this sub-step; FP64 acceleration.
+template <class R>
+__global__ void k_host_kick(int64_t N, const double* __restrict__ pos, R* __restrict__ vel,
+                            const int32_t* __restrict__ bins, int n_bins, int substep, int phase, double dt_max,
+                            double G, double Mn, double Rs, double cx, double cy, double cz)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int b = bins ? bins[i] : 0;
+        const int period = 1 << (n_bins - 1 - b);
+        const bool due = phase == 0 ? (substep % period == 0) : ((substep + 1) % period == 0);
+        if (!due) continue;
+        const double dx = pos[i] - cx, dy = pos[N + i] - cy, dz = pos[2 * N + i] - cz;
+        const double r = sqrt(dx * dx + dy * dy + dz * dz);
+        if (r == 0.0) continue;
+        const double x = r / Rs;
+        const double m = Mn * (log1p(x) - x / (1.0 + x));
+        const double f = -G * m / (r * r * r) * (0.5 * ldexp(dt_max, -b));
+        vel[i] = (R)((double)vel[i] + f * dx);
+        vel[N + i] = (R)((double)vel[N + i] + f * dy);
+        vel[2 * N + i] = (R)((double)vel[2 * N + i] + f * dz);
+    }
+}
+
+extern "C" int sidm_host_kick(sidm_ctx* c, const sidm_host* host, double dt_max, int32_t n_bins, int32_t substep,
+                              int32_t phase, const int32_t* bins, const double* pos, void* vel, cudaStream_t s)
+{
+    if (!c) return SIDM_EINVAL;
+    if (!c->has_layout) return set_err(c, SIDM_EINVAL, "sidm_build_cells must come first");
+    if (!host || ((!pos || !vel) && c->lay.N > 0)) return set_err(c, SIDM_EINVAL, "null argument");
+    if (n_bins < 1 || n_bins > 16) return set_err(c, SIDM_EINVAL, "n_bins must be in 1..16");
+    if (substep < 0 || substep >= (1 << (n_bins - 1))) return set_err(c, SIDM_EINVAL, "substep out of range");
+    if (phase != 0 && phase != 1) return set_err(c, SIDM_EINVAL, "phase must be 0 (opening) or 1 (closing)");
+    if (!(dt_max > 0.0) || !(host->M_n >= 0.0) || !(host->R_s > 0.0)) return set_err(c, SIDM_EINVAL, "bad host or dt_max");
+    SIDM_CUDA(c, ensure_device(c));
+    const int64_t N = c->lay.N;
+    if (N == 0) return SIDM_OK;
+    if (c->cfg.precision == SIDM_FP64)
+        SIDM_LAUNCH(c, k_host_kick<double><<<grid_for(c, N, 256), 256, 0, s>>>(N, pos, (double*)vel, bins, n_bins, substep,
+                                                                              phase, dt_max, host->G, host->M_n, host->R_s,
+                                                                              host->center[0], host->center[1], host->center[2]));
+    else
+        SIDM_LAUNCH(c, k_host_kick<float><<<grid_for(c, N, 256), 256, 0, s>>>(N, pos, (float*)vel, bins, n_bins, substep,
+                                                                             phase, dt_max, host->G, host->M_n, host->R_s,
+                                                                             host->center[0], host->center[1], host->center[2]));
     return SIDM_OK;
 }
 

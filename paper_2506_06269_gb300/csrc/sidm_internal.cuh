@@ -127,6 +127,12 @@ struct sidm_ctx {
     float* d_sump = nullptr;                // [N] (SIDM_FLAG_SUM_P)
     double* d_dacc = nullptr;               // [5][N] kernel-weighted moments (SIDM_FLAG_LOCAL_DIAG)
     unsigned long long* d_halo_ord = nullptr;  // [H] per-halo minima (order-preserving bits)
+
+    // individual time steps of the scatter step in flight (set by
+    // sidm_scatter_step_binned for one launch, NULL otherwise)
+    const int32_t* step_bins = nullptr;
+    int step_nbins = 1, step_sub = 0;
+    double step_dtmax = 0.0;
     sidm_step_stats* d_stats_own = nullptr; // used when the caller passes NULL
     sidm::DevCounters* d_cnt = nullptr;
 

@@ -41,6 +41,9 @@ struct PairParams {
     const double* mass;
     uint32_t seed_lo, seed_hi, step_lo;
     uint32_t rk[20];    // Philox round keys of the seed
+    const int32_t* bins;  // individual power-of-two steps (NULL: one step dt[h] for all)
+    int n_bins, substep;
+    double dt_max;
     sidm_event* ev;
     unsigned long long ev_cap;
     float* sump;
@@ -75,6 +78,14 @@ __device__ __forceinline__ uint32_t id_of(R w)
 {
     if constexpr (sizeof(R) == 4) return __float_as_uint((float)w);
     else return (uint32_t)(double)w;
+}
+
+// individual power-of-two steps: a particle of bin b (step dt_max / 2^b) opens a
+// step at sub-step s of the 2^(n_bins-1) sub-steps of the smallest bin iff s is
+// a multiple of 2^(n_bins-1-b)
+__device__ __forceinline__ bool step_opens(int b, int n_bins, int s)
+{
+    return (s & ((1 << (n_bins - 1 - b)) - 1)) == 0;
 }
 
 // position of the r-th (0-based) set bit of m (m has more than r set bits)
@@ -148,12 +159,16 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
         const int64_t slot2u = hb - (int64_t)leaf0 * kLeaf;   // padded slot -> particle index
         const int A = leaf - leaf0;
         const int countA = (int)min((int64_t)kLeaf, nh - (int64_t)A * kLeaf);
-        const bool active = lane < countA;
+        // with individual steps only particles whose step opens at this sub-step
+        // take part; a leaf without such a particle has no pair to test
+        const bool active = lane < countA &&
+                            (!p.bins || step_opens(p.bins[hb + (int64_t)A * kLeaf + lane], p.n_bins, p.substep));
+        if (p.bins && !__any_sync(0xffffffffu, active)) continue;
         const HaloFrame fr = p.frame[h];
         const float4 cA = p.cell[leaf];
         const sidm_xs xs = p.xs[h];
         const int kind = xs.kind;
-        const R pref = (R)xs.s0 * (R)p.mass[h] * (R)p.dt[h];
+        const R pref = p.bins ? R(0) : (R)xs.s0 * (R)p.mass[h] * (R)p.dt[h];
         const R inv_w = kind == 1 ? R(1) / (R)xs.w : R(0);
         const float4 qlo = p.nlo[leaf], qhi = p.nhi[leaf];
         const float hmaxA = qlo.w;
@@ -219,6 +234,13 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
                 const uint32_t ida = id_of<R>(vi.w), idb = id_of<R>(vj.w);
                 const uint32_t a = min(ida, idb), b = max(ida, idb);
                 const Philox4 x = philox4x32_10_rk(p.step_lo, a, b, (uint32_t)h, p.rk);
+                // individual steps: the pair's longer step dt_max / 2^min(b_i, b_j)
+                R prefp = pref;
+                int bmin = 0;
+                if (p.bins) {
+                    bmin = min(p.bins[slot2u + si], p.bins[slot2u + sj]);
+                    prefp = (R)xs.s0 * (R)p.mass[h] * (R)ldexp(p.dt_max, -bmin);
+                }
                 R P, pre, inv, u;
                 bool need;
                 if constexpr (sizeof(R) == 4) {
@@ -228,14 +250,14 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
                     const float v = v2 > 0.f ? v2 * rsqrtf(v2) : 0.f;
                     float sig = 1.f;
                     if (kind == 1) { const float qq = v * inv_w; const float tt = 1.f + qq * qq; sig = __fdividef(1.f, tt * tt); }
-                    pre = pref * sig * v;
+                    pre = prefp * sig * v;
                     inv = __fdividef(1.f, fmaxf(hi, hj));
                     u = (R)((float)x.x[0] * 0x1p-32f);
                 } else {
                     const R v = sqrt(v2);
                     R sig = R(1);
                     if (kind == 1) { const R qq = v * inv_w; const R tt = R(1) + qq * qq; sig = R(1) / (tt * tt); }
-                    pre = pref * sig * v;
+                    pre = prefp * sig * v;
                     inv = R(1) / (hi > hj ? hi : hj);
                     u = (R)ldexp((double)x.x[0], -32);
                 }
@@ -266,8 +288,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
                 const int64_t ui = slot2u + si, uj = slot2u + sj;
                 if constexpr (MODE == kModeDrawExact) {
                     if (p.use_sump) {
-                        atomicAdd(p.sump + ui, (float)P);
-                        atomicAdd(p.sump + uj, (float)P);
+                        // on individual steps a rate, scaled to dt_max (exact power of two)
+                        const float ps = (float)(p.bins ? P * (R)ldexp(1.0, bmin) : P);
+                        atomicAdd(p.sump + ui, ps);
+                        atomicAdd(p.sump + uj, ps);
                     }
                 }
                 if (fire) {
@@ -316,7 +340,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
                                  __double2float_rn((double)c.z - fr.O[2]));
             }
             const float rc = __fadd_ru(__fmul_ru(__fadd_ru(to_float_ru_p<R>(c.w), hmaxA), 1.0f + 0x1p-20f), fr.margin);
-            const uint32_t cmask = __ballot_sync(0xffffffffu, lane < countB && point_gap2_rd(pc, qlo, qhi) <= __fmul_ru(rc, rc));
+            const uint32_t cmask = __ballot_sync(
+                0xffffffffu, lane < countB && point_gap2_rd(pc, qlo, qhi) <= __fmul_ru(rc, rc) &&
+                                 (!p.bins || step_opens(p.bins[hb + (int64_t)Bl * kLeaf + lane], p.n_bins, p.substep)));
             // (i) in-range bits of this lane's query against every candidate of the
             //     warp-uniform mask: straight-line arithmetic, no vote per candidate
             uint32_t okm = 0u;
@@ -473,6 +499,7 @@ int launch_t(sidm_ctx* c, uint64_t seed, uint64_t step, const sidm_xs* xs, const
     p.ev = c->d_ev; p.ev_cap = (unsigned long long)c->cfg.event_cap;
     p.sump = c->d_sump; p.use_sump = (c->cfg.flags & SIDM_FLAG_SUM_P) ? 1 : 0;
     p.dacc = c->d_dacc; p.nacc = L.N;
+    p.bins = c->step_bins; p.n_bins = c->step_nbins; p.substep = c->step_sub; p.dt_max = c->step_dtmax;
     p.cnt = c->d_cnt; p.st = st;
     const int warps = c->pair_warps;
     const size_t smem = (size_t)warps * pair_warp_bytes<R, TMA>();

@@ -42,6 +42,10 @@ class SidmConfig(C.Structure):
                 ("flags", C.c_int32), ("grid_ctas", C.c_int32), ("use_tma", C.c_int32)]
 
 
+class SidmHost(C.Structure):
+    _fields_ = [("G", C.c_double), ("M_n", C.c_double), ("R_s", C.c_double), ("center", C.c_double * 3)]
+
+
 class SidmError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"libsidm error {code}: {msg}")
@@ -81,11 +85,14 @@ def load_library():
     L.sidm_warm_start.argtypes = [vp, i32]
     L.sidm_local_diagnostics.argtypes = [vp, vp, vp, vp, C.c_double, vp, vp]
     L.sidm_timestep_criterion.argtypes = [vp, C.c_double, C.c_double, C.c_double, i32, vp, vp, vp, vp, vp]
+    L.sidm_scatter_step_binned.argtypes = [vp, u64, u64, vp, C.c_double, i32, i32, vp, vp, vp, vp, vp]
+    L.sidm_host_kick.argtypes = [vp, C.POINTER(SidmHost), C.c_double, i32, i32, i32, vp, vp, vp, vp]
     L.sidm_energy_momentum_static.argtypes = [i32, vp, i32, vp, vp, vp, vp, vp]
     for f in ("sidm_create", "sidm_destroy", "sidm_build_cells", "sidm_kernel_sizes", "sidm_scatter_step",
               "sidm_energy_momentum", "sidm_status", "sidm_get_perm", "sidm_neighbours", "sidm_get_events",
               "sidm_lambda_eval", "sidm_drift", "sidm_get_sum_p", "sidm_kernel_times", "sidm_diagnostics",
-              "sidm_energy_momentum_static", "sidm_warm_start", "sidm_local_diagnostics", "sidm_timestep_criterion"):
+              "sidm_energy_momentum_static", "sidm_warm_start", "sidm_local_diagnostics", "sidm_timestep_criterion",
+              "sidm_scatter_step_binned", "sidm_host_kick"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -95,7 +102,8 @@ EXPORTED = ["sidm_create", "sidm_destroy", "sidm_last_error", "sidm_create_error
             "sidm_kernel_sizes", "sidm_scatter_step", "sidm_energy_momentum", "sidm_status", "sidm_get_perm",
             "sidm_neighbours", "sidm_get_events", "sidm_lambda_eval", "sidm_drift", "sidm_get_sum_p",
             "sidm_launch_count", "sidm_kernel_times", "sidm_diagnostics", "sidm_energy_momentum_static",
-            "sidm_warm_start", "sidm_local_diagnostics", "sidm_timestep_criterion"]
+            "sidm_warm_start", "sidm_local_diagnostics", "sidm_timestep_criterion", "sidm_scatter_step_binned",
+            "sidm_host_kick"]
 
 
 def _torch():
@@ -143,6 +151,21 @@ def sidm_build_cells(ctx, halo_off, pos, vel, ids, stream=None):
 def sidm_kernel_sizes(ctx, n_ngb, h, stream=None):
     k = np.ascontiguousarray(n_ngb, dtype=np.int32)
     _check(ctx, load_library().sidm_kernel_sizes(ctx, k.ctypes.data_as(C.c_void_p), _ptr(h), _stream(stream)))
+
+
+def sidm_scatter_step_binned(ctx, seed, step, xs, dt_max, n_bins, substep, bins, mass, vel, stats=None,
+                             stream=None):
+    _check(ctx, load_library().sidm_scatter_step_binned(ctx, C.c_uint64(int(seed)), C.c_uint64(int(step)), _ptr(xs),
+                                                        float(dt_max), int(n_bins), int(substep), _ptr(bins),
+                                                        _ptr(mass), _ptr(vel), _ptr(stats), _stream(stream)))
+
+
+def sidm_host_kick(ctx, host, dt_max, n_bins, substep, phase, bins, pos, vel, stream=None):
+    """host = (G, M_n, R_s, (cx, cy, cz)); see include/sidm.h."""
+    G, Mn, Rs, c = host
+    hs = SidmHost(float(G), float(Mn), float(Rs), (C.c_double * 3)(*[float(x) for x in c]))
+    _check(ctx, load_library().sidm_host_kick(ctx, C.byref(hs), float(dt_max), int(n_bins), int(substep), int(phase),
+                                              _ptr(bins), _ptr(pos), _ptr(vel), _stream(stream)))
 
 
 def sidm_scatter_step(ctx, seed, step, xs, dt, mass, vel, stats=None, stream=None):
@@ -310,6 +333,14 @@ class Context:
     def scatter_step(self, seed, step, xs, dt, mass, vel, stats=None, stream=None):
         sidm_scatter_step(self.handle, seed, step, xs, dt, mass, vel,
                           self.stats_buf if stats is None else stats, stream)
+
+    def scatter_step_binned(self, seed, step, xs, dt_max, n_bins, substep, bins, mass, vel, stats=None,
+                            stream=None):
+        sidm_scatter_step_binned(self.handle, seed, step, xs, dt_max, n_bins, substep, bins, mass, vel,
+                                 self.stats_buf if stats is None else stats, stream)
+
+    def host_kick(self, host, dt_max, n_bins, substep, phase, bins, pos, vel, stream=None):
+        sidm_host_kick(self.handle, host, dt_max, n_bins, substep, phase, bins, pos, vel, stream)
 
     def energy_momentum(self, mass, vel, out, comp=None, stream=None):
         sidm_energy_momentum(self.handle, mass, vel, out, comp, stream)
