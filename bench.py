@@ -420,6 +420,86 @@ def cpu_baseline(dt, vmax, threads=None):
                       f"{sec:.2f} s", "seconds": sec, "pairs": int(r["stats"][0]["n_pairs"])}
 
 
+def run_satellite(local, big_steps=8, n=1 << 22, n_bins=4, dt_max=0.02):
+    """NFW subhalo of 2^22 particles on a circular orbit at 30 of its scale radii
+    in a fixed NFW host of 1e3 times its mass (scale radius 15.3): kick-drift-
+    kick with the host's analytic force on 4 power-of-two individual steps,
+    bins from the SIDM time-step criterion (tau = 0.04) of the previous big
+    step, sigma(v) of the main workload; cells and kernel sizes every sub-step."""
+    import torch
+    from paper_2506_06269_gb300 import ics, sidm
+    halo = ics.nfw(n, 4)
+    vmax = ics.nfw_vmax()
+    G, Mn, Rs = 1.0, 1000.0 / (math.log(11.0) - 10.0 / 11.0), 15.3
+    host = (G, Mn, Rs, (0.0, 0.0, 0.0))
+    m30 = Mn * (math.log1p(30.0 / Rs) - (30.0 / Rs) / (1.0 + 30.0 / Rs))
+    vc = math.sqrt(G * m30 / 30.0)
+    ctx = sidm.Context(n_max=n, halo_max=1, ngb_max=N_NGB, event_cap=max(1 << 16, n // 8), device=local,
+                       flags=sidm.SIDM_FLAG_SUM_P)
+    dev = ctx.device
+    pos = torch.tensor(halo.pos + np.array([[30.0], [0.0], [0.0]]), device=dev)
+    vel = torch.tensor((halo.vel + np.array([[0.0], [vc], [0.0]])).astype(np.float32), device=dev)
+    ids = torch.tensor(halo.ids.astype(np.int64), device=dev).to(torch.int32)
+    h = torch.zeros(n, dtype=torch.float32, device=dev)
+    xs = ctx.xs_tensor([(1, S0, vmax)])
+    mass = ctx.f64([halo.mass])
+    S = 1 << (n_bins - 1)
+    dtt = ctx.f64([dt_max / S])
+    dtm = ctx.f64([dt_max])
+    bins = torch.zeros(n, dtype=torch.int32, device=dev)
+    stats = torch.zeros((big_steps * S, sidm.STATS_DTYPE.itemsize), dtype=torch.uint8, device=dev)
+
+    def energy():
+        r = torch.linalg.norm(pos, dim=0)
+        phi = -G * Mn * torch.log1p(r / Rs) / r
+        return float((0.5 * (vel.double() ** 2).sum(0) + phi).sum().item()) * halo.mass
+
+    def big_step(k, record):
+        nonlocal bins
+        nxt = bins
+        for s in range(S):
+            ctx.host_kick(host, dt_max, n_bins, s, 0, bins, pos, vel)
+            ctx.build_cells([0, n], pos, vel, ids)
+            pm = ctx.perm(n).to(torch.int64)
+            bins, nxt = bins[pm], nxt[pm]                     # bins travel with their particles
+            ctx.kernel_sizes([N_NGB], h)
+            ctx.scatter_step_binned(SEED_IC, k * S + s, xs, dt_max, n_bins, s, bins, mass, vel,
+                                    stats[k * S + s] if record else None)
+            if s == 0:                                        # every step opens: rates of all pairs
+                _, nxt, _ = ctx.timestep_criterion(0.04, 0.0, dt_max, n_bins, dtm, n, 1)
+            ctx.drift(dtt, pos, vel)
+            ctx.host_kick(host, dt_max, n_bins, s, 1, bins, pos, vel)
+        bins = nxt                                            # the next big step's bins
+
+    ctx.build_cells([0, n], pos, vel, ids)                   # layout for the first kicks
+    big_step(0, False)
+    torch.cuda.synchronize()
+    e0 = energy()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for k in range(big_steps):
+        big_step(k, True)
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    e1 = energy()
+    st = [sidm.parse_stats(stats[i]) for i in range(big_steps * S)]
+    hist = torch.bincount(bins.long(), minlength=n_bins).cpu().tolist()
+    status = ctx.status()
+    ctx.close()
+    return {"workload": "NFW subhalo N=2^22 at 30 r_s in an NFW host of 1e3 x its mass (R_s = 15.3), "
+                        "KDK with the host force, 4 power-of-two bins from the SIDM criterion (tau 0.04), "
+                        f"sigma/m = {S0}/(1+(v/v_max)^2)^2, N_ngb = {N_NGB}",
+            "n_particles": n, "big_steps": big_steps, "substeps_per_big_step": S, "dt_max": dt_max,
+            "particle_substeps_per_s": n * big_steps * S / (ms * 1e-3),
+            "particle_big_steps_per_s": n * big_steps / (ms * 1e-3), "ms_per_big_step": ms / big_steps,
+            "energy_drift_rel": abs(e1 - e0) / abs(e0),
+            "events_total": int(sum(x.n_events for x in st)),
+            "events_by_substep_index": [float(np.mean([st[k * S + s].n_events for k in range(big_steps)]))
+                                        for s in range(S)],
+            "bins_last": hist, "device_status": status}
+
+
 def run_batched(local, graph_steps=50, seq_steps=2):
     """64 independent NFW halos in one persistent launch per kernel, 50 steps
     captured in one CUDA graph, against 64 sequential single-halo contexts."""
@@ -627,6 +707,7 @@ def main_ours(args):
             line["mixed_over_fp64"] = value / ws / fp64["value"]
         if not args.no_batched:
             line["batched"] = run_batched(res["local"])
+            line["satellite"] = run_satellite(res["local"])
             if fp64:
                 line["batched_over_fp64_single_halo"] = line["batched"]["value"] / fp64["value"]
         if not args.no_cpu_baseline and ws == 1:
