@@ -376,23 +376,25 @@ __global__ void k_halo_min_final(int H, const unsigned long long* __restrict__ o
 // sigma_eff / s0 = (1/6) int_0^inf t^3 e^-t / (1 + beta t)^2 dt, beta = 4 nu^2 / w^2
 // (the Maxwellian average <v^5 sigma(v)> / <v^5> with t = v^2 / (4 nu^2)):
 // 4-point Gauss-Legendre on 48 panels with edges 64 (k/48)^2, which follow the
-// 1/beta scale near t = 0; error below 1e-6 up to beta = 1e4.
-__device__ double sigma_eff_ratio(double beta)
+// 1/beta scale near t = 0; error below 1e-6 up to beta = 1e4.  Evaluated in
+// the form's precision (FP32 in the mixed form, whose outputs are FP32).
+template <class R>
+__device__ R sigma_eff_ratio(R beta)
 {
-    const double a = sqrt(3.0 / 7.0 + 2.0 / 7.0 * sqrt(1.2)), b = sqrt(3.0 / 7.0 - 2.0 / 7.0 * sqrt(1.2));
-    const double wa = (18.0 - sqrt(30.0)) / 36.0, wb = (18.0 + sqrt(30.0)) / 36.0;
-    const double xg[4] = {-a, -b, b, a}, wg[4] = {wa, wb, wb, wa};
-    double tot = 0.0;
+    const R a = sqrt(R(3) / R(7) + R(2) / R(7) * sqrt(R(1.2))), b = sqrt(R(3) / R(7) - R(2) / R(7) * sqrt(R(1.2)));
+    const R wa = (R(18) - sqrt(R(30))) / R(36), wb = (R(18) + sqrt(R(30))) / R(36);
+    const R xg[4] = {-a, -b, b, a}, wg[4] = {wa, wb, wb, wa};
+    R tot = R(0);
     for (int k = 0; k < 48; ++k) {
-        const double lo = 64.0 * (k / 48.0) * (k / 48.0), hi = 64.0 * ((k + 1) / 48.0) * ((k + 1) / 48.0);
-        const double c = 0.5 * (lo + hi), hw = 0.5 * (hi - lo);
+        const R lo = R(64) * (R(k) / R(48)) * (R(k) / R(48)), hi = R(64) * (R(k + 1) / R(48)) * (R(k + 1) / R(48));
+        const R c = R(0.5) * (lo + hi), hw = R(0.5) * (hi - lo);
         for (int g = 0; g < 4; ++g) {
-            const double t = c + hw * xg[g];
-            const double den = 1.0 + beta * t;
+            const R t = c + hw * xg[g];
+            const R den = R(1) + beta * t;
             tot += hw * wg[g] * t * t * t * exp(-t) / (den * den);
         }
     }
-    return tot / 6.0;
+    return tot / R(6);
 }
 
 // Local diagnostics from the kernel-weighted pair moments plus the self term
@@ -423,7 +425,7 @@ __global__ void k_diag_final(int L, const int32_t* __restrict__ leaf_halo, const
     const double m2 = (dacc[4 * N + u] + w0 * (vx * vx + vy * vy + vz * vz)) / sw;
     const double nu = sqrt(fmax((m2 - (mx * mx + my * my + mz * mz)) / 3.0, 0.0));
     const sidm_xs x = xs[h];
-    const double se = x.kind == 1 ? x.s0 * sigma_eff_ratio(4.0 * nu * nu / (x.w * x.w)) : x.s0;
+    const double se = x.kind == 1 ? x.s0 * (double)sigma_eff_ratio<R>((R)(4.0 * nu * nu / (x.w * x.w))) : x.s0;
     const double rho = sw;
     out[u] = (R)rho;
     out[N + u] = (R)nu;
