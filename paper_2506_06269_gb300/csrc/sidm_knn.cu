@@ -256,6 +256,19 @@ __global__ void k_knn(KnnParams p)
             np = 0;
         };
 
+        float3 pq;                                     // query point in the halo frame
+        if constexpr (sizeof(R) == 4) {
+            pq = make_float3(__fadd_rn(cA.x, (float)q.x), __fadd_rn(cA.y, (float)q.y), __fadd_rn(cA.z, (float)q.z));
+        } else {
+            pq = make_float3(__double2float_rn((double)q.x - fr.O[0]), __double2float_rn((double)q.y - fr.O[1]),
+                             __double2float_rn((double)q.z - fr.O[2]));
+        }
+        auto my_r2 = [&]() -> float {
+            if (!act) return -1.0f;
+            float r = to_float_ru<R>(sqrt_ru(key_d2<R, NBR>(root)));
+            r = __fadd_ru(__fmul_ru(r, 1.0f + 0x1p-20f), fr.margin);
+            return __fmul_ru(r, r);
+        };
         auto process = [&](int Bl, bool mine) {
             const int Bg = leaf0 + Bl;
             const int countB = (int)min((int64_t)kLeaf, nh - (int64_t)Bl * kLeaf);
@@ -268,6 +281,29 @@ __global__ void k_knn(KnnParams p)
                 c.y = __fadd_rn(c.y, __fsub_rn(cB.y, cA.y));
                 c.z = __fadd_rn(c.z, __fsub_rn(cB.z, cA.z));
             }
+            // candidates farther from the query leaf's box than the largest bound
+            // of any lane cannot enter a heap: the loops skip them (an unbounded
+            // lane, before its heap is full in the cold pass, keeps them all)
+            float lr2 = -1.f;
+            if (act && mine) {
+                const float r2 = my_r2();
+                lr2 = isnan(r2) ? INFINITY : r2;
+            }
+            float r2max = lr2;
+            for (int o = 16; o > 0; o >>= 1) r2max = fmaxf(r2max, __shfl_xor_sync(0xffffffffu, r2max, o));
+            uint32_t cmask;
+            if (!(r2max < INFINITY)) {
+                cmask = countB == kLeaf ? 0xffffffffu : ((1u << countB) - 1u);
+            } else {
+                float3 pc;                             // candidate in the halo frame
+                if constexpr (sizeof(R) == 4) {
+                    pc = make_float3(__fadd_rn(cA.x, c.x), __fadd_rn(cA.y, c.y), __fadd_rn(cA.z, c.z));
+                } else {
+                    pc = make_float3(__double2float_rn((double)c.x - fr.O[0]), __double2float_rn((double)c.y - fr.O[1]),
+                                     __double2float_rn((double)c.z - fr.O[2]));
+                }
+                cmask = __ballot_sync(0xffffffffu, lane < countB && point_gap2_rd(pc, qlo, qhi) <= r2max);
+            }
             __syncwarp();
             V* sh = stage.shifted();
             sh[lane] = c;
@@ -275,12 +311,12 @@ __global__ void k_knn(KnnParams p)
             __syncwarp();
             ++n_tiles;
             if (act && mine) {
-                n_cand += (unsigned long long)countB;
+                n_cand += (unsigned long long)__popc(cmask);
                 if (nfill < k) {
                     // fill: the first k admitted keys go into the heap array unsorted
                     // (heapified at the next merge; later keys wait in the pending list)
-#pragma unroll 4
-                    for (int t = 0; t < countB; ++t) {
+                    for (uint32_t mm = cmask; mm; mm &= mm - 1u) {
+                        const int t = __ffs(mm) - 1;
                         const V cj = sh[t];
                         const R dx = sub_rn(cj.x, q.x), dy = sub_rn(cj.y, q.y), dz = sub_rn(cj.z, q.z);
                         const R d2 = fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
@@ -292,8 +328,8 @@ __global__ void k_knn(KnnParams p)
                     }
                 } else {
                     // at most 32 appends per tile: np stays below kPend
-#pragma unroll 4
-                    for (int t = 0; t < countB; ++t) {
+                    for (uint32_t mm = cmask; mm; mm &= mm - 1u) {
+                        const int t = __ffs(mm) - 1;
                         const V cj = sh[t];
                         const R dx = sub_rn(cj.x, q.x), dy = sub_rn(cj.y, q.y), dz = sub_rn(cj.z, q.z);
                         const R d2 = fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
@@ -323,19 +359,6 @@ __global__ void k_knn(KnnParams p)
         // 2) tree walk.  A node is visited iff the query point of some lane lies
         //    within that lane's current k-th distance (+ margin) of the node's box;
         //    accepted leaves are processed at once so the bound keeps shrinking.
-        float3 pq;                                     // query point in the halo frame
-        if constexpr (sizeof(R) == 4) {
-            pq = make_float3(__fadd_rn(cA.x, (float)q.x), __fadd_rn(cA.y, (float)q.y), __fadd_rn(cA.z, (float)q.z));
-        } else {
-            pq = make_float3(__double2float_rn((double)q.x - fr.O[0]), __double2float_rn((double)q.y - fr.O[1]),
-                             __double2float_rn((double)q.z - fr.O[2]));
-        }
-        auto my_r2 = [&]() -> float {
-            if (!act) return -1.0f;
-            float r = to_float_ru<R>(sqrt_ru(key_d2<R, NBR>(root)));
-            r = __fadd_ru(__fmul_ru(r, 1.0f + 0x1p-20f), fr.margin);
-            return __fmul_ru(r, r);
-        };
         // boxes of nodes g0 .. g0+n-1 (n <= kBoxes) into the warp's box buffer, one per lane
         auto load_boxes = [&](int g0, int n) {
             __syncwarp();
