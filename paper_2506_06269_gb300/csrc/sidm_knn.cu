@@ -147,8 +147,8 @@ struct Heap4 {
 template <class K>
 __host__ __device__ constexpr int heap4_groups(int kcap) { return (kcap + 2) / 4 + 1; }
 
-// pending heap insertions per lane (a tile adds at most 32, so the lists are
-// merged whenever one holds more than kPend - 32 keys), the pending count at
+// pending heap insertions per lane (a tile adds at most its masked candidates,
+// so the lists are merged before a tile that could overflow one), the pending count at
 // which the lists are merged before a tree node's tests, and the node boxes
 // tested at once (the children of one node; a wider top level in chunks)
 constexpr int kPend = 32;
@@ -304,6 +304,8 @@ __global__ void k_knn(KnnParams p)
                 }
                 cmask = __ballot_sync(0xffffffffu, lane < countB && point_gap2_rd(pc, qlo, qhi) <= r2max);
             }
+            // room for this tile's candidates in every pending list
+            if (__any_sync(0xffffffffu, np + __popc(cmask) > kPend)) flush();
             __syncwarp();
             V* sh = stage.shifted();
             sh[lane] = c;
@@ -327,7 +329,7 @@ __global__ void k_knn(KnnParams p)
                         }
                     }
                 } else {
-                    // at most 32 appends per tile: np stays below kPend
+                    // room for every masked candidate was made before the tile
                     for (uint32_t mm = cmask; mm; mm &= mm - 1u) {
                         const int t = __ffs(mm) - 1;
                         const V cj = sh[t];
@@ -382,10 +384,7 @@ __global__ void k_knn(KnnParams p)
         auto visit_leaf = [&](int Bl, int c) {
             const float r2 = my_r2();
             const bool mine = r2 >= 0.f && point_gap2_rd(pq, blo[c], bhi[c]) <= r2;
-            if (__any_sync(0xffffffffu, mine)) {
-                if (__any_sync(0xffffffffu, np > kPend - kLeaf)) flush();   // room for one tile
-                process(Bl, mine);
-            }
+            if (__any_sync(0xffffffffu, mine)) process(Bl, mine);
         };
         // Accepted children are visited nearest first (box gap to the query leaf),
         // so the k-th bound shrinks early.  rank = position among the accepted.
