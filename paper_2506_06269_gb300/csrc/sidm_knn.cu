@@ -269,7 +269,8 @@ __global__ void k_knn(KnnParams p)
             r = __fadd_ru(__fmul_ru(r, 1.0f + 0x1p-20f), fr.margin);
             return __fmul_ru(r, r);
         };
-        auto process = [&](int Bl, bool mine) {
+        // r2: the lane's current bound (my_r2) as its caller computed it
+        auto process = [&](int Bl, bool mine, float r2) {
             const int Bg = leaf0 + Bl;
             const int countB = (int)min((int64_t)kLeaf, nh - (int64_t)Bl * kLeaf);
             const V* tile = stage.load((const V*)p.P4 + (int64_t)Bg * kLeaf, lane, p.cnt);
@@ -285,10 +286,7 @@ __global__ void k_knn(KnnParams p)
             // of any lane cannot enter a heap: the loops skip them (an unbounded
             // lane, before its heap is full in the cold pass, keeps them all)
             float lr2 = -1.f;
-            if (act && mine) {
-                const float r2 = my_r2();
-                lr2 = isnan(r2) ? INFINITY : r2;
-            }
+            if (act && mine) lr2 = isnan(r2) ? INFINITY : r2;
             float r2max = lr2;
             for (int o = 16; o > 0; o >>= 1) r2max = fmaxf(r2max, __shfl_xor_sync(0xffffffffu, r2max, o));
             uint32_t cmask;
@@ -304,6 +302,8 @@ __global__ void k_knn(KnnParams p)
                 }
                 cmask = __ballot_sync(0xffffffffu, lane < countB && point_gap2_rd(pc, qlo, qhi) <= r2max);
             }
+            ++n_tiles;
+            if (cmask == 0u) return;                   // no candidate of this leaf can enter
             // room for this tile's candidates in every pending list
             if (__any_sync(0xffffffffu, np + __popc(cmask) > kPend)) flush();
             __syncwarp();
@@ -311,7 +311,6 @@ __global__ void k_knn(KnnParams p)
             sh[lane] = c;
             if (NBR) tids[lane] = p.ID[(int64_t)Bg * kLeaf + lane];
             __syncwarp();
-            ++n_tiles;
             if (act && mine) {
                 n_cand += (unsigned long long)__popc(cmask);
                 if (nfill < k) {
@@ -354,7 +353,7 @@ __global__ void k_knn(KnnParams p)
             }
             // the window holds at least k other particles, so every lane's heap is
             // full after it: order it and merge the window's keys beyond the first k
-            for (int Bl = wlo; Bl <= whi; ++Bl) process(Bl, true);
+            for (int Bl = wlo; Bl <= whi; ++Bl) process(Bl, true, my_r2());
             flush();
         }
 
@@ -384,7 +383,7 @@ __global__ void k_knn(KnnParams p)
         auto visit_leaf = [&](int Bl, int c) {
             const float r2 = my_r2();
             const bool mine = r2 >= 0.f && point_gap2_rd(pq, blo[c], bhi[c]) <= r2;
-            if (__any_sync(0xffffffffu, mine)) process(Bl, mine);
+            if (__any_sync(0xffffffffu, mine)) process(Bl, mine, r2);
         };
         // Accepted children are visited nearest first (box gap to the query leaf),
         // so the k-th bound shrinks early.  rank = position among the accepted.
