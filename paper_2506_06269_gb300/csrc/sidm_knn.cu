@@ -366,12 +366,17 @@ __global__ void k_knn(KnnParams p)
             if (lane < n) { blo[lane] = p.nlo[g0 + lane]; bhi[lane] = p.nhi[g0 + lane]; }
             __syncwarp();
         };
-        // bit c: the query of some lane lies within its bound of box c
+        // bit c: the query of some lane lies within its bound of box c; the
+        // lane's own bits and bound are kept for the leaves of this node
+        uint32_t lane_bits = 0u;
+        float node_r2 = -1.0f;
         auto accept = [&](int n, float r2, uint32_t skip) -> uint32_t {
             uint32_t bits = 0u;
             if (r2 >= 0.f)
                 for (int c = 0; c < n; ++c)
                     if (point_gap2_rd(pq, blo[c], bhi[c]) <= r2) bits |= 1u << c;
+            lane_bits = bits;
+            node_r2 = r2;
             return __reduce_or_sync(0xffffffffu, bits) & ~skip;
         };
         // leaves of the Morton window among local leaves first .. first+n-1
@@ -380,7 +385,15 @@ __global__ void k_knn(KnnParams p)
             if (lo > hi) return 0u;
             return ((2u << hi) - 1u) & ~((1u << lo) - 1u);
         };
+        // the warm pass's bound barely moves, so a leaf reuses the lane's node test
+        // (a larger, older bound only admits more); the cold pass re-tests with the
+        // bound its nearer leaves have shrunk
         auto visit_leaf = [&](int Bl, int c) {
+            if (pass == 0) {
+                const bool mine = (lane_bits >> c) & 1u;
+                if (__any_sync(0xffffffffu, mine)) process(Bl, mine, node_r2);
+                return;
+            }
             const float r2 = my_r2();
             const bool mine = r2 >= 0.f && point_gap2_rd(pq, blo[c], bhi[c]) <= r2;
             if (__any_sync(0xffffffffu, mine)) process(Bl, mine, r2);
