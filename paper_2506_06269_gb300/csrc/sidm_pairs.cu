@@ -398,12 +398,15 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
             if (lane < n) { blo[lane] = p.nlo[g0 + lane]; bhi[lane] = p.nhi[g0 + lane]; }
             __syncwarp();
         };
-        // bit c: some lane's query reaches box c
+        // bit c: some lane's query reaches box c (each lane keeps its own bits
+        // for the leaves of this node)
+        uint32_t lane_bits = 0u;
         auto accept = [&](int n, uint32_t eligible) -> uint32_t {
             uint32_t bits = 0u;
             if (active)
                 for (int c = 0; c < n; ++c)
                     if ((eligible >> c) & 1u) bits |= (near_box(c) ? 1u : 0u) << c;
+            lane_bits = bits;
             return __reduce_or_sync(0xffffffffu, bits);
         };
         // nodes whose subtree holds a leaf >= A (level lev, local indices first ..)
@@ -416,7 +419,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
         auto visit_leaves = [&](uint32_t acc, int first) {
             for (; acc; acc &= acc - 1u) {
                 const int c = __ffs(acc) - 1;
-                process(first + c, near_box(c));
+                process(first + c, (lane_bits >> c) & 1u);
             }
         };
         auto push = [&](uint32_t acc, int lev, int first, int& sp) -> bool {
