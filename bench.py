@@ -421,26 +421,27 @@ def cpu_baseline(dt, vmax, threads=None):
 
 
 def run_satellite(local, big_steps=8, n=1 << 22, n_bins=4, dt_max=0.02):
-    """NFW subhalo of 2^22 particles on a circular orbit at 30 of its scale radii
-    in a fixed NFW host of 1e3 times its mass (scale radius 15.3): kick-drift-
-    kick with the host's analytic force on 4 power-of-two individual steps,
-    bins from the SIDM time-step criterion (tau = 0.04) of the previous big
-    step, sigma(v) of the main workload; cells and kernel sizes every sub-step."""
+    """NFW subhalo of 2^22 particles at the paper's initial position and velocity
+    (123.6 kpc, 109 km/s) in its six-part Milky-Way-like host (NFW halo,
+    Hernquist bulge, four Miyamoto-Nagai disks), in the code units of the
+    subhalo: kick-drift-kick with the host's analytic force on 4 power-of-two
+    individual steps, bins from the SIDM time-step criterion (tau = 0.04) of
+    the previous big step, sigma(v) of the main workload; cells and kernel
+    sizes every sub-step."""
     import torch
     from paper_2506_06269_gb300 import ics, sidm
     halo = ics.nfw(n, 4)
     vmax = ics.nfw_vmax()
-    G, Mn, Rs = 1.0, 1000.0 / (math.log(11.0) - 10.0 / 11.0), 15.3
-    host = (G, Mn, Rs, (0.0, 0.0, 0.0))
-    m30 = Mn * (math.log1p(30.0 / Rs) - (30.0 / Rs) / (1.0 + 30.0 / Rs))
-    vc = math.sqrt(G * m30 / 30.0)
+    host = ics.milky_way_host()
+    x0, v0 = ics.satellite_orbit()
     ctx = sidm.Context(n_max=n, halo_max=1, ngb_max=N_NGB, event_cap=max(1 << 16, n // 8), device=local,
                        flags=sidm.SIDM_FLAG_SUM_P)
     dev = ctx.device
-    pos = torch.tensor(halo.pos + np.array([[30.0], [0.0], [0.0]]), device=dev)
-    vel = torch.tensor((halo.vel + np.array([[0.0], [vc], [0.0]])).astype(np.float32), device=dev)
+    pos = torch.tensor(halo.pos + x0[:, None], device=dev)
+    vel = torch.tensor((halo.vel + v0[:, None]).astype(np.float32), device=dev)
     ids = torch.tensor(halo.ids.astype(np.int64), device=dev).to(torch.int32)
     h = torch.zeros(n, dtype=torch.float32, device=dev)
+    phi = torch.zeros(n, dtype=torch.float64, device=dev)
     xs = ctx.xs_tensor([(1, S0, vmax)])
     mass = ctx.f64([halo.mass])
     S = 1 << (n_bins - 1)
@@ -450,8 +451,7 @@ def run_satellite(local, big_steps=8, n=1 << 22, n_bins=4, dt_max=0.02):
     stats = torch.zeros((big_steps * S, sidm.STATS_DTYPE.itemsize), dtype=torch.uint8, device=dev)
 
     def energy():
-        r = torch.linalg.norm(pos, dim=0)
-        phi = -G * Mn * torch.log1p(r / Rs) / r
+        ctx.host_potential(host, pos, phi)
         return float((0.5 * (vel.double() ** 2).sum(0) + phi).sum().item()) * halo.mass
 
     def big_step(k, record):
@@ -487,7 +487,8 @@ def run_satellite(local, big_steps=8, n=1 << 22, n_bins=4, dt_max=0.02):
     hist = torch.bincount(bins.long(), minlength=n_bins).cpu().tolist()
     status = ctx.status()
     ctx.close()
-    return {"workload": "NFW subhalo N=2^22 at 30 r_s in an NFW host of 1e3 x its mass (R_s = 15.3), "
+    return {"workload": "NFW subhalo N=2^22 from 123.6 kpc at 109 km/s in the six-part Milky-Way-like host "
+                        "(NFW + Hernquist bulge + 4 Miyamoto-Nagai disks), "
                         "KDK with the host force, 4 power-of-two bins from the SIDM criterion (tau 0.04), "
                         f"sigma/m = {S0}/(1+(v/v_max)^2)^2, N_ngb = {N_NGB}",
             "n_particles": n, "big_steps": big_steps, "substeps_per_big_step": S, "dt_max": dt_max,

@@ -92,14 +92,27 @@ typedef struct {
     double w;
 } sidm_xs;
 
-/* A fixed analytic NFW host (Sect. 4.1 evolves the satellite in an external
- * potential): M(<r) = M_n [ln(1 + r/R_s) - (r/R_s)/(1 + r/R_s)] about center,
- * acceleration -G M(<r) (x - center) / r^3.  Code units. */
+/* A fixed analytic host galaxy (Sect. 4.1: the satellite moves in an external
+ * potential of six parts, each given by its Eq. there), about `center`, with
+ * r = |x - center| and R, z the cylindrical radius and height about it:
+ *   NFW halo        Phi = -4 pi G rho_s r_s^3 ln(1 + r/r_s) / r        (rho_s = 0: none)
+ *   Hernquist bulge Phi = -G M_H / (r + a_H)                          (M_H = 0: none)
+ *   n_disks Miyamoto-Nagai disks
+ *                   Phi = -G M_d / sqrt(R^2 + (a_d + sqrt(z^2 + b_d^2))^2)
+ * Code units; every length > 0 (b_d > 0), every mass >= 0, 0 <= n_disks <= 4. */
+#define SIDM_HOST_MAX_DISKS 4
 typedef struct {
     double G;
-    double M_n;
-    double R_s;
     double center[3];
+    double rho_s;
+    double r_s;
+    double M_H;
+    double a_H;
+    int32_t n_disks;
+    int32_t pad_;
+    double M_d[SIDM_HOST_MAX_DISKS];
+    double a_d[SIDM_HOST_MAX_DISKS];
+    double b_d[SIDM_HOST_MAX_DISKS];
 } sidm_host;
 
 /* Per-step statistics, written by sidm_scatter_step (device memory). */
@@ -310,14 +323,24 @@ int sidm_scatter_step_binned(sidm_ctx* ctx, uint64_t seed, uint64_t step, const 
 /* Kick by the analytic host (kick-drift-kick on individual steps): every
  * particle whose step opens at sub-step `substep` (phase 0, before the drift)
  * or closes after it (phase 1, after the drift of that sub-step) gets
- * v += a(x) dt_b / 2, dt_b = dt_max / 2^b, with the acceleration of `host`
- * evaluated in FP64 at its FP64 position.
+ * v += a(x) dt_b / 2, dt_b = dt_max / 2^b, with the acceleration a = -grad Phi
+ * of `host` evaluated in FP64 at its FP64 position (zero from the spherical
+ * parts at the centre itself).
  *   host      : host-memory sidm_host
  *   bin_dev   : device int32[N] or NULL (every particle in bin 0)
  *   pos_dev   : f64 [3][N];  vel_dev : [3][N] f32 or f64 by precision, updated
  * Arrays in the order left by sidm_build_cells (which must come first). */
 int sidm_host_kick(sidm_ctx* ctx, const sidm_host* host, double dt_max, int32_t n_bins, int32_t substep,
                    int32_t phase, const int32_t* bin_dev, const double* pos_dev, void* vel_dev, cudaStream_t stream);
+
+/* Potential of the analytic host at every particle (for the energy of a
+ * satellite run, E = sum_i m (v_i^2 / 2 + Phi(x_i))), FP64.
+ *   host    : host-memory sidm_host (as sidm_host_kick)
+ *   pos_dev : f64 [3][N] in the order left by sidm_build_cells (which must come first)
+ *   phi_dev : device f64 [N], written
+ * Errors: SIDM_EINVAL for a null argument or a bad host. */
+int sidm_host_potential(sidm_ctx* ctx, const sidm_host* host, const double* pos_dev, double* phi_dev,
+                        cudaStream_t stream);
 
 /* SIDM time-step criterion (Sect. 2: a separate time-step criterion for the
  * self-interactions; tau = 0.04 in every SIDM run of the simulation table;

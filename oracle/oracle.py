@@ -80,8 +80,9 @@ def lib():
             L.orc_pairs_halo.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, i32, i32, d, d, d, d,
                                          u64, u64, u32, vp, i64, P(_PairStats), vp, vp, vp, i32, i32, d]
             L.orc_host_mass.argtypes = [d, d, d]; L.orc_host_mass.restype = d
-            L.orc_host_phi.argtypes = [d, d, d, d]; L.orc_host_phi.restype = d
-            L.orc_host_kick.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, i32, d, d, d, d, d, d, d]
+            L.orc_host_phi.argtypes = [vp, d, d, d]; L.orc_host_phi.restype = d
+            L.orc_host_accel.argtypes = [vp, d, d, d, vp]
+            L.orc_host_kick.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, i32, d, vp]
             L.orc_pairs_halo.restype = i32
             L.orc_sort_events.argtypes = [vp, i64]
             L.orc_apply_events.argtypes = [vp, i64, vp, vp, vp, vp, vp]
@@ -231,24 +232,55 @@ def timestep(sum_p, tau: float, dt: float, dt_min: float, dt_max: float, n_bins:
     return dto, bo
 
 
-def host_mass(r, Mn, Rs):
-    return float(lib().orc_host_mass(float(r), float(Mn), float(Rs)))
+def host_params(host) -> np.ndarray:
+    """Flat FP64 parameter array of an analytic host (the layout orc_host_phi reads).
+
+    host: dict with G, center (3), and any of nfw = (rho_s, r_s),
+    bulge = (M_H, a_H), disks = [(M_d, a_d, b_d), ...] (at most 4)."""
+    disks = list(host.get("disks", ()))
+    if len(disks) > 4:
+        raise ValueError("at most 4 disks")
+    rho_s, r_s = host.get("nfw") or (0.0, 1.0)
+    m_h, a_h = host.get("bulge") or (0.0, 1.0)
+    out = [float(host["G"]), *[float(c) for c in host.get("center", (0.0, 0.0, 0.0))],
+           float(rho_s), float(r_s), float(m_h), float(a_h), float(len(disks))]
+    for m, a, b in disks:
+        out += [float(m), float(a), float(b)]
+    return np.array(out, dtype=np.float64)
 
 
-def host_phi(r, G, Mn, Rs):
-    return float(lib().orc_host_phi(float(r), float(G), float(Mn), float(Rs)))
+def host_mass(r, rho_s, r_s):
+    """NFW mass inside r (see orc_host_mass)."""
+    return float(lib().orc_host_mass(float(r), float(rho_s), float(r_s)))
+
+
+def host_phi(host, x):
+    """Host potential at the points x [3] or [3][n] (see orc_host_phi)."""
+    hp = host_params(host)
+    pts = np.asarray(x, dtype=np.float64).reshape(3, -1)
+    out = np.array([lib().orc_host_phi(_p(hp), float(p[0]), float(p[1]), float(p[2])) for p in pts.T])
+    return out if np.ndim(x) > 1 else float(out[0])
+
+
+def host_accel(host, x):
+    """Host acceleration at the points x [3] or [3][n] (see orc_host_accel)."""
+    hp = host_params(host)
+    pts = np.asarray(x, dtype=np.float64).reshape(3, -1)
+    out = np.zeros((3, pts.shape[1]))
+    a = np.zeros(3)
+    for k in range(pts.shape[1]):
+        lib().orc_host_accel(_p(hp), float(pts[0, k]), float(pts[1, k]), float(pts[2, k]), _p(a))
+        out[:, k] = a
+    return out if np.ndim(x) > 1 else out[:, 0]
 
 
 def host_kick(pos, vel, host, dt_max, bins=None, n_bins=1, substep=0, phase=0):
-    """Half kick of the particles due at this sub-step (see orc_host_kick); returns new vel.
-
-    host = (G, M_n, R_s, (cx, cy, cz))."""
+    """Half kick of the particles due at this sub-step (see orc_host_kick); returns new vel."""
     p = _c(pos, np.float64); v = np.array(vel, dtype=np.float64, copy=True, order="C"); n = p.shape[1]
     bn = None if bins is None else _c(bins, np.int32)
-    G, Mn, Rs, c = host
+    hp = host_params(host)
     lib().orc_host_kick(n, _p(p[0]), _p(p[1]), _p(p[2]), _p(v[0]), _p(v[1]), _p(v[2]), _p(bn), int(n_bins),
-                        int(substep), int(phase), float(dt_max), float(G), float(Mn), float(Rs),
-                        float(c[0]), float(c[1]), float(c[2]))
+                        int(substep), int(phase), float(dt_max), _p(hp))
     return v
 
 

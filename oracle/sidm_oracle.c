@@ -850,41 +850,88 @@ void orc_timestep(int n, const double* sum_p, double tau, double dt, double dt_m
 }
 
 /* ------------------------------------------------------------------------- */
-/* Satellite in a fixed analytic host (Sect. 4.1 evolves the satellite in an  */
-/* external potential; here an NFW host, reading of the set-up):             */
-/*   M(<r) = M_n [ln(1 + x) - x / (1 + x)], x = r / R_s,                      */
-/*   Phi(r) = -G M_n ln(1 + x) / r,  a = -G M(<r) (x_vec - c) / r^3.          */
+/* Satellite in a fixed analytic host (Sect. 4.1: the host galaxy is an       */
+/* external potential of six parts, the Eqs. for the NFW halo, the Hernquist  */
+/* bulge and the Miyamoto-Nagai disks):                                      */
+/*   Phi_NFW  = -4 pi G rho_s r_s^3 ln(1 + r / r_s) / r                      */
+/*   Phi_Hern = -G M_H / (r + a_H)                                           */
+/*   Phi_disk = -G M_d / sqrt(R^2 + (a_d + sqrt(z^2 + b_d^2))^2)             */
+/* with r, R = sqrt(x^2 + y^2) and z measured from the host's centre.  The   */
+/* host is passed as a flat array:                                           */
+/*   [0] G, [1..3] centre, [4] rho_s, [5] r_s, [6] M_H, [7] a_H,              */
+/*   [8] number of disks (0..4), then M_d, a_d, b_d of each disk.             */
+/* A part with zero mass (density) is absent.  The acceleration is minus the */
+/* gradient of the sum, differentiated by hand:                              */
+/*   NFW:  -G M(<r) x / r^3,  M(<r) = 4 pi rho_s r_s^3 [ln(1+u) - u/(1+u)]   */
+/*   Hern: -G M_H x / (r (r + a_H)^2)                                        */
+/*   disk: -G M_d (x, y, z (a_d + zeta) / zeta) / D^(3/2),                   */
+/*         zeta = sqrt(z^2 + b_d^2), D = R^2 + (a_d + zeta)^2.                */
 /* Kick-drift-kick with individual power-of-two steps: at sub-step s a        */
 /* particle of bin b gets the opening half kick dt_b / 2 when its step opens  */
 /* at s (phase 0), the closing half kick after the drift of s when its step   */
 /* closes at s + 1 (phase 1); dt_b = dt_max / 2^b.                            */
 /* ------------------------------------------------------------------------- */
-double orc_host_mass(double r, double Mn, double Rs)
+double orc_host_mass(double r, double rho_s, double r_s)
 {
-    const double x = r / Rs;
-    return Mn * (log1p(x) - x / (1.0 + x));
+    const double u = r / r_s;
+    return 4.0 * ORC_PI * rho_s * r_s * r_s * r_s * (log1p(u) - u / (1.0 + u));
 }
 
-double orc_host_phi(double r, double G, double Mn, double Rs)
+double orc_host_phi(const double* host, double x, double y, double z)
 {
-    if (r == 0.0) return -G * Mn / Rs;
-    return -G * Mn * log1p(r / Rs) / r;
+    const double G = host[0];
+    const double dx = x - host[1], dy = y - host[2], dz = z - host[3];
+    const double r = sqrt(dx * dx + dy * dy + dz * dz);
+    double phi = 0.0;
+    if (host[4] != 0.0) {
+        const double k = 4.0 * ORC_PI * G * host[4] * host[5] * host[5] * host[5];
+        phi += (r == 0.0) ? -k / host[5] : -k * log1p(r / host[5]) / r;
+    }
+    if (host[6] != 0.0) phi += -G * host[6] / (r + host[7]);
+    const int nd = (int)host[8];
+    for (int d = 0; d < nd; ++d) {
+        const double M = host[9 + 3 * d], a = host[10 + 3 * d], b = host[11 + 3 * d];
+        const double s = a + sqrt(dz * dz + b * b);
+        phi += -G * M / sqrt(dx * dx + dy * dy + s * s);
+    }
+    return phi;
+}
+
+void orc_host_accel(const double* host, double x, double y, double z, double* acc)
+{
+    const double G = host[0];
+    const double dx = x - host[1], dy = y - host[2], dz = z - host[3];
+    const double r = sqrt(dx * dx + dy * dy + dz * dz);
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    if (r > 0.0) {
+        double f = 0.0;
+        if (host[4] != 0.0) f += -G * orc_host_mass(r, host[4], host[5]) / (r * r * r);
+        if (host[6] != 0.0) f += -G * host[6] / (r * (r + host[7]) * (r + host[7]));
+        ax += f * dx; ay += f * dy; az += f * dz;
+    }
+    const int nd = (int)host[8];
+    for (int d = 0; d < nd; ++d) {
+        const double M = host[9 + 3 * d], a = host[10 + 3 * d], b = host[11 + 3 * d];
+        const double zeta = sqrt(dz * dz + b * b);
+        const double D = dx * dx + dy * dy + (a + zeta) * (a + zeta);
+        const double f = -G * M / (D * sqrt(D));
+        ax += f * dx; ay += f * dy; az += f * dz * (a + zeta) / zeta;
+    }
+    acc[0] = ax; acc[1] = ay; acc[2] = az;
 }
 
 void orc_host_kick(int n, const double* px, const double* py, const double* pz, double* vx, double* vy, double* vz,
-                   const int* bins, int n_bins, int substep, int phase, double dt_max,
-                   double G, double Mn, double Rs, double cx, double cy, double cz)
+                   const int* bins, int n_bins, int substep, int phase, double dt_max, const double* host)
 {
     for (int i = 0; i < n; ++i) {
         const int b = bins ? bins[i] : 0;
         const int period = 1 << (n_bins - 1 - b);
         const int due = phase == 0 ? (substep % period == 0) : ((substep + 1) % period == 0);
         if (!due) continue;
-        const double dx = px[i] - cx, dy = py[i] - cy, dz = pz[i] - cz;
-        const double r = sqrt(dx * dx + dy * dy + dz * dz);
-        if (r == 0.0) continue;
-        const double f = -G * orc_host_mass(r, Mn, Rs) / (r * r * r) * (0.5 * ldexp(dt_max, -b));
-        vx[i] += f * dx; vy[i] += f * dy; vz[i] += f * dz;
+        double a[3];
+        orc_host_accel(host, px[i], py[i], pz[i], a);
+        const double h = 0.5 * ldexp(dt_max, -b);
+        vx[i] += a[0] * h; vy[i] += a[1] * h; vz[i] += a[2] * h;
     }
 }
 

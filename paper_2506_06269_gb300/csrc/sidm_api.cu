@@ -1407,28 +1407,100 @@ extern "C" int sidm_scatter_step_binned(sidm_ctx* c, uint64_t seed, uint64_t ste
     return rc;
 }
 
-// Half kick by the analytic NFW host for the particles whose individual step
+constexpr double kPiD = 3.14159265358979323846;
+
+// Analytic host galaxy (Sect. 4.1): NFW halo, Hernquist bulge and up to four
+// Miyamoto-Nagai disks, in FP64.  d = x - centre.  The acceleration is the
+// hand-differentiated -grad Phi of each part:
+//   spherical parts: -G [M_NFW(<r) / r^3 + M_H / (r (r + a_H)^2)] d,
+//                    M_NFW(<r) = 4 pi rho_s r_s^3 (ln(1 + u) - u / (1 + u)), u = r / r_s;
+//   disk:            -G M_d D^(-3/2) (dx, dy, dz (a_d + zeta) / zeta),
+//                    zeta = sqrt(dz^2 + b_d^2), D = R^2 + (a_d + zeta)^2.
+__device__ __forceinline__ void host_accel(const sidm_host& H, double dx, double dy, double dz, double& ax,
+                                           double& ay, double& az)
+{
+    const double R2 = dx * dx + dy * dy;
+    const double r2 = R2 + dz * dz;
+    ax = ay = az = 0.0;
+    if (r2 > 0.0) {
+        const double r = sqrt(r2);
+        double f = 0.0;
+        if (H.rho_s != 0.0) {
+            const double u = r / H.r_s;
+            const double m = 4.0 * kPiD * H.rho_s * H.r_s * H.r_s * H.r_s * (log1p(u) - u / (1.0 + u));
+            f += m / (r2 * r);
+        }
+        if (H.M_H != 0.0) {
+            const double ra = r + H.a_H;
+            f += H.M_H / (r * ra * ra);
+        }
+        ax = -H.G * f * dx; ay = -H.G * f * dy; az = -H.G * f * dz;
+    }
+    for (int k = 0; k < H.n_disks; ++k) {
+        const double zeta = sqrt(dz * dz + H.b_d[k] * H.b_d[k]);
+        const double sz = H.a_d[k] + zeta;
+        const double rd = rsqrt(R2 + sz * sz);
+        const double f = -H.G * H.M_d[k] * rd * rd * rd;
+        ax += f * dx;
+        ay += f * dy;
+        az += f * dz * (sz / zeta);
+    }
+}
+
+__device__ __forceinline__ double host_phi(const sidm_host& H, double dx, double dy, double dz)
+{
+    const double R2 = dx * dx + dy * dy;
+    const double r = sqrt(R2 + dz * dz);
+    double phi = 0.0;
+    if (H.rho_s != 0.0) {
+        const double k = 4.0 * kPiD * H.G * H.rho_s * H.r_s * H.r_s * H.r_s;
+        phi -= (r > 0.0) ? k * log1p(r / H.r_s) / r : k / H.r_s;
+    }
+    if (H.M_H != 0.0) phi -= H.G * H.M_H / (r + H.a_H);
+    for (int k = 0; k < H.n_disks; ++k) {
+        const double sz = H.a_d[k] + sqrt(dz * dz + H.b_d[k] * H.b_d[k]);
+        phi -= H.G * H.M_d[k] * rsqrt(R2 + sz * sz);
+    }
+    return phi;
+}
+
+// Half kick by the analytic host for the particles whose individual step
 // opens (phase 0) or closes (phase 1) at this sub-step; FP64 acceleration.
 template <class R>
 __global__ void k_host_kick(int64_t N, const double* __restrict__ pos, R* __restrict__ vel,
                             const int32_t* __restrict__ bins, int n_bins, int substep, int phase, double dt_max,
-                            double G, double Mn, double Rs, double cx, double cy, double cz)
+                            const sidm_host H)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const int b = bins ? bins[i] : 0;
         const int period = 1 << (n_bins - 1 - b);
         const bool due = phase == 0 ? (substep % period == 0) : ((substep + 1) % period == 0);
         if (!due) continue;
-        const double dx = pos[i] - cx, dy = pos[N + i] - cy, dz = pos[2 * N + i] - cz;
-        const double r = sqrt(dx * dx + dy * dy + dz * dz);
-        if (r == 0.0) continue;
-        const double x = r / Rs;
-        const double m = Mn * (log1p(x) - x / (1.0 + x));
-        const double f = -G * m / (r * r * r) * (0.5 * ldexp(dt_max, -b));
-        vel[i] = (R)((double)vel[i] + f * dx);
-        vel[N + i] = (R)((double)vel[N + i] + f * dy);
-        vel[2 * N + i] = (R)((double)vel[2 * N + i] + f * dz);
+        double ax, ay, az;
+        host_accel(H, pos[i] - H.center[0], pos[N + i] - H.center[1], pos[2 * N + i] - H.center[2], ax, ay, az);
+        const double hdt = 0.5 * ldexp(dt_max, -b);
+        vel[i] = (R)((double)vel[i] + ax * hdt);
+        vel[N + i] = (R)((double)vel[N + i] + ay * hdt);
+        vel[2 * N + i] = (R)((double)vel[2 * N + i] + az * hdt);
     }
+}
+
+__global__ void k_host_potential(int64_t N, const double* __restrict__ pos, double* __restrict__ phi,
+                                 const sidm_host H)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        phi[i] = host_phi(H, pos[i] - H.center[0], pos[N + i] - H.center[1], pos[2 * N + i] - H.center[2]);
+}
+
+static bool host_ok(const sidm_host* h)
+{
+    if (!(h->G >= 0.0) || !(h->rho_s >= 0.0) || !(h->r_s > 0.0) || !(h->M_H >= 0.0) || !(h->a_H > 0.0)) return false;
+    if (h->n_disks < 0 || h->n_disks > SIDM_HOST_MAX_DISKS) return false;
+    for (int k = 0; k < h->n_disks; ++k)
+        if (!(h->M_d[k] >= 0.0) || !(h->a_d[k] >= 0.0) || !(h->b_d[k] > 0.0)) return false;
+    for (int k = 0; k < 3; ++k)
+        if (!isfinite(h->center[k])) return false;
+    return true;
 }
 
 extern "C" int sidm_host_kick(sidm_ctx* c, const sidm_host* host, double dt_max, int32_t n_bins, int32_t substep,
@@ -1440,18 +1512,29 @@ extern "C" int sidm_host_kick(sidm_ctx* c, const sidm_host* host, double dt_max,
     if (n_bins < 1 || n_bins > 16) return set_err(c, SIDM_EINVAL, "n_bins must be in 1..16");
     if (substep < 0 || substep >= (1 << (n_bins - 1))) return set_err(c, SIDM_EINVAL, "substep out of range");
     if (phase != 0 && phase != 1) return set_err(c, SIDM_EINVAL, "phase must be 0 (opening) or 1 (closing)");
-    if (!(dt_max > 0.0) || !(host->M_n >= 0.0) || !(host->R_s > 0.0)) return set_err(c, SIDM_EINVAL, "bad host or dt_max");
+    if (!(dt_max > 0.0) || !host_ok(host)) return set_err(c, SIDM_EINVAL, "bad host or dt_max");
     SIDM_CUDA(c, ensure_device(c));
     const int64_t N = c->lay.N;
     if (N == 0) return SIDM_OK;
     if (c->cfg.precision == SIDM_FP64)
         SIDM_LAUNCH(c, k_host_kick<double><<<grid_for(c, N, 256), 256, 0, s>>>(N, pos, (double*)vel, bins, n_bins, substep,
-                                                                              phase, dt_max, host->G, host->M_n, host->R_s,
-                                                                              host->center[0], host->center[1], host->center[2]));
+                                                                              phase, dt_max, *host));
     else
         SIDM_LAUNCH(c, k_host_kick<float><<<grid_for(c, N, 256), 256, 0, s>>>(N, pos, (float*)vel, bins, n_bins, substep,
-                                                                             phase, dt_max, host->G, host->M_n, host->R_s,
-                                                                             host->center[0], host->center[1], host->center[2]));
+                                                                             phase, dt_max, *host));
+    return SIDM_OK;
+}
+
+extern "C" int sidm_host_potential(sidm_ctx* c, const sidm_host* host, const double* pos, double* phi, cudaStream_t s)
+{
+    if (!c) return SIDM_EINVAL;
+    if (!c->has_layout) return set_err(c, SIDM_EINVAL, "sidm_build_cells must come first");
+    if (!host || ((!pos || !phi) && c->lay.N > 0)) return set_err(c, SIDM_EINVAL, "null argument");
+    if (!host_ok(host)) return set_err(c, SIDM_EINVAL, "bad host");
+    SIDM_CUDA(c, ensure_device(c));
+    const int64_t N = c->lay.N;
+    if (N == 0) return SIDM_OK;
+    SIDM_LAUNCH(c, k_host_potential<<<grid_for(c, N, 256), 256, 0, s>>>(N, pos, phi, *host));
     return SIDM_OK;
 }
 

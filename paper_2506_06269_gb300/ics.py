@@ -17,6 +17,13 @@ Profiles (code units, G = 1, total mass inside the truncation radius = 1):
 * Uniform box: positions uniform in ``[0, L)^3``, Maxwellian velocities with a
   fixed one-dimensional dispersion.
 
+The satellite set-up of Sect. 4.1 (a Milky-Way-like host of six analytic parts
+and the satellite's initial position and velocity) is given in the paper in
+kpc, M_sun and km/s; ``milky_way_host`` and ``satellite_orbit`` convert it to
+the code units of the NFW halo above, read as the paper's halo of Sect. 2
+(rho_0 = 4.42e7 M_sun/kpc^3, r_s = 1.28 kpc): length unit r_s, mass unit the
+mass inside ``r_cut``, G = 1.
+
 Velocities of the halos are isotropic Maxwellian with the local Jeans
 dispersion of the *untruncated* profile,
 ``sigma_r^2(r) = (1/rho) int_r^inf rho(r') M(r') / r'^2 dr'``, evaluated by
@@ -37,7 +44,7 @@ from scipy import integrate
 
 __all__ = [
     "Halo", "Batch", "hernquist", "nfw", "cored_nfw", "uniform_box",
-    "batch", "nfw_vmax", "NFW_RHO_S",
+    "batch", "nfw_vmax", "NFW_RHO_S", "satellite_units", "milky_way_host", "satellite_orbit",
 ]
 
 # NFW normalisation: mass inside 10 r_s equals 1.
@@ -165,6 +172,42 @@ def nfw(n: int, seed: int, r_cut: float = 10.0) -> Halo:
     r = np.maximum(r, 1e-7)
     sigma = np.exp(np.interp(np.log(r), np.log(r_sig), np.log(sig)))
     return _finish(rng, r, sigma, "nfw", {"r_cut": r_cut})
+
+
+# The paper's halo (Sect. 2) and Milky-Way-like host (Sect. 4.1), physical units.
+G_KPC_KMS2_PER_MSUN = 4.30091727e-6          # gravitational constant in kpc (km/s)^2 / M_sun
+HALO_RHO0_MSUN_KPC3, HALO_RS_KPC = 4.42e7, 1.28
+HOST_NFW = (8.54e6, 19.6)                     # rho_s [M_sun/kpc^3], r_s [kpc]
+HOST_BULGE = (9.23e9, 1.3)                    # M_H [M_sun], a_H [kpc]
+HOST_DISKS = ((3.52e10, 2.5, 0.3),            # thin stellar: M_d [M_sun], a_d, b_d [kpc]
+              (1.05e10, 3.02, 0.9),           # thick stellar
+              (1.2e9, 1.5, 0.045),            # thin gas
+              (1.1e10, 7.0, 0.085))           # thick gas
+SATELLITE_POS_KPC = (58.16, 40.12, 101.41)
+SATELLITE_VEL_KMS = (45.94, 83.42, 53.12)
+
+
+def satellite_units(r_cut: float = 10.0):
+    """(length kpc, mass M_sun, velocity km/s) of the code units of ``nfw(r_cut=...)``
+    read as the paper's halo: length r_s, mass inside r_cut, G = 1."""
+    length = HALO_RS_KPC
+    mass = 4.0 * math.pi * HALO_RHO0_MSUN_KPC3 * length ** 3 * (math.log1p(r_cut) - r_cut / (1.0 + r_cut))
+    return length, mass, math.sqrt(G_KPC_KMS2_PER_MSUN * mass / length)
+
+
+def milky_way_host(r_cut: float = 10.0) -> dict:
+    """The six-part host of Sect. 4.1 in code units (G = 1, centre at the origin)."""
+    L, M, _ = satellite_units(r_cut)
+    return {"G": 1.0, "center": (0.0, 0.0, 0.0),
+            "nfw": (HOST_NFW[0] * L ** 3 / M, HOST_NFW[1] / L),
+            "bulge": (HOST_BULGE[0] / M, HOST_BULGE[1] / L),
+            "disks": [(m / M, a / L, b / L) for m, a, b in HOST_DISKS]}
+
+
+def satellite_orbit(r_cut: float = 10.0):
+    """Initial position and velocity of the satellite's centre (Sect. 4.1), code units."""
+    L, _, V = satellite_units(r_cut)
+    return (np.array(SATELLITE_POS_KPC) / L, np.array(SATELLITE_VEL_KMS) / V)
 
 
 def cored_nfw(n: int, seed: int, r_core: float = 0.05, contrast: float = 1e3,

@@ -43,7 +43,24 @@ class SidmConfig(C.Structure):
 
 
 class SidmHost(C.Structure):
-    _fields_ = [("G", C.c_double), ("M_n", C.c_double), ("R_s", C.c_double), ("center", C.c_double * 3)]
+    _fields_ = [("G", C.c_double), ("center", C.c_double * 3), ("rho_s", C.c_double), ("r_s", C.c_double),
+                ("M_H", C.c_double), ("a_H", C.c_double), ("n_disks", C.c_int32), ("pad_", C.c_int32),
+                ("M_d", C.c_double * 4), ("a_d", C.c_double * 4), ("b_d", C.c_double * 4)]
+
+
+def host_struct(host) -> SidmHost:
+    """sidm_host from a dict: G, center, and any of nfw = (rho_s, r_s),
+    bulge = (M_H, a_H), disks = [(M_d, a_d, b_d), ...] (at most 4)."""
+    disks = list(host.get("disks", ()))
+    if len(disks) > 4:
+        raise ValueError("at most 4 disks")
+    rho_s, r_s = host.get("nfw") or (0.0, 1.0)
+    m_h, a_h = host.get("bulge") or (0.0, 1.0)
+    pad = disks + [(0.0, 0.0, 1.0)] * (4 - len(disks))
+    return SidmHost(float(host["G"]), (C.c_double * 3)(*[float(x) for x in host.get("center", (0.0, 0.0, 0.0))]),
+                    float(rho_s), float(r_s), float(m_h), float(a_h), len(disks), 0,
+                    (C.c_double * 4)(*[float(d[0]) for d in pad]), (C.c_double * 4)(*[float(d[1]) for d in pad]),
+                    (C.c_double * 4)(*[float(d[2]) for d in pad]))
 
 
 class SidmError(RuntimeError):
@@ -87,12 +104,13 @@ def load_library():
     L.sidm_timestep_criterion.argtypes = [vp, C.c_double, C.c_double, C.c_double, i32, vp, vp, vp, vp, vp]
     L.sidm_scatter_step_binned.argtypes = [vp, u64, u64, vp, C.c_double, i32, i32, vp, vp, vp, vp, vp]
     L.sidm_host_kick.argtypes = [vp, C.POINTER(SidmHost), C.c_double, i32, i32, i32, vp, vp, vp, vp]
+    L.sidm_host_potential.argtypes = [vp, C.POINTER(SidmHost), vp, vp, vp]
     L.sidm_energy_momentum_static.argtypes = [i32, vp, i32, vp, vp, vp, vp, vp]
     for f in ("sidm_create", "sidm_destroy", "sidm_build_cells", "sidm_kernel_sizes", "sidm_scatter_step",
               "sidm_energy_momentum", "sidm_status", "sidm_get_perm", "sidm_neighbours", "sidm_get_events",
               "sidm_lambda_eval", "sidm_drift", "sidm_get_sum_p", "sidm_kernel_times", "sidm_diagnostics",
               "sidm_energy_momentum_static", "sidm_warm_start", "sidm_local_diagnostics", "sidm_timestep_criterion",
-              "sidm_scatter_step_binned", "sidm_host_kick"):
+              "sidm_scatter_step_binned", "sidm_host_kick", "sidm_host_potential"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -103,7 +121,7 @@ EXPORTED = ["sidm_create", "sidm_destroy", "sidm_last_error", "sidm_create_error
             "sidm_neighbours", "sidm_get_events", "sidm_lambda_eval", "sidm_drift", "sidm_get_sum_p",
             "sidm_launch_count", "sidm_kernel_times", "sidm_diagnostics", "sidm_energy_momentum_static",
             "sidm_warm_start", "sidm_local_diagnostics", "sidm_timestep_criterion", "sidm_scatter_step_binned",
-            "sidm_host_kick"]
+            "sidm_host_kick", "sidm_host_potential"]
 
 
 def _torch():
@@ -161,11 +179,16 @@ def sidm_scatter_step_binned(ctx, seed, step, xs, dt_max, n_bins, substep, bins,
 
 
 def sidm_host_kick(ctx, host, dt_max, n_bins, substep, phase, bins, pos, vel, stream=None):
-    """host = (G, M_n, R_s, (cx, cy, cz)); see include/sidm.h."""
-    G, Mn, Rs, c = host
-    hs = SidmHost(float(G), float(Mn), float(Rs), (C.c_double * 3)(*[float(x) for x in c]))
+    """host: a dict as host_struct takes; see include/sidm.h."""
+    hs = host_struct(host)
     _check(ctx, load_library().sidm_host_kick(ctx, C.byref(hs), float(dt_max), int(n_bins), int(substep), int(phase),
                                               _ptr(bins), _ptr(pos), _ptr(vel), _stream(stream)))
+
+
+def sidm_host_potential(ctx, host, pos, phi, stream=None):
+    """Host potential at every particle into phi (f64 [N]); see include/sidm.h."""
+    hs = host_struct(host)
+    _check(ctx, load_library().sidm_host_potential(ctx, C.byref(hs), _ptr(pos), _ptr(phi), _stream(stream)))
 
 
 def sidm_scatter_step(ctx, seed, step, xs, dt, mass, vel, stats=None, stream=None):
@@ -341,6 +364,9 @@ class Context:
 
     def host_kick(self, host, dt_max, n_bins, substep, phase, bins, pos, vel, stream=None):
         sidm_host_kick(self.handle, host, dt_max, n_bins, substep, phase, bins, pos, vel, stream)
+
+    def host_potential(self, host, pos, phi, stream=None):
+        sidm_host_potential(self.handle, host, pos, phi, stream)
 
     def energy_momentum(self, mass, vel, out, comp=None, stream=None):
         sidm_energy_momentum(self.handle, mass, vel, out, comp, stream)

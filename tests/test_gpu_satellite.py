@@ -1,14 +1,18 @@
-"""Satellite pieces on the GPU against the FP64 oracle: the analytic-host kick on
-individual power-of-two steps, the scatter step on individual steps, and a
-short kick-drift-kick run of a satellite in the host (Sect. 4.1 evolves the
-satellite in an external potential; individual time steps).
+"""Satellite pieces on the GPU against the FP64 oracle: the analytic host's
+kick on individual power-of-two steps and its potential, the scatter step on
+individual steps, and a short kick-drift-kick run of a satellite in the host
+(Sect. 4.1 evolves the satellite in an external potential of six parts --
+NFW halo, Hernquist bulge, four Miyamoto-Nagai disks -- from a given position
+and velocity; individual time steps).
 
 Tolerances: the kick adds an FP64 acceleration to FP32 velocities, so one
-kick agrees to 1e-6 of the speed; the binned scatter step obeys the scatter
-tolerances (event sets equal except |P - u| < 1e-6, velocities to 1e-5 of the
-pair speed scale, per-particle sums to 1e-5); the run without scattering
-(a spherical potential, so neighbouring orbits do not diverge) keeps
-positions to 1e-6 and velocities to 1e-5 relative over three big steps.
+kick agrees to 1e-6 of the speed; the potential is FP64 on both sides with
+different library logarithms and square roots (1e-13); the binned scatter step
+obeys the scatter tolerances (event sets equal except |P - u| < 1e-6,
+velocities to 1e-5 of the pair speed scale, per-particle sums to 1e-5); the
+run without scattering (neighbouring orbits in a smooth potential do not
+diverge) keeps positions to 1e-6 and velocities to 1e-5 relative over three
+big steps.
 """
 import math
 
@@ -26,8 +30,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
-G, MN, RS = 1.0, 1000.0 / (math.log(11.0) - 10.0 / 11.0), 15.3
-HOST = (G, MN, RS, (0.0, 0.0, 0.0))
+HOST = ics.milky_way_host()
 NB, DT_MAX = 4, 0.02
 
 
@@ -37,12 +40,18 @@ def _built():
     build.build()
 
 
-def _satellite(n, seed):
-    """An NFW subhalo on a circular orbit at 30 subhalo scale radii."""
+def _satellite(n, seed, where="orbit"):
+    """An NFW subhalo at the paper's initial position and velocity in the host
+    ("orbit"), or at rest at the host's centre, twice enlarged, so that its
+    particles sample the bulge and the disks ("centre")."""
     halo = ics.nfw(n, seed)
-    pos = halo.pos + np.array([[30.0], [0.0], [0.0]])
-    vc = math.sqrt(G * O.host_mass(30.0, MN, RS) / 30.0)
-    vel = (halo.vel + np.array([[0.0], [vc], [0.0]])).astype(np.float32).astype(np.float64)
+    if where == "orbit":
+        x0, v0 = ics.satellite_orbit()
+        pos = halo.pos + x0[:, None]
+        vel = (halo.vel + v0[:, None]).astype(np.float32).astype(np.float64)
+    else:
+        pos = 2.0 * halo.pos
+        vel = halo.vel.astype(np.float32).astype(np.float64)
     return halo, pos, vel
 
 
@@ -58,8 +67,9 @@ def _context(pos, vel, ids, k=32, flags=0, n_halo=None):
     return ctx, t, perm
 
 
-def test_host_kick_matches_oracle():
-    halo, pos, vel = _satellite(20000, 51)
+@pytest.mark.parametrize("where", ["orbit", "centre"])
+def test_host_kick_matches_oracle(where):
+    halo, pos, vel = _satellite(20000, 51, where)
     n = halo.n
     bins = np.random.default_rng(2).integers(0, NB, n).astype(np.int32)
     ctx, (p, v, ids), perm = _context(pos, vel, halo.ids)
@@ -68,10 +78,42 @@ def test_host_kick_matches_oracle():
     for substep, phase in ((0, 0), (1, 1), (3, 1), (4, 0), (6, 0), (7, 1)):
         ctx.host_kick(HOST, DT_MAX, NB, substep, phase, bins_g, p, v)
         vo = O.host_kick(pos, vo, HOST, DT_MAX, bins, NB, substep, phase)
+    assert ctx.status() == 0
     got = np.empty((3, n)); got[:, perm] = v.cpu().numpy().astype(np.float64)
     speed = np.linalg.norm(vo, axis=0)
     assert np.all(np.abs(got - vo).max(axis=0) <= 1e-6 * speed)
     assert not np.allclose(vo, vel)
+    ctx.close()
+
+
+@pytest.mark.parametrize("where", ["orbit", "centre"])
+def test_host_potential_matches_oracle(where):
+    halo, pos, vel = _satellite(5000, 54, where)
+    n = halo.n
+    ctx, (p, v, ids), perm = _context(pos, vel, halo.ids)
+    phi = torch.zeros(n, dtype=torch.float64, device=ctx.device)
+    ctx.host_potential(HOST, p, phi)
+    assert ctx.status() == 0
+    got = np.empty(n); got[perm] = phi.cpu().numpy()
+    ctx.close()
+    want = O.host_phi(HOST, pos)
+    np.testing.assert_allclose(got, want, rtol=1e-13, atol=0)
+
+
+def test_host_arguments_are_checked():
+    from paper_2506_06269_gb300 import sidm
+    halo, pos, vel = _satellite(300, 55)
+    ctx, (p, v, ids), perm = _context(pos, vel, halo.ids)
+    phi = torch.zeros(halo.n, dtype=torch.float64, device=ctx.device)
+    bad = [dict(HOST, disks=HOST["disks"] + [(1.0, 1.0, 1.0)]),      # five disks
+           dict(HOST, disks=[(1.0, 1.0, 0.0)]),                     # b_d = 0
+           dict(HOST, nfw=(1.0, 0.0)),                              # r_s = 0
+           dict(HOST, bulge=(-1.0, 1.0))]                           # negative mass
+    for host in bad:
+        with pytest.raises((sidm.SidmError, ValueError)):
+            ctx.host_potential(host, p, phi)
+        with pytest.raises((sidm.SidmError, ValueError)):
+            ctx.host_kick(host, DT_MAX, NB, 0, 0, None, p, v)
     ctx.close()
 
 
@@ -124,6 +166,7 @@ def test_satellite_run_without_scattering_matches_oracle():
     halo, pos, vel = _satellite(8192, 53)
     n = halo.n
     r = np.linalg.norm(halo.pos, axis=0)
+    assert np.linalg.norm(pos.mean(axis=1)) > 90.0          # far out on the paper's orbit
     bins = np.clip((3 - np.log2(np.maximum(r, 1e-3) / 0.25)).astype(np.int32), 0, NB - 1).astype(np.int32)
     ctx, (p, v, ids), perm = _context(pos, vel, halo.ids)
     hg = torch.zeros(n, dtype=torch.float32, device=ctx.device)
