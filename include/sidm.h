@@ -247,6 +247,18 @@ int sidm_lambda_eval(sidm_ctx* ctx, int64_t n, const double* d_dev, const double
 int sidm_drift(sidm_ctx* ctx, const double* dt_dev, double* pos_dev, const void* vel_dev,
                cudaStream_t stream);
 
+/* Reflecting spherical boundary (Sect. 2: the isolated halos are kept inside
+ * a sphere of 200 kpc that turns outward-moving particles back, leaving the
+ * energy unchanged).  Reading: a particle of halo h with |x - c_h| > R_h and
+ * v . (x - c_h) > 0 has the radial part of its velocity reversed,
+ *   v <- v - 2 (v . d) d / |d|^2,  d = x - c_h   (speed kept; FP64, then
+ * rounded to the velocity's type).  Call it after sidm_drift.
+ *   bound_dev : device f64 [n_halos][4] = (c_x, c_y, c_z, R); R <= 0: no boundary
+ *   pos_dev   : f64 [3][N];  vel_dev : [3][N] f32/f64 by precision, updated
+ * Arrays in the order left by sidm_build_cells (which must come first). */
+int sidm_reflect_boundary(sidm_ctx* ctx, const double* bound_dev, const double* pos_dev, void* vel_dev,
+                          cudaStream_t stream);
+
 /* Per-particle sum_j P_ij of the last scatter step (SIDM_FLAG_SUM_P), f32 [N]. */
 int sidm_get_sum_p(sidm_ctx* ctx, float* out_dev, cudaStream_t stream);
 

@@ -83,6 +83,7 @@ def lib():
             L.orc_host_phi.argtypes = [vp, d, d, d]; L.orc_host_phi.restype = d
             L.orc_host_accel.argtypes = [vp, d, d, d, vp]
             L.orc_host_kick.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, i32, d, vp]
+            L.orc_reflect.argtypes = [i32, vp, vp, vp, vp, vp, vp, d, d, d, d]
             L.orc_pairs_halo.restype = i32
             L.orc_sort_events.argtypes = [vp, i64]
             L.orc_apply_events.argtypes = [vp, i64, vp, vp, vp, vp, vp]
@@ -281,6 +282,14 @@ def host_kick(pos, vel, host, dt_max, bins=None, n_bins=1, substep=0, phase=0):
     hp = host_params(host)
     lib().orc_host_kick(n, _p(p[0]), _p(p[1]), _p(p[2]), _p(v[0]), _p(v[1]), _p(v[2]), _p(bn), int(n_bins),
                         int(substep), int(phase), float(dt_max), _p(hp))
+    return v
+
+
+def reflect(pos, vel, center, r_b):
+    """Reflecting sphere of radius r_b about center (see orc_reflect); returns new vel."""
+    p = _c(pos, np.float64); v = np.array(vel, dtype=np.float64, copy=True, order="C"); n = p.shape[1]
+    lib().orc_reflect(n, _p(p[0]), _p(p[1]), _p(p[2]), _p(v[0]), _p(v[1]), _p(v[2]),
+                      float(center[0]), float(center[1]), float(center[2]), float(r_b))
     return v
 
 

@@ -935,6 +935,26 @@ void orc_host_kick(int n, const double* px, const double* py, const double* pz, 
     }
 }
 
+/* Reflecting spherical boundary (Sect. 2: outward-moving particles beyond a  */
+/* sphere about the halo are turned back without changing the energy).       */
+/* Reading: outside radius rb and moving outwards, the velocity is mirrored  */
+/* in the plane tangent to the sphere through the particle,                  */
+/* v <- v - 2 (v . n) n with n the outward unit normal.                      */
+void orc_reflect(int n, const double* px, const double* py, const double* pz, double* vx, double* vy, double* vz,
+                 double cx, double cy, double cz, double rb)
+{
+    if (!(rb > 0.0)) return;
+    for (int i = 0; i < n; ++i) {
+        const double dx = px[i] - cx, dy = py[i] - cy, dz = pz[i] - cz;
+        const double r = sqrt(dx * dx + dy * dy + dz * dz);
+        if (!(r > rb)) continue;
+        const double nx = dx / r, ny = dy / r, nz = dz / r;
+        const double vn = vx[i] * nx + vy[i] * ny + vz[i] * nz;
+        if (!(vn > 0.0)) continue;
+        vx[i] -= 2.0 * vn * nx; vy[i] -= 2.0 * vn * ny; vz[i] -= 2.0 * vn * nz;
+    }
+}
+
 typedef struct { double* p; int n, cap; } orc_xsum;
 
 static void xsum_add(orc_xsum* s, double x)

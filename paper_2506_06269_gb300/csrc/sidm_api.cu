@@ -731,6 +731,29 @@ __global__ void k_drift(int64_t N, int H, const int64_t* __restrict__ halo_off, 
     }
 }
 
+// Reflecting sphere per halo: an outward-moving particle outside it gets the
+// radial part of its velocity reversed (speed kept).
+template <class R>
+__global__ void k_reflect(int64_t N, int H, const int64_t* __restrict__ halo_off, const double* __restrict__ bound,
+                          const double* __restrict__ pos, R* __restrict__ vel)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+        const double* b = bound + 4 * halo_of(halo_off, H, s);
+        const double rb = b[3];
+        if (!(rb > 0.0)) continue;
+        const double dx = pos[s] - b[0], dy = pos[N + s] - b[1], dz = pos[2 * N + s] - b[2];
+        const double d2 = dx * dx + dy * dy + dz * dz;
+        if (!(d2 > rb * rb)) continue;
+        const double vx = vel[s], vy = vel[N + s], vz = vel[2 * N + s];
+        const double vr = vx * dx + vy * dy + vz * dz;
+        if (!(vr > 0.0)) continue;
+        const double k = 2.0 * vr / d2;
+        vel[s] = (R)(vx - k * dx);
+        vel[N + s] = (R)(vy - k * dy);
+        vel[2 * N + s] = (R)(vz - k * dz);
+    }
+}
+
 template <class R>
 __global__ void k_lambda_eval(int64_t n, const double* __restrict__ d, const double* __restrict__ hi,
                               const double* __restrict__ hj, double* __restrict__ out, const R* __restrict__ T)
@@ -1631,6 +1654,22 @@ extern "C" int sidm_drift(sidm_ctx* c, const double* dt, double* pos, const void
     else
         SIDM_LAUNCH(c, k_drift<float><<<grid_for(c, c->lay.N, 256), 256, 0, s>>>(c->lay.N, c->lay.H, c->d_halo_off, dt, pos,
                                                                                (const float*)vel));
+    return SIDM_OK;
+}
+
+extern "C" int sidm_reflect_boundary(sidm_ctx* c, const double* bound, const double* pos, void* vel, cudaStream_t s)
+{
+    if (!c) return SIDM_EINVAL;
+    if (!c->has_layout) return set_err(c, SIDM_EINVAL, "sidm_build_cells must come first");
+    if (!bound || (c->lay.N > 0 && (!pos || !vel))) return set_err(c, SIDM_EINVAL, "null argument");
+    if (c->lay.N == 0) return SIDM_OK;
+    SIDM_CUDA(c, ensure_device(c));
+    if (c->cfg.precision == SIDM_FP64)
+        SIDM_LAUNCH(c, k_reflect<double><<<grid_for(c, c->lay.N, 256), 256, 0, s>>>(c->lay.N, c->lay.H, c->d_halo_off,
+                                                                                  bound, pos, (double*)vel));
+    else
+        SIDM_LAUNCH(c, k_reflect<float><<<grid_for(c, c->lay.N, 256), 256, 0, s>>>(c->lay.N, c->lay.H, c->d_halo_off,
+                                                                                 bound, pos, (float*)vel));
     return SIDM_OK;
 }
 

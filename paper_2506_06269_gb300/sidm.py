@@ -105,12 +105,13 @@ def load_library():
     L.sidm_scatter_step_binned.argtypes = [vp, u64, u64, vp, C.c_double, i32, i32, vp, vp, vp, vp, vp]
     L.sidm_host_kick.argtypes = [vp, C.POINTER(SidmHost), C.c_double, i32, i32, i32, vp, vp, vp, vp]
     L.sidm_host_potential.argtypes = [vp, C.POINTER(SidmHost), vp, vp, vp]
+    L.sidm_reflect_boundary.argtypes = [vp, vp, vp, vp, vp]
     L.sidm_energy_momentum_static.argtypes = [i32, vp, i32, vp, vp, vp, vp, vp]
     for f in ("sidm_create", "sidm_destroy", "sidm_build_cells", "sidm_kernel_sizes", "sidm_scatter_step",
               "sidm_energy_momentum", "sidm_status", "sidm_get_perm", "sidm_neighbours", "sidm_get_events",
               "sidm_lambda_eval", "sidm_drift", "sidm_get_sum_p", "sidm_kernel_times", "sidm_diagnostics",
               "sidm_energy_momentum_static", "sidm_warm_start", "sidm_local_diagnostics", "sidm_timestep_criterion",
-              "sidm_scatter_step_binned", "sidm_host_kick", "sidm_host_potential"):
+              "sidm_scatter_step_binned", "sidm_host_kick", "sidm_host_potential", "sidm_reflect_boundary"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -121,7 +122,7 @@ EXPORTED = ["sidm_create", "sidm_destroy", "sidm_last_error", "sidm_create_error
             "sidm_neighbours", "sidm_get_events", "sidm_lambda_eval", "sidm_drift", "sidm_get_sum_p",
             "sidm_launch_count", "sidm_kernel_times", "sidm_diagnostics", "sidm_energy_momentum_static",
             "sidm_warm_start", "sidm_local_diagnostics", "sidm_timestep_criterion", "sidm_scatter_step_binned",
-            "sidm_host_kick", "sidm_host_potential"]
+            "sidm_host_kick", "sidm_host_potential", "sidm_reflect_boundary"]
 
 
 def _torch():
@@ -189,6 +190,11 @@ def sidm_host_potential(ctx, host, pos, phi, stream=None):
     """Host potential at every particle into phi (f64 [N]); see include/sidm.h."""
     hs = host_struct(host)
     _check(ctx, load_library().sidm_host_potential(ctx, C.byref(hs), _ptr(pos), _ptr(phi), _stream(stream)))
+
+
+def sidm_reflect_boundary(ctx, bound, pos, vel, stream=None):
+    """bound: device f64 [H][4] = (cx, cy, cz, R) per halo; see include/sidm.h."""
+    _check(ctx, load_library().sidm_reflect_boundary(ctx, _ptr(bound), _ptr(pos), _ptr(vel), _stream(stream)))
 
 
 def sidm_scatter_step(ctx, seed, step, xs, dt, mass, vel, stats=None, stream=None):
@@ -367,6 +373,9 @@ class Context:
 
     def host_potential(self, host, pos, phi, stream=None):
         sidm_host_potential(self.handle, host, pos, phi, stream)
+
+    def reflect_boundary(self, bound, pos, vel, stream=None):
+        sidm_reflect_boundary(self.handle, bound, pos, vel, stream)
 
     def energy_momentum(self, mass, vel, out, comp=None, stream=None):
         sidm_energy_momentum(self.handle, mass, vel, out, comp, stream)
