@@ -168,41 +168,47 @@ __global__ void k_sort_hist(const unsigned long long* __restrict__ key, int64_t 
     hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = cnt[threadIdx.x];
 }
 
-// exclusive scan of hist[0..len) in one CTA of 1024 threads: coalesced tiles
-// of 1024 entries, warp-shuffle scans, a running carry between tiles
-__global__ void __launch_bounds__(1024) k_sort_scan(uint32_t* __restrict__ hist, int64_t len)
+// exclusive scan of x over the 256 threads of a CTA (warp shuffles, then the
+// eight warp totals); *total receives the sum
+__device__ __forceinline__ uint32_t cta256_exclusive(uint32_t x, uint32_t* wsum, uint32_t* total)
 {
-    __shared__ uint32_t wsum[32];
-    __shared__ uint32_t carry_sh;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t carry = 0;
-    for (int64_t base = 0; base < len; base += 1024) {
-        const int64_t i = base + threadIdx.x;
-        const uint32_t v = i < len ? hist[i] : 0u;
-        uint32_t x = v;
+    uint32_t inc = x;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) wsum[warp] = x;
-        __syncthreads();
-        if (warp == 0) {
-            const uint32_t w = wsum[lane];
-            uint32_t z = w;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
-                if (lane >= o) z += y;
-            }
-            wsum[lane] = z - w;                 // exclusive warp offsets
-            if (lane == 31) carry_sh = z;       // tile total
-        }
-        __syncthreads();
-        if (i < len) hist[i] = carry + wsum[warp] + x - v;
-        carry += carry_sh;
-        __syncthreads();
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
     }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    uint32_t before = 0u, all = 0u;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) {
+        const uint32_t t = wsum[w];
+        before += w < warp ? t : 0u;
+        all += t;
+    }
+    __syncthreads();
+    *total = all;
+    return before + inc - x;
+}
+
+// Row d of hist (the counts of digit d in every block) scanned in place to its
+// exclusive prefix over blocks, one CTA per digit; rowsum[d] = the row total.
+__global__ void __launch_bounds__(256) k_sort_scan(uint32_t* __restrict__ hist, int nblk, uint32_t* __restrict__ rowsum)
+{
+    __shared__ uint32_t wsum[kSortWarps];
+    uint32_t* row = hist + (int64_t)blockIdx.x * nblk;
+    uint32_t carry = 0u;
+    for (int base = 0; base < nblk; base += 256) {
+        const int i = base + threadIdx.x;
+        const uint32_t v = i < nblk ? row[i] : 0u;
+        uint32_t tot;
+        const uint32_t ex = cta256_exclusive(v, wsum, &tot);
+        if (i < nblk) row[i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) rowsum[blockIdx.x] = carry;
 }
 
 // Scatter of one tile in 16 rounds of 256 consecutive keys; the rank of a key
@@ -210,12 +216,20 @@ __global__ void __launch_bounds__(1024) k_sort_scan(uint32_t* __restrict__ hist,
 // which keeps the sort stable.
 __global__ void k_sort_scatter(const unsigned long long* __restrict__ key, const uint32_t* __restrict__ val,
                                int64_t n, int shift, int nblk, const uint32_t* __restrict__ hist,
-                               unsigned long long* __restrict__ okey, uint32_t* __restrict__ oval)
+                               const uint32_t* __restrict__ rowsum, unsigned long long* __restrict__ okey,
+                               uint32_t* __restrict__ oval)
 {
     __shared__ uint32_t run[256];
     __shared__ uint32_t woff[kSortWarps][256];
+    __shared__ uint32_t wsum[kSortWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    run[threadIdx.x] = hist[(int64_t)threadIdx.x * nblk + blockIdx.x];
+    {
+        // first slot of digit d in this block: all smaller digits, then digit d
+        // of the earlier blocks
+        uint32_t tot;
+        const uint32_t digit_base = cta256_exclusive(rowsum[threadIdx.x], wsum, &tot);
+        run[threadIdx.x] = digit_base + hist[(int64_t)threadIdx.x * nblk + blockIdx.x];
+    }
     const int64_t tile = (int64_t)blockIdx.x * kSortTile;
     for (int r = 0; r < kSortItems; ++r) {
         if (tile + r * kSortThreads >= n) break;          // uniform across the CTA
@@ -1006,7 +1020,7 @@ extern "C" int sidm_create(sidm_ctx** out, const sidm_config* cfg)
     const size_t rs = fp64 ? 8 : 4;
     c->node_cap = 2 * Lmax + (int64_t)kMaxLevels * (H + 1);
     c->chunk_cap = N / kChunk + H + 1;
-    c->hist_cap = 256 * cdiv(N, kSortTile);
+    c->hist_cap = 256 * cdiv(N, kSortTile) + 256;          // per-block digit counts, then digit totals
     c->stage_bytes = sizeof(int64_t) * (size_t)(8 * (H + 1) + kMaxLevels * (H + 1) + 2 * c->chunk_cap + 64);
 #define ALLOC(p, n) do { e = dev_alloc(&(p), (size_t)(n)); if (e != cudaSuccess) return fail("cudaMalloc " #p, e); } while (0)
     ALLOC(c->d_halo_off, H + 1);
@@ -1186,8 +1200,9 @@ static int build_impl(sidm_ctx* c, double* pos, R* vel, uint32_t* id, cudaStream
     for (int p = 0; p < L.sort_passes; ++p) {
         const int shift = 8 * p;
         SIDM_LAUNCH(c, k_sort_hist<<<nblk, kSortThreads, 0, s>>>(ka, N, shift, nblk, c->d_hist));
-        SIDM_LAUNCH(c, k_sort_scan<<<1, 1024, 0, s>>>(c->d_hist, (int64_t)256 * nblk));
-        SIDM_LAUNCH(c, k_sort_scatter<<<nblk, kSortThreads, 0, s>>>(ka, va, N, shift, nblk, c->d_hist, kb, vb));
+        SIDM_LAUNCH(c, k_sort_scan<<<256, 256, 0, s>>>(c->d_hist, nblk, c->d_hist + (int64_t)256 * nblk));
+        SIDM_LAUNCH(c, k_sort_scatter<<<nblk, kSortThreads, 0, s>>>(ka, va, N, shift, nblk, c->d_hist,
+                                                                     c->d_hist + (int64_t)256 * nblk, kb, vb));
         std::swap(ka, kb);
         std::swap(va, vb);
     }
