@@ -203,9 +203,12 @@ int sidm_scatter_step(sidm_ctx* ctx, uint64_t seed, uint64_t step, const sidm_xs
                       sidm_step_stats* stats_dev, cudaStream_t stream);
 
 /* (a5) Per-halo kinetic energy and momentum, E = sum 1/2 m |v|^2,
- * p = sum m v, in FP64 with compensated (two-sum) accumulation in a fixed
- * order, so repeated calls give identical bits (the paper tracks energy
- * conservation throughout, Sect. 3.4).
+ * p = sum m v (the paper tracks energy conservation throughout, Sect. 3.4).
+ * FP32 velocities are summed exactly as 128-bit integers per chunk of 16384
+ * particles (bits below 2^-94 of the chunk's largest term may drop), FP64
+ * velocities with compensated (two-sum) FP64 accumulation; chunk sums are
+ * merged as double-doubles in a fixed order and scaled by the mass once, so
+ * repeated calls give identical bits.
  *   mass_dev : device f64[n_halos]
  *   vel_dev  : [3][N] velocities (f32 or f64 by precision)
  *   out_dev  : device f64[n_halos][4] = (E, px, py, pz)

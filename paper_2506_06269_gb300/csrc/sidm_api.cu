@@ -12,6 +12,7 @@
 #include <cstdlib>
 
 #include "sidm_internal.cuh"
+#include "sidm_sum.cuh"
 
 using namespace sidm;
 
@@ -649,88 +650,38 @@ __global__ void __launch_bounds__(1024) k_resolve(const sidm_event* __restrict__
 }
 
 // ------------------------------------------------------------------ a5 reduce
-__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e)
-{
-    s = __dadd_rn(a, b);
-    const double bb = __dsub_rn(s, a);
-    e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
-}
+// Per chunk of kChunk particles: the unscaled sums (|v|^2, vx, vy, vz) as
+// double-doubles, exact integers for FP32 velocities (sidm_sum.cuh).
+static_assert(kChunk <= sidm_sum::kMaxChunk, "chunk larger than the exact-sum windows allow");
 
-struct Comp { double s, c; };
-
-__device__ __forceinline__ void comp_add(Comp& x, double v)
-{
-    double s, e;
-    two_sum(x.s, v, s, e);
-    x.s = s;
-    x.c = __dadd_rn(x.c, e);
-}
-
-__device__ __forceinline__ void comp_merge(Comp& x, const Comp& y)
-{
-    double s, e;
-    two_sum(x.s, y.s, s, e);
-    x.s = s;
-    x.c = __dadd_rn(__dadd_rn(x.c, y.c), e);
-}
-
-// Per-chunk compensated partial sums in a fixed order: thread t takes
-// elements t, t+256, ...; then a fixed binary tree over the 256 threads.
 template <class R>
-__global__ void __launch_bounds__(256) k_energy_partial(const R* __restrict__ vel, int64_t N,
-                                                         const int32_t* __restrict__ chunk_halo,
-                                                         const int64_t* __restrict__ chunk_begin,
-                                                         const int64_t* __restrict__ halo_off,
-                                                         const double* __restrict__ mass, double* __restrict__ part)
+__global__ void __launch_bounds__(sidm_sum::chunk_threads<R>()) k_energy_partial(const R* __restrict__ vel, int64_t N,
+                                                                      const int32_t* __restrict__ chunk_halo,
+                                                                      const int64_t* __restrict__ chunk_begin,
+                                                                      const int64_t* __restrict__ halo_off,
+                                                                      double* __restrict__ part)
 {
-    __shared__ Comp sh[4][256];
     const int c = blockIdx.x;
     const int h = chunk_halo[c];
     const int64_t b = chunk_begin[c];
-    int64_t e = b + kChunk; if (e > halo_off[h + 1]) e = halo_off[h + 1];
-    const double m = mass[h];
-    const double hm = __dmul_rn(0.5, m);
-    Comp acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-    for (int64_t s = b + threadIdx.x; s < e; s += 256) {
-        const double x = (double)vel[s], y = (double)vel[N + s], z = (double)vel[2 * N + s];
-        double q = __dmul_rn(x, x);
-        q = __dadd_rn(q, __dmul_rn(y, y));
-        q = __dadd_rn(q, __dmul_rn(z, z));
-        comp_add(acc[0], __dmul_rn(hm, q));
-        comp_add(acc[1], __dmul_rn(m, x));
-        comp_add(acc[2], __dmul_rn(m, y));
-        comp_add(acc[3], __dmul_rn(m, z));
-    }
-#pragma unroll
-    for (int a = 0; a < 4; ++a) sh[a][threadIdx.x] = acc[a];
-    __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if (threadIdx.x < w)
-#pragma unroll
-            for (int a = 0; a < 4; ++a) comp_merge(sh[a][threadIdx.x], sh[a][threadIdx.x + w]);
-        __syncthreads();
-    }
-    if (threadIdx.x < 4) {
-        part[c * 8 + 2 * threadIdx.x] = sh[threadIdx.x][0].s;
-        part[c * 8 + 2 * threadIdx.x + 1] = sh[threadIdx.x][0].c;
-    }
+    int64_t e = b + kChunk;
+    if (e > halo_off[h + 1]) e = halo_off[h + 1];
+    sidm_sum::chunk_sums(vel, N, b, e, part + 8 * (int64_t)c);
 }
 
+// One warp per halo: its chunks merged in a fixed order, scaled by the particle mass.
 __global__ void k_energy_final(int H, int nchunk, const int32_t* __restrict__ chunk_halo,
-                               const double* __restrict__ part, double* __restrict__ out, double* __restrict__ comp)
+                               const double* __restrict__ mass, const double* __restrict__ part,
+                               double* __restrict__ out, double* __restrict__ comp)
 {
-    const int h = blockIdx.x * blockDim.x + threadIdx.x;
-    if (h >= H) return;
-    int lo = 0, hi = nchunk;                        // first chunk of halo h
-    while (lo < hi) { int mid = (lo + hi) >> 1; if (chunk_halo[mid] < h) lo = mid + 1; else hi = mid; }
-    Comp acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-    for (int c = lo; c < nchunk && chunk_halo[c] == h; ++c)
-        for (int a = 0; a < 4; ++a) comp_merge(acc[a], Comp{part[c * 8 + 2 * a], part[c * 8 + 2 * a + 1]});
-    for (int a = 0; a < 4; ++a) {
-        const double v = __dadd_rn(acc[a].s, acc[a].c);
-        out[h * 4 + a] = v;
-        if (comp) comp[h * 4 + a] = __dsub_rn(acc[a].c, __dsub_rn(v, acc[a].s));
-    }
+    const int h = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (h >= H) return;                                  // whole warps
+    auto first_chunk = [&](int hh) {
+        int lo = 0, hi = nchunk;
+        while (lo < hi) { const int mid = (lo + hi) >> 1; if (chunk_halo[mid] < hh) lo = mid + 1; else hi = mid; }
+        return lo;
+    };
+    sidm_sum::halo_result(part, first_chunk(h), first_chunk(h + 1), mass[h], out + 4 * h, comp ? comp + 4 * h : nullptr);
 }
 
 // ------------------------------------------------------------------ harness
@@ -1586,13 +1537,14 @@ extern "C" int sidm_energy_momentum(sidm_ctx* c, const double* mass, const void*
     const LayoutHost& L = c->lay;
     if (L.nchunk > 0) {
         if (c->cfg.precision == SIDM_FP64)
-            SIDM_LAUNCH(c, k_energy_partial<double><<<L.nchunk, 256, 0, s>>>((const double*)vel, L.N, c->d_chunk_halo,
-                                                                            c->d_chunk_begin, c->d_halo_off, mass, c->d_epart));
+            SIDM_LAUNCH(c, k_energy_partial<double><<<L.nchunk, sidm_sum::chunk_threads<double>(), 0, s>>>(
+                (const double*)vel, L.N, c->d_chunk_halo, c->d_chunk_begin, c->d_halo_off, c->d_epart));
         else
-            SIDM_LAUNCH(c, k_energy_partial<float><<<L.nchunk, 256, 0, s>>>((const float*)vel, L.N, c->d_chunk_halo,
-                                                                           c->d_chunk_begin, c->d_halo_off, mass, c->d_epart));
+            SIDM_LAUNCH(c, k_energy_partial<float><<<L.nchunk, sidm_sum::chunk_threads<float>(), 0, s>>>(
+                (const float*)vel, L.N, c->d_chunk_halo, c->d_chunk_begin, c->d_halo_off, c->d_epart));
     }
-    SIDM_LAUNCH(c, k_energy_final<<<(L.H + 127) / 128, 128, 0, s>>>(L.H, L.nchunk, c->d_chunk_halo, c->d_epart, out, comp));
+    SIDM_LAUNCH(c, k_energy_final<<<(L.H + 3) / 4, 128, 0, s>>>(L.H, L.nchunk, c->d_chunk_halo, mass, c->d_epart,
+                                                                     out, comp));
     return SIDM_OK;
 }
 

@@ -4,19 +4,18 @@
 // a host application whose framework owns every byte of the device (its own
 // caching allocator, a fixed memory budget) must not call cudaMalloc or
 // cudaFree.  sidm_energy_momentum_static serves them: it needs no context and
-// keeps its scratch (one FP64 partial sum pair per chunk of 16384 particles)
+// keeps its scratch (four double-double sums per chunk of 16384 particles)
 // in a file-scope __device__ array of fixed size, which every GPU that loads
 // this library holds until the process exits.
 //
-// The arithmetic and its order are those of sidm_energy_momentum: per chunk,
-// thread t sums elements t, t+256, ... with two-sum compensation, then a
-// fixed binary tree over the 256 threads; per halo the chunk partials are
-// merged in chunk order.  The result is therefore bit-identical to the
-// context-based call on the same inputs.
+// The arithmetic is that of sidm_energy_momentum (sidm_sum.cuh, the same
+// chunks of 16384 particles and the same per-chunk and per-halo code), so the
+// result is bit-identical to the context-based call on the same inputs.
 #include <mutex>
 #include <string>
 
 #include "../../include/sidm.h"
+#include "sidm_sum.cuh"
 
 namespace {
 
@@ -34,83 +33,28 @@ struct StaticLayout {
     int chunk_off[SIDM_STATIC_MAX_HALOS + 1];   // first chunk of each halo
 };
 
-struct Comp2 { double s, c; };
-
-__device__ __forceinline__ void two_sum2(double a, double b, double& s, double& e)
-{
-    s = __dadd_rn(a, b);
-    const double bb = __dsub_rn(s, a);
-    e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
-}
-
-__device__ __forceinline__ void comp_add2(Comp2& x, double v)
-{
-    double s, e;
-    two_sum2(x.s, v, s, e);
-    x.s = s;
-    x.c = __dadd_rn(x.c, e);
-}
-
-__device__ __forceinline__ void comp_merge2(Comp2& x, const Comp2& y)
-{
-    double s, e;
-    two_sum2(x.s, y.s, s, e);
-    x.s = s;
-    x.c = __dadd_rn(__dadd_rn(x.c, y.c), e);
-}
+static_assert(kStaticChunk <= sidm_sum::kMaxChunk, "chunk larger than the exact-sum windows allow");
 
 template <class R>
-__global__ void __launch_bounds__(256) k_static_partial(StaticLayout lay, const R* __restrict__ vel, long long N,
-                                                        const double* __restrict__ mass, double* __restrict__ part)
+__global__ void __launch_bounds__(sidm_sum::chunk_threads<R>()) k_static_partial(StaticLayout lay, const R* __restrict__ vel,
+                                                                      long long N, double* __restrict__ part)
 {
-    __shared__ Comp2 sh[4][256];
     const int c = blockIdx.x;
     int h = 0;
     while (h + 1 < lay.n_halos && lay.chunk_off[h + 1] <= c) ++h;
     const long long b = lay.halo_off[h] + (long long)(c - lay.chunk_off[h]) * kStaticChunk;
     long long e = b + kStaticChunk;
     if (e > lay.halo_off[h + 1]) e = lay.halo_off[h + 1];
-    const double m = mass[h];
-    const double hm = __dmul_rn(0.5, m);
-    Comp2 acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-    for (long long s = b + threadIdx.x; s < e; s += 256) {
-        const double x = (double)vel[s], y = (double)vel[N + s], z = (double)vel[2 * N + s];
-        double q = __dmul_rn(x, x);
-        q = __dadd_rn(q, __dmul_rn(y, y));
-        q = __dadd_rn(q, __dmul_rn(z, z));
-        comp_add2(acc[0], __dmul_rn(hm, q));
-        comp_add2(acc[1], __dmul_rn(m, x));
-        comp_add2(acc[2], __dmul_rn(m, y));
-        comp_add2(acc[3], __dmul_rn(m, z));
-    }
-#pragma unroll
-    for (int a = 0; a < 4; ++a) sh[a][threadIdx.x] = acc[a];
-    __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if (threadIdx.x < w)
-#pragma unroll
-            for (int a = 0; a < 4; ++a) comp_merge2(sh[a][threadIdx.x], sh[a][threadIdx.x + w]);
-        __syncthreads();
-    }
-    if (threadIdx.x < 4) {
-        part[c * 8 + 2 * threadIdx.x] = sh[threadIdx.x][0].s;
-        part[c * 8 + 2 * threadIdx.x + 1] = sh[threadIdx.x][0].c;
-    }
+    sidm_sum::chunk_sums(vel, N, b, e, part + 8 * (long long)c);
 }
 
-__global__ void k_static_final(StaticLayout lay, const double* __restrict__ part, double* __restrict__ out,
-                               double* __restrict__ comp)
+__global__ void k_static_final(StaticLayout lay, const double* __restrict__ mass, const double* __restrict__ part,
+                               double* __restrict__ out, double* __restrict__ comp)
 {
-    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    const int h = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);   // one warp per halo
     if (h >= lay.n_halos) return;
-    Comp2 acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-    for (int c = lay.chunk_off[h]; c < lay.chunk_off[h + 1]; ++c)
-        for (int a = 0; a < 4; ++a) comp_merge2(acc[a], Comp2{part[c * 8 + 2 * a], part[c * 8 + 2 * a + 1]});
-    for (int a = 0; a < 4; ++a) {
-        const double v = __dadd_rn(acc[a].s, acc[a].c);
-        out[h * 4 + a] = v;
-        if (comp) comp[h * 4 + a] = __dsub_rn(acc[a].c, __dsub_rn(v, acc[a].s));
-    }
+    sidm_sum::halo_result(part, lay.chunk_off[h], lay.chunk_off[h + 1], mass[h], out + 4 * h,
+                          comp ? comp + 4 * h : nullptr);
 }
 
 constexpr int kMaxDevices = 64;
@@ -169,13 +113,15 @@ extern "C" int sidm_energy_momentum_static(int32_t n_halos, const int64_t* halo_
     const long long N = halo_off[n_halos];
     if (chunks > 0) {
         if (precision == SIDM_FP64)
-            k_static_partial<double><<<(unsigned)chunks, 256, 0, stream>>>(lay, (const double*)vel_dev, N, mass_dev, part);
+            k_static_partial<double><<<(unsigned)chunks, sidm_sum::chunk_threads<double>(), 0, stream>>>(lay, (const double*)vel_dev, N,
+                                                                                          part);
         else
-            k_static_partial<float><<<(unsigned)chunks, 256, 0, stream>>>(lay, (const float*)vel_dev, N, mass_dev, part);
+            k_static_partial<float><<<(unsigned)chunks, sidm_sum::chunk_threads<float>(), 0, stream>>>(lay, (const float*)vel_dev, N,
+                                                                                         part);
         e = cudaGetLastError();
         if (e != cudaSuccess) return static_fail(SIDM_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
     }
-    k_static_final<<<(n_halos + 127) / 128, 128, 0, stream>>>(lay, part, out_dev, comp_dev);
+    k_static_final<<<(n_halos + 3) / 4, 128, 0, stream>>>(lay, mass_dev, part, out_dev, comp_dev);
     e = cudaGetLastError();
     if (e != cudaSuccess) return static_fail(SIDM_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
     return SIDM_OK;

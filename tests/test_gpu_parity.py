@@ -201,6 +201,56 @@ def test_energy_momentum_exact_and_deterministic():
         ctx.close()
 
 
+def test_energy_momentum_sums_fp32_velocities_exactly():
+    # the mixed form sums the FP32 velocities of a chunk as exact integers, so
+    # a chunk whose terms cancel leaves exactly the survivors.  Halo 0: +v / -v
+    # pairs spread over twelve decades, each pair at one position (so the
+    # pair stays together in the cell order and inside one chunk), then seven
+    # tiny survivors at a far corner (last in the cell order): with a
+    # power-of-two mass each result is the correctly rounded exact sum, checked
+    # against Python's math.fsum (exactly rounded) of the exact FP64 squares
+    # and components -- a 16-decade cancellation a plain or strided compensated
+    # FP64 sum does not resolve to the last bit.  Halo 1: subnormal FP32
+    # values; halo 2: all zero.
+    import math
+    from paper_2506_06269_gb300 import sidm
+    rng = np.random.default_rng(77)
+    half = 20000
+    v = (rng.normal(0, 1, (3, half)) * 10.0 ** rng.uniform(-6, 6, (3, half))).astype(np.float32)
+    tiny = (rng.normal(0, 1, (3, 7)) * 1e-9).astype(np.float32)
+    v0 = np.empty((3, 2 * half + 7), np.float32)
+    v0[:, 0:2 * half:2], v0[:, 1:2 * half:2], v0[:, 2 * half:] = v, -v, tiny
+    p = rng.uniform(0.0, 0.9, (3, half))
+    p0 = np.empty((3, 2 * half + 7))
+    p0[:, 0:2 * half:2], p0[:, 1:2 * half:2], p0[:, 2 * half:] = p, p, 0.999
+    v1 = (rng.integers(-2 ** 23 + 1, 2 ** 23, (3, 3000)).astype(np.float64) * 2.0 ** -149).astype(np.float32)
+    v2 = np.zeros((3, 500), np.float32)
+    vels = [v0, v1, v2]
+    poss = [p0, rng.uniform(0, 1, (3, 3000)), rng.uniform(0, 1, (3, 500))]
+    offs = [0] + list(np.cumsum([x.shape[1] for x in vels]))
+    n = int(offs[-1])
+    ctx = sidm.Context(n_max=n, halo_max=3, precision="mixed")
+    vel = torch.tensor(np.concatenate(vels, axis=1), device="cuda")
+    ids = torch.tensor(np.concatenate([np.arange(x.shape[1]) for x in vels]).astype(np.int64), device="cuda").to(torch.int32)
+    ctx.build_cells(offs, torch.tensor(np.concatenate(poss, axis=1), device="cuda"), vel, ids)
+    mass = ctx.f64([0.25, 2.0, 1.0])
+    out = torch.zeros((3, 4), dtype=torch.float64, device="cuda")
+    ctx.energy_momentum(mass, vel, out)
+    got = out.cpu().numpy()
+    w = vel.cpu().numpy().astype(np.float64)                  # the order the context left
+    ctx.close()
+    # the survivors are last and every pair is adjacent, starting at an even index
+    np.testing.assert_array_equal(w[:, 2 * half:2 * half + 7], tiny.astype(np.float64))
+    np.testing.assert_array_equal(w[:, 0:2 * half:2], -w[:, 1:2 * half:2])
+    for hh, m in enumerate((0.25, 2.0, 1.0)):
+        x = w[:, offs[hh]:offs[hh + 1]]
+        want = [0.5 * m * math.fsum((x * x).ravel())] + [m * math.fsum(x[a]) for a in range(3)]
+        for a in range(4):
+            assert abs(got[hh, a] - want[a]) <= 2.0 ** -52 * abs(want[a]), (hh, a, got[hh, a], want[a])
+    assert np.all(got[2] == 0.0)
+    assert 0 < np.abs(got[0, 1:]).max() < 1e-8                # only the tiny survivors are left
+
+
 # ---------------------------------------------------------------- failure paths
 def test_event_overflow_leaves_velocities_untouched():
     h = ics.hernquist(3000, 16)
