@@ -367,17 +367,27 @@ __global__ void k_knn(KnnParams p)
             __syncwarp();
         };
         // bit c: the query of some lane lies within its bound of box c; the
-        // lane's own bits and bound are kept for the leaves of this node
+        // lane's own bits and bound are kept for the leaves of this node.
+        // Every query point lies in the query leaf's box, so a child farther
+        // from that box than the largest lane bound is out of reach of every
+        // lane: one box test per child (a lane each) leaves the per-lane
+        // point tests to the children that pass it.
         uint32_t lane_bits = 0u;
         float node_r2 = -1.0f;
         auto accept = [&](int n, float r2, uint32_t skip) -> uint32_t {
+            float r2max = r2;
+            for (int o = 16; o > 0; o >>= 1) r2max = fmaxf(r2max, __shfl_xor_sync(0xffffffffu, r2max, o));
+            const uint32_t near =
+                __ballot_sync(0xffffffffu, lane < n && box_gap2_rd(qlo, qhi, blo[lane], bhi[lane]) <= r2max) & ~skip;
             uint32_t bits = 0u;
             if (r2 >= 0.f)
-                for (int c = 0; c < n; ++c)
+                for (uint32_t m = near; m; m &= m - 1u) {
+                    const int c = __ffs(m) - 1;
                     if (point_gap2_rd(pq, blo[c], bhi[c]) <= r2) bits |= 1u << c;
+                }
             lane_bits = bits;
             node_r2 = r2;
-            return __reduce_or_sync(0xffffffffu, bits) & ~skip;
+            return __reduce_or_sync(0xffffffffu, bits);
         };
         // leaves of the Morton window among local leaves first .. first+n-1
         auto window_mask = [&](int first, int n) -> uint32_t {

@@ -399,13 +399,27 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
             __syncwarp();
         };
         // bit c: some lane's query reaches box c (each lane keeps its own bits
-        // for the leaves of this node)
+        // for the leaves of this node).  Every query point lies in the leaf's
+        // box, so a child farther from that box than the reach of the largest
+        // h_i is out of reach of every lane: one box test per child (a lane
+        // each) leaves the per-lane point tests to the children that pass it.
+        float hqmax = hq;
+        for (int o = 16; o > 0; o >>= 1) hqmax = fmaxf(hqmax, __shfl_xor_sync(0xffffffffu, hqmax, o));
         uint32_t lane_bits = 0u;
         auto accept = [&](int n, uint32_t eligible) -> uint32_t {
+            bool reach = false;
+            if (lane < n && ((eligible >> lane) & 1u)) {
+                const float4 lo = blo[lane], hi = bhi[lane];
+                const float r = __fadd_ru(__fmul_ru(__fadd_ru(hqmax, lo.w), 1.0f + 0x1p-20f), fr.margin);
+                reach = box_gap2_rd(qlo, qhi, lo, hi) <= __fmul_ru(r, r);
+            }
+            const uint32_t near = __ballot_sync(0xffffffffu, reach);
             uint32_t bits = 0u;
             if (active)
-                for (int c = 0; c < n; ++c)
-                    if ((eligible >> c) & 1u) bits |= (near_box(c) ? 1u : 0u) << c;
+                for (uint32_t m = near; m; m &= m - 1u) {
+                    const int c = __ffs(m) - 1;
+                    bits |= (near_box(c) ? 1u : 0u) << c;
+                }
             lane_bits = bits;
             return __reduce_or_sync(0xffffffffu, bits);
         };
