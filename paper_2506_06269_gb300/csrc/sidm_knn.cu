@@ -313,29 +313,28 @@ __global__ void k_knn(KnnParams p)
             __syncwarp();
             if (act && mine) {
                 n_cand += (unsigned long long)__popc(cmask);
-                if (nfill < k) {
-                    // fill: the first k admitted keys go into the heap array unsorted
-                    // (heapified at the next merge; later keys wait in the pending list)
-                    for (uint32_t mm = cmask; mm; mm &= mm - 1u) {
-                        const int t = __ffs(mm) - 1;
-                        const V cj = sh[t];
+                // the masked candidates four at a time (independent distance
+                // chains); an admitted key fills the heap array (unsorted, heapified
+                // at the next merge) until it holds k keys, then waits in the
+                // pending list, for which room was made before the tile
+                for (uint32_t mm = cmask; mm;) {
+                    int t[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) { t[u] = __ffs(mm) - 1; mm &= mm - 1u; }   // -1: none left
+                    K key[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const V cj = sh[t[u] >= 0 ? t[u] : t[0]];
                         const R dx = sub_rn(cj.x, q.x), dy = sub_rn(cj.y, q.y), dz = sub_rn(cj.z, q.z);
                         const R d2 = fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
-                        const K key = make_key<R, NBR>(d2, NBR ? tids[t] : 0u);
-                        if (key < root && !(Bl == A && t == lane)) {
-                            if (nfill < k) hp.at(nfill++) = key;
-                            else pend[(np++) * 32 + lane] = key;
-                        }
+                        key[u] = make_key<R, NBR>(d2, NBR ? tids[t[u] >= 0 ? t[u] : t[0]] : 0u);
                     }
-                } else {
-                    // room for every masked candidate was made before the tile
-                    for (uint32_t mm = cmask; mm; mm &= mm - 1u) {
-                        const int t = __ffs(mm) - 1;
-                        const V cj = sh[t];
-                        const R dx = sub_rn(cj.x, q.x), dy = sub_rn(cj.y, q.y), dz = sub_rn(cj.z, q.z);
-                        const R d2 = fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
-                        const K key = make_key<R, NBR>(d2, NBR ? tids[t] : 0u);
-                        if (key < root && !(Bl == A && t == lane)) pend[(np++) * 32 + lane] = key;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if (t[u] >= 0 && key[u] < root && !(Bl == A && t[u] == lane)) {
+                            if (nfill < k) hp.at(nfill++) = key[u];
+                            else pend[(np++) * 32 + lane] = key[u];
+                        }
                     }
                 }
             }
