@@ -727,11 +727,6 @@ __global__ void k_lambda_eval(int64_t n, const double* __restrict__ d, const dou
         out[t] = (double)lambda_lookup<R>(T, (R)d[t], (R)hi[t], (R)hj[t]);
 }
 
-__global__ void k_fill_u64(unsigned long long* p, int64_t n, unsigned long long v)
-{
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) p[t] = v;
-}
-
 // ------------------------------------------------------------------ Lambda table (host)
 // Gauss-Legendre nodes on [-1, 1] by Newton iteration on P_n.
 void gauss_legendre(int n, double* x, double* w)
@@ -1253,7 +1248,7 @@ extern "C" int sidm_kernel_sizes(sidm_ctx* c, const int32_t* n_ngb, void* h_dev,
     c->ngb_prev = c->ngb_host;
     if (c->cfg.precision == SIDM_FP64)
         SIDM_LAUNCH(c, k_leaf_hmax<double><<<(L.L * 32 + 255) / 256, 256, 0, s>>>(L.L, L.H, c->d_leaf_halo, c->d_leaf_off,
-                                                                                 c->d_halo_off, (const double4*)c->d_P4, c->d_nlo));
+                                                                                 c->d_halo_off, (const double4_16a*)c->d_P4, c->d_nlo));
     else
         SIDM_LAUNCH(c, k_leaf_hmax<float><<<(L.L * 32 + 255) / 256, 256, 0, s>>>(L.L, L.H, c->d_leaf_halo, c->d_leaf_off,
                                                                                c->d_halo_off, (const float4*)c->d_P4, c->d_nlo));
@@ -1292,7 +1287,7 @@ static int scatter_impl(sidm_ctx* c, uint64_t seed, uint64_t step, const sidm_xs
     const bool fp64 = c->cfg.precision == SIDM_FP64;
     if (fp64)
         SIDM_LAUNCH(c, k_vel_refresh<double><<<grid_for(c, L.N, 256), 256, 0, s>>>(L.N, L.H, c->d_halo_off, c->d_halo_pad,
-                                                                                  (const double*)vel, c->d_ID, (double4*)c->d_V4));
+                                                                                  (const double*)vel, c->d_ID, (double4_16a*)c->d_V4));
     else
         SIDM_LAUNCH(c, k_vel_refresh<float><<<grid_for(c, L.N, 256), 256, 0, s>>>(L.N, L.H, c->d_halo_off, c->d_halo_pad,
                                                                                 (const float*)vel, c->d_ID, (float4*)c->d_V4));
@@ -1349,7 +1344,7 @@ extern "C" int sidm_local_diagnostics(sidm_ctx* c, const sidm_xs* xs, const doub
     SIDM_CUDA(c, cudaMemsetAsync(c->d_dacc, 0, sizeof(double) * 5 * L.N, s));
     if (fp64)
         SIDM_LAUNCH(c, k_vel_refresh<double><<<grid_for(c, L.N, 256), 256, 0, s>>>(L.N, L.H, c->d_halo_off, c->d_halo_pad,
-                                                                                  (const double*)vel, c->d_ID, (double4*)c->d_V4));
+                                                                                  (const double*)vel, c->d_ID, (double4_16a*)c->d_V4));
     else
         SIDM_LAUNCH(c, k_vel_refresh<float><<<grid_for(c, L.N, 256), 256, 0, s>>>(L.N, L.H, c->d_halo_off, c->d_halo_pad,
                                                                                 (const float*)vel, c->d_ID, (float4*)c->d_V4));
@@ -1358,7 +1353,7 @@ extern "C" int sidm_local_diagnostics(sidm_ctx* c, const sidm_xs* xs, const doub
     const int blocks = (int)(((int64_t)L.L * kLeaf + 255) / 256);
     if (fp64)
         SIDM_LAUNCH(c, k_diag_final<double><<<blocks, 256, 0, s>>>(L.L, c->d_leaf_halo, c->d_leaf_off, c->d_halo_off,
-                                                                   (const double4*)c->d_P4, (const double4*)c->d_V4,
+                                                                   (const double4_16a*)c->d_P4, (const double4_16a*)c->d_V4,
                                                                    c->d_dacc, L.N, mass, xs, c->d_ngb, G, (double*)out));
     else
         SIDM_LAUNCH(c, k_diag_final<float><<<blocks, 256, 0, s>>>(L.L, c->d_leaf_halo, c->d_leaf_off, c->d_halo_off,

@@ -352,6 +352,6 @@ __device__ __forceinline__ double ord_to_dbl(unsigned long long u)
 
 template <class R> struct Vec4;
 template <> struct Vec4<float> { using T = float4; };
-template <> struct Vec4<double> { using T = double4; };
+template <> struct Vec4<double> { using T = double4_16a; };   // 16-byte aligned, as staged
 
 }  // namespace sidm

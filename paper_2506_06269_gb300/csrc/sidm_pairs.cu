@@ -88,18 +88,6 @@ __device__ __forceinline__ bool step_opens(int b, int n_bins, int s)
     return (s & ((1 << (n_bins - 1 - b)) - 1)) == 0;
 }
 
-// position of the r-th (0-based) set bit of m (m has more than r set bits)
-__device__ __forceinline__ int nth_set_bit(uint32_t m, int r)
-{
-    int pos = 0;
-#pragma unroll
-    for (int w = 16; w > 0; w >>= 1) {
-        const int c = __popc(m & ((1u << w) - 1u));
-        if (r >= c) { r -= c; m >>= w; pos += w; }
-    }
-    return pos;
-}
-
 template <class R>
 __device__ __forceinline__ float to_float_ru_p(R v)
 {
