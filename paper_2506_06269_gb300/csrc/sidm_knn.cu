@@ -152,6 +152,7 @@ __host__ __device__ constexpr int heap4_groups(int kcap) { return (kcap + 2) / 4
 // which the lists are merged before a tree node's tests, and the node boxes
 // tested at once (the children of one node; a wider top level in chunks)
 constexpr int kPend = 32;
+static_assert(kPend >= kLeaf, "a tile can admit all of its candidates: one empty pending list must hold them");
 constexpr int kFlushNode = 8;
 constexpr int kBoxes = 8;
 // warm start: the search bound is the previous kernel size times this factor
