@@ -270,13 +270,21 @@ __global__ void k_knn(KnnParams p)
             r = __fadd_ru(__fmul_ru(r, 1.0f + 0x1p-20f), fr.margin);
             return __fmul_ru(r, r);
         };
-        // r2: the lane's current bound (my_r2) as its caller computed it
-        auto process = [&](int Bl, bool mine, float r2) {
+        // this lane's entry of candidate leaf Bl (the plain path loads it straight
+        // into a register, so a caller can fetch the next leaf early)
+        auto fetch = [&](int Bl) -> V {
+            if constexpr (TMA) return V{};
+            else return ((const V*)p.P4)[(int64_t)(leaf0 + Bl) * kLeaf + lane];
+        };
+        // r2: the lane's current bound (my_r2) as its caller computed it;
+        // craw: fetch(Bl) (unused on the bulk-copy path, which stages the leaf here)
+        auto process = [&](int Bl, bool mine, float r2, const V& craw) {
             const int Bg = leaf0 + Bl;
             const int countB = (int)min((int64_t)kLeaf, nh - (int64_t)Bl * kLeaf);
-            const V* tile = stage.load((const V*)p.P4 + (int64_t)Bg * kLeaf, lane, p.cnt);
+            V c;
+            if constexpr (TMA) c = stage.load((const V*)p.P4 + (int64_t)Bg * kLeaf, lane, p.cnt)[lane];
+            else c = craw;
             // shift the candidates into the query leaf's frame (exact shift)
-            V c = tile[lane];
             if constexpr (sizeof(R) == 4) {
                 const float4 cB = p.cell[Bg];
                 c.x = __fadd_rn(c.x, __fsub_rn(cB.x, cA.x));
@@ -353,7 +361,7 @@ __global__ void k_knn(KnnParams p)
             }
             // the window holds at least k other particles, so every lane's heap is
             // full after it: order it and merge the window's keys beyond the first k
-            for (int Bl = wlo; Bl <= whi; ++Bl) process(Bl, true, my_r2());
+            for (int Bl = wlo; Bl <= whi; ++Bl) process(Bl, true, my_r2(), fetch(Bl));
             flush();
         }
 
@@ -399,14 +407,9 @@ __global__ void k_knn(KnnParams p)
         // (a larger, older bound only admits more); the cold pass re-tests with the
         // bound its nearer leaves have shrunk
         auto visit_leaf = [&](int Bl, int c) {
-            if (pass == 0) {
-                const bool mine = (lane_bits >> c) & 1u;
-                if (__any_sync(0xffffffffu, mine)) process(Bl, mine, node_r2);
-                return;
-            }
             const float r2 = my_r2();
             const bool mine = r2 >= 0.f && point_gap2_rd(pq, blo[c], bhi[c]) <= r2;
-            if (__any_sync(0xffffffffu, mine)) process(Bl, mine, r2);
+            if (__any_sync(0xffffffffu, mine)) process(Bl, mine, r2, fetch(Bl));
         };
         // Accepted children are visited nearest first (box gap to the query leaf),
         // so the k-th bound shrinks early.  rank = position among the accepted.
@@ -423,7 +426,28 @@ __global__ void k_knn(KnnParams p)
         // the warm pass starts from a tight bound, so it takes the accepted
         // children in index order; the cold pass visits the nearest first
         auto visit_leaves_in_order = [&](uint32_t acc, int n, int first_local) {
-            const int rank = pass == 0 ? __popc(acc & ((1u << lane) - 1u)) : order_rank(acc, n);
+            if (acc == 0u) return;
+            if (pass == 0) {
+                // index order; the next accepted leaf is fetched before this one is
+                // processed, so its load overlaps this leaf's candidate loop
+                uint32_t m = acc;
+                int c = __ffs(m) - 1;
+                m &= m - 1u;
+                V cur = fetch(first_local + c);
+                while (true) {
+                    const int cn = __ffs(m) - 1;       // -1: none left
+                    m &= m - 1u;
+                    V nxt{};
+                    if (cn >= 0) nxt = fetch(first_local + cn);
+                    const bool mine = (lane_bits >> c) & 1u;
+                    if (__any_sync(0xffffffffu, mine)) process(first_local + c, mine, node_r2, cur);
+                    if (cn < 0) break;
+                    c = cn;
+                    cur = nxt;
+                }
+                return;
+            }
+            const int rank = order_rank(acc, n);
             const int cnt = __popc(acc);
             for (int r = 0; r < cnt; ++r) {
                 const uint32_t m = __ballot_sync(0xffffffffu, lane < n && ((acc >> lane) & 1u) && rank == r);
