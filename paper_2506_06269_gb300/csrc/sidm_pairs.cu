@@ -302,12 +302,20 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
             __syncwarp();
         };
 
-        auto process = [&](int Bl, bool mine) {
+        // this lane's entry of candidate leaf Bl (the plain path loads it straight
+        // into a register, so the walk can fetch the next leaf early)
+        auto fetch = [&](int Bl) -> V {
+            if constexpr (TMA) return V{};
+            else return P4[(int64_t)(leaf0 + Bl) * kLeaf + lane];
+        };
+        // craw: fetch(Bl) (unused on the bulk-copy path, which stages the leaf here)
+        auto process = [&](int Bl, bool mine, const V& craw) {
             const int Bg = leaf0 + Bl;
             ++n_tiles;
             const int countB = (int)min((int64_t)kLeaf, nh - (int64_t)Bl * kLeaf);
-            const V* rp = st_pos.load(P4 + (int64_t)Bg * kLeaf, lane, p.cnt);
-            V c = rp[lane];
+            V c;
+            if constexpr (TMA) c = st_pos.load(P4 + (int64_t)Bg * kLeaf, lane, p.cnt)[lane];
+            else c = craw;
             if constexpr (sizeof(R) == 4) {
                 const float4 cB = p.cell[Bg];
                 c.x = __fadd_rn(c.x, __fsub_rn(cB.x, cA.x));
@@ -418,10 +426,22 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
                 if (((int64_t)(first + c + 1) << (3 * lev)) > A) m |= 1u << c;
             return m;
         };
+        // accepted leaves in index order; the next one is fetched before this one
+        // is processed, so its load overlaps this leaf's tests
         auto visit_leaves = [&](uint32_t acc, int first) {
-            for (; acc; acc &= acc - 1u) {
-                const int c = __ffs(acc) - 1;
-                process(first + c, (lane_bits >> c) & 1u);
+            if (acc == 0u) return;
+            int c = __ffs(acc) - 1;
+            acc &= acc - 1u;
+            V cur = fetch(first + c);
+            while (true) {
+                const int cn = __ffs(acc) - 1;         // -1: none left
+                acc &= acc - 1u;
+                V nxt{};
+                if (cn >= 0) nxt = fetch(first + cn);
+                process(first + c, (lane_bits >> c) & 1u, cur);
+                if (cn < 0) break;
+                c = cn;
+                cur = nxt;
             }
         };
         auto push = [&](uint32_t acc, int lev, int first, int& sp) -> bool {
