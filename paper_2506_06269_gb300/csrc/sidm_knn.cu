@@ -153,7 +153,7 @@ __host__ __device__ constexpr int heap4_groups(int kcap) { return (kcap + 2) / 4
 // tested at once (the children of one node; a wider top level in chunks)
 constexpr int kPend = 32;
 static_assert(kPend >= kLeaf, "a tile can admit all of its candidates: one empty pending list must hold them");
-constexpr int kFlushNode = 8;
+constexpr int kFlushNode = 16;
 constexpr int kBoxes = 8;
 // warm start: the search bound is the previous kernel size times this factor
 constexpr float kGuessSlack = 1.0625f;
