@@ -72,8 +72,8 @@ typedef struct {
     int64_t event_cap;   /* scatter events kept per step, >= 1                      */
     int32_t precision;   /* SIDM_MIXED or SIDM_FP64                                 */
     int32_t device;      /* CUDA device ordinal                                      */
-    int32_t knn_warps;   /* warps per CTA of the neighbour kernel, 0 = default       */
-    int32_t pair_warps;  /* warps per CTA of the pair kernel, 0 = default            */
+    int32_t knn_warps;   /* warps per CTA of the neighbour kernel, 0..16, 0 = 8      */
+    int32_t pair_warps;  /* warps per CTA of the pair kernel, 0..8, 0 = 8            */
     int32_t max_rounds;  /* resolve round limit, 0 = default (256)                   */
     int32_t flags;       /* SIDM_FLAG_*                                              */
     int32_t grid_ctas;   /* persistent CTAs per kernel, 0 = SM count x occupancy     */

@@ -939,14 +939,15 @@ extern "C" int sidm_create(sidm_ctx** out, const sidm_config* cfg)
     if (cfg->ngb_max < 1 || cfg->ngb_max > kMaxNgb) { g_create_err = "ngb_max must be in [1, 128]"; return SIDM_EINVAL; }
     if (cfg->event_cap < 1) { g_create_err = "event_cap must be >= 1"; return SIDM_EINVAL; }
     if (cfg->precision != SIDM_MIXED && cfg->precision != SIDM_FP64) { g_create_err = "bad precision"; return SIDM_EINVAL; }
-    if (cfg->knn_warps < 0 || cfg->knn_warps > 16 || cfg->pair_warps < 0 || cfg->pair_warps > 16) {
-        g_create_err = "warps per CTA must be in [0, 16]"; return SIDM_EINVAL;
+    if (cfg->knn_warps < 0 || cfg->knn_warps > 16) { g_create_err = "knn_warps must be in [0, 16]"; return SIDM_EINVAL; }
+    if (cfg->pair_warps < 0 || cfg->pair_warps > 8) {       // the pair kernel is built for CTAs of <= 256 threads
+        g_create_err = "pair_warps must be in [0, 8]"; return SIDM_EINVAL;
     }
     sidm_ctx* c = new sidm_ctx();
     c->cfg = *cfg;
     if (c->cfg.max_rounds <= 0) c->cfg.max_rounds = 256;
     c->knn_warps = cfg->knn_warps ? cfg->knn_warps : 8;
-    c->pair_warps = cfg->pair_warps ? cfg->pair_warps : 4;
+    c->pair_warps = cfg->pair_warps ? cfg->pair_warps : 8;
     auto fail = [&](const std::string& m, cudaError_t e) {
         g_create_err = m + ": " + cudaGetErrorString(e);
         free_all(c);

@@ -55,7 +55,7 @@ def autotune(make_inputs, ks, xs_list, dts, masses, halo_off, precision="mixed",
         try:
             ms = _trial(make_inputs, ks, xs_list, dts, masses, halo_off, n, H, kmax, precision,
                         dict(knn_warps=w, pair_warps=w, use_tma=t))
-        except Exception as e:   # a shape that does not fit (shared memory) is skipped
+        except Exception as e:   # a shape that does not fit (shared memory, pair CTAs > 8 warps) is skipped
             table.append({"warps": w, "use_tma": t, "error": str(e)})
             continue
         table.append({"warps": w, "use_tma": t, "knn_ms": float(ms[1]), "pairs_ms": float(ms[2])})
