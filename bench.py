@@ -4,11 +4,12 @@ Workload (one "step" = one pass of the whole hot path over the halo):
   NFW halo, r_s = 1, truncated at 10 r_s, N = 1,048,576 equal-mass particles,
   isotropic Maxwellian velocities with the Jeans dispersion (seed 1),
   sigma(v)/m = 100 / (1 + (v/v_max)^2)^2 with v_max the halo's maximum circular
-  velocity, N_ngb = 64, FP32 storage with FP64 reductions (mixed form),
+  velocity, N_ngb = 64, FP32 storage with exact/FP64 reductions (mixed form),
   fixed dt from the SIDM time-step proxy dt = 0.04 / q99.9(sum_j P_ij / dt)
   on the initial state.  Synthetic inputs (seeded), no datasets.
   A step = ballistic drift + cell build + kernel sizes + pair probabilities,
-  draws and scatter + FP64 energy/momentum.  L2 is flushed (256 MiB write)
+  draws and scatter + per-halo energy/momentum (exact integer sums of the
+  FP32 velocities).  L2 is flushed (256 MiB write)
   before every timed step, outside the step's events.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -678,7 +679,7 @@ def main_ours(args):
             "config": {"workload": WORKLOAD, "n_particles": n, "n_ngb": N_NGB,
                        "cross_section": f"sigma/m = {S0}/(1+(v/{res['vmax']:.4f})^2)^2", "dt": res["dt"],
                        "dt_rule": "0.04 / q99.9(sum_j P_ij/dt) on the initial state", "precision": "mixed",
-                       "step": "drift + cell build + kernel sizes + pairs/draws/scatter + FP64 E,p",
+                       "step": "drift + cell build + kernel sizes + pairs/draws/scatter + exact E,p",
                        "l2": "flushed before every timed step (256 MiB write, outside the step events)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU", "use_tma": args.use_tma},
             "pair_evals_per_s": ws * res["n_pairs"] / (total_ms * 1e-3),
