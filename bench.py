@@ -502,6 +502,55 @@ def run_satellite(local, big_steps=8, n=1 << 22, n_bins=4, dt_max=0.02):
             "bins_last": hist, "device_status": status}
 
 
+def run_streaming(local, n=1 << 25, reps=5):
+    """The HBM-bound kernels of the step on a halo far larger than L2: 2^25
+    particles uniform in a cube (seeded, generated on the device), FP32
+    velocities.  Times the cell build (Morton keys, 7-pass radix sort, gather,
+    leaf boxes, tree), the drift and the energy/momentum sums with CUDA
+    events, and reports algorithmic bytes / time against the measured HBM
+    peak.  Algorithmic bytes per particle: build 520 (bbox 24, keys 24 + 12,
+    7 sort passes x 32, gather 52 + 64, copy-back 80, leaf boxes 24), drift 60
+    (pos 24 read + 24 write, vel 12), energy 12 (one read of the velocities)."""
+    import torch
+    from paper_2506_06269_gb300 import sidm
+    peaks, src = load_peaks()
+    g = torch.Generator(device=f"cuda:{local}")
+    g.manual_seed(SEED_IC)
+    ctx = sidm.Context(n_max=n, halo_max=1, ngb_max=N_NGB, event_cap=1 << 16, device=local)
+    dev = ctx.device
+    pos = torch.rand((3, n), generator=g, dtype=torch.float64, device=dev)
+    vel = torch.randn((3, n), generator=g, dtype=torch.float32, device=dev)
+    ids = torch.arange(n, dtype=torch.int32, device=dev)
+    dt = ctx.f64([1e-6])
+    mass = ctx.f64([1.0 / n])
+    out = torch.zeros((1, 4), dtype=torch.float64, device=dev)
+    ctx.build_cells([0, n], pos, vel, ids)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    legs = {"build": (lambda: ctx.build_cells([0, n], pos, vel, ids), 520),
+            "drift": (lambda: ctx.drift(dt, pos, vel), 60),
+            "energy_momentum": (lambda: ctx.energy_momentum(mass, vel, out), 12)}
+    res = {"n_particles": n, "workload": "uniform cube, 2^25 particles (seeded, on the device)",
+           "peak_gbs": peaks["hbm_gbs"], "peak_source": src}
+    for name, (fn, bpp) in legs.items():
+        ms = timed(fn)
+        gbs = bpp * n / (ms * 1e-3) / 1e9
+        res[name] = {"ms": ms, "bytes_per_particle": bpp, "achieved_gbs": gbs, "frac": gbs / peaks["hbm_gbs"]}
+    res["device_status"] = ctx.status()
+    ctx.close()
+    return res
+
+
 def run_batched(local, graph_steps=50, seq_steps=2):
     """64 independent NFW halos in one persistent launch per kernel, 50 steps
     captured in one CUDA graph, against 64 sequential single-halo contexts."""
@@ -710,6 +759,7 @@ def main_ours(args):
         if not args.no_batched:
             line["batched"] = run_batched(res["local"])
             line["satellite"] = run_satellite(res["local"])
+            line["streaming_kernels"] = run_streaming(res["local"])
             if fp64:
                 line["batched_over_fp64_single_halo"] = line["batched"]["value"] / fp64["value"]
         if not args.no_cpu_baseline and ws == 1:

@@ -126,6 +126,7 @@ __global__ void k_frame(int H, const int64_t* __restrict__ halo_off, const unsig
     if (ext > 0.0) frexp(ext, &E);           // ext = m 2^E, m in [1/2, 1)
     for (int a = 0; a < 3; ++a) f.O[a] = ldexp(floor(ldexp(mn[a], -E)), E);
     f.E = E;
+    f.qs = ldexp(1.0, kMortonBits - E - 1);
     f.cube = (float)ldexp(1.0, E + 1);
     f.margin = (float)ldexp(1.0, E + 1 - 20);
     f.fine = (float)ldexp(1.0, E + 1 - kMortonBits);
@@ -143,9 +144,11 @@ __global__ void k_keys(const double* __restrict__ pos, int64_t N, const int64_t*
         uint32_t q[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            double t = ldexp(__dsub_rn(pos[a * N + s], f.O[a]), kMortonBits - f.E - 1);
-            double fl = floor(t);
-            q[a] = fl <= 0.0 ? 0u : (fl >= (double)qmax ? qmax : (uint32_t)fl);
+            // (x - O) 2^(17-E-1): the product by a power of two is the exact scaling;
+            // one conversion rounds down (floor), the clamp is integer work
+            const double t = __dmul_rn(__dsub_rn(pos[a * N + s], f.O[a]), f.qs);
+            const int fl = __double2int_rd(t);
+            q[a] = fl <= 0 ? 0u : ((uint32_t)fl >= qmax ? qmax : (uint32_t)fl);
         }
         key[s] = ((unsigned long long)h << kHaloShift) | spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2);
         val[s] = (uint32_t)s;
@@ -341,19 +344,25 @@ __global__ void k_leaf_bbox(int L, int64_t N, const int32_t* __restrict__ leaf_h
     const int64_t b = halo_off[h] + (int64_t)(leaf - leaf_off[h]) * kLeaf;
     int64_t e = b + kLeaf; if (e > halo_off[h + 1]) e = halo_off[h + 1];
     const HaloFrame f = fr[h];
-    double mn[3], mx[3];
     const int64_t s = b + lane < e ? b + lane : b;
+    // rounding down (up) is monotone, so the FP32 minimum of the rounded-down
+    // offsets is the rounded-down FP64 minimum: the reduction runs in FP32
+    float mn[3], mx[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) { mn[a] = mx[a] = __dsub_rn(pos[a * N + s], f.O[a]); }
+    for (int a = 0; a < 3; ++a) {
+        const double y = __dsub_rn(pos[a * N + s], f.O[a]);
+        mn[a] = __double2float_rd(y);
+        mx[a] = __double2float_ru(y);
+    }
 #pragma unroll
     for (int a = 0; a < 3; ++a)
         for (int o = 16; o > 0; o >>= 1) {
-            mn[a] = fmin(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
-            mx[a] = fmax(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+            mn[a] = fminf(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+            mx[a] = fmaxf(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
         }
     if (lane == 0) {
-        nlo[leaf] = make_float4(__double2float_rd(mn[0]), __double2float_rd(mn[1]), __double2float_rd(mn[2]), 0.f);
-        nhi[leaf] = make_float4(__double2float_ru(mx[0]), __double2float_ru(mx[1]), __double2float_ru(mx[2]), 0.f);
+        nlo[leaf] = make_float4(mn[0], mn[1], mn[2], 0.f);
+        nhi[leaf] = make_float4(mx[0], mx[1], mx[2], 0.f);
     }
 }
 

@@ -29,6 +29,7 @@ constexpr uint32_t kIdLimit = 1u << 27;
 // Morton quantisation with 17 bits per axis.
 struct HaloFrame {
     double O[3];
+    double qs;         // Morton quantisation scale 2^(17-E-1) (a power of two)
     int E;
     float cube;        // 2^(E+1)
     float margin;      // pruning margin: 2^(E+1) * 2^-20 (canonical vs exact distance)
