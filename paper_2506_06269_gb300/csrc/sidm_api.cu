@@ -71,7 +71,8 @@ __device__ __forceinline__ uint32_t compact3(unsigned long long x)
 }
 
 // ------------------------------------------------------------------ a0 kernels
-// Per-halo bounding box (exact FP64 min/max through order-preserving atomics).
+// Per-halo bounding box: exact min/max of the FP64 positions as integer
+// min/max of their order-preserving bit images (integer pipes, not FP64).
 __global__ void k_bbox(const double* __restrict__ pos, int64_t N, const int32_t* __restrict__ chunk_halo,
                        const int64_t* __restrict__ chunk_begin, const int64_t* __restrict__ halo_off,
                        int H, unsigned long long* __restrict__ bb)
@@ -81,28 +82,28 @@ __global__ void k_bbox(const double* __restrict__ pos, int64_t N, const int32_t*
     const int64_t b = chunk_begin[c];
     int64_t e = b + kChunk;
     if (e > halo_off[h + 1]) e = halo_off[h + 1];
-    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0ull, 0ull, 0ull};
     for (int64_t s = b + threadIdx.x; s < e; s += blockDim.x) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            double v = pos[a * N + s];
-            mn[a] = fmin(mn[a], v);
-            mx[a] = fmax(mx[a], v);
+            const unsigned long long v = dbl_to_ord(pos[a * N + s]);
+            mn[a] = min(mn[a], v);
+            mx[a] = max(mx[a], v);
         }
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         for (int o = 16; o > 0; o >>= 1) {
-            mn[a] = fmin(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
-            mx[a] = fmax(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+            mn[a] = min(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+            mx[a] = max(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
         }
     }
     if ((threadIdx.x & 31) == 0) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             if (mn[a] <= mx[a]) {
-                atomicMin(&bb[a * H + h], dbl_to_ord(mn[a]));
-                atomicMax(&bb[(3 + a) * H + h], dbl_to_ord(mx[a]));
+                atomicMin(&bb[a * H + h], mn[a]);
+                atomicMax(&bb[(3 + a) * H + h], mx[a]);
             }
         }
     }
@@ -332,7 +333,39 @@ __global__ void k_gather(int64_t N, int H, const int64_t* __restrict__ halo_off,
     }
 }
 
-// Leaf bounding boxes in the halo frame (FP32, rounded outward); one warp per leaf.
+// Leaf bounding boxes in the halo frame (FP32, rounded outward) of the mixed
+// form, from the FP32 offsets and cell origins the gather just wrote: each
+// point cell + offset is added with rounding down and up (no FP64), so the
+// box holds it exactly; the canonical positions the kernels test against it
+// lie within a few FP32 ulps, far inside the pruning margin.  One warp per leaf.
+__global__ void k_leaf_bbox_p4(int L, const int32_t* __restrict__ leaf_halo, const int32_t* __restrict__ leaf_off,
+                               const int64_t* __restrict__ halo_off, const float4* __restrict__ cell,
+                               const float4* __restrict__ P4, float4* __restrict__ nlo, float4* __restrict__ nhi)
+{
+    const int lane = threadIdx.x & 31;
+    const int leaf = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (leaf >= L) return;
+    const int h = leaf_halo[leaf];
+    const int64_t local = (int64_t)(leaf - leaf_off[h]) * kLeaf;
+    const int count = (int)min((int64_t)kLeaf, halo_off[h + 1] - halo_off[h] - local);
+    const float4 c = cell[leaf];
+    const float4 p = P4[(int64_t)leaf * kLeaf + (lane < count ? lane : 0)];
+    float mn[3] = {__fadd_rd(c.x, p.x), __fadd_rd(c.y, p.y), __fadd_rd(c.z, p.z)};
+    float mx[3] = {__fadd_ru(c.x, p.x), __fadd_ru(c.y, p.y), __fadd_ru(c.z, p.z)};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[a] = fminf(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+            mx[a] = fmaxf(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+        }
+    if (lane == 0) {
+        nlo[leaf] = make_float4(mn[0], mn[1], mn[2], 0.f);
+        nhi[leaf] = make_float4(mx[0], mx[1], mx[2], 0.f);
+    }
+}
+
+// Leaf bounding boxes in the halo frame (FP32, rounded outward) from the FP64
+// positions (the FP64 form); one warp per leaf.
 __global__ void k_leaf_bbox(int L, int64_t N, const int32_t* __restrict__ leaf_halo, const int32_t* __restrict__ leaf_off,
                             const int64_t* __restrict__ halo_off, const HaloFrame* __restrict__ fr,
                             const double* __restrict__ pos, float4* __restrict__ nlo, float4* __restrict__ nhi)
@@ -1183,8 +1216,14 @@ static int build_impl(sidm_ctx* c, double* pos, R* vel, uint32_t* id, cudaStream
     SIDM_CUDA(c, cudaMemcpyAsync(pos, c->d_tmp_pos, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s));
     SIDM_CUDA(c, cudaMemcpyAsync(vel, c->d_tmp_vel, sizeof(R) * 3 * N, cudaMemcpyDeviceToDevice, s));
     SIDM_CUDA(c, cudaMemcpyAsync(id, c->d_tmp_id, sizeof(uint32_t) * N, cudaMemcpyDeviceToDevice, s));
-    SIDM_LAUNCH(c, k_leaf_bbox<<<(L.L * 32 + 255) / 256, 256, 0, s>>>(L.L, N, c->d_leaf_halo, c->d_leaf_off, c->d_halo_off,
-                                                                       c->d_frame, pos, c->d_nlo, c->d_nhi));
+    if (mixed)
+        SIDM_LAUNCH(c, k_leaf_bbox_p4<<<(L.L * 32 + 255) / 256, 256, 0, s>>>(L.L, c->d_leaf_halo, c->d_leaf_off, c->d_halo_off,
+                                                                              c->d_cell, (const float4*)c->d_P4, c->d_nlo,
+                                                                              c->d_nhi));
+    else
+        SIDM_LAUNCH(c, k_leaf_bbox<<<(L.L * 32 + 255) / 256, 256, 0, s>>>(L.L, N, c->d_leaf_halo, c->d_leaf_off,
+                                                                           c->d_halo_off, c->d_frame, pos, c->d_nlo,
+                                                                           c->d_nhi));
     for (int l = 1; l < L.nlev; ++l) {
         const int cnt = L.lvl_off[(size_t)l * (H + 1) + H] - L.lvl_off[(size_t)l * (H + 1)];
         SIDM_LAUNCH(c, k_tree_level<<<std::max(1, (cnt + 255) / 256), 256, 0, s>>>(l, H, c->d_lvl_off, c->d_nlo, c->d_nhi));
