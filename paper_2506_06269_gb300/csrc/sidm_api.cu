@@ -734,7 +734,7 @@ __global__ void k_drift(int64_t N, int H, const int64_t* __restrict__ halo_off, 
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
         const double d = dt[halo_of(halo_off, H, s)];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) pos[a * N + s] = __dadd_rn(pos[a * N + s], __dmul_rn((double)vel[a * N + s], d));
+        for (int a = 0; a < 3; ++a) pos[a * N + s] = __fma_rn((double)vel[a * N + s], d, pos[a * N + s]);   // one FP64 op
     }
 }
 
