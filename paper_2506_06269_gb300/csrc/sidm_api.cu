@@ -512,7 +512,7 @@ __global__ void k_leaf_hmax(int L, int H, const int32_t* __restrict__ leaf_halo,
     if (lane == 0) nlo[leaf].w = m;
 }
 
-// One tree level: union of up to 8 children (bbox and max h).
+// One tree level: union of up to kArity children (bbox and max h).
 __global__ void k_tree_level(int lev, int H, const int32_t* __restrict__ lvl_off, float4* __restrict__ nlo,
                              float4* __restrict__ nhi)
 {
@@ -523,8 +523,8 @@ __global__ void k_tree_level(int lev, int H, const int32_t* __restrict__ lvl_off
         const int node = off[0] + t;
         const int h = bsearch32(off, H, node);
         const int local = node - off[h];
-        const int c0 = coff[h] + local * 8;
-        const int c1 = min(c0 + 8, coff[h + 1]);
+        const int c0 = coff[h] + local * kArity;
+        const int c1 = min(c0 + kArity, coff[h + 1]);
         float4 lo = make_float4(INFINITY, INFINITY, INFINITY, 0.f);
         float4 hi = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
         for (int c = c0; c < c1; ++c) {
@@ -1111,7 +1111,7 @@ static int make_layout(sidm_ctx* c, int H, const int64_t* off, LayoutHost& L)
     for (int h = 0; h < H; ++h) {
         int64_t cnt = L.leaf_off[h + 1] - L.leaf_off[h];
         int t = 0;
-        while (cnt > 32) { cnt = cdiv(cnt, 8); ++t; }
+        while (cnt > kArity) { cnt = cdiv(cnt, kArity); ++t; }
         L.top[h] = t;
         maxtop = std::max(maxtop, t);
     }
@@ -1124,7 +1124,7 @@ static int make_layout(sidm_ctx* c, int H, const int64_t* off, LayoutHost& L)
         for (int h = 0; h < H; ++h) {
             L.lvl_off[(size_t)l * (H + 1) + h] = (int32_t)run;
             int64_t cnt = L.leaf_off[h + 1] - L.leaf_off[h];
-            for (int k = 0; k < l; ++k) cnt = cdiv(cnt, 8);
+            for (int k = 0; k < l; ++k) cnt = cdiv(cnt, kArity);
             run += cnt;
         }
         L.lvl_off[(size_t)l * (H + 1) + H] = (int32_t)run;

@@ -20,6 +20,8 @@ constexpr int kHaloShift = 51;       // halo index sits above the 51 Morton bits
 constexpr int kMaxHalos = 1024;
 constexpr int kMaxNgb = 128;
 constexpr int kMaxLevels = 12;       // tree levels including the leaf level
+constexpr int kArityLog = 5;         // tree nodes have 2^kArityLog = 32 children: one per lane
+constexpr int kArity = 1 << kArityLog;
 constexpr int kStack = 160;          // traversal stack entries per warp
 constexpr int kLamNX = 257;          // Lambda table: x = d / (h_i + h_j) in [0, 1]
 constexpr int kLamNR = 65;           //               rho = h_min / h_max in [0, 1]

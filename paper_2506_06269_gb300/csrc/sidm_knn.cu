@@ -148,13 +148,11 @@ template <class K>
 __host__ __device__ constexpr int heap4_groups(int kcap) { return (kcap + 2) / 4 + 1; }
 
 // pending heap insertions per lane (a tile adds at most its masked candidates,
-// so the lists are merged before a tile that could overflow one), the pending count at
-// which the lists are merged before a tree node's tests, and the node boxes
-// tested at once (the children of one node; a wider top level in chunks)
+// so the lists are merged before a tile that could overflow one), and the
+// pending count at which the lists are merged before a tree node's tests
 constexpr int kPend = 32;
 static_assert(kPend >= kLeaf, "a tile can admit all of its candidates: one empty pending list must hold them");
 constexpr int kFlushNode = 16;
-constexpr int kBoxes = 8;
 // warm start: the search bound is the previous kernel size times this factor
 constexpr float kGuessSlack = 1.0625f;
 
@@ -166,14 +164,19 @@ __device__ __forceinline__ float to_float_ru(R v)
 }
 
 // shared memory of one warp: staged tile (shifted in place) | ids | traversal
-// stack | node boxes (kBoxes lo + kBoxes hi) | heap groups | pending keys;
-// 14.3 KB at N_ngb = 64 in the mixed form, so 16 warps fit on an SM
+// stack | heap groups | pending keys (the child boxes of a node live in
+// registers, one per lane); 14.1 KB at N_ngb = 64 in the mixed form, so 16
+// warps fit on an SM
 template <class R, class K>
 __host__ __device__ constexpr size_t knn_warp_bytes_t(int kcap)
 {
-    return (TileStageT<R, false, 1>::bytes() + 32 * 4 + kStack * 4 + 2 * kBoxes * 16 +
+    return (TileStageT<R, false, 1>::bytes() + 32 * 4 + kStack * 4 +
             (size_t)heap4_groups<K>(kcap) * 32 * 4 * sizeof(K) + (size_t)kPend * 32 * sizeof(K) + 15) / 16 * 16;
 }
+
+static_assert((TileStageT<float, false, 1>::bytes() + 32 * 4 + kStack * 4) % 16 == 0 &&
+                  (TileStageT<double, false, 1>::bytes() + 32 * 4 + kStack * 4) % 16 == 0,
+              "the heap groups are read as 16-byte vectors");
 
 template <class R, bool NBR, bool TMA>
 __global__ void k_knn(KnnParams p)
@@ -186,9 +189,7 @@ __global__ void k_knn(KnnParams p)
     TileStageT<R, TMA, 1> stage(base);
     uint32_t* tids = (uint32_t*)(base + TileStageT<R, TMA, 1>::bytes());
     int* stack = (int*)(tids + 32);
-    float4* blo = (float4*)(stack + kStack);       // [kBoxes] boxes of the children being tested
-    float4* bhi = blo + kBoxes;
-    K* heapg = (K*)(bhi + kBoxes);
+    K* heapg = (K*)(stack + kStack);               // 16-byte aligned: 528 + 128 + 4 kStack bytes in
     K* pend = heapg + (size_t)heap4_groups<K>(p.kcap) * 32 * 4;   // [kPend][32]
     const Heap4<K> hp{heapg, lane};
     stage.init(lane);
@@ -368,11 +369,18 @@ __global__ void k_knn(KnnParams p)
         // 2) tree walk.  A node is visited iff the query point of some lane lies
         //    within that lane's current k-th distance (+ margin) of the node's box;
         //    accepted leaves are processed at once so the bound keeps shrinking.
-        // boxes of nodes g0 .. g0+n-1 (n <= kBoxes) into the warp's box buffer, one per lane
+        // the boxes of the children being tested, one per lane, in registers
+        float4 clo = make_float4(0.f, 0.f, 0.f, 0.f), chi = clo;
         auto load_boxes = [&](int g0, int n) {
-            __syncwarp();
-            if (lane < n) { blo[lane] = p.nlo[g0 + lane]; bhi[lane] = p.nhi[g0 + lane]; }
-            __syncwarp();
+            if (lane < n) { clo = p.nlo[g0 + lane]; chi = p.nhi[g0 + lane]; }
+        };
+        // this lane's query within r2 of child c's box (every lane takes part)
+        auto near_child = [&](int c, float r2) -> bool {
+            const float4 lo = make_float4(__shfl_sync(0xffffffffu, clo.x, c), __shfl_sync(0xffffffffu, clo.y, c),
+                                          __shfl_sync(0xffffffffu, clo.z, c), 0.f);
+            const float4 hi = make_float4(__shfl_sync(0xffffffffu, chi.x, c), __shfl_sync(0xffffffffu, chi.y, c),
+                                          __shfl_sync(0xffffffffu, chi.z, c), 0.f);
+            return r2 >= 0.f && point_gap2_rd(pq, lo, hi) <= r2;
         };
         // bit c: the query of some lane lies within its bound of box c; the
         // lane's own bits and bound are kept for the leaves of this node.
@@ -386,13 +394,12 @@ __global__ void k_knn(KnnParams p)
             float r2max = r2;
             for (int o = 16; o > 0; o >>= 1) r2max = fmaxf(r2max, __shfl_xor_sync(0xffffffffu, r2max, o));
             const uint32_t near =
-                __ballot_sync(0xffffffffu, lane < n && box_gap2_rd(qlo, qhi, blo[lane], bhi[lane]) <= r2max) & ~skip;
+                __ballot_sync(0xffffffffu, lane < n && box_gap2_rd(qlo, qhi, clo, chi) <= r2max) & ~skip;
             uint32_t bits = 0u;
-            if (r2 >= 0.f)
-                for (uint32_t m = near; m; m &= m - 1u) {
-                    const int c = __ffs(m) - 1;
-                    if (point_gap2_rd(pq, blo[c], bhi[c]) <= r2) bits |= 1u << c;
-                }
+            for (uint32_t m = near; m; m &= m - 1u) {
+                const int c = __ffs(m) - 1;
+                if (near_child(c, r2)) bits |= 1u << c;
+            }
             lane_bits = bits;
             node_r2 = r2;
             return __reduce_or_sync(0xffffffffu, bits);
@@ -408,14 +415,14 @@ __global__ void k_knn(KnnParams p)
         // bound its nearer leaves have shrunk
         auto visit_leaf = [&](int Bl, int c) {
             const float r2 = my_r2();
-            const bool mine = r2 >= 0.f && point_gap2_rd(pq, blo[c], bhi[c]) <= r2;
+            const bool mine = near_child(c, r2);
             if (__any_sync(0xffffffffu, mine)) process(Bl, mine, r2, fetch(Bl));
         };
         // Accepted children are visited nearest first (box gap to the query leaf),
         // so the k-th bound shrinks early.  rank = position among the accepted.
         auto order_rank = [&](uint32_t acc, int n) -> int {
             const bool mine_acc = lane < n && ((acc >> lane) & 1u);
-            const float pr = mine_acc ? box_gap2_rd(qlo, qhi, blo[lane], bhi[lane]) : INFINITY;
+            const float pr = mine_acc ? box_gap2_rd(qlo, qhi, clo, chi) : INFINITY;
             int rank = 0;
             for (int j = 0; j < n; ++j) {
                 const float pj = __shfl_sync(0xffffffffu, pr, j);
@@ -470,14 +477,11 @@ __global__ void k_knn(KnnParams p)
         int sp = 0;
         {
             const int nb = loff[top * Hp + h];
-            const int ntop = loff[top * Hp + h + 1] - nb;   // at most 32
-            for (int c0 = 0; c0 < ntop && !failed; c0 += kBoxes) {
-                const int n = min(kBoxes, ntop - c0);
-                load_boxes(nb + c0, n);
-                const uint32_t acc = accept(n, my_r2(), top == 0 ? window_mask(c0, n) : 0u);
-                if (top == 0) visit_leaves_in_order(acc, n, c0);
-                else if (!push_in_order(acc, n, top, c0, sp)) failed = true;
-            }
+            const int ntop = loff[top * Hp + h + 1] - nb;   // at most kArity
+            load_boxes(nb, ntop);
+            const uint32_t acc = accept(ntop, my_r2(), top == 0 ? window_mask(0, ntop) : 0u);
+            if (top == 0) visit_leaves_in_order(acc, ntop, 0);
+            else if (!push_in_order(acc, ntop, top, 0, sp)) failed = true;
         }
         while (sp > 0 && !failed) {
             const int e = stack[--sp];
@@ -486,8 +490,8 @@ __global__ void k_knn(KnnParams p)
             const int cl = lev - 1;
             const int cb = loff[cl * Hp + h];
             const int cc = loff[cl * Hp + h + 1] - cb;
-            const int first = idx * 8;
-            const int nch = min(8, cc - first);
+            const int first = idx * kArity;
+            const int nch = min(kArity, cc - first);
             // tighten the bounds before the node tests once enough keys wait
             if (__any_sync(0xffffffffu, np >= kFlushNode)) flush();
             load_boxes(cb + first, nch);

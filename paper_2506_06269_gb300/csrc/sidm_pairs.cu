@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
             const float r = __fadd_ru(__fmul_ru(__fadd_ru(hq, lo.w), 1.0f + 0x1p-20f), fr.margin);
             return active && point_gap2_rd(pq, lo, hi) <= __fmul_ru(r, r);
         };
-        // boxes of nodes g0 .. g0+n-1 (n <= 32), one per lane
+        // boxes of nodes g0 .. g0+n-1 (n <= kArity = 32), one per lane
         auto load_boxes = [&](int g0, int n) {
             __syncwarp();
             if (lane < n) { blo[lane] = p.nlo[g0 + lane]; bhi[lane] = p.nhi[g0 + lane]; }
@@ -421,10 +421,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
         };
         // nodes whose subtree holds a leaf >= A (level lev, local indices first ..)
         auto eligible_mask = [&](int lev, int first, int n) -> uint32_t {
-            uint32_t m = 0u;
-            for (int c = 0; c < n; ++c)
-                if (((int64_t)(first + c + 1) << (3 * lev)) > A) m |= 1u << c;
-            return m;
+            return __ballot_sync(0xffffffffu, lane < n && ((int64_t)(first + lane + 1) << (kArityLog * lev)) > A);
         };
         // accepted leaves in index order; the next one is fetched before this one
         // is processed, so its load overlaps this leaf's tests
@@ -472,8 +469,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
             const int cl = lev - 1;
             const int cb = p.lvl_off[cl * Hp + h];
             const int cc = p.lvl_off[cl * Hp + h + 1] - cb;
-            const int first = idx * 8;
-            const int nch = min(8, cc - first);
+            const int first = idx * kArity;
+            const int nch = min(kArity, cc - first);
             load_boxes(cb + first, nch);
             const uint32_t acc = accept(nch, eligible_mask(cl, first, nch));
             if (cl == 0) visit_leaves(acc, first);
