@@ -265,6 +265,30 @@ __global__ void k_knn(KnnParams p)
             pq = make_float3(__double2float_rn((double)q.x - fr.O[0]), __double2float_rn((double)q.y - fr.O[1]),
                              __double2float_rn((double)q.z - fr.O[2]));
         }
+        // boxes of the query points of lanes 0-15 and of lanes 16-31 (every lane
+        // holds both): a candidate is kept if it lies within the largest bound of
+        // either half's lanes from that half's box (the union of the two is
+        // tighter than the whole leaf's box; the mask stays warp-uniform)
+        float4 hlo[2], hhi[2];
+        {
+            float lx = active ? pq.x : INFINITY, ly = active ? pq.y : INFINITY, lz = active ? pq.z : INFINITY;
+            float ux = active ? pq.x : -INFINITY, uy = active ? pq.y : -INFINITY, uz = active ? pq.z : -INFINITY;
+            for (int o = 8; o > 0; o >>= 1) {
+                lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
+                ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
+                lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
+                ux = fmaxf(ux, __shfl_xor_sync(0xffffffffu, ux, o));
+                uy = fmaxf(uy, __shfl_xor_sync(0xffffffffu, uy, o));
+                uz = fmaxf(uz, __shfl_xor_sync(0xffffffffu, uz, o));
+            }
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                hlo[hh] = make_float4(__shfl_sync(0xffffffffu, lx, 16 * hh), __shfl_sync(0xffffffffu, ly, 16 * hh),
+                                      __shfl_sync(0xffffffffu, lz, 16 * hh), 0.f);
+                hhi[hh] = make_float4(__shfl_sync(0xffffffffu, ux, 16 * hh), __shfl_sync(0xffffffffu, uy, 16 * hh),
+                                      __shfl_sync(0xffffffffu, uz, 16 * hh), 0.f);
+            }
+        }
         auto my_r2 = [&]() -> float {
             if (!act) return -1.0f;
             float r = to_float_ru<R>(sqrt_ru(key_d2<R, NBR>(root)));
@@ -292,15 +316,16 @@ __global__ void k_knn(KnnParams p)
                 c.y = __fadd_rn(c.y, __fsub_rn(cB.y, cA.y));
                 c.z = __fadd_rn(c.z, __fsub_rn(cB.z, cA.z));
             }
-            // candidates farther from the query leaf's box than the largest bound
-            // of any lane cannot enter a heap: the loops skip them (an unbounded
-            // lane, before its heap is full in the cold pass, keeps them all)
+            // candidates farther from a half-leaf's box than the largest bound of
+            // its lanes cannot enter one of their heaps: the loops skip the
+            // candidates neither half can reach (an unbounded lane, before its heap
+            // is full in the cold pass, keeps them all)
             float lr2 = -1.f;
             if (act && mine) lr2 = isnan(r2) ? INFINITY : r2;
-            float r2max = lr2;
-            for (int o = 16; o > 0; o >>= 1) r2max = fmaxf(r2max, __shfl_xor_sync(0xffffffffu, r2max, o));
+            for (int o = 8; o > 0; o >>= 1) lr2 = fmaxf(lr2, __shfl_xor_sync(0xffffffffu, lr2, o));
+            const float r2h0 = __shfl_sync(0xffffffffu, lr2, 0), r2h1 = __shfl_sync(0xffffffffu, lr2, 16);
             uint32_t cmask;
-            if (!(r2max < INFINITY)) {
+            if (!(fmaxf(r2h0, r2h1) < INFINITY)) {
                 cmask = countB == kLeaf ? 0xffffffffu : ((1u << countB) - 1u);
             } else {
                 float3 pc;                             // candidate in the halo frame
@@ -310,7 +335,8 @@ __global__ void k_knn(KnnParams p)
                     pc = make_float3(__double2float_rn((double)c.x - fr.O[0]), __double2float_rn((double)c.y - fr.O[1]),
                                      __double2float_rn((double)c.z - fr.O[2]));
                 }
-                cmask = __ballot_sync(0xffffffffu, lane < countB && point_gap2_rd(pc, qlo, qhi) <= r2max);
+                cmask = __ballot_sync(0xffffffffu, lane < countB && (point_gap2_rd(pc, hlo[0], hhi[0]) <= r2h0 ||
+                                                                     point_gap2_rd(pc, hlo[1], hhi[1]) <= r2h1));
             }
             ++n_tiles;
             if (cmask == 0u) return;                   // no candidate of this leaf can enter
