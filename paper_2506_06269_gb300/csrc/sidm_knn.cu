@@ -151,6 +151,8 @@ __host__ __device__ constexpr int heap4_groups(int kcap) { return (kcap + 2) / 4
 // so the lists are merged before a tile that could overflow one), and the
 // pending count at which the lists are merged before a tree node's tests
 constexpr int kPend = 32;
+// query groups of 32 / kGroups consecutive lanes whose boxes filter the candidates
+constexpr int kGroups = 4;
 static_assert(kPend >= kLeaf, "a tile can admit all of its candidates: one empty pending list must hold them");
 constexpr int kFlushNode = 16;
 // warm start: the search bound is the previous kernel size times this factor
@@ -170,13 +172,14 @@ __device__ __forceinline__ float to_float_ru(R v)
 template <class R, class K>
 __host__ __device__ constexpr size_t knn_warp_bytes_t(int kcap)
 {
-    return (TileStageT<R, false, 1>::bytes() + 32 * 4 + kStack * 4 +
+    return (TileStageT<R, false, 1>::bytes() + 32 * 4 + kStack * 4 + 2 * kGroups * 16 +
             (size_t)heap4_groups<K>(kcap) * 32 * 4 * sizeof(K) + (size_t)kPend * 32 * sizeof(K) + 15) / 16 * 16;
 }
 
 static_assert((TileStageT<float, false, 1>::bytes() + 32 * 4 + kStack * 4) % 16 == 0 &&
                   (TileStageT<double, false, 1>::bytes() + 32 * 4 + kStack * 4) % 16 == 0,
               "the heap groups are read as 16-byte vectors");
+static_assert(kGroups == 2 || kGroups == 4 || kGroups == 8, "lane groups are 16, 8 or 4 lanes");
 
 template <class R, bool NBR, bool TMA>
 __global__ void k_knn(KnnParams p)
@@ -189,7 +192,8 @@ __global__ void k_knn(KnnParams p)
     TileStageT<R, TMA, 1> stage(base);
     uint32_t* tids = (uint32_t*)(base + TileStageT<R, TMA, 1>::bytes());
     int* stack = (int*)(tids + 32);
-    K* heapg = (K*)(stack + kStack);               // 16-byte aligned: 528 + 128 + 4 kStack bytes in
+    float4* gbox = (float4*)(stack + kStack);      // [kGroups][2]: box lo, hi of each lane group
+    K* heapg = (K*)(gbox + 2 * kGroups);           // 16-byte aligned: 528 + 128 + 4 kStack bytes in, + boxes
     K* pend = heapg + (size_t)heap4_groups<K>(p.kcap) * 32 * 4;   // [kPend][32]
     const Heap4<K> hp{heapg, lane};
     stage.init(lane);
@@ -265,15 +269,15 @@ __global__ void k_knn(KnnParams p)
             pq = make_float3(__double2float_rn((double)q.x - fr.O[0]), __double2float_rn((double)q.y - fr.O[1]),
                              __double2float_rn((double)q.z - fr.O[2]));
         }
-        // boxes of the query points of lanes 0-15 and of lanes 16-31 (every lane
-        // holds both): a candidate is kept if it lies within the largest bound of
-        // either half's lanes from that half's box (the union of the two is
+        // boxes of the query points of each group of 32 / kGroups consecutive
+        // lanes (shared memory): a candidate is kept if it lies within the
+        // largest bound of some group's lanes from that group's box (the union is
         // tighter than the whole leaf's box; the mask stays warp-uniform)
-        float4 hlo[2], hhi[2];
+        constexpr int kGL = 32 / kGroups;
         {
             float lx = active ? pq.x : INFINITY, ly = active ? pq.y : INFINITY, lz = active ? pq.z : INFINITY;
             float ux = active ? pq.x : -INFINITY, uy = active ? pq.y : -INFINITY, uz = active ? pq.z : -INFINITY;
-            for (int o = 8; o > 0; o >>= 1) {
+            for (int o = kGL / 2; o > 0; o >>= 1) {
                 lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
                 ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
                 lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
@@ -281,13 +285,12 @@ __global__ void k_knn(KnnParams p)
                 uy = fmaxf(uy, __shfl_xor_sync(0xffffffffu, uy, o));
                 uz = fmaxf(uz, __shfl_xor_sync(0xffffffffu, uz, o));
             }
-#pragma unroll
-            for (int hh = 0; hh < 2; ++hh) {
-                hlo[hh] = make_float4(__shfl_sync(0xffffffffu, lx, 16 * hh), __shfl_sync(0xffffffffu, ly, 16 * hh),
-                                      __shfl_sync(0xffffffffu, lz, 16 * hh), 0.f);
-                hhi[hh] = make_float4(__shfl_sync(0xffffffffu, ux, 16 * hh), __shfl_sync(0xffffffffu, uy, 16 * hh),
-                                      __shfl_sync(0xffffffffu, uz, 16 * hh), 0.f);
+            __syncwarp();
+            if (lane % kGL == 0) {
+                gbox[2 * (lane / kGL)] = make_float4(lx, ly, lz, 0.f);
+                gbox[2 * (lane / kGL) + 1] = make_float4(ux, uy, uz, 0.f);
             }
+            __syncwarp();
         }
         auto my_r2 = [&]() -> float {
             if (!act) return -1.0f;
@@ -316,16 +319,22 @@ __global__ void k_knn(KnnParams p)
                 c.y = __fadd_rn(c.y, __fsub_rn(cB.y, cA.y));
                 c.z = __fadd_rn(c.z, __fsub_rn(cB.z, cA.z));
             }
-            // candidates farther from a half-leaf's box than the largest bound of
+            // candidates farther from a lane group's box than the largest bound of
             // its lanes cannot enter one of their heaps: the loops skip the
-            // candidates neither half can reach (an unbounded lane, before its heap
-            // is full in the cold pass, keeps them all)
+            // candidates no group can reach (an unbounded lane, before its heap is
+            // full in the cold pass, keeps them all)
             float lr2 = -1.f;
             if (act && mine) lr2 = isnan(r2) ? INFINITY : r2;
-            for (int o = 8; o > 0; o >>= 1) lr2 = fmaxf(lr2, __shfl_xor_sync(0xffffffffu, lr2, o));
-            const float r2h0 = __shfl_sync(0xffffffffu, lr2, 0), r2h1 = __shfl_sync(0xffffffffu, lr2, 16);
+            for (int o = kGL / 2; o > 0; o >>= 1) lr2 = fmaxf(lr2, __shfl_xor_sync(0xffffffffu, lr2, o));
+            float r2g[kGroups];
+            float r2all = -1.f;
+#pragma unroll
+            for (int g = 0; g < kGroups; ++g) {
+                r2g[g] = __shfl_sync(0xffffffffu, lr2, g * kGL);
+                r2all = fmaxf(r2all, r2g[g]);
+            }
             uint32_t cmask;
-            if (!(fmaxf(r2h0, r2h1) < INFINITY)) {
+            if (!(r2all < INFINITY)) {
                 cmask = countB == kLeaf ? 0xffffffffu : ((1u << countB) - 1u);
             } else {
                 float3 pc;                             // candidate in the halo frame
@@ -335,8 +344,11 @@ __global__ void k_knn(KnnParams p)
                     pc = make_float3(__double2float_rn((double)c.x - fr.O[0]), __double2float_rn((double)c.y - fr.O[1]),
                                      __double2float_rn((double)c.z - fr.O[2]));
                 }
-                cmask = __ballot_sync(0xffffffffu, lane < countB && (point_gap2_rd(pc, hlo[0], hhi[0]) <= r2h0 ||
-                                                                     point_gap2_rd(pc, hlo[1], hhi[1]) <= r2h1));
+                bool reach = false;
+#pragma unroll
+                for (int g = 0; g < kGroups; ++g)
+                    reach = reach || (r2g[g] >= 0.f && point_gap2_rd(pc, gbox[2 * g], gbox[2 * g + 1]) <= r2g[g]);
+                cmask = __ballot_sync(0xffffffffu, lane < countB && reach);
             }
             ++n_tiles;
             if (cmask == 0u) return;                   // no candidate of this leaf can enter
