@@ -14,8 +14,8 @@
  *               kernel overlap); Eq. hDl ties h to the sphere holding N_ngb
  *               particles.
  *   Sect. 3.8 : velocity-dependent cross-section, Eq. vel_dep.
- *   Sect. 5   : energy conservation of the pairwise scheme is independent of
- *               the kernel ("by construction").
+ *   Sect. 5   : the pairwise scheme conserves energy whatever the kernel,
+ *               since every scatter conserves it on its own.
  *   App. A    : viscosity cross-section normalised to the total one for
  *               isotropic scattering (so sigma_V = sigma here).
  *   Sect. 3.5, Sect. 3.6, App. C : local diagnostics -- SPH density and

@@ -1,6 +1,7 @@
 // sidm_knn.cu -- (a1) kernel sizes: h_i = distance to the N_ngb-th nearest
-// other particle of the halo (Sect. 2: "set by the next N_ngb neighbours";
-// Eq. hDl: h is the radius of the sphere holding N_ngb particles).
+// other particle of the halo (Sect. 2: each particle's kernel size adapts to
+// its N_ngb nearest neighbours; Eq. hDl: h is the radius of the sphere holding
+// N_ngb particles).
 //
 // One warp per leaf of 32 consecutive Morton-ordered particles, one query per
 // lane.  Candidate leaves are staged through shared memory (plain coalesced
