@@ -7,6 +7,8 @@
 // geometric factor Lambda of the interaction probability), Sect. 5
 // (conservation independent of the kernel).
 #include <algorithm>
+#include <mutex>
+#include <vector>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -906,11 +908,35 @@ cudaError_t ensure_device(sidm_ctx* c)
     return cur == c->dev ? cudaSuccess : cudaSetDevice(c->dev);
 }
 
+// A kernel's dynamic shared-memory limit belongs to the kernel (per device),
+// not to a context, so it is tracked process-wide and only ever raised: a
+// launch of any context may use every size queried before, by any context.
+static cudaError_t raise_smem_limit(const void* fn, size_t smem)
+{
+    struct Limit { int dev; const void* fn; size_t smem; };
+    static std::mutex mu;
+    static std::vector<Limit> limits;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto& l : limits)
+        if (l.dev == dev && l.fn == fn) {
+            if (smem <= l.smem) return cudaSuccess;
+            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess) l.smem = smem;
+            return e;
+        }
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) limits.push_back({dev, fn, smem});
+    return e;
+}
+
 int occupancy(sidm_ctx* c, const void* fn, int threads, size_t smem, int* occ)
 {
     for (const auto& e : c->launch_cache)
         if (e.fn == fn && e.smem == smem) { *occ = e.occ; return SIDM_OK; }
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem_limit(fn, smem);
     if (e != cudaSuccess) return cuda_check(c, e, "shared-memory attribute");
     int o = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, threads, smem);

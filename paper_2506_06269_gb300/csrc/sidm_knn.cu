@@ -599,17 +599,23 @@ int launch_t(sidm_ctx* c, void* h_out, uint32_t* nbr, int k_stride, bool use_gue
     p.hprev = NBR ? nullptr : c->d_hprev;
     p.use_guess = use_guess ? 1 : 0;
     p.slack = kGuessSlack;
-    // the configured warps per CTA, halved while a CTA would exceed the 227 KB
-    // of shared memory one block may use (large N_ngb in the FP64 form)
-    int warps = c->knn_warps;
-    while (warps > 1 && (size_t)warps * knn_warp_bytes_t<R, K>(p.kcap) > (size_t)227 * 1024) warps /= 2;
-    const size_t smem = (size_t)warps * knn_warp_bytes_t<R, K>(p.kcap);
+    // warps per CTA: at most the configured number, and of those the one with
+    // the most resident warps per SM (with large N_ngb the per-warp heaps make
+    // two small CTAs hold more warps than one large one); a CTA may use at most
+    // 227 KB of shared memory
     auto kern = k_knn<R, NBR, TMA>;
-    int occ = 0;
-    int rc = occupancy(c, (const void*)kern, warps * 32, smem, &occ);
-    if (rc) return rc;
+    const size_t per_warp = knn_warp_bytes_t<R, K>(p.kcap);
+    int warps = 0, occ = 0;
+    for (int w = c->knn_warps; w >= 1; --w) {
+        if ((size_t)w * per_warp > (size_t)227 * 1024) continue;
+        int o = 0;
+        const int rc = occupancy(c, (const void*)kern, w * 32, (size_t)w * per_warp, &o);
+        if (rc) return rc;
+        if (o * w > occ * warps) { warps = w; occ = o; }
+    }
+    const size_t smem = (size_t)warps * per_warp;
     cudaError_t e;
-    if (occ < 1) return set_err(c, SIDM_ECAPACITY, "knn kernel does not fit on an SM (ngb_max too large for knn_warps)");
+    if (warps < 1 || occ < 1) return set_err(c, SIDM_ECAPACITY, "knn kernel does not fit on an SM (ngb_max too large)");
     int grid = c->cfg.grid_ctas > 0 ? c->cfg.grid_ctas : c->sm_count * occ;
     grid = std::max(1, std::min(grid, (L.L + warps - 1) / warps));
     c->knn_grid = grid;
