@@ -229,3 +229,23 @@ def test_binned_pairs_reduce_to_the_plain_pass():
     opened = bins >= 2
     assert np.all(sps[~opened] == 0.0)
     assert np.all(sps[opened] <= sp0[opened] * (1 + 1e-12))
+
+
+def test_host_edge_cases():
+    # a host with no parts exerts nothing; moving the centre with the point
+    # changes nothing; the spherical parts pull towards the centre
+    empty = {"G": 1.0, "center": (1.0, 2.0, 3.0)}
+    x = np.array([4.0, -1.0, 0.5])
+    assert O.host_phi(empty, x) == 0.0
+    assert np.all(O.host_accel(empty, x) == 0.0)
+    shift = np.array([7.0, -3.0, 11.0])
+    moved = dict(MW, center=tuple(shift))
+    assert O.host_phi(moved, x + shift) == pytest.approx(O.host_phi(MW, x), rel=1e-13)
+    np.testing.assert_allclose(O.host_accel(moved, x + shift), O.host_accel(MW, x), rtol=1e-12)
+    for part in _parts(MW)[:2]:                      # the NFW halo and the bulge
+        a = O.host_accel(part, x)
+        assert np.dot(a, x) < 0 and np.linalg.norm(np.cross(a, x)) <= 1e-12 * np.linalg.norm(a) * np.linalg.norm(x)
+    # at the centre itself the spherical parts add nothing (and stay finite)
+    assert np.all(np.isfinite(O.host_accel(MW, [0.0, 0.0, 0.0])))
+    np.testing.assert_allclose(O.host_accel({"G": 1.0, "center": (0, 0, 0), "nfw": MW["nfw"], "bulge": MW["bulge"]},
+                                            [0.0, 0.0, 0.0]), 0.0, atol=0)
