@@ -160,6 +160,23 @@ def test_launch_shape_invariance():
         assert np.array_equal(g["vel"], ref["vel"])
 
 
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_launch_shape_invariance_large_ngb(precision):
+    # N_ngb = 128: the kernel-size launch picks the CTA size with the most
+    # resident warps (smaller than the configured 8 when the per-warp heaps are
+    # large); every shape gives the same bits
+    b = ics.batch([ics.nfw(6000, 17)])
+    args = ([128], [(1, 100.0, 0.3811)], [0.2], 7, 3)
+    ref = gpu_step(b, *args, precision=precision)
+    assert ref["status"] == 0
+    for kw in (dict(knn_warps=1), dict(knn_warps=3), dict(knn_warps=16)):
+        g = gpu_step(b, *args, precision=precision, ctx_kw=kw)
+        assert g["status"] == 0
+        assert np.array_equal(g["h"], ref["h"])
+        assert np.array_equal(g["events"]["key"], ref["events"]["key"])
+        assert np.array_equal(g["vel"], ref["vel"])
+
+
 def test_tma_staging_identical():
     h = ics.nfw(6000, 13)
     b = ics.batch([h])
