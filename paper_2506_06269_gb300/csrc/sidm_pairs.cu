@@ -167,6 +167,14 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
         const float hmaxA = qlo.w;
         const uint32_t slotA = (uint32_t)leaf * kLeaf + lane;
         const V q = P4[slotA];
+        // the queries in their own frame, for tiles tested candidate by lane (the
+        // plain path stages tiles in registers, so the first staging buffer is free)
+        V* qsh = st_pos.raw();
+        if constexpr (!TMA) {
+            __syncwarp();
+            qsh[lane] = q;
+            __syncwarp();
+        }
         int qhead = 0, qn = 0;
         unsigned long long n_tiles = 0ull;
 
@@ -344,22 +352,42 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
             const uint32_t cmask = __ballot_sync(
                 0xffffffffu, lane < countB && point_gap2_rd(pc, qlo, qhi) <= __fmul_ru(rc, rc) &&
                                  (!p.bins || step_opens(p.bins[hb + (int64_t)Bl * kLeaf + lane], p.n_bins, p.substep)));
-            // (i) in-range bits of this lane's query against every candidate of the
-            //     warp-uniform mask: straight-line arithmetic, no vote per candidate
-            uint32_t okm = 0u;
-            for (uint32_t mm = cmask; mm; mm &= mm - 1u) {
-                const int t = __ffs(mm) - 1;
-                const V pj = tp[t];
-                const R dx = sub_rn(pj.x, q.x), dy = sub_rn(pj.y, q.y), dz = sub_rn(pj.z, q.z);
-                const R d2 = fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
-                const R hs = add_rn(q.w, pj.w);
-                okm |= (d2 < mul_rn(hs, hs) ? 1u : 0u) << t;
+            // (i) the pairs to test: queries that reach B (qmask) x candidates that
+            //     can reach some query (cmask), inside A only candidate > query.  The
+            //     warp loops over the smaller mask: lane = query, candidates from the
+            //     staged tile (bits of okm = candidates), or lane = candidate, queries
+            //     from their staged copy (bits = queries).  Same tests, same operands.
+            const uint32_t qmask = __ballot_sync(0xffffffffu, mine);
+            const bool by_cand = !TMA && __popc(qmask) < __popc(cmask);
+            uint32_t okm = 0u, allow;
+            if (!by_cand) {
+                for (uint32_t mm = cmask; mm; mm &= mm - 1u) {
+                    const int t = __ffs(mm) - 1;
+                    const V pj = tp[t];
+                    const R dx = sub_rn(pj.x, q.x), dy = sub_rn(pj.y, q.y), dz = sub_rn(pj.z, q.z);
+                    const R d2 = fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
+                    const R hs = add_rn(q.w, pj.w);
+                    okm |= (d2 < mul_rn(hs, hs) ? 1u : 0u) << t;
+                }
+                allow = mine ? cmask : 0u;
+                if (Bl == A) allow &= 0xFFFFFFFEu << lane;
+            } else {
+                for (uint32_t mm = qmask; mm; mm &= mm - 1u) {
+                    const int i = __ffs(mm) - 1;
+                    const V qi = qsh[i];
+                    const R dx = sub_rn(c.x, qi.x), dy = sub_rn(c.y, qi.y), dz = sub_rn(c.z, qi.z);
+                    const R d2 = fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
+                    const R hs = add_rn(qi.w, c.w);
+                    okm |= (d2 < mul_rn(hs, hs) ? 1u : 0u) << i;
+                }
+                allow = ((cmask >> lane) & 1u) ? qmask : 0u;
+                if (Bl == A) allow &= (1u << lane) - 1u;
             }
-            // pairs this lane owns: its query reaches B, and inside A only t > lane
-            uint32_t allow = mine ? cmask : 0u;
-            if (Bl == A) allow &= 0xFFFFFFFEu << lane;
             n_tested += (unsigned long long)__popc(allow);
             okm &= allow;
+            // queue entry of bit t: (query slot, candidate slot)
+            const uint32_t own = by_cand ? slotB + lane : slotA;
+            const uint32_t base = by_cand ? (uint32_t)leaf * kLeaf : slotB;
             // (ii) queue the pairs in rounds: every lane with pairs left adds up to
             //      kPerRound, after the entries of the lanes below it
             for (uint32_t m = __ballot_sync(0xffffffffu, okm != 0u); m; m = __ballot_sync(0xffffffffu, okm != 0u)) {
@@ -376,8 +404,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
                 for (int k = 0; k < take; ++k, ++e) {
                     const int t = __ffs(okm) - 1;
                     okm &= okm - 1u;
-                    q_si[e & (kQueue - 1)] = slotA;
-                    q_sj[e & (kQueue - 1)] = slotB + t;
+                    q_si[e & (kQueue - 1)] = by_cand ? base + t : own;
+                    q_sj[e & (kQueue - 1)] = by_cand ? own : base + t;
                 }
                 qn += c2;
                 n_pairs += (unsigned long long)c2;
