@@ -100,8 +100,10 @@ __device__ __forceinline__ float to_float_ru_p(R v)
     else return (float)v;
 }
 
-// per warp: staged candidate leaf, queue of in-range pairs (slot i, slot j),
-// traversal stack, boxes of the nodes under test (32 lo + 32 hi)
+// per warp: staging buffers (the bulk-copy path lands a candidate leaf in the
+// first; the plain path keeps the query leaf's own points there), the shifted
+// candidate leaf, queue of in-range pairs (slot i, slot j), traversal stack,
+// boxes of the nodes under test (32 lo + 32 hi)
 template <class R, bool TMA>
 constexpr size_t pair_warp_bytes()
 {
