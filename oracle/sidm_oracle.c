@@ -22,7 +22,7 @@
  *               velocity dispersion over the particle's kernel, the effective
  *               cross-section (Eq. effective_cross_section), h/l (Eq. hDl) and
  *               the Knudsen number (Eq. knudsen_number).
- * Readings where the paper is silent (all listed in the design doc):
+ * Readings where the paper is silent:
  *   h_i      = distance to the N_ngb-th nearest *other* particle of the halo,
  *              ties broken by id; the kernel support radius is h_i.
  *   W(r,h)   = 8/(pi h^3) {1-6q^2+6q^3 (q<1/2); 2(1-q)^3 (q<1); 0}, q=r/h.
@@ -226,13 +226,25 @@ static uint64_t spread3(uint32_t v)
     return r;
 }
 
-static uint64_t* g_sort_keys;  /* used by the qsort comparator only */
-static int cmp_key_stable(const void* a, const void* b)
+/* Stable LSD radix sort of 0..n-1 by a 64-bit key (13-bit digits over the
+ * key's 51 Morton bits): order[s] = index of the s-th smallest key, equal keys
+ * in input order. */
+static void sort_by_key_stable(int n, const uint64_t* key, uint32_t* order)
 {
-    uint32_t i = *(const uint32_t*)a, j = *(const uint32_t*)b;
-    uint64_t ki = g_sort_keys[i], kj = g_sort_keys[j];
-    if (ki != kj) return ki < kj ? -1 : 1;
-    return (i > j) - (i < j);   /* stable: input order */
+    const int bits = 13, nb = 1 << 13;
+    uint32_t* tmp = (uint32_t*)malloc(sizeof(uint32_t) * (n ? n : 1));
+    size_t* cnt = (size_t*)malloc(sizeof(size_t) * (size_t)nb);
+    for (int i = 0; i < n; ++i) order[i] = (uint32_t)i;
+    for (int shift = 0; shift < 3 * ORC_MBITS; shift += bits) {
+        memset(cnt, 0, sizeof(size_t) * (size_t)nb);
+        for (int s = 0; s < n; ++s) cnt[(key[order[s]] >> shift) & (uint64_t)(nb - 1)]++;
+        size_t run = 0;
+        for (int d = 0; d < nb; ++d) { size_t c = cnt[d]; cnt[d] = run; run += c; }
+        for (int s = 0; s < n; ++s) tmp[cnt[(key[order[s]] >> shift) & (uint64_t)(nb - 1)]++] = order[s];
+        memcpy(order, tmp, sizeof(uint32_t) * (size_t)n);
+    }
+    free(cnt);
+    free(tmp);
 }
 
 static void geom_build(orc_geom* g, int n, const double* px, const double* py, const double* pz)
@@ -265,11 +277,9 @@ static void geom_build(orc_geom* g, int n, const double* px, const double* py, c
     }
     g->order = (uint32_t*)malloc(sizeof(uint32_t) * (n ? n : 1));
     g->rank = (uint32_t*)malloc(sizeof(uint32_t) * (n ? n : 1));
-    for (int i = 0; i < n; ++i) g->order[i] = (uint32_t)i;
-    g_sort_keys = key;
-    qsort(g->order, n, sizeof(uint32_t), cmp_key_stable);
+    sort_by_key_stable(n, key, g->order);
     for (int s = 0; s < n; ++s) g->rank[g->order[s]] = (uint32_t)s;
-    g->cell = (float*)malloc(sizeof(float) * 3 * (g->nleaf ? g->nleaf : 1));
+    g->cell = (float*)malloc(sizeof(float) * 3 * (g->nleaf > 0 ? (size_t)g->nleaf : 1u));
     g->off = (float*)malloc(sizeof(float) * 3 * (n ? n : 1));
     const double fine = ldexp(1.0, E + 1 - ORC_MBITS);   /* finest Morton cell */
     for (int L = 0; L < g->nleaf; ++L) {
@@ -296,25 +306,39 @@ static void geom_free(orc_geom* g)
     memset(g, 0, sizeof(*g));
 }
 
-/* canonical FP32 squared distance from i (its leaf frame) to j; local indices */
-static float d2_mixed(const orc_geom* g, uint32_t i, uint32_t j)
+/* canonical FP32 squared distance from a point of offset oi in a leaf with
+ * frame origin cA to a point of offset oj in a leaf with origin cB, in the
+ * frame cA */
+static float d2_mixed_core(const float* cA, const float* oi, const float* cB, const float* oj)
 {
     volatile float dx[3];
-    int A = (int)(g->rank[i] / ORC_LEAF), B = (int)(g->rank[j] / ORC_LEAF);
     for (int a = 0; a < 3; ++a) {
-        float s = g->cell[3 * B + a] - g->cell[3 * A + a];       /* exact */
-        float t = g->off[3 * j + a] + s;
-        dx[a] = t - g->off[3 * i + a];
+        float s = cB[a] - cA[a];                                  /* exact */
+        float t = oj[a] + s;
+        dx[a] = t - oi[a];
     }
     float xx = dx[0] * dx[0];
     return fmaf(dx[2], dx[2], fmaf(dx[1], dx[1], xx));
 }
 
-static double d2_fp64(const double* px, const double* py, const double* pz, uint32_t i, uint32_t j)
+/* canonical FP32 squared distance from i (its leaf frame) to j; local indices */
+static float d2_mixed(const orc_geom* g, uint32_t i, uint32_t j)
 {
-    double dx = px[j] - px[i], dy = py[j] - py[i], dz = pz[j] - pz[i];
+    int A = (int)(g->rank[i] / ORC_LEAF), B = (int)(g->rank[j] / ORC_LEAF);
+    return d2_mixed_core(g->cell + 3 * A, g->off + 3 * (size_t)i, g->cell + 3 * B, g->off + 3 * (size_t)j);
+}
+
+static double d2_fp64_core(const double* xi, const double* xj)
+{
+    double dx = xj[0] - xi[0], dy = xj[1] - xi[1], dz = xj[2] - xi[2];
     double xx = dx * dx;
     return fma(dz, dz, fma(dy, dy, xx));
+}
+
+static double d2_fp64(const double* px, const double* py, const double* pz, uint32_t i, uint32_t j)
+{
+    const double xi[3] = {px[i], py[i], pz[i]}, xj[3] = {px[j], py[j], pz[j]};
+    return d2_fp64_core(xi, xj);
 }
 
 /* float/double -> order-preserving unsigned bits (non-negative values) */
@@ -322,63 +346,147 @@ static uint32_t fbits(float f) { uint32_t u; memcpy(&u, &f, 4); return u; }
 static uint64_t dbits(double f) { uint64_t u; memcpy(&u, &f, 8); return u; }
 
 /* ------------------------------------------------------------------------- */
-/* Uniform search grid (a plain accelerator; the kNN result is defined by     */
-/* the exhaustive order of (d2, id), which the grid search reproduces).       */
+/* k-d tree over the particles of a halo: a plain search accelerator.  Every  */
+/* search below returns what an exhaustive scan over all particles returns    */
+/* (the tests pin both against brute force); the tree only skips boxes that   */
+/* provably hold no candidate.  Nodes split their particles at the median of  */
+/* the widest axis of their bounding box; leaves hold at most ORC_KD_LEAF.    */
 /* ------------------------------------------------------------------------- */
-typedef struct {
-    int n, dim[3];
-    double lo[3], cs;
-    int* start;     /* [ncell+1] */
-    int* items;     /* [n] local indices */
-} orc_grid;
+#define ORC_KD_LEAF 16
 
-static void grid_build(orc_grid* G, int n, const double* px, const double* py, const double* pz, double occ)
+typedef struct {
+    double lo[3], hi[3];   /* bounding box of the node's particles (FP64)     */
+    double hmax;           /* largest kernel size in the node (pair searches) */
+    int start, count;      /* items[start .. start + count)                   */
+    int left, right;       /* children, -1 at a leaf                          */
+} orc_kdnode;
+
+typedef struct {
+    int n, nnode;
+    orc_kdnode* node;
+    int* items;            /* local particle indices                          */
+    /* copies in item order, so that a leaf's candidates are read from       */
+    /* consecutive memory (kd_attach; NULL until then)                        */
+    float* toff;           /* [n][3] canonical offsets (mixed form)           */
+    int* tleaf;            /* [n] canonical leaf (mixed form)                 */
+    double* tpos;          /* [n][3] FP64 positions (FP64 form)               */
+    uint32_t* tid;         /* [n] ids                                         */
+} orc_kdtree;
+
+/* reorder items[lo..hi) so that the element of rank m (by coordinate c) sits
+ * at m, smaller ones before it and larger ones after it (quickselect) */
+static void kd_select(int* it, int lo, int hi, int m, const double* c)
 {
-    const double* p[3] = {px, py, pz};
-    double hi[3], vol = 1.0;
-    for (int a = 0; a < 3; ++a) {
-        G->lo[a] = INFINITY; hi[a] = -INFINITY;
-        for (int i = 0; i < n; ++i) { if (p[a][i] < G->lo[a]) G->lo[a] = p[a][i]; if (p[a][i] > hi[a]) hi[a] = p[a][i]; }
-        double e = hi[a] - G->lo[a];
-        vol *= (e > 0 ? e : 1e-30);
-    }
-    double cs = cbrt(vol * occ / (n > 0 ? n : 1));
-    double ext = 0.0;
-    for (int a = 0; a < 3; ++a) if (hi[a] - G->lo[a] > ext) ext = hi[a] - G->lo[a];
-    if (!(cs > 0.0)) cs = ext > 0 ? ext : 1.0;
-    if (ext / cs > 256.0) cs = ext / 256.0;
-    G->cs = cs; G->n = n;
-    long ncell = 1;
-    for (int a = 0; a < 3; ++a) { G->dim[a] = (int)floor((hi[a] - G->lo[a]) / cs) + 1; ncell *= G->dim[a]; }
-    G->start = (int*)calloc((size_t)ncell + 1, sizeof(int));
-    G->items = (int*)malloc(sizeof(int) * (n ? n : 1));
-    int* cid = (int*)malloc(sizeof(int) * (n ? n : 1));
-    for (int i = 0; i < n; ++i) {
-        int c[3];
-        for (int a = 0; a < 3; ++a) {
-            c[a] = (int)floor((p[a][i] - G->lo[a]) / cs);
-            if (c[a] < 0) c[a] = 0;
-            if (c[a] >= G->dim[a]) c[a] = G->dim[a] - 1;
+    while (hi - lo > 1) {
+        const double piv = c[it[lo + (hi - lo) / 2]];
+        int i = lo, j = hi - 1;
+        while (i <= j) {
+            while (c[it[i]] < piv) ++i;
+            while (c[it[j]] > piv) --j;
+            if (i <= j) { int t = it[i]; it[i] = it[j]; it[j] = t; ++i; --j; }
         }
-        cid[i] = (c[2] * G->dim[1] + c[1]) * G->dim[0] + c[0];
-        G->start[cid[i] + 1]++;
+        if (m <= j) hi = j + 1;
+        else if (m >= i) lo = i;
+        else return;
     }
-    for (long c = 0; c < ncell; ++c) G->start[c + 1] += G->start[c];
-    int* fill = (int*)malloc(sizeof(int) * (size_t)ncell);
-    for (long c = 0; c < ncell; ++c) fill[c] = G->start[c];
-    for (int i = 0; i < n; ++i) G->items[fill[cid[i]]++] = i;
-    free(fill); free(cid);
 }
 
-static void grid_free(orc_grid* G) { free(G->start); free(G->items); memset(G, 0, sizeof(*G)); }
-
-static void grid_cell_of(const orc_grid* G, const double x[3], int c[3])
+static int kd_build_node(orc_kdtree* T, const double* const p[3], const double* h, int start, int count)
 {
-    for (int a = 0; a < 3; ++a) {
-        c[a] = (int)floor((x[a] - G->lo[a]) / G->cs);
-        if (c[a] < 0) c[a] = 0;
-        if (c[a] >= G->dim[a]) c[a] = G->dim[a] - 1;
+    int id;
+    #pragma omp atomic capture
+    id = T->nnode++;
+    orc_kdnode* nd = &T->node[id];
+    nd->start = start; nd->count = count; nd->left = nd->right = -1;
+    nd->hmax = 0.0;
+    for (int a = 0; a < 3; ++a) { nd->lo[a] = INFINITY; nd->hi[a] = -INFINITY; }
+    for (int t = start; t < start + count; ++t) {
+        const int i = T->items[t];
+        for (int a = 0; a < 3; ++a) {
+            if (p[a][i] < nd->lo[a]) nd->lo[a] = p[a][i];
+            if (p[a][i] > nd->hi[a]) nd->hi[a] = p[a][i];
+        }
+        if (h && h[i] > nd->hmax) nd->hmax = h[i];
     }
+    if (count <= ORC_KD_LEAF) return id;
+    int ax = 0;
+    for (int a = 1; a < 3; ++a) if (nd->hi[a] - nd->lo[a] > nd->hi[ax] - nd->lo[ax]) ax = a;
+    const int half = count / 2;
+    kd_select(T->items, start, start + count, start + half, p[ax]);
+    int l, r;
+    if (count > (1 << 16)) {               /* large subtrees are built in parallel */
+        #pragma omp task shared(l)
+        l = kd_build_node(T, p, h, start, half);
+        r = kd_build_node(T, p, h, start + half, count - half);
+        #pragma omp taskwait
+    } else {
+        l = kd_build_node(T, p, h, start, half);
+        r = kd_build_node(T, p, h, start + half, count - half);
+    }
+    nd->left = l;                          /* T->node is sized up front, never moved */
+    nd->right = r;
+    return id;
+}
+
+/* h may be NULL (no per-node kernel sizes).  Node ids depend on the thread
+ * schedule; the tree's shape and every search result do not. */
+static void kd_build(orc_kdtree* T, int n, const double* px, const double* py, const double* pz, const double* h)
+{
+    const double* p[3] = {px, py, pz};
+    memset(T, 0, sizeof(*T));
+    T->n = n;
+    T->items = (int*)malloc(sizeof(int) * (n ? n : 1));
+    for (int i = 0; i < n; ++i) T->items[i] = i;
+    /* leaves hold at least ORC_KD_LEAF / 2 particles (or all n <= ORC_KD_LEAF) */
+    T->node = (orc_kdnode*)malloc(sizeof(orc_kdnode) * (size_t)(2 * (n / (ORC_KD_LEAF / 2) + 1)));
+    if (n > 0) {
+        #pragma omp parallel
+        #pragma omp single
+        kd_build_node(T, p, h, 0, n);
+    }
+}
+
+static void kd_attach(orc_kdtree* T, const orc_geom* g, int mode, const double* px, const double* py,
+                      const double* pz, const uint32_t* ids)
+{
+    const int n = T->n;
+    T->tid = (uint32_t*)malloc(sizeof(uint32_t) * (n ? n : 1));
+    if (mode == 0) {
+        T->toff = (float*)malloc(sizeof(float) * 3 * (size_t)(n ? n : 1));
+        T->tleaf = (int*)malloc(sizeof(int) * (n ? n : 1));
+    } else {
+        T->tpos = (double*)malloc(sizeof(double) * 3 * (size_t)(n ? n : 1));
+    }
+    #pragma omp parallel for schedule(static)
+    for (int t = 0; t < n; ++t) {
+        const int j = T->items[t];
+        T->tid[t] = ids[j];
+        if (mode == 0) {
+            T->tleaf[t] = (int)(g->rank[j] / ORC_LEAF);
+            for (int a = 0; a < 3; ++a) T->toff[3 * (size_t)t + a] = g->off[3 * (size_t)j + a];
+        } else {
+            T->tpos[3 * (size_t)t] = px[j]; T->tpos[3 * (size_t)t + 1] = py[j]; T->tpos[3 * (size_t)t + 2] = pz[j];
+        }
+    }
+}
+
+static void kd_free(orc_kdtree* T)
+{
+    free(T->node); free(T->items); free(T->toff); free(T->tleaf); free(T->tpos); free(T->tid);
+    memset(T, 0, sizeof(*T));
+}
+
+/* squared FP64 distance from x to the node's box (0 inside) */
+static double kd_box_d2(const orc_kdnode* nd, const double x[3])
+{
+    double s = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double g = 0.0;
+        if (x[a] < nd->lo[a]) g = nd->lo[a] - x[a];
+        else if (x[a] > nd->hi[a]) g = x[a] - nd->hi[a];
+        s += g * g;
+    }
+    return s;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -387,7 +495,7 @@ static void grid_cell_of(const orc_grid* G, const double x[3], int c[3])
 /* the halo.  mode 0: mixed (canonical FP32 d2), mode 1: FP64.               */
 /* Outputs per local particle (input order): h (as double), d2k bits, and    */
 /* optionally the k neighbour ids in ascending (d2, id) order.               */
-/* brute != 0 scans all particles (O(N^2)); otherwise the grid shells.       */
+/* brute != 0 scans all particles (O(N^2)); otherwise the k-d tree.         */
 /* ------------------------------------------------------------------------- */
 typedef struct { uint64_t d; uint32_t id; uint32_t idx; } knn_ent;
 
@@ -406,9 +514,14 @@ static void topk_insert(knn_ent* list, int* cnt, int k, knn_ent e)
 }
 
 /* The k nearest other particles of particle i, sorted by (d^2, id), into
- * list[0..k); returns how many were found (k unless the halo is too small). */
+ * list[0..k); returns how many were found (k unless the halo is too small).
+ * brute: every particle is a candidate.  Otherwise the k-d tree is walked,
+ * nearer child first, and a box is skipped once the list holds k entries and
+ * the box lies farther (exact FP64 distance) than the k-th entry's distance
+ * with a margin of 1e-5 relative plus absmargin, which covers the difference
+ * between the canonical FP32 distance and the exact one. */
 static int knn_one(int i, int n, const double* px, const double* py, const double* pz, const uint32_t* ids,
-                   int k, int mode, int brute, const orc_geom* g, const orc_grid* G, double absmargin,
+                   int k, int mode, int brute, const orc_geom* g, const orc_kdtree* T, double absmargin,
                    knn_ent* list)
 {
     int cnt = 0;
@@ -423,43 +536,37 @@ static int knn_one(int i, int n, const double* px, const double* py, const doubl
         }
         return cnt;
     }
-    double xi[3] = {px[i], py[i], pz[i]};
-    int ci[3]; grid_cell_of(G, xi, ci);
-    int maxs = G->dim[0] > G->dim[1] ? G->dim[0] : G->dim[1];
-    if (G->dim[2] > maxs) maxs = G->dim[2];
-    for (int s = 0; s <= maxs; ++s) {
-        for (int cz = ci[2] - s; cz <= ci[2] + s; ++cz) {
-            if (cz < 0 || cz >= G->dim[2]) continue;
-            for (int cy = ci[1] - s; cy <= ci[1] + s; ++cy) {
-                if (cy < 0 || cy >= G->dim[1]) continue;
-                for (int cx = ci[0] - s; cx <= ci[0] + s; ++cx) {
-                    if (cx < 0 || cx >= G->dim[0]) continue;
-                    int cheb = abs(cx - ci[0]);
-                    if (abs(cy - ci[1]) > cheb) cheb = abs(cy - ci[1]);
-                    if (abs(cz - ci[2]) > cheb) cheb = abs(cz - ci[2]);
-                    if (cheb != s) continue;
-                    long c = ((long)cz * G->dim[1] + cy) * G->dim[0] + cx;
-                    for (int t = G->start[c]; t < G->start[c + 1]; ++t) {
-                        int j = G->items[t];
-                        if (j == i) continue;
-                        knn_ent e;
-                        e.d = mode == 0 ? (uint64_t)fbits(d2_mixed(g, (uint32_t)i, (uint32_t)j))
-                                        : dbits(d2_fp64(px, py, pz, (uint32_t)i, (uint32_t)j));
-                        e.id = ids[j]; e.idx = (uint32_t)j;
-                        topk_insert(list, &cnt, k, e);
-                    }
-                }
-            }
-        }
+    const double xi[3] = {px[i], py[i], pz[i]};
+    const float* cA = mode == 0 ? g->cell + 3 * (size_t)(g->rank[i] / ORC_LEAF) : NULL;
+    const float* oi = mode == 0 ? g->off + 3 * (size_t)i : NULL;
+    int stack[128], sp = 0;
+    if (T->nnode > 0) stack[sp++] = 0;
+    while (sp > 0) {
+        const orc_kdnode* nd = &T->node[stack[--sp]];
         if (cnt == k) {
-            /* every unvisited particle lies at exact distance >= s*cs;
-             * the canonical distance differs from the exact one by far
-             * less than the 1e-5 relative margin used here.           */
             double kth;
             if (mode == 0) { float f; uint32_t u = (uint32_t)list[k - 1].d; memcpy(&f, &u, 4); kth = sqrt((double)f); }
             else { double f; uint64_t u = list[k - 1].d; memcpy(&f, &u, 8); kth = sqrt(f); }
-            if ((double)s * G->cs > kth * (1.0 + 1e-5) + absmargin) break;
+            const double lim = kth * (1.0 + 1e-5) + absmargin;
+            if (kd_box_d2(nd, xi) > lim * lim) continue;
         }
+        if (nd->left < 0) {
+            for (int t = nd->start; t < nd->start + nd->count; ++t) {
+                const int j = T->items[t];
+                if (j == i) continue;
+                knn_ent e;
+                e.d = mode == 0 ? (uint64_t)fbits(d2_mixed_core(cA, oi, g->cell + 3 * (size_t)T->tleaf[t],
+                                                                T->toff + 3 * (size_t)t))
+                                : dbits(d2_fp64_core(xi, T->tpos + 3 * (size_t)t));
+                e.id = T->tid[t]; e.idx = (uint32_t)j;
+                topk_insert(list, &cnt, k, e);
+            }
+            continue;
+        }
+        const int l = nd->left, r = nd->right;
+        const int near_l = kd_box_d2(&T->node[l], xi) <= kd_box_d2(&T->node[r], xi);
+        stack[sp++] = near_l ? r : l;          /* the nearer child is popped first */
+        stack[sp++] = near_l ? l : r;
     }
     return cnt;
 }
@@ -471,8 +578,11 @@ int orc_knn_halo(int n, const double* px, const double* py, const double* pz, co
     if (k < 1 || k > n - 1) return -1;
     orc_geom g; memset(&g, 0, sizeof(g));
     if (mode == 0) geom_build(&g, n, px, py, pz);
-    orc_grid G; memset(&G, 0, sizeof(G));
-    if (!brute) grid_build(&G, n, px, py, pz, 8.0);
+    orc_kdtree T; memset(&T, 0, sizeof(T));
+    if (!brute) {
+        kd_build(&T, n, px, py, pz, NULL);
+        kd_attach(&T, &g, mode, px, py, pz, ids);
+    }
     int err = 0;
     /* the canonical FP32 distance is within (cube edge) * 2^-22 of the exact one */
     const double absmargin = mode == 0 ? ldexp(1.0, g.E + 1 - 20) : 0.0;
@@ -482,7 +592,7 @@ int orc_knn_halo(int n, const double* px, const double* py, const double* pz, co
         #pragma omp for schedule(dynamic, 64)
         for (int i = 0; i < n; ++i) {
             if (query_mask && !query_mask[i]) continue;
-            int cnt = knn_one(i, n, px, py, pz, ids, k, mode, brute, &g, &G, absmargin, list);
+            int cnt = knn_one(i, n, px, py, pz, ids, k, mode, brute, &g, &T, absmargin, list);
             if (cnt < k) {
                 #pragma omp atomic write
                 err = -2;
@@ -501,7 +611,7 @@ int orc_knn_halo(int n, const double* px, const double* py, const double* pz, co
         }
         free(list);
     }
-    if (!brute) grid_free(&G);
+    if (!brute) kd_free(&T);
     if (mode == 0) geom_free(&g);
     return err;
 }
@@ -509,15 +619,16 @@ int orc_knn_halo(int n, const double* px, const double* py, const double* pz, co
 /* Kernel sizes of a list of particles for every N_ngb = 1..k at once: for the
  * t-th listed particle i = qidx[t], h_out[t*k + r] is the distance to its
  * (r+1)-th nearest other particle (same distance and order as orc_knn_halo),
- * from one geometry and grid build (test sampling of very large halos). */
+ * from one geometry and tree build (test sampling of very large halos). */
 int orc_knn_sample(int n, const double* px, const double* py, const double* pz, const uint32_t* ids,
                    int k, int mode, int64_t nq, const int64_t* qidx, double* h_out)
 {
     if (k < 1 || k > n - 1) return -1;
     orc_geom g; memset(&g, 0, sizeof(g));
     if (mode == 0) geom_build(&g, n, px, py, pz);
-    orc_grid G; memset(&G, 0, sizeof(G));
-    grid_build(&G, n, px, py, pz, 8.0);
+    orc_kdtree T;
+    kd_build(&T, n, px, py, pz, NULL);
+    kd_attach(&T, &g, mode, px, py, pz, ids);
     int err = 0;
     const double absmargin = mode == 0 ? ldexp(1.0, g.E + 1 - 20) : 0.0;
     #pragma omp parallel
@@ -526,7 +637,7 @@ int orc_knn_sample(int n, const double* px, const double* py, const double* pz, 
         #pragma omp for schedule(dynamic, 1)
         for (int64_t t = 0; t < nq; ++t) {
             const int i = (int)qidx[t];
-            int cnt = knn_one(i, n, px, py, pz, ids, k, mode, 0, &g, &G, absmargin, list);
+            int cnt = knn_one(i, n, px, py, pz, ids, k, mode, 0, &g, &T, absmargin, list);
             if (cnt < k) {
                 #pragma omp atomic write
                 err = -2;
@@ -544,18 +655,20 @@ int orc_knn_sample(int n, const double* px, const double* py, const double* pz, 
         }
         free(list);
     }
-    grid_free(&G);
+    kd_free(&T);
     if (mode == 0) geom_free(&g);
     return err;
 }
 
 /* ------------------------------------------------------------------------- */
 /* Pair probabilities and draws (Sect. 3.5, Eq. vel_dep).                    */
-/* Every unordered in-range pair of the halo once: found from the endpoint   */
-/* with the larger h (d < h_i + h_j <= 2 h_big), kept iff h_i > h_j or       */
-/* (h_i == h_j and i < j).  Mixed: range test d2 < RN32(RN32(h_i+h_j)^2) on  */
-/* the canonical FP32 d2 in the lower leaf's frame; FP64: d2 < (h_i+h_j)^2.  */
-/* Lambda uses the FP64 distance of the FP64 positions.                      */
+/* Every unordered in-range pair of the halo once.  Mixed: range test         */
+/* d2 < RN32(RN32(h_i+h_j)^2) on the canonical FP32 d2 in the lower leaf's   */
+/* frame; FP64: d2 < (h_i+h_j)^2.  Each pair is evaluated in one orientation, */
+/* (a, b) with h_a > h_b or (h_a == h_b and a < b); Lambda uses the FP64      */
+/* distance of the FP64 positions.  The partners of a particle are found      */
+/* with the k-d tree: a box is skipped if it lies farther (exact FP64) than   */
+/* (h_i + largest h in the box)(1 + 1e-5) plus the canonical-distance margin. */
 /* pair_mask (may be NULL): evaluate only the pairs with an endpoint i whose  */
 /* pair_mask[i] is non-zero (test sampling at full size; the arithmetic of   */
 /* every evaluated pair is unchanged).                                        */
@@ -587,8 +700,9 @@ int orc_pairs_halo(int n, const double* px, const double* py, const double* pz,
 {
     orc_geom g; memset(&g, 0, sizeof(g));
     if (mode == 0) geom_build(&g, n, px, py, pz);
-    orc_grid G; memset(&G, 0, sizeof(G));
-    grid_build(&G, n, px, py, pz, 8.0);
+    orc_kdtree T;
+    kd_build(&T, n, px, py, pz, h);
+    const double absmargin = mode == 0 ? ldexp(1.0, g.E + 1 - 20) : 0.0;
     double* sump = (double*)calloc((size_t)(n ? n : 1), sizeof(double));
     int64_t n_pairs = 0, n_gt1 = 0, n_near = 0, n_ev = 0;
     int overflow = 0;
@@ -596,25 +710,25 @@ int orc_pairs_halo(int n, const double* px, const double* py, const double* pz,
     #pragma omp parallel reduction(+:n_pairs, n_gt1, n_near)
     {
         #pragma omp for schedule(dynamic, 64)
-        for (int i = 0; i < n; ++i) {
-            double xi[3] = {px[i], py[i], pz[i]};
-            double rad = 2.0 * h[i] * (1.0 + 1e-5) + (mode == 0 ? ldexp(1.0, g.E + 1 - 20) : 0.0);
-            int lo[3], hi[3];
-            for (int a = 0; a < 3; ++a) {
-                lo[a] = (int)floor((xi[a] - rad - G.lo[a]) / G.cs);
-                hi[a] = (int)floor((xi[a] + rad - G.lo[a]) / G.cs);
-                if (lo[a] < 0) lo[a] = 0;
-                if (hi[a] >= G.dim[a]) hi[a] = G.dim[a] - 1;
-            }
-            for (int cz = lo[2]; cz <= hi[2]; ++cz)
-            for (int cy = lo[1]; cy <= hi[1]; ++cy)
-            for (int cx = lo[0]; cx <= hi[0]; ++cx) {
-                long c = ((long)cz * G.dim[1] + cy) * G.dim[0] + cx;
-                for (int t = G.start[c]; t < G.start[c + 1]; ++t) {
-                    int j = G.items[t];
-                    if (j == i) continue;
-                    if (!(h[i] > h[j] || (h[i] == h[j] && i < j))) continue;
-                    if (pair_mask && !pair_mask[i] && !pair_mask[j]) continue;
+        for (int q = 0; q < n; ++q) {
+            /* every pair is met from both ends; it is taken from the end q
+             * that is in the mask with the other end either outside it or
+             * of a larger index (no mask: the larger index) */
+            if (pair_mask && !pair_mask[q]) continue;
+            const double xq[3] = {px[q], py[q], pz[q]};
+            int stack[128], sp = 0;
+            if (T.nnode > 0) stack[sp++] = 0;
+            while (sp > 0) {
+                const orc_kdnode* nd = &T.node[stack[--sp]];
+                const double lim = (h[q] + nd->hmax) * (1.0 + 1e-5) + absmargin;
+                if (kd_box_d2(nd, xq) > lim * lim) continue;
+                if (nd->left >= 0) { stack[sp++] = nd->left; stack[sp++] = nd->right; continue; }
+                for (int t = nd->start; t < nd->start + nd->count; ++t) {
+                    const int o = T.items[t];
+                    if (o == q) continue;
+                    if ((!pair_mask || pair_mask[o]) && o < q) continue;
+                    const int i = (h[q] > h[o] || (h[q] == h[o] && q < o)) ? q : o;
+                    const int j = i == q ? o : q;
                     /* individual steps: only pairs whose particles both start a step at
                      * this sub-step, on the longer of the two steps */
                     double dtp = dt;
@@ -629,8 +743,8 @@ int orc_pairs_halo(int n, const double* px, const double* py, const double* pz,
                         float d2 = Ai <= Aj ? d2_mixed(&g, (uint32_t)i, (uint32_t)j)
                                             : d2_mixed(&g, (uint32_t)j, (uint32_t)i);
                         volatile float hs = (float)h[i] + (float)h[j];
-                        volatile float lim = hs * hs;
-                        inr = d2 < lim;
+                        volatile float lim2 = hs * hs;
+                        inr = d2 < lim2;
                     } else {
                         double hs = h[i] + h[j];
                         inr = d2_fp64(px, py, pz, (uint32_t)i, (uint32_t)j) < hs * hs;
@@ -682,7 +796,7 @@ int orc_pairs_halo(int n, const double* px, const double* py, const double* pz,
     free(sump);
     st->n_pairs = n_pairs; st->n_events = n_ev; st->n_p_gt1 = n_gt1; st->n_near = n_near;
     st->max_sum_p = mx;
-    grid_free(&G);
+    kd_free(&T);
     if (mode == 0) geom_free(&g);
     return overflow ? -3 : 0;
 }
@@ -780,26 +894,21 @@ int orc_local_diag(int n, const double* px, const double* py, const double* pz,
                    const double* vx, const double* vy, const double* vz, const double* h,
                    double m, int nngb, int kind, double s0, double w, double G, double* out)
 {
-    orc_grid Gr; memset(&Gr, 0, sizeof(Gr));
-    grid_build(&Gr, n, px, py, pz, 8.0);
+    orc_kdtree T;
+    kd_build(&T, n, px, py, pz, NULL);
     #pragma omp parallel for schedule(dynamic, 64)
     for (int i = 0; i < n; ++i) {
         double sw = 0.0, sv[3] = {0.0, 0.0, 0.0}, sv2 = 0.0;
         const double hi = h[i];
-        int lo[3], hc[3];
         const double xi[3] = {px[i], py[i], pz[i]};
-        for (int a = 0; a < 3; ++a) {
-            lo[a] = (int)floor((xi[a] - hi - Gr.lo[a]) / Gr.cs);
-            hc[a] = (int)floor((xi[a] + hi - Gr.lo[a]) / Gr.cs);
-            if (lo[a] < 0) lo[a] = 0;
-            if (hc[a] >= Gr.dim[a]) hc[a] = Gr.dim[a] - 1;
-        }
-        for (int cz = lo[2]; cz <= hc[2]; ++cz)
-        for (int cy = lo[1]; cy <= hc[1]; ++cy)
-        for (int cx = lo[0]; cx <= hc[0]; ++cx) {
-            long c = ((long)cz * Gr.dim[1] + cy) * Gr.dim[0] + cx;
-            for (int t = Gr.start[c]; t < Gr.start[c + 1]; ++t) {
-                const int j = Gr.items[t];
+        int stack[128], sp = 0;
+        if (T.nnode > 0) stack[sp++] = 0;
+        while (sp > 0) {
+            const orc_kdnode* nd = &T.node[stack[--sp]];
+            if (kd_box_d2(nd, xi) >= hi * hi) continue;      /* every point of the box is >= h_i away */
+            if (nd->left >= 0) { stack[sp++] = nd->left; stack[sp++] = nd->right; continue; }
+            for (int t = nd->start; t < nd->start + nd->count; ++t) {
+                const int j = T.items[t];
                 const double dx = px[j] - px[i], dy = py[j] - py[i], dz = pz[j] - pz[i];
                 const double d = sqrt(dx * dx + dy * dy + dz * dz);
                 if (!(d < hi)) continue;          /* j == i contributes W(0, h_i) */
@@ -821,7 +930,7 @@ int orc_local_diag(int n, const double* px, const double* py, const double* pz,
         out[3 * (size_t)n + i] = se * pow(rho, 2.0 / 3.0) * cbrt(3.0 * m * nngb / (ORC_PI * sqrt(2.0)));
         out[4 * (size_t)n + i] = sqrt(4.0 * ORC_PI * G / (rho * nu * nu)) / se;
     }
-    grid_free(&Gr);
+    kd_free(&T);
     return 0;
 }
 

@@ -17,12 +17,55 @@ from paper_2506_06269_gb300 import ics
 
 # ---------------------------------------------------------------- kNN
 @pytest.mark.parametrize("k", [1, 16, 32, 64, 128])
-def test_knn_grid_equals_brute_force(k):
+def test_knn_tree_equals_brute_force(k):
     h = ics.hernquist(3000, 1)
     for mode in (O.MODE_MIXED, O.MODE_FP64):
         hb, db, nb = O.knn(h.pos, h.ids, k, mode, brute=True, want_nbrs=True)
         hg, dg, ng = O.knn(h.pos, h.ids, k, mode, brute=False, want_nbrs=True)
         assert np.array_equal(hb, hg) and np.array_equal(db, dg) and np.array_equal(nb, ng)
+
+
+@pytest.mark.parametrize("k", [16, 64])
+def test_knn_tree_equals_brute_force_on_a_cored_halo(k):
+    # 10^3 rho_s core of radius 0.05 inside NFW: a density contrast of ~10^6
+    # between the core and the truncation radius, where a wrong box skip shows
+    h = ics.cored_nfw(4000, 12)
+    for mode in (O.MODE_MIXED, O.MODE_FP64):
+        hb, db, nb = O.knn(h.pos, h.ids, k, mode, brute=True, want_nbrs=True)
+        ht, dt_, nt = O.knn(h.pos, h.ids, k, mode, brute=False, want_nbrs=True)
+        assert np.array_equal(hb, ht) and np.array_equal(db, dt_) and np.array_equal(nb, nt)
+
+
+def test_pair_pass_finds_every_in_range_pair_of_a_cored_halo():
+    # The pair pass (k-d tree) against a brute-force list of the in-range pairs,
+    # canonical d2 < RN32(RN32(h_i + h_j)^2) over all N(N-1)/2 pairs (mixed
+    # form).  A huge cross-section makes P > 1 for every in-range pair with a
+    # nonzero overlap, so the event set is that list (less pairs whose FP64
+    # distance rounds onto the support edge, where Lambda is exactly zero).
+    h = ics.cored_nfw(3000, 13)
+    n = h.n
+    vel = h.vel.astype(np.float32).astype(np.float64)
+    hh, _, _ = O.knn(h.pos, h.ids, 32, O.MODE_MIXED)
+    ev, st, _ = O.pairs(h.pos, vel, h.ids, hh, O.MODE_MIXED, (0, 1e300, 1.0), h.mass, 1.0, 1, 0, 0,
+                        ev_cap=n * n // 2)
+    got = {(int(e["key"]) >> 27 & ((1 << 27) - 1), int(e["key"]) & ((1 << 27) - 1)) for e in ev}
+    order, _, _, _, _ = O.geometry(h.pos)
+    rank = np.empty(n, np.int64); rank[order] = np.arange(n)
+    ii, jj = np.triu_indices(n, 1)
+    lower_first = rank[ii] // 32 <= rank[jj] // 32          # each pair in its lower leaf's frame
+    qi, qj = np.where(lower_first, ii, jj), np.where(lower_first, jj, ii)
+    d2 = O.d2_mixed(h.pos, qi, qj)
+    hs = hh.astype(np.float32)[ii] + hh.astype(np.float32)[jj]
+    inr = d2 < hs * hs
+    ids = h.ids.astype(np.int64)
+    want = {(min(a, b), max(a, b)): (a_, b_)
+            for a, b, a_, b_ in zip(ids[ii[inr]], ids[jj[inr]], ii[inr], jj[inr])}
+    assert st["n_pairs"] == len(want) > 30000
+    assert got <= set(want)
+    for key in set(want) - got:
+        a_, b_ = want[key]
+        d = np.linalg.norm(h.pos[:, a_] - h.pos[:, b_])
+        assert d >= (hh[a_] + hh[b_]) * (1 - 1e-6), key
 
 
 def test_knn_sample_equals_knn_for_every_k():
