@@ -125,26 +125,24 @@ def tainted_particles(o_ev, g_ev, only_keys, n):
     return mask
 
 
-def velocity_scale(o_ev, vel_in, n):
-    """Per-particle velocity scale: max over its event component of |v_i|+|v_j| (step start)."""
-    sp = np.linalg.norm(vel_in, axis=0)
-    parent = np.arange(n)
+def velocity_scale(o_ev, vel_in, masses):
+    """Per-particle speed scale of the scatter arithmetic: for a particle in one
+    event, its own speed plus its partner's at the step start; for a particle in
+    several, the largest such pair speed, each taken from the velocities the
+    oracle's sequential application (ascending key order) has just before that
+    event.  A particle without events keeps its own speed.
 
-    def find(x):
-        while parent[x] != x:
-            parent[x] = parent[parent[x]]
-            x = parent[x]
-        return x
-
-    for e in o_ev:
-        a, b = find(int(e["i"])), find(int(e["j"]))
-        if a != b:
-            parent[a] = b
-    comp = {}
-    for e in o_ev:
-        r = find(int(e["i"]))
-        comp[r] = max(comp.get(r, 0.0), sp[int(e["i"])] + sp[int(e["j"])])
-    scale = sp.copy()
-    for i in set(int(x) for x in np.concatenate([o_ev["i"], o_ev["j"]])) if len(o_ev) else []:
-        scale[i] = comp[find(i)]
+    o_ev: the oracle's events (key order, global indices); vel_in [3, n] the
+    step-start velocities; masses [n] per-particle masses."""
+    cur = np.array(vel_in, dtype=np.float64, copy=True)
+    scale = np.linalg.norm(cur, axis=0)
+    for e in np.sort(np.asarray(o_ev), order="key") if len(o_ev) else []:
+        i, j = int(e["i"]), int(e["j"])
+        s = np.linalg.norm(cur[:, i]) + np.linalg.norm(cur[:, j])
+        scale[i] = max(scale[i], s)
+        scale[j] = max(scale[j], s)
+        loc = np.array([e]).copy()
+        loc["i"], loc["j"] = 0, 1
+        v2, _ = O.apply_events(loc, np.array([masses[i], masses[j]]), cur[:, [i, j]])
+        cur[:, [i, j]] = v2
     return scale

@@ -1,11 +1,13 @@
 """GPU parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
-Tolerances (stated in the spec contract of this build and derived in
-the design doc): kernel sizes and neighbour lists bit-exact (same canonical FP32 /
-FP64 distance); event sets equal except pairs with |P - u| < 1e-6; velocities
-within 1e-5 of the pair's speed scale (mixed form) or 1e-12 (FP64 form);
-untouched particles bit-identical; energy/momentum sums within 1e-14 of the
-exact sums.
+Tolerances: kernel sizes and neighbour lists bit-exact (both sides rank the
+same canonical FP32 / FP64 distance); event sets equal except pairs with
+|P - u| < 1e-6 (the GPU forms P in FP32 to about 1e-7 relative, the oracle in
+FP64, so only draws that close to P can decide differently); velocities
+within 1e-5 relative of the pair speed of each scatter (mixed form: a scatter
+is about ten FP32 operations on values of that size, so its rounding stays
+near 1e-6 of it) or 1e-12 (FP64 form); particles without events
+bit-identical; energy/momentum sums within 1e-14 of the exact sums.
 """
 import numpy as np
 import pytest
@@ -29,10 +31,10 @@ def _built():
     build.build()
 
 
-def _check_velocities(g, o, tol, n):
+def _check_velocities(g, o, tol, n, masses):
     only_o, only_g = compare_events(g["events"], o["events"])
     bad = tainted_particles(o["events"], g["events"], only_o + only_g, n)
-    scale = velocity_scale(o["events"], g["vel_in"], n)
+    scale = velocity_scale(o["events"], g["vel_in"], masses)
     err = np.abs(g["vel"] - o["vel_out"]).max(axis=0)
     touched = np.zeros(n, bool)
     if len(o["events"]):
@@ -105,7 +107,7 @@ def test_step_parity_hernquist_config():
     assert g["status"] == 0
     assert g["stats"].n_pairs == o["stats"][0]["n_pairs"]
     assert np.array_equal(g["h"], o["h"])
-    only_o, only_g, _ = _check_velocities(g, o, 1e-5, b.n)
+    only_o, only_g, _ = _check_velocities(g, o, 1e-5, b.n, np.repeat(b.mass, np.diff(b.offsets)))
     assert len(only_o) + len(only_g) <= max(2, o["stats"][0]["n_near"])
     assert g["n_events"] == len(g["events"]) and abs(g["n_events"] - len(o["events"])) <= len(only_o) + len(only_g)
 
@@ -119,7 +121,7 @@ def test_step_parity_dense_events_multi_hit():
     o = oracle_step(b, *args)
     assert g["status"] == 0
     assert g["stats"].n_multi > 10 and g["stats"].rounds >= 2
-    _check_velocities(g, o, 1e-5, b.n)
+    _check_velocities(g, o, 1e-5, b.n, np.repeat(b.mass, np.diff(b.offsets)))
     # pair energy and momentum conserved by every event: totals within FP32 rounding
     m = np.repeat(b.mass, np.diff(b.offsets))
     e0 = 0.5 * (m * (g["vel_in"] ** 2).sum(0)).sum(); e1 = 0.5 * (m * (g["vel"] ** 2).sum(0)).sum()
@@ -136,7 +138,7 @@ def test_fp64_form_parity():
     assert g["status"] == 0
     assert np.array_equal(g["h"], o["h"])
     assert g["stats"].n_pairs == o["stats"][0]["n_pairs"]
-    _check_velocities(g, o, 1e-12, b.n)
+    _check_velocities(g, o, 1e-12, b.n, np.repeat(b.mass, np.diff(b.offsets)))
 
 
 def test_zero_cross_section_is_identity():
@@ -374,4 +376,4 @@ def test_batched_64_halos_four_smallest_match_oracle():
         ge = g["events"][(g["events"]["i"] >= a) & (g["events"]["i"] < e)].copy()
         ge["i"] -= a; ge["j"] -= a
         sub_g = {"events": ge, "vel_in": g["vel_in"][:, a:e], "vel": g["vel"][:, a:e]}
-        _check_velocities(sub_g, o, 1e-5, e - a)
+        _check_velocities(sub_g, o, 1e-5, e - a, np.full(e - a, hh.mass))
