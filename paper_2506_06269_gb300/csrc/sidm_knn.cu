@@ -311,7 +311,7 @@ __global__ void k_knn(KnnParams p)
             const int Bg = leaf0 + Bl;
             const int countB = (int)min((int64_t)kLeaf, nh - (int64_t)Bl * kLeaf);
             V c;
-            if constexpr (TMA) c = stage.load((const V*)p.P4 + (int64_t)Bg * kLeaf, lane, p.cnt)[lane];
+            if constexpr (TMA) c = stage.load_lane((const V*)p.P4 + (int64_t)Bg * kLeaf, lane, p.cnt);
             else c = craw;
             // shift the candidates into the query leaf's frame (exact shift)
             if constexpr (sizeof(R) == 4) {

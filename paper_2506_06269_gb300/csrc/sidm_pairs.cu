@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
             ++n_tiles;
             const int countB = (int)min((int64_t)kLeaf, nh - (int64_t)Bl * kLeaf);
             V c;
-            if constexpr (TMA) c = st_pos.load(P4 + (int64_t)Bg * kLeaf, lane, p.cnt)[lane];
+            if constexpr (TMA) c = st_pos.load_lane(P4 + (int64_t)Bg * kLeaf, lane, p.cnt);
             else c = craw;
             if constexpr (sizeof(R) == 4) {
                 const float4 cB = p.cell[Bg];
