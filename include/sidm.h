@@ -412,9 +412,11 @@ int sidm_warm_start(sidm_ctx* ctx, int32_t enable);
  * quantity per chunk, 256 KiB in all) is a fixed file-scope device array,
  * which every GPU that loads libsidm holds until the process exits.
  *
- * The first call on a device, with that device current, looks up the device
- * address of the scratch array (cudaGetSymbolAddress) and caches it; make that
- * first call before any stream capture.  Every call shares the same scratch
+ * Every call outside stream capture looks up the device address of the
+ * scratch array on the current device (cudaGetSymbolAddress, which allocates
+ * nothing) and remembers it for that device; a call made while its stream is
+ * being captured uses the remembered address, so the first call on a device
+ * must come before any stream capture.  Every call shares the same scratch
  * and overwrites what it uses (nothing has to start at zero), so calls that
  * overlap on the GPU -- on different streams, or from different threads --
  * race and must be serialised by the caller.
@@ -430,12 +432,17 @@ int sidm_warm_start(sidm_ctx* ctx, int32_t enable);
  *   vel_dev   : device [3][N] velocities, N = halo_off[n_halos]
  *   out_dev   : device f64[n_halos][4] = (E, px, py, pz)
  *   comp_dev  : device f64[n_halos][4] residual compensation terms, or NULL
- * Returns SIDM_OK, SIDM_EINVAL (bad argument), SIDM_ECAPACITY (too many
- * chunks) or SIDM_ECUDA (device lookup or launch failed).  Asynchronous on
- * the stream. */
+ * Returns SIDM_OK, SIDM_EINVAL (bad argument, or a first call on a device
+ * made during stream capture), SIDM_ECAPACITY (too many chunks) or
+ * SIDM_ECUDA (device lookup or launch failed); sidm_static_last_error() gives
+ * the reason.  Asynchronous on the stream. */
 int sidm_energy_momentum_static(int32_t n_halos, const int64_t* halo_off, int32_t precision,
                                 const double* mass_dev, const void* vel_dev, double* out_dev,
                                 double* comp_dev, cudaStream_t stream);
+
+/* Message of the last failed sidm_energy_momentum_static call of the calling
+ * thread ("" after a successful call; never NULL). */
+const char* sidm_static_last_error(void);
 
 #ifdef __cplusplus
 }

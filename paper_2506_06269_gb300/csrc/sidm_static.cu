@@ -59,10 +59,11 @@ __global__ void k_static_final(StaticLayout lay, const double* __restrict__ mass
 
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
-double* g_static_ptr[kMaxDevices] = {};
+double* g_static_ptr[kMaxDevices] = {};   // address of the last lookup per device
+thread_local std::string g_static_err;
 int static_fail(int code, const std::string& m)
 {
-    (void)m;   // the return code carries the failure; the texts document each case
+    g_static_err = m;
     return code;
 }
 
@@ -92,21 +93,31 @@ extern "C" int sidm_energy_momentum_static(int32_t n_halos, const int64_t* halo_
     lay.n_chunks = (int)chunks;
     if (!mass_dev || !out_dev || (halo_off[n_halos] > 0 && !vel_dev)) return static_fail(SIDM_EINVAL, "null argument");
 
-    // Device address of the scratch array, looked up once per device with
-    // that device current (host code only sees a stand-in for the symbol).
+    // Device address of the scratch array, with this device current (host code
+    // only sees a stand-in for the symbol).  Outside stream capture it is looked
+    // up on every call, so a context torn down and re-created (cudaDeviceReset)
+    // never leaves a stale address behind; during capture the address of the
+    // last uncaptured call on this device is used.
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return static_fail(SIDM_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return static_fail(SIDM_EINVAL, "device ordinal out of range");
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(stream, &cap);
+    if (e != cudaSuccess) return static_fail(SIDM_ECUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
     double* part = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_static_mu);
-        if (!g_static_ptr[dev]) {
-            e = cudaGetSymbolAddress((void**)&g_static_ptr[dev], g_static_partials);
+        if (cap == cudaStreamCaptureStatusNone) {
+            double* p = nullptr;
+            e = cudaGetSymbolAddress((void**)&p, g_static_partials);
             if (e != cudaSuccess) {
                 g_static_ptr[dev] = nullptr;
                 return static_fail(SIDM_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
             }
+            g_static_ptr[dev] = p;
+        } else if (!g_static_ptr[dev]) {
+            return static_fail(SIDM_EINVAL, "the first call on a device must come before any stream capture");
         }
         part = g_static_ptr[dev];
     }
@@ -124,5 +135,8 @@ extern "C" int sidm_energy_momentum_static(int32_t n_halos, const int64_t* halo_
     k_static_final<<<(n_halos + 3) / 4, 128, 0, stream>>>(lay, mass_dev, part, out_dev, comp_dev);
     e = cudaGetLastError();
     if (e != cudaSuccess) return static_fail(SIDM_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
+    g_static_err.clear();
     return SIDM_OK;
 }
+
+extern "C" const char* sidm_static_last_error(void) { return g_static_err.c_str(); }

@@ -25,6 +25,7 @@ SIDM_MIXED, SIDM_FP64 = 0, 1
 SIDM_FLAG_SUM_P = 1
 SIDM_FLAG_LOCAL_DIAG = 4
 SIDM_FLAG_TIMING = 2
+SIDM_STATIC_MAX_HALOS, SIDM_STATIC_MAX_CHUNKS = 64, 4096
 
 XS_DTYPE = np.dtype([("kind", "<i4"), ("pad", "<i4"), ("s0", "<f8"), ("w", "<f8")])
 STATS_DTYPE = np.dtype([("n_pairs", "<u8"), ("n_events", "<u8"), ("n_p_gt1", "<u8"), ("n_near", "<u8"),
@@ -107,6 +108,7 @@ def load_library():
     L.sidm_host_potential.argtypes = [vp, C.POINTER(SidmHost), vp, vp, vp]
     L.sidm_reflect_boundary.argtypes = [vp, vp, vp, vp, vp]
     L.sidm_energy_momentum_static.argtypes = [i32, vp, i32, vp, vp, vp, vp, vp]
+    L.sidm_static_last_error.restype = C.c_char_p
     for f in ("sidm_create", "sidm_destroy", "sidm_build_cells", "sidm_kernel_sizes", "sidm_scatter_step",
               "sidm_energy_momentum", "sidm_status", "sidm_get_perm", "sidm_neighbours", "sidm_get_events",
               "sidm_lambda_eval", "sidm_drift", "sidm_get_sum_p", "sidm_kernel_times", "sidm_diagnostics",
@@ -122,7 +124,7 @@ EXPORTED = ["sidm_create", "sidm_destroy", "sidm_last_error", "sidm_create_error
             "sidm_neighbours", "sidm_get_events", "sidm_lambda_eval", "sidm_drift", "sidm_get_sum_p",
             "sidm_launch_count", "sidm_kernel_times", "sidm_diagnostics", "sidm_energy_momentum_static",
             "sidm_warm_start", "sidm_local_diagnostics", "sidm_timestep_criterion", "sidm_scatter_step_binned",
-            "sidm_host_kick", "sidm_host_potential", "sidm_reflect_boundary"]
+            "sidm_host_kick", "sidm_host_potential", "sidm_reflect_boundary", "sidm_static_last_error"]
 
 
 def _torch():
@@ -254,8 +256,7 @@ def sidm_energy_momentum_static(halo_off, precision, mass, vel, out, comp=None, 
     rc = load_library().sidm_energy_momentum_static(len(off) - 1, off.ctypes.data_as(C.c_void_p), prec, _ptr(mass),
                                                     _ptr(vel), _ptr(out), _ptr(comp), _stream(stream))
     if rc != SIDM_OK:
-        raise SidmError(rc, {SIDM_EINVAL: "bad argument", SIDM_ECAPACITY: "more chunks than the static scratch holds",
-                             SIDM_ECUDA: "CUDA call failed"}.get(rc, "error"))
+        raise SidmError(rc, load_library().sidm_static_last_error().decode())
 
 
 def sidm_local_diagnostics(ctx, xs, mass, vel, G, out, stream=None):
