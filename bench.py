@@ -46,11 +46,19 @@ WORKLOAD = "nfw_rcut10_N1048576_ngb64_veldep_s0_100_w_vmax"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # issue slots of the FP32/INT32 pipes: SMs x lanes per SM (GB300, 152 SMs x 128)
 N_SM, LANES_PER_SM = 152, 128
-# algorithmic lane operations per unit of the two ALU-bound kernels (derived in the design doc)
+# algorithmic lane operations per unit of the two ALU-bound kernels: the operation
+# counts of the formulas as written, not counts of issued instructions
 OPS_PER_TEST = 10          # canonical d^2 (3 sub, 1 mul, 2 fma), sum, square, compare, ballot
 OPS_PER_PAIR = 121         # |v_ij| + sigma(v) + Philox4x32-10 + upper bound of P + draw decision + bookkeeping
 OPS_PER_LAMBDA = 50        # sqrt(d^2) + Lambda table (bicubic, 16 loads) + P + exact decision, when looked up
 OPS_PER_KNN_CAND = 8       # canonical d^2 (6) + key compare (2)
+# the kernel-size search as the scope table counts it: about 6 N_ngb candidate
+# distances of about 9 FP32 operations per particle
+KNN_SURVEY_CANDS_PER_NGB, KNN_SURVEY_OPS_PER_CAND = 6, 9
+
+# the paper's top resolution: cored-isothermal inner profile joined to NFW
+CFG3_N, CFG3_SEED, CFG3_SWEEP = 50_000_000, 2, (16, 32, 64, 128)
+CFG3_WORKLOAD = "cored_nfw_N50000000_core0.05rs_rho1e3rhos_ngb16-128_veldep_s0_100_w_vmax"
 
 
 def parse():
@@ -421,6 +429,106 @@ def cpu_baseline(dt, vmax, threads=None):
                       f"{sec:.2f} s", "seconds": sec, "pairs": int(r["stats"][0]["n_pairs"])}
 
 
+def run_config3(local, steps=3, n=CFG3_N, oracle_sample=True):
+    """The paper's top resolution: N = 5e7 particles of a cored-isothermal halo
+    (King-like core of 0.05 r_s at 1e3 rho_s joined to NFW, truncated at
+    10 r_s; seed 2), sigma(v)/m of the main workload, dt by the same rule at
+    N_ngb = 64.  For each N_ngb of {16, 32, 64, 128}: the initial state, one
+    warm-up step (a new N_ngb starts the kernel-size search cold), then `steps`
+    timed steps (drift + cell build + kernel sizes + scatter + exact E,p) with
+    CUDA events and the per-kernel split.  The all-FP64 form runs the same
+    steps at N_ngb = 64 on identical inputs.  The oracle baseline is one full
+    oracle step of an N/64-particle realisation of the same profile."""
+    import torch
+    from paper_2506_06269_gb300 import ics, sidm
+    halo = ics.cored_nfw(n, CFG3_SEED)
+    vmax = ics.nfw_vmax()
+    dt, q999 = dt_rule(sidm.Context, halo, vmax, local)
+    torch.cuda.empty_cache()
+    dev = torch.device("cuda", local)
+    pos_h = torch.tensor(halo.pos).pin_memory()
+    ids_h = torch.tensor(halo.ids.astype(np.int64)).to(torch.int32).pin_memory()
+    out = {"workload": CFG3_WORKLOAD, "n_particles": n, "dt": dt,
+           "dt_rule": "0.04 / q99.9(sum_j P_ij/dt) on the initial state at N_ngb = 64",
+           "cross_section": f"sigma/m = {S0}/(1+(v/{vmax:.4f})^2)^2", "steps_timed": steps,
+           "l2": "inputs far larger than L2 (2.4 GB of particle state)"}
+
+    def run_form(precision, ks):
+        vdt = torch.float32 if precision == "mixed" else torch.float64
+        vel_h = torch.tensor(halo.vel.astype(np.float32).astype(np.float64 if precision == "fp64" else np.float32))
+        vel_h = vel_h.pin_memory()
+        ctx = sidm.Context(n_max=n, halo_max=1, ngb_max=max(ks), event_cap=1 << 22, precision=precision,
+                           device=local, flags=sidm.SIDM_FLAG_TIMING)
+        pos = torch.empty((3, n), dtype=torch.float64, device=dev)
+        vel = torch.empty((3, n), dtype=vdt, device=dev)
+        ids = torch.empty(n, dtype=torch.int32, device=dev)
+        h = torch.zeros(n, dtype=vdt, device=dev)
+        xs = ctx.xs_tensor([(1, S0, vmax)]); dt_t = ctx.f64([dt]); mass_t = ctx.f64([halo.mass])
+        stats = torch.zeros((steps + 1, sidm.STATS_DTYPE.itemsize), dtype=torch.uint8, device=dev)
+        energy = torch.zeros((steps + 2, 4), dtype=torch.float64, device=dev)
+        rows = []
+        for k in ks:
+            pos.copy_(pos_h); vel.copy_(vel_h); ids.copy_(ids_h)
+
+            def step(i, slot):
+                ctx.drift(dt_t, pos, vel)
+                ctx.build_cells([0, n], pos, vel, ids)
+                ctx.kernel_sizes([k], h)
+                ctx.scatter_step(20250617, i, xs, dt_t, mass_t, vel, stats[slot])
+                ctx.energy_momentum(mass_t, vel, energy[slot + 1])
+
+            ctx.build_cells([0, n], pos, vel, ids)
+            step(0, 0)                                   # warm-up (cold kernel-size search)
+            torch.cuda.synchronize()
+            ctx.energy_momentum(mass_t, vel, energy[0])
+            ctx.kernel_times(reset=True)
+            s = torch.cuda.current_stream()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * steps)]
+            for i in range(steps):
+                ev[2 * i].record(s)
+                step(1 + i, i)
+                ev[2 * i + 1].record(s)
+            torch.cuda.synchronize()
+            ms = [ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(steps)]
+            kms, _ = ctx.kernel_times(reset=True)
+            st = [sidm.parse_stats(stats[i]) for i in range(steps)]
+            E = energy.cpu().numpy()
+            tot = float(sum(ms))
+            rows.append({"n_ngb": k, "value": n * steps / (tot * 1e-3), "unit": UNIT, "ms_per_step": tot / steps,
+                         "kernel_ms_per_step": {"build": kms[0] / steps, "knn": kms[1] / steps,
+                                                "pairs": kms[2] / steps, "resolve": kms[3] / steps,
+                                                "other": tot / steps - sum(kms) / steps},
+                         "pair_evals_per_s": sum(x.n_pairs for x in st) / (tot * 1e-3),
+                         "events_per_step": sum(x.n_events for x in st) / steps,
+                         "energy_drift": float(np.max(np.abs(E[1:steps + 1, 0] - E[0, 0])) / abs(E[0, 0])),
+                         "device_status": ctx.status()})
+        ctx.close()
+        del pos, vel, ids, h
+        torch.cuda.empty_cache()
+        return rows
+
+    out["sweep"] = run_form("mixed", CFG3_SWEEP)
+    out["fp64_form"] = run_form("fp64", (64,))[0]
+    mixed64 = [r for r in out["sweep"] if r["n_ngb"] == 64][0]
+    out["mixed_over_fp64_ngb64"] = mixed64["value"] / out["fp64_form"]["value"]
+    if oracle_sample:
+        from oracle import oracle as O
+        ns = n // 64
+        th = os.cpu_count() or 1
+        O.set_num_threads(th)
+        small = ics.cored_nfw(ns, CFG3_SEED)
+        vel = small.vel.astype(np.float32).astype(np.float64)
+        t0 = time.perf_counter()
+        O.step(small.pos, vel, small.ids, [0, ns], [64], [small.mass], [(1, S0, vmax)], [dt], 1, 0, O.MODE_MIXED)
+        sec = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": ns / sec, "unit": UNIT, "cores": int(O.num_threads()), "kind": "oracle",
+                               "sample": f"one full oracle step (kNN, pair probabilities with exact Lambda "
+                                         f"quadrature, draws, sequential scatter) of an N/64 = {ns}-particle "
+                                         f"realisation of the same cored profile, N_ngb = 64, same sigma(v) and dt; "
+                                         f"{sec:.1f} s", "seconds": sec}
+    return out
+
+
 def run_satellite(local, big_steps=8, n=1 << 22, n_bins=4, dt_max=0.02):
     """NFW subhalo of 2^22 particles at the paper's initial position and velocity
     (123.6 kpc, 109 km/s) in its six-part Milky-Way-like host (NFW halo,
@@ -661,15 +769,16 @@ def run_batched(local, graph_steps=50, seq_steps=2):
             "gpu_launches": int(round(per_step_launches * graph_steps))}
 
 
-def roofline(res, peaks, peak_src):
-    """Roofline of the dominant hot kernel (by measured event time)."""
+def roofline(res, peaks, peak_src, name=None):
+    """Roofline of one hot kernel, by default the dominant one (by measured
+    event time)."""
     kms, kcnt = res["kms"], res["kcnt"]
     K = max(1, len(res["times"]))
     clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = N_SM * LANES_PER_SM * clock_mhz * 1e6 / 1e12          # T lane-ops/s
     traffic = load_traffic()
     names = {0: "build", 1: "knn", 2: "pairs", 3: "resolve"}
-    dom = max(range(4), key=lambda i: kms[i])
+    dom = max(range(4), key=lambda i: kms[i]) if name is None else [i for i in names if names[i] == name][0]
     name = names[dom]
     launches = max(1, int(kcnt[dom]))
     per_launch_ms = kms[dom] / launches
@@ -689,10 +798,16 @@ def roofline(res, peaks, peak_src):
         cand = res.get("knn_candidates_per_step")
         tr = traffic.get("knn")
         achieved = (cand * OPS_PER_KNN_CAND) / (per_launch_ms * 1e-3) / 1e12 if cand else None
+        survey_ops = n * KNN_SURVEY_CANDS_PER_NGB * N_NGB * KNN_SURVEY_OPS_PER_CAND
+        survey = survey_ops / (per_launch_ms * 1e-3) / 1e12
         return {"kernel": "k_knn", "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
                 "frac": (achieved / alu_peak) if achieved else None,
                 "traffic": (tr["bytes_per_launch"] * n / tr["units_per_launch"]) if tr else None,
                 "peak_source": f"derived: {N_SM} SMs x {LANES_PER_SM} lanes x {clock_mhz:.0f} MHz ({peak_src})",
+                "ops_per_unit": {"candidate_distance": OPS_PER_KNN_CAND},
+                "candidates_per_particle": (cand / n) if cand else None,
+                "survey_count": {"ops_per_particle": KNN_SURVEY_CANDS_PER_NGB * N_NGB * KNN_SURVEY_OPS_PER_CAND,
+                                 "achieved": survey, "frac": survey / alu_peak},
                 "ms_per_launch": per_launch_ms}
     # the cell build is a streaming (HBM) sequence
     hbm = float(peaks.get("hbm_gbs", 6800.0))
@@ -746,6 +861,7 @@ def main_ours(args):
             "energy_bookkeeping_dE": res["book"],
             "kernel_ms_per_step": {"build": kms[0] / K, "knn": kms[1] / K, "pairs": kms[2] / K, "resolve": kms[3] / K},
             "roofline": roofline(res, peaks, peak_src),
+            "roofline_knn": roofline(res, peaks, peak_src, "knn"),
             "e2e": e2e,
             "clocks": res["clocks"],
             "gpu_launches": int(res["gpu_launches"]),
@@ -769,6 +885,7 @@ def main_ours(args):
             line["batched"] = run_batched(res["local"])
             line["satellite"] = run_satellite(res["local"])
             line["streaming_kernels"] = run_streaming(res["local"])
+            line["config3"] = run_config3(res["local"], oracle_sample=not args.no_cpu_baseline)
             if fp64:
                 line["batched_over_fp64_single_halo"] = line["batched"]["value"] / fp64["value"]
         if not args.no_cpu_baseline and ws == 1:
