@@ -78,7 +78,8 @@ def lib():
             L.orc_local_diag.restype = i32
             L.orc_timestep.argtypes = [i32, vp, d, d, d, d, i32, vp, vp]
             L.orc_pairs_halo.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, i32, i32, d, d, d, d,
-                                         u64, u64, u32, vp, i64, P(_PairStats), vp, vp, vp, i32, i32, d]
+                                         u64, u64, u32, vp, i64, P(_PairStats), vp, vp, vp, i32, i32, d, i32]
+            L.orc_apply_drag.argtypes = [vp, i64, vp, i32, d, d, vp, vp, vp, vp, vp]
             L.orc_host_mass.argtypes = [d, d, d]; L.orc_host_mass.restype = d
             L.orc_host_phi.argtypes = [vp, d, d, d]; L.orc_host_phi.restype = d
             L.orc_host_accel.argtypes = [vp, d, d, d, vp]
@@ -297,6 +298,12 @@ def pairs(pos, vel, ids, h, mode, xs, mass, dt, seed, step, halo, ev_cap=None, m
           n_bins=1, substep=0, dt_max=0.0):
     """Pair probabilities and draws of one halo.
 
+    xs = (kind, s0, w) or (kind, s0, w, angular): angular 1 is the
+    forward-dominated (frictional) limit (Sect. 3.8), where every in-range
+    pair is returned as a record whose "P" field holds G = m_j Lambda_ij dt
+    (u = -1, no draw), to be applied by apply_drag; n_p_gt1 then counts pairs
+    whose step-start D = P/3 exceeds 1, and n_near is 0.
+
     bins (int [n], optional): individual power-of-two steps; only pairs whose
     particles both open a step at `substep` are evaluated, on the longer step
     dt_max / 2^min(b_i, b_j) (dt is then unused); sum_p then holds the sums of
@@ -314,12 +321,13 @@ def pairs(pos, vel, ids, h, mode, xs, mass, dt, seed, step, halo, ev_cap=None, m
     st = _PairStats(); sump = np.zeros(n)
     pm = None if mask is None else _c(mask, np.uint8)
     bn = None if bins is None else _c(bins, np.int32)
-    kind, s0, w = xs
+    kind, s0, w = xs[:3]
+    angular = int(xs[3]) if len(xs) > 3 else 0
     rc = lib().orc_pairs_halo(n, _p(p[0]), _p(p[1]), _p(p[2]), _p(v[0]), _p(v[1]), _p(v[2]),
                               _p(idv), _p(hh), int(mode), int(kind), float(s0), float(w),
                               float(mass), float(dt), C.c_uint64(int(seed)), C.c_uint64(int(step)),
                               C.c_uint32(int(halo)), _p(ev), cap, C.byref(st), _p(sump),
-                              _p(pm), _p(bn), int(n_bins), int(substep), float(dt_max))
+                              _p(pm), _p(bn), int(n_bins), int(substep), float(dt_max), angular)
     if rc != 0:
         raise RuntimeError(f"oracle pair pass failed ({rc}): event buffer too small")
     ne = int(st.n_events)
@@ -343,6 +351,23 @@ def apply_events(events: np.ndarray, masses: np.ndarray, vel: np.ndarray):
     return v, dE[:ev.size]
 
 
+def apply_drag(records: np.ndarray, masses: np.ndarray, xs, vel: np.ndarray):
+    """Forward-dominated (frictional) scattering of key-sorted pair records,
+    one after another from the current FP64 velocities (Sect. 3.8, App. A).
+
+    records: pairs(..., xs with angular 1) output ("P" = G = m_j Lambda dt);
+    xs = (kind, s0, w[, angular]) gives sigma_V / m.  Returns (new vel [3,n],
+    per-record pair kinetic-energy change, per-record D).
+    """
+    ev = np.ascontiguousarray(records, dtype=EVENT_DTYPE)
+    v = np.array(vel, dtype=np.float64, copy=True, order="C")
+    m = _c(masses, np.float64)
+    dE = np.zeros(max(ev.size, 1)); D = np.zeros(max(ev.size, 1))
+    lib().orc_apply_drag(_p(ev), ev.size, _p(m), int(xs[0]), float(xs[1]), float(xs[2]),
+                         _p(v[0]), _p(v[1]), _p(v[2]), _p(dE), _p(D))
+    return v, dE[:ev.size], D[:ev.size]
+
+
 def step(pos, vel, ids, offsets, k_per_halo, masses, xs_per_halo, dt_per_halo, seed, step_no,
          mode: int = MODE_MIXED):
     """One full SIDM scattering pass of a batch of halos (oracle form).
@@ -363,12 +388,28 @@ def step(pos, vel, ids, offsets, k_per_halo, masses, xs_per_halo, dt_per_halo, s
             continue
         hh, _, _ = knn(pos[:, a:b], ids[a:b], int(k_per_halo[hidx]), mode)
         h_all[a:b] = hh
-        ev, st, _ = pairs(pos[:, a:b], vel[:, a:b], ids[a:b], hh, mode, xs_per_halo[hidx],
-                          float(masses[hidx]), float(dt_per_halo[hidx]), seed, step_no, hidx)
+        xs = xs_per_halo[hidx]
+        # forward-dominated halos return every in-range pair (about 2 N_ngb per particle)
+        cap = (b - a) * 8 * int(k_per_halo[hidx]) if len(xs) > 3 and int(xs[3]) == 1 else None
+        ev, st, _ = pairs(pos[:, a:b], vel[:, a:b], ids[a:b], hh, mode, xs,
+                          float(masses[hidx]), float(dt_per_halo[hidx]), seed, step_no, hidx, ev_cap=cap)
         ev["i"] += a; ev["j"] += a
         evs.append(ev); stats.append(st)
     events = np.concatenate(evs) if evs else np.zeros(0, EVENT_DTYPE)
     events = np.sort(events, order="key")
     pm = np.repeat(np.asarray(masses, np.float64), np.diff(offsets))
-    vout, dE = apply_events(events, pm, vel)
+    # halos hold disjoint particles: isotropic events and forward-dominated pair
+    # records are applied halo by halo, each in key order
+    vout = np.array(vel, dtype=np.float64, copy=True)
+    dE = np.zeros(events.size)
+    hof = (events["key"] >> np.uint64(54)).astype(np.int64)
+    for hidx in range(H):
+        sel = np.flatnonzero(hof == hidx)
+        if sel.size == 0:
+            continue
+        xs = xs_per_halo[hidx]
+        if len(xs) > 3 and int(xs[3]) == 1:
+            vout, dE[sel], _ = apply_drag(events[sel], pm, xs, vout)
+        else:
+            vout, dE[sel] = apply_events(events[sel], pm, vout)
     return {"h": h_all, "events": events, "vel_out": vout, "dE": dE, "stats": stats}

@@ -38,6 +38,22 @@
  *   multi-hit: events are accepted from step-start velocities and applied
  *              one after another in ascending (halo, min id, max id) order,
  *              each with the *current* velocities.
+ *   forward-dominated (frictional) scattering, Sect. 3.8 with App. A: the
+ *              limit theta -> 0 at fixed momentum transfer.  Every in-range
+ *              pair interacts every step (no draw): its relative velocity
+ *              u = v_i - v_j (i the smaller id) turns by the angle alpha with
+ *              cos(alpha) = 1 - D, sin(alpha) = sqrt(D (2 - D)) (alpha = pi
+ *              for D >= 2), D = (sigma_T/m) m_j |u| Lambda_ij dt, where
+ *              sigma_T = sigma_V / 3 is the momentum-transfer cross-section of
+ *              that limit at the given viscosity cross-section sigma_V
+ *              (App. A: sigma_V = (3/2) int sin^2 dsigma, sigma_T =
+ *              int (1 - cos) dsigma, both (1/2) int theta^2 dsigma at small
+ *              angles), about the azimuth phi = 2 pi u_2 in the orthonormal
+ *              basis (b1, b2) of u's normal plane of Duff et al. (2017); |u|
+ *              and v_cm are kept (energy and momentum conserved).  The mean
+ *              change of u is the drag -D u; pairs are applied in ascending
+ *              key order from the current velocities, with Lambda_ij, m_j and
+ *              dt of the step start.
  *   mixed form: the FP32 pair distance is computed from FP32 offsets to
  *              power-of-two cell origins (see "canonical FP32 geometry").
  *
@@ -696,7 +712,8 @@ int orc_pairs_halo(int n, const double* px, const double* py, const double* pz,
                    int xs_kind, double s0, double w, double mass, double dt,
                    uint64_t seed, uint64_t step, uint32_t halo,
                    orc_event* ev_out, int64_t ev_cap, orc_pair_stats* st, double* sum_p_out,
-                   const uint8_t* pair_mask, const int* bins, int n_bins, int substep, double dt_max)
+                   const uint8_t* pair_mask, const int* bins, int n_bins, int substep, double dt_max,
+                   int angular)
 {
     orc_geom g; memset(&g, 0, sizeof(g));
     if (mode == 0) geom_build(&g, n, px, py, pz);
@@ -764,13 +781,19 @@ int orc_pairs_halo(int n, const double* px, const double* py, const double* pz,
                     uint32_t ctr[4] = {(uint32_t)step, a, b, halo}, x[4];
                     orc_philox4x32_10(ctr, key, x);
                     double u = ldexp((double)x[0], -32);
-                    if (P > 1.0) n_gt1++;
-                    if (fabs(P - u) < 1e-6) n_near++;
+                    if (angular) {
+                        /* forward-dominated: every pair interacts; its record carries
+                         * the step-start factor G = m_j Lambda dt instead of P */
+                        if (P / 3.0 > 1.0) n_gt1++;
+                    } else {
+                        if (P > 1.0) n_gt1++;
+                        if (fabs(P - u) < 1e-6) n_near++;
+                    }
                     #pragma omp atomic
                     sump[i] += Psum;
                     #pragma omp atomic
                     sump[j] += Psum;
-                    if (u < P) {
+                    if (angular || u < P) {
                         int64_t slot;
                         #pragma omp atomic capture
                         slot = n_ev++;
@@ -780,7 +803,8 @@ int orc_pairs_halo(int n, const double* px, const double* py, const double* pz,
                             e->i = ids[i] < ids[j] ? (uint32_t)i : (uint32_t)j;
                             e->j = ids[i] < ids[j] ? (uint32_t)j : (uint32_t)i;
                             e->x1 = x[1]; e->x2 = x[2];
-                            e->P = P; e->u = u;
+                            if (angular) { e->P = mass * lam * dtp; e->u = -1.0; }
+                            else { e->P = P; e->u = u; }
                         } else {
                             #pragma omp atomic write
                             overflow = 1;
@@ -844,6 +868,63 @@ void orc_apply_events(const orc_event* ev, int64_t n_ev, const double* m,
         vx[j] = nj[0]; vy[j] = nj[1]; vz[j] = nj[2];
         e1 = 0.5 * mi * (ni[0] * ni[0] + ni[1] * ni[1] + ni[2] * ni[2])
            + 0.5 * mj * (nj[0] * nj[0] + nj[1] * nj[1] + nj[2] * nj[2]);
+        if (dE_out) dE_out[e] = e1 - e0;
+    }
+}
+
+/* Orthonormal basis (b1, b2) of the plane normal to the unit vector n, from
+ * Duff et al. (2017), "Building an orthonormal basis, revisited" (JCGT 6):
+ * s = sign(n_z) (+1 for +0), a = -1/(s + n_z), b = n_x n_y a,
+ * b1 = (1 + s n_x^2 a, s b, -s n_x), b2 = (b, s + n_y^2 a, -n_y). */
+static void orc_normal_basis(const double n[3], double b1[3], double b2[3])
+{
+    const double sg = signbit(n[2]) ? -1.0 : 1.0;
+    const double a = -1.0 / (sg + n[2]);
+    const double b = n[0] * n[1] * a;
+    b1[0] = 1.0 + sg * n[0] * n[0] * a; b1[1] = sg * b; b1[2] = -sg * n[0];
+    b2[0] = b; b2[1] = sg + n[1] * n[1] * a; b2[2] = -n[1];
+}
+
+/* Forward-dominated (frictional) scattering of key-sorted pair records, one
+ * after another from the current FP64 velocities (reading in the header).
+ * ev[e].P holds G = m_j Lambda_ij dt of the step start; kind, s0, w give
+ * sigma_V / m (Eq. vel_dep).  Outputs (may be NULL): the pair kinetic-energy
+ * change and D of every record.  A record with D = 0 (zero cross-section,
+ * equal velocities) leaves the velocities untouched. */
+void orc_apply_drag(const orc_event* ev, int64_t n_ev, const double* m, int kind, double s0, double w,
+                    double* vx, double* vy, double* vz, double* dE_out, double* D_out)
+{
+    for (int64_t e = 0; e < n_ev; ++e) {
+        uint32_t i = ev[e].i, j = ev[e].j;
+        double mi = m[i], mj = m[j], M = mi + mj;
+        double vi[3] = {vx[i], vy[i], vz[i]}, vj[3] = {vx[j], vy[j], vz[j]};
+        double vcm[3], u[3], u2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            vcm[a] = (mi * vi[a] + mj * vj[a]) / M;
+            u[a] = vi[a] - vj[a];
+            u2 += u[a] * u[a];
+        }
+        double un = sqrt(u2);
+        double D = orc_sigma(kind, s0, w, un) / 3.0 * un * ev[e].P;
+        if (D_out) D_out[e] = D;
+        if (dE_out) dE_out[e] = 0.0;
+        if (!(D > 0.0)) continue;               /* no turn (zero cross-section or equal velocities) */
+        double ca = 1.0 - D, sa = D < 2.0 ? sqrt(D * (2.0 - D)) : 0.0;
+        if (D >= 2.0) ca = -1.0;
+        double up[3];
+        double nh[3] = {u[0] / un, u[1] / un, u[2] / un}, b1[3], b2[3];
+        orc_normal_basis(nh, b1, b2);
+        double phi = 2.0 * ORC_PI * ldexp((double)ev[e].x2, -32);
+        double cp = cos(phi), sp = sin(phi);
+        for (int a = 0; a < 3; ++a) up[a] = ca * u[a] + un * sa * (cp * b1[a] + sp * b2[a]);
+        double e0 = 0.5 * mi * (vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2])
+                  + 0.5 * mj * (vj[0] * vj[0] + vj[1] * vj[1] + vj[2] * vj[2]);
+        double ni[3], nj[3];
+        for (int a = 0; a < 3; ++a) { ni[a] = vcm[a] + mj / M * up[a]; nj[a] = vcm[a] - mi / M * up[a]; }
+        vx[i] = ni[0]; vy[i] = ni[1]; vz[i] = ni[2];
+        vx[j] = nj[0]; vy[j] = nj[1]; vz[j] = nj[2];
+        double e1 = 0.5 * mi * (ni[0] * ni[0] + ni[1] * ni[1] + ni[2] * ni[2])
+                  + 0.5 * mj * (nj[0] * nj[0] + nj[1] * nj[1] + nj[2] * nj[2]);
         if (dE_out) dE_out[e] = e1 - e0;
     }
 }
