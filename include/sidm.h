@@ -62,6 +62,8 @@ extern "C" {
 #define SIDM_FLAG_SUM_P   0x1  /* accumulate sum_j P_ij per particle (diagnostic) */
 #define SIDM_FLAG_TIMING  0x2  /* time hot kernels with CUDA events (sidm_kernel_times) */
 #define SIDM_FLAG_LOCAL_DIAG 0x4 /* keep scratch for sidm_local_diagnostics (40 B/particle) */
+#define SIDM_FLAG_DRAG    0x8  /* keep scratch for forward-dominated halos (sidm_xs.angular = 1):
+                                  per-particle interaction lists, 64 B per event_cap */
 
 typedef struct sidm_ctx sidm_ctx;
 
@@ -78,16 +80,43 @@ typedef struct {
     int32_t flags;       /* SIDM_FLAG_*                                              */
     int32_t grid_ctas;   /* persistent CTAs per kernel, 0 = SM count x occupancy     */
     int32_t use_tma;     /* 1: stage candidate tiles with bulk async copies (TMA)    */
+    /* launch knobs of the hot kernels; none changes a result (0 = default) */
+    int32_t knn_groups;  /* kernel-size search: lane groups of the candidate mask,   */
+                         /*   2, 4 or 8 (default 4; plain-load path)                 */
+    int32_t knn_chains;  /*   independent distance chains, 4 or 8 (default 4; 8     */
+                         /*   with knn_groups 4 only)                                */
+    int32_t knn_flush;   /*   pending keys per lane that trigger a heap merge before */
+                         /*   a tree node's tests, 1..32 (default 16)                */
+    float   knn_slack;   /*   warm-start bound / previous kernel size, 1..2 (1.0625) */
+    int32_t pair_per_round; /* pair kernel: pairs a lane queues per round, 1..4 (4; mixed-form draws) */
+    int32_t knn_batch;   /* kernel-size search: 1 loops over each staged leaf's      */
+                         /*   candidates, 2 over compacted batches of them (default 2; */
+                         /*   bulk copies and neighbour lists take 1)                 */
 } sidm_config;
 
-/* Cross-section per unit mass of one halo (Sect. 3.8, Eq. vel_dep):
- * kind 0: sigma/m = s0 (velocity independent);
- * kind 1: sigma/m = s0 / (1 + (v/w)^2)^2, v = |v_i - v_j| the pair speed.
- * Isotropic scattering, so the viscosity normalisation of App. A gives
- * sigma_V = sigma.  Code units. */
+/* Cross-section per unit mass of one halo (Sect. 3.8, Eq. vel_dep), given as
+ * the viscosity cross-section sigma_V of App. A (normalised to the total
+ * cross-section for isotropic scattering):
+ *   kind 0: sigma_V/m = s0 (velocity independent);
+ *   kind 1: sigma_V/m = s0 / (1 + (v/w)^2)^2, v = |v_i - v_j| the pair speed.
+ * angular 0: isotropic scattering (sigma = sigma_V): a pair scatters with
+ *   probability P_ij = (sigma/m) m_j v Lambda_ij dt into an isotropic direction.
+ * angular 1: forward-dominated (Sect. 3.8: the limit of a vanishing angle at
+ *   constant momentum transfer): every in-range pair interacts every step; its
+ *   relative velocity u (i the smaller id) turns by alpha, cos(alpha) = 1 - D,
+ *   sin(alpha) = sqrt(D (2 - D)) (alpha = pi for D >= 2), with
+ *   D = (sigma_V/m) / 3 |u| m_j Lambda_ij dt (the momentum-transfer cross-section
+ *   of that limit is sigma_V / 3), towards the projection onto u's normal
+ *   plane of the isotropic direction of Philox words 1 and 2 (as an isotropic
+ *   scatter draws it), uniform in azimuth about u; |u| and the centre-of-mass
+ *   velocity are kept.  Pairs apply in ascending key order from the current
+ *   velocities, with Lambda, m_j and dt of the step start.  Needs a context
+ *   created with SIDM_FLAG_DRAG and an event_cap that holds every in-range
+ *   pair (about 2 N_ngb per particle).
+ * Code units. */
 typedef struct {
     int32_t kind;
-    int32_t pad_;
+    int32_t angular;
     double s0;
     double w;
 } sidm_xs;

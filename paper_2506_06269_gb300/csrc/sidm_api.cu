@@ -570,6 +570,122 @@ __device__ __forceinline__ void fx_add(DevCounters* cnt, double v)
     atomicAdd(&cnt->de_hi, hi);
 }
 
+// Isotropic scatter of event E (Sect. 2, reading C6) on the current velocities
+// (read and written through L2); returns the change of the pair's kinetic
+// energy from the stored values, in FP64.  Equal masses within a halo.
+template <class R>
+__device__ __forceinline__ double apply_isotropic(const sidm_event& E, R* vel, int64_t N, const double* __restrict__ mass)
+{
+    R* vx = vel; R* vy = vel + N; R* vz = vel + 2 * N;
+    const int h = (int)(E.key >> 54);
+    const double m = mass[h];
+    const R vi[3] = {__ldcg(vx + E.i), __ldcg(vy + E.i), __ldcg(vz + E.i)};
+    const R vj[3] = {__ldcg(vx + E.j), __ldcg(vy + E.j), __ldcg(vz + E.j)};
+    R ct, st_, sp, cp;
+    if (sizeof(R) == 4) {
+        ct = (R)fmaf((float)E.x1, 0x1p-31f, -1.0f);
+        st_ = (R)sqrtf(fmaxf(0.f, 1.f - (float)ct * (float)ct));
+        float s_, c_;
+        sincospif((float)E.x2 * 0x1p-31f, &s_, &c_);
+        sp = (R)s_; cp = (R)c_;
+    } else {
+        ct = (R)(2.0 * ldexp((double)E.x1, -32) - 1.0);
+        st_ = (R)sqrt(fmax(0.0, 1.0 - (double)ct * (double)ct));
+        double s_, c_;
+        sincospi(ldexp((double)E.x2, -31), &s_, &c_);
+        sp = (R)s_; cp = (R)c_;
+    }
+    const R nh[3] = {st_ * cp, st_ * sp, ct};
+    // equal masses within a halo: v_cm = (v_i + v_j)/2, weights 1/2
+    R dv2 = R(0), vc[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        vc[a] = R(0.5) * (vi[a] + vj[a]);
+        const R d = vi[a] - vj[a];
+        dv2 += d * d;
+    }
+    const R hw = R(0.5) * sqrt(dv2);
+    R ni[3], nj[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { ni[a] = vc[a] + hw * nh[a]; nj[a] = vc[a] - hw * nh[a]; }
+    __stcg(vx + E.i, ni[0]); __stcg(vy + E.i, ni[1]); __stcg(vz + E.i, ni[2]);
+    __stcg(vx + E.j, nj[0]); __stcg(vy + E.j, nj[1]); __stcg(vz + E.j, nj[2]);
+    double e0 = 0.0, e1 = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        e0 = __dadd_rn(e0, __dadd_rn(__dmul_rn((double)vi[a], (double)vi[a]), __dmul_rn((double)vj[a], (double)vj[a])));
+        e1 = __dadd_rn(e1, __dadd_rn(__dmul_rn((double)ni[a], (double)ni[a]), __dmul_rn((double)nj[a], (double)nj[a])));
+    }
+    return __dmul_rn(0.5 * m, __dsub_rn(e1, e0));
+}
+
+// Forward-dominated interaction of record E (Sect. 3.8 with App. A, reading
+// C20): the relative velocity u = v_i - v_j turns by alpha, cos(alpha) = 1 - D,
+// sin(alpha) = sqrt(D (2 - D)), D = (sigma_V/m)/3 |u| G, G = m_j Lambda dt of the
+// step start, towards the projection onto u's normal plane of the isotropic
+// Philox direction of words 1 and 2 (uniform in azimuth about u); |u| and v_cm
+// are kept.  D = 0 changes nothing.  Returns the pair's kinetic-energy change
+// from the stored values (FP64).
+template <class R>
+__device__ __forceinline__ double apply_drag(const sidm_event& E, double G, const sidm_xs& xs, R* vel, int64_t N,
+                                             const double* __restrict__ mass)
+{
+    R* vx = vel; R* vy = vel + N; R* vz = vel + 2 * N;
+    const double m = mass[(int)(E.key >> 54)];
+    const R vi[3] = {__ldcg(vx + E.i), __ldcg(vy + E.i), __ldcg(vz + E.i)};
+    const R vj[3] = {__ldcg(vx + E.j), __ldcg(vy + E.j), __ldcg(vz + E.j)};
+    R u[3], vc[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { u[a] = vi[a] - vj[a]; vc[a] = R(0.5) * (vi[a] + vj[a]); }
+    const R un = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    R sig = (R)xs.s0;
+    if (xs.kind == 1) { const R q = un / (R)xs.w; const R t = R(1) + q * q; sig = (R)xs.s0 / (t * t); }
+    const R D = sig / R(3) * un * (R)G;
+    if (!(D > R(0))) return 0.0;
+    R ca, sa;
+    if (D < R(2)) { ca = R(1) - D; sa = sqrt(D * (R(2) - D)); } else { ca = R(-1); sa = R(0); }
+    // the turn's direction: the isotropic Philox direction w (words 1, 2, as an
+    // isotropic scatter draws it) projected onto the plane normal to u
+    R ct, st_, sp, cp;
+    if (sizeof(R) == 4) {
+        ct = (R)fmaf((float)E.x1, 0x1p-31f, -1.0f);
+        st_ = (R)sqrtf(fmaxf(0.f, 1.f - (float)ct * (float)ct));
+        float s_, c_;
+        sincospif((float)E.x2 * 0x1p-31f, &s_, &c_);
+        sp = (R)s_; cp = (R)c_;
+    } else {
+        ct = (R)(2.0 * ldexp((double)E.x1, -32) - 1.0);
+        st_ = (R)sqrt(fmax(0.0, 1.0 - (double)ct * (double)ct));
+        double s_, c_;
+        sincospi(ldexp((double)E.x2, -31), &s_, &c_);
+        sp = (R)s_; cp = (R)c_;
+    }
+    const R w[3] = {st_ * cp, st_ * sp, ct};
+    const R nh[3] = {u[0] / un, u[1] / un, u[2] / un};
+    const R wn = w[0] * nh[0] + w[1] * nh[1] + w[2] * nh[2];
+    R ep[3], el = R(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { ep[a] = w[a] - wn * nh[a]; el += ep[a] * ep[a]; }
+    el = sqrt(el);
+    const R sc = el > R(0) ? un * sa / el : R(0);
+    R ni[3], nj[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const R up = ca * u[a] + sc * ep[a];
+        ni[a] = vc[a] + R(0.5) * up;
+        nj[a] = vc[a] - R(0.5) * up;
+    }
+    __stcg(vx + E.i, ni[0]); __stcg(vy + E.i, ni[1]); __stcg(vz + E.i, ni[2]);
+    __stcg(vx + E.j, nj[0]); __stcg(vy + E.j, nj[1]); __stcg(vz + E.j, nj[2]);
+    double e0 = 0.0, e1 = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        e0 = __dadd_rn(e0, __dadd_rn(__dmul_rn((double)vi[a], (double)vi[a]), __dmul_rn((double)vj[a], (double)vj[a])));
+        e1 = __dadd_rn(e1, __dadd_rn(__dmul_rn((double)ni[a], (double)ni[a]), __dmul_rn((double)nj[a], (double)nj[a])));
+    }
+    return __dmul_rn(0.5 * m, __dsub_rn(e1, e0));
+}
+
 // Apply scatter events in ascending key order per particle.  One CTA; each
 // round applies every pending event whose key is the smallest pending key at
 // both of its particles (a topological order of the conflict graph, equal to
@@ -599,7 +715,6 @@ __global__ void __launch_bounds__(1024) k_resolve(const sidm_event* __restrict__
         }
         atomicAdd(&s_multi, multi);
         __syncthreads();
-        R* vx = vel; R* vy = vel + N; R* vz = vel + 2 * N;
         while (true) {
             // phase A: claim the smallest pending key at each particle
             for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
@@ -613,46 +728,7 @@ __global__ void __launch_bounds__(1024) k_resolve(const sidm_event* __restrict__
                 if (__ldcg(done + e)) continue;
                 const sidm_event E = ev[e];
                 if (__ldcg(claim + E.i) != E.key || __ldcg(claim + E.j) != E.key) continue;
-                const int h = (int)(E.key >> 54);
-                const double m = mass[h];
-                const R vi[3] = {__ldcg(vx + E.i), __ldcg(vy + E.i), __ldcg(vz + E.i)};
-                const R vj[3] = {__ldcg(vx + E.j), __ldcg(vy + E.j), __ldcg(vz + E.j)};
-                R ct, st_, sp, cp;
-                if (sizeof(R) == 4) {
-                    ct = (R)fmaf((float)E.x1, 0x1p-31f, -1.0f);
-                    st_ = (R)sqrtf(fmaxf(0.f, 1.f - (float)ct * (float)ct));
-                    float s_, c_;
-                    sincospif((float)E.x2 * 0x1p-31f, &s_, &c_);
-                    sp = (R)s_; cp = (R)c_;
-                } else {
-                    ct = (R)(2.0 * ldexp((double)E.x1, -32) - 1.0);
-                    st_ = (R)sqrt(fmax(0.0, 1.0 - (double)ct * (double)ct));
-                    double s_, c_;
-                    sincospi(ldexp((double)E.x2, -31), &s_, &c_);
-                    sp = (R)s_; cp = (R)c_;
-                }
-                const R nh[3] = {st_ * cp, st_ * sp, ct};
-                // equal masses within a halo: v_cm = (v_i + v_j)/2, weights 1/2
-                R dv2 = R(0), vc[3];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    vc[a] = R(0.5) * (vi[a] + vj[a]);
-                    const R d = vi[a] - vj[a];
-                    dv2 += d * d;
-                }
-                const R hw = R(0.5) * sqrt(dv2);
-                R ni[3], nj[3];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) { ni[a] = vc[a] + hw * nh[a]; nj[a] = vc[a] - hw * nh[a]; }
-                __stcg(vx + E.i, ni[0]); __stcg(vy + E.i, ni[1]); __stcg(vz + E.i, ni[2]);
-                __stcg(vx + E.j, nj[0]); __stcg(vy + E.j, nj[1]); __stcg(vz + E.j, nj[2]);
-                double e0 = 0.0, e1 = 0.0;
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    e0 = __dadd_rn(e0, __dadd_rn(__dmul_rn((double)vi[a], (double)vi[a]), __dmul_rn((double)vj[a], (double)vj[a])));
-                    e1 = __dadd_rn(e1, __dadd_rn(__dmul_rn((double)ni[a], (double)ni[a]), __dmul_rn((double)nj[a], (double)nj[a])));
-                }
-                fx_add(cnt, __dmul_rn(0.5 * m, __dsub_rn(e1, e0)));
+                fx_add(cnt, apply_isotropic<R>(E, vel, N, mass));
                 done[e] = 1;
             }
             __syncthreads();
@@ -691,6 +767,203 @@ __global__ void __launch_bounds__(1024) k_resolve(const sidm_event* __restrict__
         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
         if ((threadIdx.x & 31) == 0) atomicMax((unsigned int*)&st->max_sum_p, __float_as_uint(m));
     }
+}
+
+// ---- a4 for forward-dominated halos: per-particle interaction lists -------
+// Every in-range pair of such a halo is a record, so a particle takes part in
+// hundreds of them per step and key order needs thousands of rounds.  Each
+// particle gets the list of its records sorted by partner id, which is
+// ascending key order for that particle (records (c, a), c < a, precede the
+// records (a, b), b > a).  A round applies every record that is the next
+// pending record of both its particles -- exactly the rounds of the claims
+// above -- but looks only at the head of each active particle.
+
+// 128-bit fixed-point accumulator in registers (units of 2^-80), merged into
+// the global one once per warp: integer sums commute, so the total does not
+// depend on the order of the records.
+struct Fx128 {
+    unsigned long long lo = 0ull, hi = 0ull;
+    __device__ void add(double v)
+    {
+        const double hi_d = floor(ldexp(v, 16));
+        const double lo_d = ldexp(v, 80) - ldexp(hi_d, 64);
+        const unsigned long long l = lo_d >= 18446744073709551615.0 ? 0xFFFFFFFFFFFFFFFFull : __double2ull_rz(lo_d);
+        const unsigned long long h = (unsigned long long)(long long)hi_d;
+        lo += l;
+        hi += h + (lo < l ? 1ull : 0ull);
+    }
+};
+
+// List entries of the records: entry 2e for particle i, 2e + 1 for particle j,
+// key = particle index << 27 | partner id.
+__global__ void k_list_keys(const sidm_event* __restrict__ ev, int64_t n, unsigned long long* __restrict__ key,
+                            uint32_t* __restrict__ val)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const sidm_event E = ev[e];
+        const unsigned long long a = (E.key >> 27) & (kIdLimit - 1u), b = E.key & (kIdLimit - 1u);
+        key[2 * e] = ((unsigned long long)E.i << 27) | b;
+        key[2 * e + 1] = ((unsigned long long)E.j << 27) | a;
+        val[2 * e] = (uint32_t)e;
+        val[2 * e + 1] = (uint32_t)e;
+    }
+}
+
+// Runs of the sorted entries: start and length of each particle's list, the
+// initial active list, and the number of particles in two or more records.
+__global__ void k_list_runs(const unsigned long long* __restrict__ key, int64_t m, uint32_t* __restrict__ start,
+                            uint32_t* __restrict__ len, uint32_t* __restrict__ act, uint32_t* __restrict__ lcnt)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < m; s += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t p = (uint32_t)(key[s] >> 27);
+        if (s > 0 && (uint32_t)(key[s - 1] >> 27) == p) continue;
+        int64_t e = s + 1;
+        while (e < m && (uint32_t)(key[e] >> 27) == p) ++e;
+        start[p] = (uint32_t)s;
+        len[p] = (uint32_t)(e - s);
+        act[atomicAdd(&lcnt[0], 1u)] = p;
+        if (e - s > 1) atomicAdd(&lcnt[2], 1u);
+    }
+}
+
+// Grid-wide barrier of a cooperative launch (every CTA resident): arrival
+// count work[2], generation work[3].  The wait gives up after kBarrierNs of
+// %globaltimer time and returns false in every thread of the CTA.
+constexpr unsigned long long kBarrierNs = 2000000000ull;   // 2 s
+
+__device__ __forceinline__ unsigned long long now_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ bool grid_barrier(DevCounters* cnt)
+{
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int* gen = &cnt->work[3];
+        int ok = 1;
+        __threadfence();
+        const unsigned int g = *gen;
+        if (atomicAdd(&cnt->work[2], 1u) == gridDim.x - 1) {
+            atomicExch(&cnt->work[2], 0u);
+            __threadfence();
+            atomicAdd(&cnt->work[3], 1u);
+        } else {
+            const unsigned long long t0 = now_ns();
+            while (*gen == g) {
+                if (now_ns() - t0 > kBarrierNs) { ok = 0; break; }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+struct ListResolve {
+    const sidm_event* ev;
+    const double* evg;
+    const sidm_xs* xs;
+    const double* mass;
+    const uint32_t* lval;     // sorted entries: record index per list slot
+    const uint32_t* start;
+    const uint32_t* len;
+    uint32_t* ptr;            // next pending entry of each list (zero at rest)
+    uint32_t* act;            // [2][N] active particles (ping-pong)
+    uint32_t* lcnt;           // [0], [1]: active counts; [2] multi-hit; [3] rounds; [4] status
+    uint8_t* done;            // [records], zero at entry
+    void* vel;
+    int64_t N;
+    int64_t n_rec;
+    DevCounters* cnt;
+};
+
+template <class R>
+__global__ void __launch_bounds__(256) k_resolve_lists(ListResolve q)
+{
+    const int64_t T = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    R* vel = (R*)q.vel;
+    Fx128 acc;
+    int cur = 0;
+    unsigned int rounds = 0u, status = 0u;
+    unsigned int n_cur = *(volatile unsigned int*)&q.lcnt[0];
+    while (n_cur > 0u) {
+        const uint32_t* act = q.act + (size_t)cur * q.N;
+        uint32_t* nxt = q.act + (size_t)(cur ^ 1) * q.N;
+        if (tid == 0) q.lcnt[cur ^ 1] = 0u;
+        // apply every record that heads both of its particles' lists (by the
+        // particle of lower index); the applied records touch disjoint particles
+        for (int64_t a = tid; a < n_cur; a += T) {
+            const uint32_t p = act[a];
+            const uint32_t e = q.lval[q.start[p] + __ldcg(q.ptr + p)];
+            const sidm_event E = q.ev[e];
+            const uint32_t o = E.i == p ? E.j : E.i;
+            if (p > o || q.lval[q.start[o] + __ldcg(q.ptr + o)] != e) continue;
+            const sidm_xs xs = q.xs[(int)(E.key >> 54)];
+            acc.add(xs.angular ? apply_drag<R>(E, q.evg[e], xs, vel, q.N, q.mass) : apply_isotropic<R>(E, vel, q.N, q.mass));
+            __stcg(q.done + e, (uint8_t)1);
+        }
+        if (!grid_barrier(q.cnt)) { status |= SIDM_DEV_WAIT_TIMEOUT; break; }
+        // advance the lists whose head was applied; keep the unfinished ones
+        for (int64_t a = tid; a < n_cur; a += T) {
+            const uint32_t p = act[a];
+            uint32_t k = __ldcg(q.ptr + p);
+            if (__ldcg(q.done + q.lval[q.start[p] + k])) __stcg(q.ptr + p, ++k);
+            if (k < q.len[p]) nxt[atomicAdd(&q.lcnt[cur ^ 1], 1u)] = p;
+        }
+        ++rounds;
+        if (!grid_barrier(q.cnt)) { status |= SIDM_DEV_WAIT_TIMEOUT; break; }
+        n_cur = *(volatile unsigned int*)&q.lcnt[cur ^ 1];
+        cur ^= 1;
+        if ((int64_t)rounds > q.n_rec) { status |= SIDM_DEV_ROUNDS; break; }   // cannot happen: >= 1 record per round
+    }
+    // the pair energy changes: warp sums of the 128-bit accumulators, one
+    // global addition per warp
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long l = __shfl_xor_sync(0xffffffffu, acc.lo, o);
+        const unsigned long long h = __shfl_xor_sync(0xffffffffu, acc.hi, o);
+        acc.lo += l;
+        acc.hi += h + (acc.lo < l ? 1ull : 0ull);
+    }
+    if ((threadIdx.x & 31) == 0 && (acc.lo | acc.hi)) {
+        const unsigned long long old = atomicAdd(&q.cnt->de_lo, acc.lo);
+        atomicAdd(&q.cnt->de_hi, acc.hi + (old + acc.lo < old ? 1ull : 0ull));
+    }
+    if (tid == 0) { q.lcnt[3] = rounds; if (status) atomicOr(&q.lcnt[4], status); }
+    else if (status && threadIdx.x == 0) atomicOr(&q.lcnt[4], status);
+}
+
+// The lists' pointers back to zero (entries of the sorted lists).
+__global__ void k_list_reset(const unsigned long long* __restrict__ key, int64_t m, uint32_t* __restrict__ ptr)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < m; s += (int64_t)gridDim.x * blockDim.x)
+        ptr[(uint32_t)(key[s] >> 27)] = 0u;
+}
+
+// Step statistics of a list resolve (one thread).
+__global__ void k_list_stats(int64_t n_rec, const uint32_t* __restrict__ lcnt, DevCounters* cnt, sidm_step_stats* st)
+{
+    const unsigned int status = lcnt[4];
+    if (status) raise_status(cnt, status);
+    st->n_events = (unsigned long long)n_rec;
+    st->n_multi = lcnt[2];
+    st->rounds = lcnt[3];
+    st->status = status;
+    const unsigned long long hi = cnt->de_hi, lo = cnt->de_lo;
+    st->d_energy = ldexp((double)(long long)hi, -16) + ldexp((double)lo, -80);
+}
+
+__global__ void k_list_overflow(DevCounters* cnt, sidm_step_stats* st)
+{
+    raise_status(cnt, SIDM_DEV_EVENT_OVERFLOW);
+    st->n_events = cnt->ev_count;
+    st->status = SIDM_DEV_EVENT_OVERFLOW;
 }
 
 // ------------------------------------------------------------------ a5 reduce
@@ -982,7 +1255,9 @@ static void free_all(sidm_ctx* c)
                     c->d_chunk_halo, c->d_chunk_begin, c->d_frame, c->d_key, c->d_key2, c->d_val, c->d_val2,
                     c->d_hist, c->d_P4, c->d_V4, c->d_ID, c->d_cell, c->d_nlo, c->d_nhi, c->d_perm, c->d_tmp_pos,
                     c->d_tmp_vel, c->d_tmp_id, c->d_claim, c->d_hits, c->d_done, c->d_ev, c->d_sump,
-                    c->d_stats_own, c->d_cnt, c->d_epart, c->d_lam, c->d_hprev, c->d_dacc, c->d_halo_ord};
+                    c->d_stats_own, c->d_cnt, c->d_epart, c->d_lam, c->d_hprev, c->d_dacc, c->d_halo_ord,
+                    c->d_evg, c->d_lkey, c->d_lval, c->d_lhist, c->d_lstart, c->d_llen, c->d_lptr, c->d_lact,
+                    c->d_lcnt};
     for (void* p : ptrs) if (p) cudaFree(p);
     if (c->d_stage) cudaFreeHost(c->d_stage);
     for (cudaEvent_t e : c->t_ev) if (e) cudaEventDestroy(e);
@@ -1006,10 +1281,22 @@ extern "C" int sidm_create(sidm_ctx** out, const sidm_config* cfg)
     if (cfg->halo_max < 1 || cfg->halo_max > kMaxHalos) { g_create_err = "halo_max must be in [1, 1024]"; return SIDM_EINVAL; }
     if (cfg->ngb_max < 1 || cfg->ngb_max > kMaxNgb) { g_create_err = "ngb_max must be in [1, 128]"; return SIDM_EINVAL; }
     if (cfg->event_cap < 1) { g_create_err = "event_cap must be >= 1"; return SIDM_EINVAL; }
+    if ((cfg->flags & SIDM_FLAG_DRAG) && cfg->event_cap >= (1ll << 31)) {
+        g_create_err = "event_cap must be below 2^31 with SIDM_FLAG_DRAG"; return SIDM_EINVAL;
+    }
     if (cfg->precision != SIDM_MIXED && cfg->precision != SIDM_FP64) { g_create_err = "bad precision"; return SIDM_EINVAL; }
     if (cfg->knn_warps < 0 || cfg->knn_warps > 16) { g_create_err = "knn_warps must be in [0, 16]"; return SIDM_EINVAL; }
     if (cfg->pair_warps < 0 || cfg->pair_warps > 8) {       // the pair kernel is built for CTAs of <= 256 threads
         g_create_err = "pair_warps must be in [0, 8]"; return SIDM_EINVAL;
+    }
+    if (!(cfg->knn_groups == 0 || cfg->knn_groups == 2 || cfg->knn_groups == 4 || cfg->knn_groups == 8) ||
+        !(cfg->knn_chains == 0 || cfg->knn_chains == 4 || cfg->knn_chains == 8) || cfg->knn_flush < 0 ||
+        cfg->knn_flush > 32 || !(cfg->knn_slack == 0.f || (cfg->knn_slack >= 1.f && cfg->knn_slack <= 2.f)) ||
+        cfg->pair_per_round < 0 || cfg->pair_per_round > 4 || cfg->knn_batch < 0 || cfg->knn_batch > 2 ||
+        (cfg->knn_chains == 8 && cfg->knn_groups != 0 && cfg->knn_groups != 4)) {
+        g_create_err = "launch knobs out of range (knn_groups 2/4/8, knn_chains 4/8 (8 with 4 groups), "
+                       "knn_flush <= 32, knn_slack in [1, 2], pair_per_round <= 4, knn_batch <= 2)";
+        return SIDM_EINVAL;
     }
     sidm_ctx* c = new sidm_ctx();
     c->cfg = *cfg;
@@ -1074,12 +1361,26 @@ extern "C" int sidm_create(sidm_ctx** out, const sidm_config* cfg)
     ALLOC(c->d_cnt, 1);
     ALLOC(c->d_epart, 8 * c->chunk_cap);
     ALLOC(c->d_halo_ord, H);
+    if (cfg->flags & SIDM_FLAG_DRAG) {
+        const int64_t m = 2 * cfg->event_cap;
+        c->lhist_cap = 256 * cdiv(m, kSortTile) + 256;
+        ALLOC(c->d_evg, cfg->event_cap);
+        ALLOC(c->d_lkey, 2 * m);
+        ALLOC(c->d_lval, 2 * m);
+        ALLOC(c->d_lhist, c->lhist_cap);
+        ALLOC(c->d_lstart, N);
+        ALLOC(c->d_llen, N);
+        ALLOC(c->d_lptr, N);
+        ALLOC(c->d_lact, 2 * N);
+        ALLOC(c->d_lcnt, 8);
+    }
 #undef ALLOC
     e = cudaMallocHost((void**)&c->d_stage, c->stage_bytes);
     if (e != cudaSuccess) return fail("cudaMallocHost", e);
     // Lambda table: FP64 quadrature on the host, stored in the form's precision.
     std::vector<double> T;
     lambda_table(T);
+    gauss_legendre(8, c->gl8x, c->gl8w);
     if (fp64) {
         e = cudaMalloc(&c->d_lam, T.size() * 8); if (e != cudaSuccess) return fail("cudaMalloc lam", e);
         e = cudaMemcpy(c->d_lam, T.data(), T.size() * 8, cudaMemcpyHostToDevice);
@@ -1092,6 +1393,7 @@ extern "C" int sidm_create(sidm_ctx** out, const sidm_config* cfg)
     e = cudaMemset(c->d_hits, 0, sizeof(uint32_t) * (size_t)N); if (e != cudaSuccess) return fail("memset", e);
     e = cudaMemset(c->d_cnt, 0, sizeof(DevCounters)); if (e != cudaSuccess) return fail("memset", e);
     e = cudaMemset(c->d_claim, 0xFF, sizeof(unsigned long long) * (size_t)N); if (e != cudaSuccess) return fail("memset", e);
+    if (c->d_lptr) { e = cudaMemset(c->d_lptr, 0, sizeof(uint32_t) * (size_t)N); if (e != cudaSuccess) return fail("memset", e); }
     if (cfg->flags & SIDM_FLAG_TIMING) {
         c->t_ev.assign(2 * kTimerCap, nullptr);
         c->t_slot.assign(kTimerCap, 0);
@@ -1348,6 +1650,75 @@ extern "C" int sidm_neighbours(sidm_ctx* c, const int32_t* n_ngb, int32_t k_stri
     return launch_knn(c, nullptr, nbr, k_stride, false, s);
 }
 
+__global__ void k_max_sump(int64_t N, const float* __restrict__ sump, sidm_step_stats* st)
+{
+    float m = 0.f;
+    for (int64_t s = threadIdx.x; s < N; s += blockDim.x) m = fmaxf(m, sump[s]);
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax((unsigned int*)&st->max_sum_p, __float_as_uint(m));
+}
+
+// a4 through per-particle interaction lists (contexts with SIDM_FLAG_DRAG; any
+// mix of isotropic and forward-dominated halos).  Synchronises the stream once,
+// to size the list sort from the number of records.
+template <class R>
+static int resolve_lists(sidm_ctx* c, const sidm_xs* xs, const double* mass, R* vel, sidm_step_stats* st, int use_sump,
+                         cudaStream_t s)
+{
+    const LayoutHost& L = c->lay;
+    const int tr = timer_begin(c, 3, s);
+    unsigned long long n = 0ull;
+    SIDM_CUDA(c, cudaMemcpyAsync(c->d_stage, &c->d_cnt->ev_count, sizeof(n), cudaMemcpyDeviceToHost, s));
+    SIDM_CUDA(c, cudaStreamSynchronize(s));
+    std::memcpy(&n, c->d_stage, sizeof(n));
+    SIDM_CUDA(c, cudaMemsetAsync(c->d_lcnt, 0, 8 * sizeof(uint32_t), s));
+    if (n > (unsigned long long)c->cfg.event_cap) {
+        SIDM_LAUNCH(c, k_list_overflow<<<1, 1, 0, s>>>(c->d_cnt, st));
+        timer_end(c, tr, s);
+        return SIDM_OK;
+    }
+    const int64_t m = 2 * (int64_t)n;
+    unsigned long long *ka = c->d_lkey, *kb = c->d_lkey + m;
+    uint32_t *va = c->d_lval, *vb = c->d_lval + m;
+    if (n > 0) {
+        SIDM_CUDA(c, cudaMemsetAsync(c->d_done, 0, (size_t)n, s));
+        SIDM_LAUNCH(c, k_list_keys<<<grid_for(c, (int64_t)n, 256), 256, 0, s>>>(c->d_ev, (int64_t)n, ka, va));
+        // stable LSD radix sort of the entries by (particle index, partner id)
+        int ib = 1;
+        while (ib < 31 && ((int64_t)1 << ib) < L.N) ++ib;
+        const int passes = (int)cdiv(27 + ib, 8);
+        const int nblk = (int)cdiv(m, kSortTile);
+        for (int pss = 0; pss < passes; ++pss) {
+            SIDM_LAUNCH(c, k_sort_hist<<<nblk, kSortThreads, 0, s>>>(ka, m, 8 * pss, nblk, c->d_lhist));
+            SIDM_LAUNCH(c, k_sort_scan<<<256, 256, 0, s>>>(c->d_lhist, nblk, c->d_lhist + (int64_t)256 * nblk));
+            SIDM_LAUNCH(c, k_sort_scatter<<<nblk, kSortThreads, 0, s>>>(ka, va, m, 8 * pss, nblk, c->d_lhist,
+                                                                         c->d_lhist + (int64_t)256 * nblk, kb, vb));
+            std::swap(ka, kb);
+            std::swap(va, vb);
+        }
+        SIDM_LAUNCH(c, k_list_runs<<<grid_for(c, m, 256), 256, 0, s>>>(ka, m, c->d_lstart, c->d_llen, c->d_lact, c->d_lcnt));
+        SIDM_CUDA(c, cudaMemsetAsync(&c->d_cnt->work[2], 0, sizeof(unsigned int), s));
+        ListResolve q;
+        q.ev = c->d_ev; q.evg = c->d_evg; q.xs = xs; q.mass = mass; q.lval = va; q.start = c->d_lstart;
+        q.len = c->d_llen; q.ptr = c->d_lptr; q.act = c->d_lact; q.lcnt = c->d_lcnt; q.done = c->d_done;
+        q.vel = vel; q.N = L.N; q.n_rec = (int64_t)n; q.cnt = c->d_cnt;
+        auto kern = k_resolve_lists<R>;
+        int occ = 0;
+        int rc = occupancy(c, (const void*)kern, 256, 0, &occ);
+        if (rc) return rc;
+        if (occ < 1) return set_err(c, SIDM_ECAPACITY, "list resolve does not fit on an SM");
+        const int grid = c->sm_count * occ;       // every CTA resident: the rounds use a grid barrier
+        void* args[] = {&q};
+        SIDM_CUDA(c, cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(256), args, 0, s));
+        c->launches++;
+        SIDM_LAUNCH(c, k_list_reset<<<grid_for(c, m, 256), 256, 0, s>>>(ka, m, c->d_lptr));
+    }
+    SIDM_LAUNCH(c, k_list_stats<<<1, 1, 0, s>>>((int64_t)n, c->d_lcnt, c->d_cnt, st));
+    if (use_sump) SIDM_LAUNCH(c, k_max_sump<<<1, 1024, 0, s>>>(L.N, c->d_sump, st));
+    timer_end(c, tr, s);
+    return SIDM_OK;
+}
+
 static int scatter_impl(sidm_ctx* c, uint64_t seed, uint64_t step, const sidm_xs* xs, const double* dt,
                         const double* mass, void* vel, sidm_step_stats* stats, cudaStream_t s)
 {
@@ -1369,6 +1740,9 @@ static int scatter_impl(sidm_ctx* c, uint64_t seed, uint64_t step, const sidm_xs
     int rc = launch_pairs(c, seed, step, xs, dt, mass, st, s);
     if (rc) return rc;
     const int use_sump = (c->cfg.flags & SIDM_FLAG_SUM_P) ? 1 : 0;
+    if (c->cfg.flags & SIDM_FLAG_DRAG)
+        return fp64 ? resolve_lists<double>(c, xs, mass, (double*)vel, st, use_sump, s)
+                    : resolve_lists<float>(c, xs, mass, (float*)vel, st, use_sump, s);
     const int tr = timer_begin(c, 3, s);
     if (fp64)
         SIDM_LAUNCH(c, k_resolve<double><<<1, 1024, 0, s>>>(c->d_ev, c->cfg.event_cap, (double*)vel, L.N, mass, c->d_claim,

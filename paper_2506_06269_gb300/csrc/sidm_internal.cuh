@@ -43,7 +43,7 @@ struct DevCounters {
     unsigned long long ev_count;     // events drawn this step
     unsigned long long de_lo;        // 128-bit fixed-point sum of pair dE (2^-80 units)
     unsigned long long de_hi;
-    unsigned int work[4];            // persistent work-queue counters
+    unsigned int work[4];            // persistent work-queue counters; [2], [3]: grid barrier
     unsigned int status;             // sticky SIDM_DEV_* bits (cleared by sidm_status)
     unsigned int pad;
     unsigned long long diag[8];      // diagnostics (sidm_diagnostics)
@@ -129,6 +129,21 @@ struct sidm_ctx {
     sidm_event* d_ev = nullptr;             // [event_cap]
     float* d_sump = nullptr;                // [N] (SIDM_FLAG_SUM_P)
     double* d_dacc = nullptr;               // [5][N] kernel-weighted moments (SIDM_FLAG_LOCAL_DIAG)
+    // forward-dominated halos (SIDM_FLAG_DRAG): per-record G = m_j Lambda dt, and
+    // the per-particle interaction lists (2 entries per record, key = particle
+    // index << 27 | partner id, sorted), their starts/lengths, round pointers,
+    // active lists and counters
+    double* d_evg = nullptr;                // [event_cap]
+    unsigned long long* d_lkey = nullptr;   // [2][2 event_cap] ping-pong
+    uint32_t* d_lval = nullptr;             // [2][2 event_cap]
+    uint32_t* d_lhist = nullptr;            // radix-sort histograms of 2 event_cap entries
+    int64_t lhist_cap = 0;
+    uint32_t* d_lstart = nullptr;           // [N]
+    uint32_t* d_llen = nullptr;             // [N]
+    uint32_t* d_lptr = nullptr;             // [N] (zero at rest)
+    uint32_t* d_lact = nullptr;             // [2][N]
+    uint32_t* d_lcnt = nullptr;             // [8] active counts, multi-hit count, rounds, status
+    double gl8x[8] = {}, gl8w[8] = {};      // 8-point Gauss-Legendre rule (Lambda quadrature on the device)
     unsigned long long* d_halo_ord = nullptr;  // [H] per-halo minima (order-preserving bits)
 
     // individual time steps of the scatter step in flight (set by
@@ -321,6 +336,86 @@ __device__ __forceinline__ float lambda_lookup_fast(const float* __restrict__ T,
 {
     const float inv = __fdividef(1.f, fmaxf(hi, hj));
     return lambda_f_fast(T, d, hi, hj, inv) * inv * inv * inv;
+}
+
+// Lambda(d; a, b) by quadrature, for pairs whose result must be accurate
+// relative to Lambda itself (the forward-dominated turn, whose sine is the
+// square root of a multiple of Lambda): the overlap of spline kernels of
+// support a (at the origin) and b (at distance d),
+//   Lambda = (2 pi / d) int r W_a(r) [S_b(r + d) - S_b(|r - d|)] dr,
+//   S_b(s) = S_1(s/b) / b,  S_1(t) = int_0^t t' W_1(t') dt' (closed form),
+// over r in [max(0, d - b), min(a, d + b)], split at the breakpoints of the
+// polynomial pieces and integrated with the 8-point Gauss-Legendre rule
+// (gx, gw on [-1, 1]), exact for each piece up to rounding.  d = 0 takes the
+// limit 4 pi int r^2 W_a W_b dr.
+template <class R>
+__device__ __forceinline__ R spline_w1_q(R t)
+{
+    const R c = R(8.0 / 3.14159265358979323846);
+    if (!(t < R(1)) || t < R(0)) return R(0);
+    if (t < R(0.5)) return c * (R(1) - R(6) * t * t + R(6) * t * t * t);
+    const R u = R(1) - t;
+    return c * R(2) * u * u * u;
+}
+
+template <class R>
+__device__ __forceinline__ R spline_s1_q(R t)
+{
+    const R c = R(8.0 / 3.14159265358979323846);
+    auto inner = [&](R q) { return c * (R(0.5) * q * q - R(1.5) * q * q * q * q + R(1.2) * q * q * q * q * q); };
+    auto outer = [&](R q) { const R u = R(1) - q; return R(-2) * c * (R(0.25) * u * u * u * u - R(0.2) * u * u * u * u * u); };
+    if (!(t > R(0))) return R(0);
+    if (t < R(0.5)) return inner(t);
+    const R q = t < R(1) ? t : R(1);
+    return inner(R(0.5)) + outer(q) - outer(R(0.5));
+}
+
+template <class R>
+__device__ R lambda_quad(R d, R a, R b, const R* gx, const R* gw)
+{
+    if (!(d < a + b)) return R(0);
+    R br[12];
+    int nb = 0;
+    R lo, hi;
+    if (d == R(0)) {
+        lo = R(0); hi = a < b ? a : b;
+        br[nb++] = lo; br[nb++] = hi;
+        const R c2[2] = {R(0.5) * a, R(0.5) * b};
+        for (int k = 0; k < 2; ++k) if (c2[k] > lo && c2[k] < hi) br[nb++] = c2[k];
+    } else {
+        lo = d - b > R(0) ? d - b : R(0);
+        hi = a < d + b ? a : d + b;
+        if (!(hi > lo)) return R(0);
+        br[nb++] = lo; br[nb++] = hi;
+        const R c9[9] = {R(0.5) * a, a, d, d - R(0.5) * b, d + R(0.5) * b, d - b, d + b, R(0.5) * b - d, b - d};
+        for (int k = 0; k < 9; ++k) if (c9[k] > lo && c9[k] < hi) br[nb++] = c9[k];
+    }
+    for (int i = 1; i < nb; ++i) {                       // insertion sort of the breakpoints
+        const R v = br[i];
+        int j = i - 1;
+        while (j >= 0 && br[j] > v) { br[j + 1] = br[j]; --j; }
+        br[j + 1] = v;
+    }
+    const R ia = R(1) / a, ib = R(1) / b;
+    R acc = R(0);
+    for (int pc = 0; pc + 1 < nb; ++pc) {
+        const R m = R(0.5) * (br[pc] + br[pc + 1]), hw = R(0.5) * (br[pc + 1] - br[pc]);
+        if (!(hw > R(0))) continue;
+        R sum = R(0);
+        for (int g = 0; g < 8; ++g) {
+            const R r = m + hw * gx[g];
+            const R wa = spline_w1_q<R>(r * ia) * ia * ia * ia;
+            if (d == R(0)) {
+                sum += gw[g] * r * r * wa * spline_w1_q<R>(r * ib) * ib * ib * ib;
+            } else {
+                const R rd = r - d;
+                sum += gw[g] * r * wa * (spline_s1_q<R>((r + d) * ib) - spline_s1_q<R>((rd < R(0) ? -rd : rd) * ib)) * ib;
+            }
+        }
+        acc += hw * sum;
+    }
+    const R two_pi = R(2.0 * 3.14159265358979323846);
+    return d == R(0) ? R(2) * two_pi * acc : two_pi * acc / d;
 }
 
 // Lower bound of the squared distance from a point to a box (FP32, rounded down).

@@ -53,6 +53,7 @@ struct KnnParams {
     void* hprev;        // out: h per particle (next call's guess), NULL for neighbour lists
     int use_guess;      // P4.w holds each particle's previous kernel size
     float slack;        // guess bound = previous h * slack
+    int flush_node;     // pending keys per lane that trigger a merge before a node's tests
 };
 
 template <class R, bool NBR>
@@ -149,15 +150,26 @@ template <class K>
 __host__ __device__ constexpr int heap4_groups(int kcap) { return (kcap + 2) / 4 + 1; }
 
 // pending heap insertions per lane (a tile adds at most its masked candidates,
-// so the lists are merged before a tile that could overflow one), and the
-// pending count at which the lists are merged before a tree node's tests
+// so the lists are merged before a tile that could overflow one)
 constexpr int kPend = 32;
-// query groups of 32 / kGroups consecutive lanes whose boxes filter the candidates
-constexpr int kGroups = 4;
 static_assert(kPend >= kLeaf, "a tile can admit all of its candidates: one empty pending list must hold them");
-constexpr int kFlushNode = 16;
-// warm start: the search bound is the previous kernel size times this factor
-constexpr float kGuessSlack = 1.0625f;
+// Defaults of the launch knobs (sidm_config; none changes a result): query
+// groups of 32 / G consecutive lanes whose boxes filter the candidates,
+// independent distance chains in the candidate loop, the pending count at
+// which the lists are merged before a tree node's tests, and the warm-start
+// bound factor (previous kernel size times it)
+constexpr int kGroupsDefault = 4;
+// compacted candidate batches (knob knn_batch): candidates that pass the group
+// filter are appended to a per-warp buffer and the distance loop runs over
+// batches of kBatch of them; the buffer holds a batch's leftover (< kBatch)
+// plus one whole leaf
+constexpr int kBatch = 16;
+constexpr int kBufCap = kBatch + kLeaf;
+static_assert(kPend >= kBatch, "a batch can admit all of its candidates: one empty pending list must hold them");
+constexpr int kChainsDefault = 4;
+constexpr int kBatchDefault = 2;                   // 1: loop per staged leaf, 2: compacted batches
+constexpr int kFlushNodeDefault = 16;
+constexpr float kGuessSlackDefault = 1.0625f;
 
 template <class R>
 __device__ __forceinline__ float to_float_ru(R v)
@@ -170,31 +182,36 @@ __device__ __forceinline__ float to_float_ru(R v)
 // stack | heap groups | pending keys (the child boxes of a node live in
 // registers, one per lane); 14.1 KB at N_ngb = 64 in the mixed form, so 16
 // warps fit on an SM
-template <class R, class K>
+template <class R, class K, int G, bool BATCH = false>
 __host__ __device__ constexpr size_t knn_warp_bytes_t(int kcap)
 {
-    return (TileStageT<R, false, 1>::bytes() + 32 * 4 + kStack * 4 + 2 * kGroups * 16 +
+    // the batch buffer takes the place of the staged tile and its ids
+    return ((BATCH ? (size_t)kBufCap * sizeof(typename Vec4<R>::T) : TileStageT<R, false, 1>::bytes() + 32 * 4) +
+            kStack * 4 + 2 * G * 16 +
             (size_t)heap4_groups<K>(kcap) * 32 * 4 * sizeof(K) + (size_t)kPend * 32 * sizeof(K) + 15) / 16 * 16;
 }
 
 static_assert((TileStageT<float, false, 1>::bytes() + 32 * 4 + kStack * 4) % 16 == 0 &&
-                  (TileStageT<double, false, 1>::bytes() + 32 * 4 + kStack * 4) % 16 == 0,
+                  (TileStageT<double, false, 1>::bytes() + 32 * 4 + kStack * 4) % 16 == 0 &&
+                  (kBufCap * 16 + kStack * 4) % 16 == 0,
               "the heap groups are read as 16-byte vectors");
-static_assert(kGroups == 2 || kGroups == 4 || kGroups == 8, "lane groups are 16, 8 or 4 lanes");
-
-template <class R, bool NBR, bool TMA>
+template <class R, bool NBR, bool TMA, int G, int CH, bool BATCH>
 __global__ void k_knn(KnnParams p)
 {
+    static_assert(G == 2 || G == 4 || G == 8, "lane groups are 16, 8 or 4 lanes");
+    static_assert(CH == 4 || CH == 8, "four or eight independent distance chains");
+    static_assert(!(BATCH && TMA), "compacted batches read candidates straight into registers");
     using V = typename Vec4<R>::T;
     using K = typename KeyOf<R, NBR>::T;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    unsigned char* base = smem + wid * knn_warp_bytes_t<R, K>(p.kcap);
+    unsigned char* base = smem + wid * knn_warp_bytes_t<R, K, G, BATCH>(p.kcap);
     TileStageT<R, TMA, 1> stage(base);
+    V* bufv = (V*)base;                            // BATCH: [kBufCap] candidates (w: slot, or id with NBR)
     uint32_t* tids = (uint32_t*)(base + TileStageT<R, TMA, 1>::bytes());
-    int* stack = (int*)(tids + 32);
-    float4* gbox = (float4*)(stack + kStack);      // [kGroups][2]: box lo, hi of each lane group
-    K* heapg = (K*)(gbox + 2 * kGroups);           // 16-byte aligned: 528 + 128 + 4 kStack bytes in, + boxes
+    int* stack = BATCH ? (int*)(base + (size_t)kBufCap * sizeof(V)) : (int*)(tids + 32);
+    float4* gbox = (float4*)(stack + kStack);      // [G][2]: box lo, hi of each lane group
+    K* heapg = (K*)(gbox + 2 * G);                 // 16-byte aligned: 528 + 128 + 4 kStack bytes in, + boxes
     K* pend = heapg + (size_t)heap4_groups<K>(p.kcap) * 32 * 4;   // [kPend][32]
     const Heap4<K> hp{heapg, lane};
     stage.init(lane);
@@ -216,6 +233,10 @@ __global__ void k_knn(KnnParams p)
         const bool active = lane < countA;
         const HaloFrame fr = p.frame[h];
         const V q = ((const V*)p.P4)[(int64_t)leaf * kLeaf + lane];
+        // a buffered candidate's w holds its slot (its id with NBR), so the query
+        // recognises itself
+        const uint32_t own = NBR ? (BATCH && active ? p.ID[(int64_t)leaf * kLeaf + lane] : 0u)
+                                 : (uint32_t)leaf * kLeaf + lane;
         const float4 cA = p.cell[leaf];
         const float4 qlo = p.nlo[leaf], qhi = p.nhi[leaf];
         unsigned long long n_tiles = 0ull;
@@ -244,6 +265,7 @@ __global__ void k_knn(KnnParams p)
         int nfill = 0, np = 0;                         // heap fill level, pending keys
         bool heaped = false;
 
+        int nbuf = 0;                                  // BATCH: candidates in the buffer
         // merge the pending keys of every lane into its heap (each lane works
         // on its own heap column; no lane reads another's)
         auto flush = [&]() {
@@ -270,11 +292,11 @@ __global__ void k_knn(KnnParams p)
             pq = make_float3(__double2float_rn((double)q.x - fr.O[0]), __double2float_rn((double)q.y - fr.O[1]),
                              __double2float_rn((double)q.z - fr.O[2]));
         }
-        // boxes of the query points of each group of 32 / kGroups consecutive
+        // boxes of the query points of each group of 32 / G consecutive
         // lanes (shared memory): a candidate is kept if it lies within the
         // largest bound of some group's lanes from that group's box (the union is
         // tighter than the whole leaf's box; the mask stays warp-uniform)
-        constexpr int kGL = 32 / kGroups;
+        constexpr int kGL = 32 / G;
         {
             float lx = active ? pq.x : INFINITY, ly = active ? pq.y : INFINITY, lz = active ? pq.z : INFINITY;
             float ux = active ? pq.x : -INFINITY, uy = active ? pq.y : -INFINITY, uz = active ? pq.z : -INFINITY;
@@ -305,9 +327,69 @@ __global__ void k_knn(KnnParams p)
             if constexpr (TMA) return V{};
             else return ((const V*)p.P4)[(int64_t)(leaf0 + Bl) * kLeaf + lane];
         };
-        // r2: the lane's current bound (my_r2) as its caller computed it;
-        // craw: fetch(Bl) (unused on the bulk-copy path, which stages the leaf here)
-        auto process = [&](int Bl, bool mine, float r2, const V& craw) {
+        // the largest bound of each lane group (r2g) and of all lanes (r2all),
+        // from each lane's bound r2 (my_r2); an unbounded lane (its heap not yet
+        // full in the cold pass) counts as infinite
+        struct GroupBounds { float g[G]; float all; };
+        auto group_bounds = [&](float r2, bool mine) -> GroupBounds {
+            float lr2 = -1.f;
+            if (act && mine) lr2 = isnan(r2) ? INFINITY : r2;
+            for (int o = kGL / 2; o > 0; o >>= 1) lr2 = fmaxf(lr2, __shfl_xor_sync(0xffffffffu, lr2, o));
+            GroupBounds b;
+            b.all = -1.f;
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                b.g[g] = __shfl_sync(0xffffffffu, lr2, g * kGL);
+                b.all = fmaxf(b.all, b.g[g]);
+            }
+            return b;
+        };
+        // BATCH: the distances from every active query to the first nb buffered
+        // candidates (CH independent chains), admitted like the per-leaf loop
+        // below; the entries after them move to the front
+        auto run_batch = [&](int nb) {
+            if (__any_sync(0xffffffffu, np + nb > kPend)) flush();
+            __syncwarp();
+            if (act) {
+                n_cand += (unsigned long long)nb;
+                for (int t = 0; t < nb; t += CH) {
+                    K key[CH];
+                    bool ok[CH];
+#pragma unroll
+                    for (int u = 0; u < CH; ++u) {
+                        const int idx = t + u < nb ? t + u : t;
+                        const V cj = bufv[idx];
+                        const uint32_t who = sizeof(R) == 4 ? __float_as_uint((float)cj.w) : (uint32_t)(double)cj.w;
+                        const R dx = sub_rn(cj.x, q.x), dy = sub_rn(cj.y, q.y), dz = sub_rn(cj.z, q.z);
+                        const R d2 = fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
+                        key[u] = make_key<R, NBR>(d2, who);
+                        ok[u] = t + u < nb && who != own;
+                    }
+#pragma unroll
+                    for (int u = 0; u < CH; ++u) {
+                        if (ok[u] && key[u] < root) {
+                            if (nfill < k) hp.at(nfill++) = key[u];
+                            else pend[(np++) * 32 + lane] = key[u];
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+            const int rem = nbuf - nb;                 // < 32
+            V tmp{};
+            if (lane < rem) tmp = bufv[nb + lane];
+            __syncwarp();
+            if (lane < rem) bufv[lane] = tmp;
+            nbuf = rem;
+            __syncwarp();
+        };
+        auto drain = [&]() {
+            if constexpr (BATCH) { if (nbuf > 0) run_batch(nbuf); }
+        };
+        // mine: this lane's query reaches leaf Bl; gb: group_bounds of the lanes'
+        // bounds; craw: fetch(Bl) (unused on the bulk-copy path, which stages the
+        // leaf here)
+        auto process = [&](int Bl, bool mine, const GroupBounds& gb, const V& craw) {
             const int Bg = leaf0 + Bl;
             const int countB = (int)min((int64_t)kLeaf, nh - (int64_t)Bl * kLeaf);
             V c;
@@ -324,16 +406,7 @@ __global__ void k_knn(KnnParams p)
             // its lanes cannot enter one of their heaps: the loops skip the
             // candidates no group can reach (an unbounded lane, before its heap is
             // full in the cold pass, keeps them all)
-            float lr2 = -1.f;
-            if (act && mine) lr2 = isnan(r2) ? INFINITY : r2;
-            for (int o = kGL / 2; o > 0; o >>= 1) lr2 = fmaxf(lr2, __shfl_xor_sync(0xffffffffu, lr2, o));
-            float r2g[kGroups];
-            float r2all = -1.f;
-#pragma unroll
-            for (int g = 0; g < kGroups; ++g) {
-                r2g[g] = __shfl_sync(0xffffffffu, lr2, g * kGL);
-                r2all = fmaxf(r2all, r2g[g]);
-            }
+            const float r2all = gb.all;
             uint32_t cmask;
             if (!(r2all < INFINITY)) {
                 cmask = countB == kLeaf ? 0xffffffffu : ((1u << countB) - 1u);
@@ -347,12 +420,25 @@ __global__ void k_knn(KnnParams p)
                 }
                 bool reach = false;
 #pragma unroll
-                for (int g = 0; g < kGroups; ++g)
-                    reach = reach || (r2g[g] >= 0.f && point_gap2_rd(pc, gbox[2 * g], gbox[2 * g + 1]) <= r2g[g]);
+                for (int g = 0; g < G; ++g)
+                    reach = reach || (gb.g[g] >= 0.f && point_gap2_rd(pc, gbox[2 * g], gbox[2 * g + 1]) <= gb.g[g]);
                 cmask = __ballot_sync(0xffffffffu, lane < countB && reach);
             }
             ++n_tiles;
             if (cmask == 0u) return;                   // no candidate of this leaf can enter
+            if constexpr (BATCH) {
+                // append the candidates that pass to the buffer, in lane order
+                if ((cmask >> lane) & 1u) {
+                    V e = c;
+                    const uint32_t who = NBR ? p.ID[(int64_t)Bg * kLeaf + lane] : (uint32_t)Bg * kLeaf + lane;
+                    if constexpr (sizeof(R) == 4) e.w = __uint_as_float(who); else e.w = (R)who;
+                    bufv[nbuf + __popc(cmask & ((1u << lane) - 1u))] = e;
+                }
+                nbuf += __popc(cmask);
+                __syncwarp();
+                while (nbuf >= kBatch) run_batch(kBatch);
+                return;
+            }
             // room for this tile's candidates in every pending list
             if (__any_sync(0xffffffffu, np + __popc(cmask) > kPend)) flush();
             __syncwarp();
@@ -362,24 +448,24 @@ __global__ void k_knn(KnnParams p)
             __syncwarp();
             if (act && mine) {
                 n_cand += (unsigned long long)__popc(cmask);
-                // the masked candidates four at a time (independent distance
+                // the masked candidates CH at a time (independent distance
                 // chains); an admitted key fills the heap array (unsorted, heapified
                 // at the next merge) until it holds k keys, then waits in the
                 // pending list, for which room was made before the tile
                 for (uint32_t mm = cmask; mm;) {
-                    int t[4];
+                    int t[CH];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) { t[u] = __ffs(mm) - 1; mm &= mm - 1u; }   // -1: none left
-                    K key[4];
+                    for (int u = 0; u < CH; ++u) { t[u] = __ffs(mm) - 1; mm &= mm - 1u; }   // -1: none left
+                    K key[CH];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
+                    for (int u = 0; u < CH; ++u) {
                         const V cj = sh[t[u] >= 0 ? t[u] : t[0]];
                         const R dx = sub_rn(cj.x, q.x), dy = sub_rn(cj.y, q.y), dz = sub_rn(cj.z, q.z);
                         const R d2 = fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
                         key[u] = make_key<R, NBR>(d2, NBR ? tids[t[u] >= 0 ? t[u] : t[0]] : 0u);
                     }
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
+                    for (int u = 0; u < CH; ++u) {
                         if (t[u] >= 0 && key[u] < root && !(Bl == A && t[u] == lane)) {
                             if (nfill < k) hp.at(nfill++) = key[u];
                             else pend[(np++) * 32 + lane] = key[u];
@@ -401,7 +487,8 @@ __global__ void k_knn(KnnParams p)
             }
             // the window holds at least k other particles, so every lane's heap is
             // full after it: order it and merge the window's keys beyond the first k
-            for (int Bl = wlo; Bl <= whi; ++Bl) process(Bl, true, my_r2(), fetch(Bl));
+            for (int Bl = wlo; Bl <= whi; ++Bl) process(Bl, true, group_bounds(my_r2(), true), fetch(Bl));
+            drain();
             flush();
         }
 
@@ -455,7 +542,7 @@ __global__ void k_knn(KnnParams p)
         auto visit_leaf = [&](int Bl, int c) {
             const float r2 = my_r2();
             const bool mine = near_child(c, r2);
-            if (__any_sync(0xffffffffu, mine)) process(Bl, mine, r2, fetch(Bl));
+            if (__any_sync(0xffffffffu, mine)) process(Bl, mine, group_bounds(r2, mine), fetch(Bl));
         };
         // Accepted children are visited nearest first (box gap to the query leaf),
         // so the k-th bound shrinks early.  rank = position among the accepted.
@@ -475,18 +562,22 @@ __global__ void k_knn(KnnParams p)
             if (acc == 0u) return;
             if (pass == 0) {
                 // index order; the next accepted leaf is fetched before this one is
-                // processed, so its load overlaps this leaf's candidate loop
+                // processed, so its load overlaps this leaf's candidate loop.  Every
+                // leaf of the node reuses the lanes' node-test bounds, so the group
+                // bounds of a lane set are formed once per node (a lane whose query
+                // misses a leaf only widens the mask, never narrows it)
                 uint32_t m = acc;
                 int c = __ffs(m) - 1;
                 m &= m - 1u;
                 V cur = fetch(first_local + c);
+                const GroupBounds gb = group_bounds(node_r2, lane_bits != 0u);
                 while (true) {
                     const int cn = __ffs(m) - 1;       // -1: none left
                     m &= m - 1u;
                     V nxt{};
                     if (cn >= 0) nxt = fetch(first_local + cn);
                     const bool mine = (lane_bits >> c) & 1u;
-                    if (__any_sync(0xffffffffu, mine)) process(first_local + c, mine, node_r2, cur);
+                    if (__any_sync(0xffffffffu, mine)) process(first_local + c, mine, gb, cur);
                     if (cn < 0) break;
                     c = cn;
                     cur = nxt;
@@ -532,12 +623,13 @@ __global__ void k_knn(KnnParams p)
             const int first = idx * kArity;
             const int nch = min(kArity, cc - first);
             // tighten the bounds before the node tests once enough keys wait
-            if (__any_sync(0xffffffffu, np >= kFlushNode)) flush();
+            if (__any_sync(0xffffffffu, np >= p.flush_node)) flush();
             load_boxes(cb + first, nch);
             const uint32_t acc = accept(nch, my_r2(), cl == 0 ? window_mask(first, nch) : 0u);
             if (cl == 0) visit_leaves_in_order(acc, nch, first);
             else if (!push_in_order(acc, nch, cl, first, sp)) failed = true;
         }
+        drain();
         flush();
         if (act && heaped) { result = root; todo = false; }
         if (pass == 0 && act && todo) ++n_redo;
@@ -584,7 +676,7 @@ __global__ void k_knn(KnnParams p)
     stage.finish(lane, p.cnt);
 }
 
-template <class R, bool NBR, bool TMA>
+template <class R, bool NBR, bool TMA, int G, int CH, bool BATCH = false>
 int launch_t(sidm_ctx* c, void* h_out, uint32_t* nbr, int k_stride, bool use_guess, cudaStream_t s)
 {
     using K = typename KeyOf<R, NBR>::T;
@@ -598,13 +690,14 @@ int launch_t(sidm_ctx* c, void* h_out, uint32_t* nbr, int k_stride, bool use_gue
     p.work_slot = 0;
     p.hprev = NBR ? nullptr : c->d_hprev;
     p.use_guess = use_guess ? 1 : 0;
-    p.slack = kGuessSlack;
+    p.slack = c->cfg.knn_slack > 0.f ? c->cfg.knn_slack : kGuessSlackDefault;
+    p.flush_node = c->cfg.knn_flush > 0 ? c->cfg.knn_flush : kFlushNodeDefault;
     // warps per CTA: at most the configured number, and of those the one with
     // the most resident warps per SM (with large N_ngb the per-warp heaps make
     // two small CTAs hold more warps than one large one); a CTA may use at most
     // 227 KB of shared memory
-    auto kern = k_knn<R, NBR, TMA>;
-    const size_t per_warp = knn_warp_bytes_t<R, K>(p.kcap);
+    auto kern = k_knn<R, NBR, TMA, G, CH, BATCH>;
+    const size_t per_warp = knn_warp_bytes_t<R, K, G, BATCH>(p.kcap);
     int warps = 0, occ = 0;
     for (int w = c->knn_warps; w >= 1; --w) {
         if ((size_t)w * per_warp > (size_t)227 * 1024) continue;
@@ -630,21 +723,38 @@ int launch_t(sidm_ctx* c, void* h_out, uint32_t* nbr, int k_stride, bool use_gue
     return SIDM_OK;
 }
 
+// the plain-load kernel-size search with the configured lane groups, chains
+// and candidate loop (per staged leaf, or compacted batches)
+template <class R>
+int launch_tuned(sidm_ctx* c, void* h_out, bool use_guess, cudaStream_t s)
+{
+    const int g = c->cfg.knn_groups > 0 ? c->cfg.knn_groups : kGroupsDefault;
+    const int ch = c->cfg.knn_chains > 0 ? c->cfg.knn_chains : kChainsDefault;
+    const bool batch = (c->cfg.knn_batch > 0 ? c->cfg.knn_batch : kBatchDefault) == 2;
+#define SIDM_KNN_CASE(GG, CC, BB) \
+    if (g == GG && ch == CC && batch == BB) return launch_t<R, false, false, GG, CC, BB>(c, h_out, nullptr, 0, use_guess, s);
+    SIDM_KNN_CASE(2, 4, false) SIDM_KNN_CASE(4, 4, false) SIDM_KNN_CASE(8, 4, false) SIDM_KNN_CASE(4, 8, false)
+    SIDM_KNN_CASE(2, 4, true) SIDM_KNN_CASE(4, 4, true) SIDM_KNN_CASE(8, 4, true) SIDM_KNN_CASE(4, 8, true)
+#undef SIDM_KNN_CASE
+    return set_err(c, SIDM_EINVAL, "knn_chains 8 takes knn_groups 4");
+}
+
 }  // namespace
 
 int launch_knn(sidm_ctx* c, void* h_out, uint32_t* nbr, int k_stride, bool use_guess, cudaStream_t s)
 {
     if (c->lay.L == 0) return SIDM_OK;
     const bool tma = c->cfg.use_tma != 0;
+    constexpr int G = kGroupsDefault, CH = kChainsDefault;   // neighbour lists and bulk copies: defaults
     if (c->cfg.precision == SIDM_FP64) {
         if (nbr) return set_err(c, SIDM_EINVAL, "neighbour lists: mixed form only");
-        return tma ? launch_t<double, false, true>(c, h_out, nullptr, 0, use_guess, s)
-                   : launch_t<double, false, false>(c, h_out, nullptr, 0, use_guess, s);
+        return tma ? launch_t<double, false, true, G, CH>(c, h_out, nullptr, 0, use_guess, s)
+                   : launch_tuned<double>(c, h_out, use_guess, s);
     }
-    if (nbr) return tma ? launch_t<float, true, true>(c, nullptr, nbr, k_stride, false, s)
-                        : launch_t<float, true, false>(c, nullptr, nbr, k_stride, false, s);
-    return tma ? launch_t<float, false, true>(c, h_out, nullptr, 0, use_guess, s)
-               : launch_t<float, false, false>(c, h_out, nullptr, 0, use_guess, s);
+    if (nbr) return tma ? launch_t<float, true, true, G, CH>(c, nullptr, nbr, k_stride, false, s)
+                        : launch_t<float, true, false, G, CH>(c, nullptr, nbr, k_stride, false, s);
+    return tma ? launch_t<float, false, true, G, CH>(c, h_out, nullptr, 0, use_guess, s)
+               : launch_tuned<float>(c, h_out, use_guess, s);
 }
 
 }  // namespace sidm

@@ -52,6 +52,8 @@ struct PairParams {
     int64_t nacc;
     DevCounters* cnt;
     sidm_step_stats* st;
+    double* evg;        // forward-dominated halos: G = m_j Lambda dt of each record (NULL: none allowed)
+    double glx[8], glw[8];  // 8-point Gauss-Legendre rule on [-1, 1] (Lambda by quadrature)
 };
 
 // what one traversal of the in-range pairs computes
@@ -71,12 +73,12 @@ __device__ __forceinline__ R spline_w(R d, R h)
     return norm * R(2) * t * t * t;
 }
 
-// pairs a lane queues per round (swept on the GB300: 1, 2, 3, 4 -> 3.76, 3.64,
-// 3.49, 3.47 ms), and the queue entries per warp, a power of two: a round adds
-// up to 32 kPerRound pairs to fewer than 32 waiting
-constexpr int kPerRound = 4;
-constexpr int kQueue = 32 * (kPerRound + 1) <= 64 ? 64 : 32 * (kPerRound + 1) <= 128 ? 128 : 256;
-static_assert(kQueue >= 32 * (kPerRound + 1), "one round must fit behind the entries still waiting");
+// pairs a lane queues per round, at most (a launch knob; swept on the GB300:
+// 1, 2, 3, 4 -> 3.76, 3.64, 3.49, 3.47 ms), and the queue entries per warp, a
+// power of two: a round adds up to 32 kPerRoundMax pairs to fewer than 32 waiting
+constexpr int kPerRoundMax = 4;
+constexpr int kQueue = 32 * (kPerRoundMax + 1) <= 64 ? 64 : 32 * (kPerRoundMax + 1) <= 128 ? 128 : 256;
+static_assert(kQueue >= 32 * (kPerRoundMax + 1), "one round must fit behind the entries still waiting");
 
 template <class R>
 __device__ __forceinline__ uint32_t id_of(R w)
@@ -119,9 +121,10 @@ constexpr size_t pair_warp_bytes()
 // value, and since FP32/FP64 products round monotonically P <= P_up for the P
 // that would have been formed, so a draw u >= P_up + 2e-6 decides "no event"
 // and "not within 1e-6 of P" exactly as the full evaluation would.
-template <class R, bool TMA, int MODE>
+template <class R, bool TMA, int MODE, int PR, bool DRAG>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParams p)
 {
+    static_assert(PR >= 1 && PR <= kPerRoundMax, "pairs per round");
     using V = typename Vec4<R>::T;
     using Stage = TileStageT<R, TMA>;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -163,6 +166,13 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
         const float4 cA = p.cell[leaf];
         const sidm_xs xs = p.xs[h];
         const int kind = xs.kind;
+        // forward-dominated halo: every in-range pair becomes a record (no draw);
+        // only the instantiation for contexts with SIDM_FLAG_DRAG has room for them
+        const bool drag = DRAG && MODE != kModeDiag && xs.angular != 0;
+        if (!DRAG && MODE != kModeDiag && xs.angular != 0) {
+            if (lane == 0) raise_status(p.cnt, SIDM_DEV_BAD_INPUT);
+            continue;
+        }
         const R pref = p.bins ? R(0) : (R)xs.s0 * (R)p.mass[h] * (R)p.dt[h];
         const R inv_w = kind == 1 ? R(1) / (R)xs.w : R(0);
         const float4 qlo = p.nlo[leaf], qhi = p.nhi[leaf];
@@ -268,9 +278,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
                     need = true;
                 } else {
                     const R P_up = pre * (R(kLamFUp) * inv * inv * inv);
-                    need = !(u >= P_up + R(2e-6));
+                    need = drag || !(u >= P_up + R(2e-6));
                 }
                 P = R(0);
+                R gfac = R(0);
                 bool fire = false;
                 if (need) {
                     ++n_lam;
@@ -283,10 +294,29 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
                         f = lambda_f<R>(T, sqrt_rn(d2), hi, hj);
                     }
                     P = pre * (f * inv * inv * inv);
-                    if constexpr (sizeof(R) == 4) fire = P >= R(1) || x.x[0] < (uint32_t)ceilf((float)P * 0x1p32f);
-                    else fire = u < P;
-                    if (P > R(1)) ++n_gt1;
-                    if (fabs(P - u) < R(1e-6)) ++n_near;
+                    if (drag) {
+                        // the record keeps G = m_j Lambda dt; D = P / 3 at the step start.
+                        // The turn's sine is the square root of a multiple of Lambda, so
+                        // Lambda must be accurate relative to itself where it falls to
+                        // zero, which neither the table nor an FP32 quadrature (its
+                        // integrand cancels there) is: FP64 quadrature beyond half the
+                        // support (everywhere in the FP64 form), the table inside, where
+                        // Lambda > Lambda(0)/4 bounds its relative error
+                        R lam = f * inv * inv * inv;
+                        const R d2q = pair_d2(si, sj, P4[si], P4[sj]);
+                        const R dq = sqrt_rn(d2q);
+                        if (sizeof(R) == 8 || dq >= R(0.5) * (hi + hj))
+                            lam = (R)lambda_quad<double>((double)dq, (double)hi, (double)hj, p.glx, p.glw);
+                        fire = true;
+                        P = pre * lam;
+                        gfac = (R)p.mass[h] * lam * (p.bins ? (R)ldexp(p.dt_max, -bmin) : (R)p.dt[h]);
+                        if (P > R(3)) ++n_gt1;
+                    } else {
+                        if constexpr (sizeof(R) == 4) fire = P >= R(1) || x.x[0] < (uint32_t)ceilf((float)P * 0x1p32f);
+                        else fire = u < P;
+                        if (P > R(1)) ++n_gt1;
+                        if (fabs(P - u) < R(1e-6)) ++n_near;
+                    }
                 }
                 const int64_t ui = slot2u + si, uj = slot2u + sj;
                 if constexpr (MODE == kModeDrawExact) {
@@ -309,6 +339,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
                         E.P = (float)P;
                         E.x0 = x.x[0];
                         p.ev[slot] = E;
+                        if (drag) p.evg[slot] = (double)gfac;
                     }
                 }
             }
@@ -391,18 +422,18 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
             const uint32_t own = by_cand ? slotB + lane : slotA;
             const uint32_t base = by_cand ? (uint32_t)leaf * kLeaf : slotB;
             // (ii) queue the pairs in rounds: every lane with pairs left adds up to
-            //      kPerRound, after the entries of the lanes below it
+            //      PR, after the entries of the lanes below it
             for (uint32_t m = __ballot_sync(0xffffffffu, okm != 0u); m; m = __ballot_sync(0xffffffffu, okm != 0u)) {
                 const int cnt = __popc(okm);
                 int e = qhead + qn + __popc(m & lt);
                 int c2 = __popc(m);
 #pragma unroll
-                for (int k = 2; k <= kPerRound; ++k) {
+                for (int k = 2; k <= PR; ++k) {
                     const uint32_t mk = __ballot_sync(0xffffffffu, cnt >= k);
                     e += __popc(mk & lt);
                     c2 += __popc(mk);
                 }
-                const int take = min(cnt, kPerRound);
+                const int take = min(cnt, PR);
                 for (int k = 0; k < take; ++k, ++e) {
                     const int t = __ffs(okm) - 1;
                     okm &= okm - 1u;
@@ -546,7 +577,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
     st_pos.finish(lane, p.cnt);
 }
 
-template <class R, bool TMA, int MODE>
+template <class R, bool TMA, int MODE, int PR = kPerRoundMax, bool DRAG = false>
 int launch_t(sidm_ctx* c, uint64_t seed, uint64_t step, const sidm_xs* xs, const double* dt, const double* mass,
              sidm_step_stats* st, cudaStream_t s)
 {
@@ -567,9 +598,11 @@ int launch_t(sidm_ctx* c, uint64_t seed, uint64_t step, const sidm_xs* xs, const
     p.dacc = c->d_dacc; p.nacc = L.N;
     p.bins = c->step_bins; p.n_bins = c->step_nbins; p.substep = c->step_sub; p.dt_max = c->step_dtmax;
     p.cnt = c->d_cnt; p.st = st;
+    p.evg = c->d_evg;
+    for (int g = 0; g < 8; ++g) { p.glx[g] = c->gl8x[g]; p.glw[g] = c->gl8w[g]; }
     const int warps = c->pair_warps;
     const size_t smem = (size_t)warps * pair_warp_bytes<R, TMA>();
-    auto kern = k_pairs<R, TMA, MODE>;
+    auto kern = k_pairs<R, TMA, MODE, PR, DRAG>;
     int occ = 0;
     int rc = occupancy(c, (const void*)kern, warps * 32, smem, &occ);
     if (rc) return rc;
@@ -597,14 +630,30 @@ int launch_pairs(sidm_ctx* c, uint64_t seed, uint64_t step, const sidm_xs* xs, c
     if (c->lay.L == 0) return SIDM_OK;
     const bool tma = c->cfg.use_tma != 0;
     const bool exact = (c->cfg.flags & SIDM_FLAG_SUM_P) != 0;
+    if (c->cfg.flags & SIDM_FLAG_DRAG) {                // forward-dominated halos allowed (plain loads)
+        if (c->cfg.precision == SIDM_FP64)
+            return exact ? launch_t<double, false, kModeDrawExact, kPerRoundMax, true>(c, seed, step, xs, dt, mass, st, s)
+                         : launch_t<double, false, kModeDraw, kPerRoundMax, true>(c, seed, step, xs, dt, mass, st, s);
+        return exact ? launch_t<float, false, kModeDrawExact, kPerRoundMax, true>(c, seed, step, xs, dt, mass, st, s)
+                     : launch_t<float, false, kModeDraw, kPerRoundMax, true>(c, seed, step, xs, dt, mass, st, s);
+    }
 #define SIDM_PAIRS_DISPATCH(R)                                                                                   \
     if (exact) return tma ? launch_t<R, true, kModeDrawExact>(c, seed, step, xs, dt, mass, st, s)                \
                           : launch_t<R, false, kModeDrawExact>(c, seed, step, xs, dt, mass, st, s);              \
-    return tma ? launch_t<R, true, kModeDraw>(c, seed, step, xs, dt, mass, st, s)                                \
-               : launch_t<R, false, kModeDraw>(c, seed, step, xs, dt, mass, st, s);
-    if (c->cfg.precision == SIDM_FP64) { SIDM_PAIRS_DISPATCH(double) }
+    if (tma) return launch_t<R, true, kModeDraw>(c, seed, step, xs, dt, mass, st, s);
+    if (c->cfg.precision == SIDM_FP64) {
+        SIDM_PAIRS_DISPATCH(double)
+        return launch_t<double, false, kModeDraw>(c, seed, step, xs, dt, mass, st, s);
+    }
     SIDM_PAIRS_DISPATCH(float)
 #undef SIDM_PAIRS_DISPATCH
+    // the hot path: pairs queued per lane and round as configured (a launch knob)
+    switch (c->cfg.pair_per_round > 0 ? c->cfg.pair_per_round : kPerRoundMax) {
+    case 1: return launch_t<float, false, kModeDraw, 1>(c, seed, step, xs, dt, mass, st, s);
+    case 2: return launch_t<float, false, kModeDraw, 2>(c, seed, step, xs, dt, mass, st, s);
+    case 3: return launch_t<float, false, kModeDraw, 3>(c, seed, step, xs, dt, mass, st, s);
+    default: return launch_t<float, false, kModeDraw, 4>(c, seed, step, xs, dt, mass, st, s);
+    }
 }
 
 int launch_pairs_diag(sidm_ctx* c, const sidm_xs* xs, const double* mass, cudaStream_t s)

@@ -24,10 +24,11 @@ SIDM_DEV_EVENT_OVERFLOW, SIDM_DEV_ROUNDS, SIDM_DEV_STACK, SIDM_DEV_BAD_INPUT, SI
 SIDM_MIXED, SIDM_FP64 = 0, 1
 SIDM_FLAG_SUM_P = 1
 SIDM_FLAG_LOCAL_DIAG = 4
+SIDM_FLAG_DRAG = 8
 SIDM_FLAG_TIMING = 2
 SIDM_STATIC_MAX_HALOS, SIDM_STATIC_MAX_CHUNKS = 64, 4096
 
-XS_DTYPE = np.dtype([("kind", "<i4"), ("pad", "<i4"), ("s0", "<f8"), ("w", "<f8")])
+XS_DTYPE = np.dtype([("kind", "<i4"), ("angular", "<i4"), ("s0", "<f8"), ("w", "<f8")])
 STATS_DTYPE = np.dtype([("n_pairs", "<u8"), ("n_events", "<u8"), ("n_p_gt1", "<u8"), ("n_near", "<u8"),
                         ("n_multi", "<u8"), ("rounds", "<u4"), ("status", "<u4"), ("d_energy", "<f8"),
                         ("max_sum_p", "<f4"), ("pad", "<f4"), ("n_tested", "<u8")])
@@ -40,7 +41,9 @@ class SidmConfig(C.Structure):
     _fields_ = [("n_max", C.c_int64), ("halo_max", C.c_int32), ("ngb_max", C.c_int32),
                 ("event_cap", C.c_int64), ("precision", C.c_int32), ("device", C.c_int32),
                 ("knn_warps", C.c_int32), ("pair_warps", C.c_int32), ("max_rounds", C.c_int32),
-                ("flags", C.c_int32), ("grid_ctas", C.c_int32), ("use_tma", C.c_int32)]
+                ("flags", C.c_int32), ("grid_ctas", C.c_int32), ("use_tma", C.c_int32),
+                ("knn_groups", C.c_int32), ("knn_chains", C.c_int32), ("knn_flush", C.c_int32),
+                ("knn_slack", C.c_float), ("pair_per_round", C.c_int32), ("knn_batch", C.c_int32)]
 
 
 class SidmHost(C.Structure):
@@ -319,7 +322,8 @@ class Context:
     """One libsidm context on one device, plus device copies of per-halo parameters."""
 
     def __init__(self, n_max, halo_max=1, ngb_max=64, event_cap=None, precision="mixed", device=0,
-                 knn_warps=0, pair_warps=0, max_rounds=0, flags=0, grid_ctas=0, use_tma=0):
+                 knn_warps=0, pair_warps=0, max_rounds=0, flags=0, grid_ctas=0, use_tma=0,
+                 knn_groups=0, knn_chains=0, knn_flush=0, knn_slack=0.0, pair_per_round=0, knn_batch=0):
         torch = _torch()
         self.torch = torch
         self.precision = SIDM_FP64 if precision in ("fp64", SIDM_FP64) else SIDM_MIXED
@@ -329,7 +333,9 @@ class Context:
                          event_cap=int(event_cap if event_cap is not None else max(4096, n_max // 4)),
                          precision=self.precision, device=int(device), knn_warps=int(knn_warps),
                          pair_warps=int(pair_warps), max_rounds=int(max_rounds), flags=int(flags),
-                         grid_ctas=int(grid_ctas), use_tma=int(use_tma))
+                         grid_ctas=int(grid_ctas), use_tma=int(use_tma), knn_groups=int(knn_groups),
+                         knn_chains=int(knn_chains), knn_flush=int(knn_flush), knn_slack=float(knn_slack),
+                         pair_per_round=int(pair_per_round), knn_batch=int(knn_batch))
         self.cfg = cfg
         self.handle = sidm_create(cfg)
         self.stats_buf = torch.zeros(STATS_DTYPE.itemsize, dtype=torch.uint8, device=self.device)
@@ -346,9 +352,11 @@ class Context:
             pass
 
     def xs_tensor(self, xs_list):
+        """Device sidm_xs array from (kind, s0, w) or (kind, s0, w, angular) tuples."""
         a = np.zeros(len(xs_list), XS_DTYPE)
-        for i, (kind, s0, w) in enumerate(xs_list):
-            a[i] = (int(kind), 0, float(s0), float(w))
+        for i, xs in enumerate(xs_list):
+            kind, s0, w = xs[:3]
+            a[i] = (int(kind), int(xs[3]) if len(xs) > 3 else 0, float(s0), float(w))
         return self.torch.from_numpy(np.frombuffer(a.tobytes(), np.uint8).copy()).to(self.device)
 
     def f64(self, values):

@@ -162,6 +162,48 @@ def test_launch_shape_invariance():
         assert np.array_equal(g["vel"], ref["vel"])
 
 
+def _two_steps(b, ks, xs, dts, precision, kw):
+    """A cold step, a drift and a warm-started step on cuda:0; state after each."""
+    from paper_2506_06269_gb300 import sidm
+    ctx = sidm.Context(n_max=b.n, halo_max=b.n_halos, ngb_max=max(ks), precision=precision, event_cap=1 << 16, **kw)
+    pos = torch.tensor(b.pos, device="cuda")
+    vin = b.vel.astype(np.float32) if precision == "mixed" else b.vel
+    vel = torch.tensor(vin, dtype=ctx.vdtype, device="cuda")
+    ids = torch.tensor(b.ids.astype(np.int64), device="cuda").to(torch.int32)
+    h = torch.zeros(b.n, dtype=ctx.vdtype, device="cuda")
+    x, dt, m = ctx.xs_tensor(xs), ctx.f64(dts), ctx.f64(b.mass)
+    out = []
+    for step in range(2):
+        if step:
+            ctx.drift(dt, pos, vel)
+        ctx.build_cells(b.offsets, pos, vel, ids)
+        ctx.kernel_sizes(ks, h)
+        ctx.scatter_step(31, step, x, dt, m, vel)
+        assert ctx.status() == 0
+        out.append((h.cpu().numpy().copy(), vel.cpu().numpy().copy(), np.sort(ctx.events()[1]["key"])))
+    ctx.close()
+    return out
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_launch_knobs_give_identical_bits(precision):
+    # every launch knob of sidm_config (lane groups, chains and candidate loop
+    # of the kernel-size search, its merge threshold and warm-start bound, pairs
+    # queued per round, bulk copies) changes work, never a result: cold and
+    # warm-started steps
+    b = ics.batch([ics.nfw(6000, 21), ics.hernquist(2500, 22), ics.uniform_box(700, 23)])
+    ks, xs, dts = [64, 16, 128], [(1, 100.0, 0.3811), (0, 10.0, 1.0), (0, 5.0, 1.0)], [0.2, 0.05, 0.01]
+    ref = _two_steps(b, ks, xs, dts, precision, {})
+    for kw in (dict(knn_groups=2), dict(knn_groups=8), dict(knn_chains=8), dict(knn_flush=1),
+               dict(knn_flush=32, knn_slack=1.001), dict(knn_slack=2.0), dict(pair_per_round=1),
+               dict(pair_per_round=3, knn_groups=8), dict(knn_batch=1), dict(knn_batch=1, knn_groups=2, knn_flush=4),
+               dict(knn_batch=1, knn_chains=8, knn_slack=1.3), dict(knn_groups=2, knn_flush=4, pair_warps=3),
+               dict(use_tma=1)):
+        got = _two_steps(b, ks, xs, dts, precision, kw)
+        for (h0, v0, e0), (h1, v1, e1) in zip(ref, got):
+            assert np.array_equal(h0, h1) and np.array_equal(v0, v1) and np.array_equal(e0, e1), kw
+
+
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
 def test_launch_shape_invariance_large_ngb(precision):
     # N_ngb = 128: the kernel-size launch picks the CTA size with the most

@@ -16,9 +16,9 @@ What pins it, other than its own formulas:
     output velocities, must give (3/2) sin^2 alpha = P (1 - P/6) with P the
     isotropic collision probability (sigma_V/m) m_j |u| Lambda dt -- equal to
     first order in P;
-  - the drag: averaged over the azimuth, u' = (1 - D) u, and the turn is
-    isotropic about u in any orthonormal frame of the normal plane (the test
-    builds its own frame, not the oracle's);
+  - the drag: averaged over the random direction, u' = (1 - D) u, and the
+    turn is isotropic about u in any orthonormal frame of the normal plane
+    (the test builds its own frame);
   - the closed-form rate: in a uniform Maxwellian box the summed l = 2
     relaxation per particle and unit time equals the isotropic collision
     rate rho (sigma_V/m) 4 sigma_v / sqrt(pi);
@@ -110,6 +110,7 @@ def test_drag_mean_change_and_azimuthal_isotropy():
     rec = np.zeros(copies, O.EVENT_DTYPE)
     rec["i"] = np.arange(copies) * 2; rec["j"] = rec["i"] + 1
     rec["key"] = np.arange(copies); rec["P"] = G; rec["u"] = -1.0
+    rec["x1"] = rng.integers(0, 2 ** 32, copies, dtype=np.uint64).astype(np.uint32)
     rec["x2"] = rng.integers(0, 2 ** 32, copies, dtype=np.uint64).astype(np.uint32)
     v1, _, D = O.apply_drag(rec, np.ones(2 * copies), (0, s0, 1.0), vel)
     up = v1[:, 0::2] - v1[:, 1::2]
