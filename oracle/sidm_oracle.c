@@ -48,9 +48,10 @@
  *              that limit at the given viscosity cross-section sigma_V
  *              (App. A: sigma_V = (3/2) int sin^2 dsigma, sigma_T =
  *              int (1 - cos) dsigma, both (1/2) int theta^2 dsigma at small
- *              angles), about the azimuth phi = 2 pi u_2 in the orthonormal
- *              basis (b1, b2) of u's normal plane of Duff et al. (2017); |u|
- *              and v_cm are kept (energy and momentum conserved).  The mean
+ *              angles), towards the projection onto u's normal plane of the
+ *              isotropic Philox direction w (cos(theta) = 2 u_1 - 1,
+ *              phi = 2 pi u_2), whose azimuth about u is uniform; |u| and
+ *              v_cm are kept (energy and momentum conserved).  The mean
  *              change of u is the drag -D u; pairs are applied in ascending
  *              key order from the current velocities, with Lambda_ij, m_j and
  *              dt of the step start.
@@ -872,19 +873,6 @@ void orc_apply_events(const orc_event* ev, int64_t n_ev, const double* m,
     }
 }
 
-/* Orthonormal basis (b1, b2) of the plane normal to the unit vector n, from
- * Duff et al. (2017), "Building an orthonormal basis, revisited" (JCGT 6):
- * s = sign(n_z) (+1 for +0), a = -1/(s + n_z), b = n_x n_y a,
- * b1 = (1 + s n_x^2 a, s b, -s n_x), b2 = (b, s + n_y^2 a, -n_y). */
-static void orc_normal_basis(const double n[3], double b1[3], double b2[3])
-{
-    const double sg = signbit(n[2]) ? -1.0 : 1.0;
-    const double a = -1.0 / (sg + n[2]);
-    const double b = n[0] * n[1] * a;
-    b1[0] = 1.0 + sg * n[0] * n[0] * a; b1[1] = sg * b; b1[2] = -sg * n[0];
-    b2[0] = b; b2[1] = sg + n[1] * n[1] * a; b2[2] = -n[1];
-}
-
 /* Forward-dominated (frictional) scattering of key-sorted pair records, one
  * after another from the current FP64 velocities (reading in the header).
  * ev[e].P holds G = m_j Lambda_ij dt of the step start; kind, s0, w give
@@ -911,12 +899,19 @@ void orc_apply_drag(const orc_event* ev, int64_t n_ev, const double* m, int kind
         if (!(D > 0.0)) continue;               /* no turn (zero cross-section or equal velocities) */
         double ca = 1.0 - D, sa = D < 2.0 ? sqrt(D * (2.0 - D)) : 0.0;
         if (D >= 2.0) ca = -1.0;
-        double up[3];
-        double nh[3] = {u[0] / un, u[1] / un, u[2] / un}, b1[3], b2[3];
-        orc_normal_basis(nh, b1, b2);
+        /* the turn's direction: an isotropic unit vector w (cos(theta) = 2 u_1 - 1,
+         * phi = 2 pi u_2) projected onto the plane normal to u, normalised */
+        double ct = 2.0 * ldexp((double)ev[e].x1, -32) - 1.0;
+        double st = sqrt(fmax(0.0, 1.0 - ct * ct));
         double phi = 2.0 * ORC_PI * ldexp((double)ev[e].x2, -32);
-        double cp = cos(phi), sp = sin(phi);
-        for (int a = 0; a < 3; ++a) up[a] = ca * u[a] + un * sa * (cp * b1[a] + sp * b2[a]);
+        double wv[3] = {st * cos(phi), st * sin(phi), ct};
+        double nh[3] = {u[0] / un, u[1] / un, u[2] / un};
+        double wn = wv[0] * nh[0] + wv[1] * nh[1] + wv[2] * nh[2];
+        double ep[3], el = 0.0;
+        for (int a = 0; a < 3; ++a) { ep[a] = wv[a] - wn * nh[a]; el += ep[a] * ep[a]; }
+        el = sqrt(el);
+        double up[3];
+        for (int a = 0; a < 3; ++a) up[a] = ca * u[a] + (el > 0.0 ? un * sa * ep[a] / el : 0.0);
         double e0 = 0.5 * mi * (vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2])
                   + 0.5 * mj * (vj[0] * vj[0] + vj[1] * vj[1] + vj[2] * vj[2]);
         double ni[3], nj[3];
