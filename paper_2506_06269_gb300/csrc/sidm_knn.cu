@@ -321,11 +321,15 @@ __global__ void k_knn(KnnParams p)
             r = __fadd_ru(__fmul_ru(r, 1.0f + 0x1p-20f), fr.margin);
             return __fmul_ru(r, r);
         };
-        // this lane's entry of candidate leaf Bl (the plain path loads it straight
-        // into a register, so a caller can fetch the next leaf early)
-        auto fetch = [&](int Bl) -> V {
-            if constexpr (TMA) return V{};
-            else return ((const V*)p.P4)[(int64_t)(leaf0 + Bl) * kLeaf + lane];
+        // this lane's entry of candidate leaf Bl and the leaf's frame origin (the
+        // plain path loads both straight into registers, so a caller can fetch
+        // the next leaf early; the shift needs the origin as soon as the entry)
+        struct Fetched { V c; float4 cell; };
+        auto fetch = [&](int Bl) -> Fetched {
+            Fetched f{};
+            if constexpr (!TMA) f.c = ((const V*)p.P4)[(int64_t)(leaf0 + Bl) * kLeaf + lane];
+            if constexpr (sizeof(R) == 4) f.cell = p.cell[leaf0 + Bl];
+            return f;
         };
         // the largest bound of each lane group (r2g) and of all lanes (r2all),
         // from each lane's bound r2 (my_r2); an unbounded lane (its heap not yet
@@ -389,15 +393,15 @@ __global__ void k_knn(KnnParams p)
         // mine: this lane's query reaches leaf Bl; gb: group_bounds of the lanes'
         // bounds; craw: fetch(Bl) (unused on the bulk-copy path, which stages the
         // leaf here)
-        auto process = [&](int Bl, bool mine, const GroupBounds& gb, const V& craw) {
+        auto process = [&](int Bl, bool mine, const GroupBounds& gb, const Fetched& craw) {
             const int Bg = leaf0 + Bl;
             const int countB = (int)min((int64_t)kLeaf, nh - (int64_t)Bl * kLeaf);
             V c;
             if constexpr (TMA) c = stage.load_lane((const V*)p.P4 + (int64_t)Bg * kLeaf, lane, p.cnt);
-            else c = craw;
+            else c = craw.c;
             // shift the candidates into the query leaf's frame (exact shift)
             if constexpr (sizeof(R) == 4) {
-                const float4 cB = p.cell[Bg];
+                const float4 cB = craw.cell;
                 c.x = __fadd_rn(c.x, __fsub_rn(cB.x, cA.x));
                 c.y = __fadd_rn(c.y, __fsub_rn(cB.y, cA.y));
                 c.z = __fadd_rn(c.z, __fsub_rn(cB.z, cA.z));
@@ -569,12 +573,12 @@ __global__ void k_knn(KnnParams p)
                 uint32_t m = acc;
                 int c = __ffs(m) - 1;
                 m &= m - 1u;
-                V cur = fetch(first_local + c);
+                Fetched cur = fetch(first_local + c);
                 const GroupBounds gb = group_bounds(node_r2, lane_bits != 0u);
                 while (true) {
                     const int cn = __ffs(m) - 1;       // -1: none left
                     m &= m - 1u;
-                    V nxt{};
+                    Fetched nxt{};
                     if (cn >= 0) nxt = fetch(first_local + cn);
                     const bool mine = (lane_bits >> c) & 1u;
                     if (__any_sync(0xffffffffu, mine)) process(first_local + c, mine, gb, cur);

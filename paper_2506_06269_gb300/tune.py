@@ -17,8 +17,8 @@ leaf size that defines the canonical FP32 distance is not a knob):
 The search is coordinate descent from the defaults: one knob at a time over
 its values, keeping the fastest, two sweeps.  A trial builds a context with the
 knobs (they are fixed at creation) on the caller's workload, runs a cell build,
-a cold kernel-size search and a scatter step, then times `reps` warm-started
-steps (drift, build, kernel sizes, scatter) by the library's CUDA-event kernel
+a cold step and two warm-started steps (drift, build, kernel sizes, scatter),
+then times `reps` more warm-started steps by the library's CUDA-event kernel
 timers; the score of a knob is the time of the kernel it acts on.
 """
 from __future__ import annotations
@@ -41,7 +41,7 @@ DEFAULTS = {"knn_warps": 8, "knn_batch": 2, "knn_groups": 4, "knn_chains": 4, "k
             "pair_warps": 8, "pair_per_round": 4, "use_tma": 0}
 
 
-def _trial(make_inputs, ks, xs_list, dts, masses, halo_off, precision, kw, reps):
+def _trial(make_inputs, ks, xs_list, dts, masses, halo_off, precision, kw, reps, settle=2):
     import torch
     from paper_2506_06269_gb300 import sidm
     n = int(halo_off[-1])
@@ -59,10 +59,11 @@ def _trial(make_inputs, ks, xs_list, dts, masses, halo_off, precision, kw, reps)
             ctx.scatter_step(12345, i, xs, dt, mass, vel)
 
         ctx.build_cells(halo_off, pos, vel, ids)
-        step(0)                                   # cold search; the next ones start warm
+        for i in range(1 + settle):               # a cold search, then warm-started ones settle
+            step(i)
         ctx.kernel_times(reset=True)
         for i in range(reps):
-            step(1 + i)
+            step(1 + settle + i)
         ms, _ = ctx.kernel_times(reset=True)
         status = ctx.status()
     finally:
@@ -72,7 +73,7 @@ def _trial(make_inputs, ks, xs_list, dts, masses, halo_off, precision, kw, reps)
     return float(ms[1]) / reps, float(ms[2]) / reps
 
 
-def autotune(make_inputs, ks, xs_list, dts, masses, halo_off, precision="mixed", reps=2, sweeps=2, tma=(0,)):
+def autotune(make_inputs, ks, xs_list, dts, masses, halo_off, precision="mixed", reps=4, sweeps=2, tma=(0,)):
     """Return (knobs for sidm.Context, table of trials).
 
     make_inputs(ctx) -> (pos, vel, ids): fresh device copies of the workload.

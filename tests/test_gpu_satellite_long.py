@@ -1,0 +1,150 @@
+"""The satellite run at its stated length: an NFW subhalo in the six-part host
+of Sect. 4.1 (NFW halo, Hernquist bulge, four Miyamoto-Nagai disks) from the
+paper's initial position and velocity, kick-drift-kick with the host's
+analytic force on 4 power-of-two individual steps whose bins follow the SIDM
+time-step criterion (tau = 0.04), sigma(v)/m = 100/(1+(v/v_max)^2)^2, N_ngb 64.
+
+  - 2^22 particles, 1000 big steps (8000 sub-steps) on the GPU: the relative
+    drift of the total energy (kinetic + host potential) stays below 1e-4
+    (the target of the scattering pass over 1000 steps); its series and the
+    scatter-rate series are recorded every 10 big steps and the rate stays
+    near its start (the halo is not disrupted in this time);
+  - the N/64 = 65,536-particle realisation, run by the GPU and by the FP64
+    oracle (same steps, same bins rule, same draws), over a window of big
+    steps: the trajectories part as soon as one draw falls differently, so
+    the two are compared by statistics -- the events per big step agree within
+    Poisson error and both energy drifts stay below 1e-4.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2506_06269_gb300 import ics
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+HOST = ics.milky_way_host()
+NB, DT_MAX, K, S0, TAU, SEED = 4, 0.02, 64, 100.0, 0.04, 4
+S = 1 << (NB - 1)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2506_06269_gb300 import build
+    build.build()
+
+
+def _initial(n):
+    halo = ics.nfw(n, SEED)
+    x0, v0 = ics.satellite_orbit()
+    return halo, halo.pos + x0[:, None], (halo.vel + v0[:, None]).astype(np.float32).astype(np.float64)
+
+
+def _gpu_run(n, big_steps, every=10):
+    """big_steps big steps on the GPU; (energies, events) every `every` big steps."""
+    from paper_2506_06269_gb300 import sidm
+    halo, pos0, vel0 = _initial(n)
+    vmax = ics.nfw_vmax()
+    ctx = sidm.Context(n_max=n, ngb_max=K, event_cap=max(1 << 16, n // 8), flags=sidm.SIDM_FLAG_SUM_P)
+    dev = ctx.device
+    pos = torch.tensor(pos0, device=dev)
+    vel = torch.tensor(vel0.astype(np.float32), device=dev)
+    ids = torch.tensor(halo.ids.astype(np.int64), device=dev).to(torch.int32)
+    h = torch.zeros(n, dtype=torch.float32, device=dev)
+    phi = torch.zeros(n, dtype=torch.float64, device=dev)
+    xs, mass = ctx.xs_tensor([(1, S0, vmax)]), ctx.f64([halo.mass])
+    dtt, dtm = ctx.f64([DT_MAX / S]), ctx.f64([DT_MAX])
+    bins = torch.zeros(n, dtype=torch.int32, device=dev)
+    stats = torch.zeros((S, sidm.STATS_DTYPE.itemsize), dtype=torch.uint8, device=dev)
+
+    def energy():
+        ctx.host_potential(HOST, pos, phi)
+        return float((0.5 * (vel.double() ** 2).sum(0) + phi).sum().item()) * halo.mass
+
+    ctx.build_cells([0, n], pos, vel, ids)
+    e0 = energy()
+    series, events, window = [], [], 0
+    for big in range(big_steps):
+        nxt = bins
+        for s in range(S):
+            ctx.host_kick(HOST, DT_MAX, NB, s, 0, bins, pos, vel)
+            ctx.build_cells([0, n], pos, vel, ids)
+            pm = ctx.perm(n).to(torch.int64)
+            bins, nxt = bins[pm], nxt[pm]
+            ctx.kernel_sizes([K], h)
+            ctx.scatter_step_binned(SEED, big * S + s, xs, DT_MAX, NB, s, bins, mass, vel, stats[s])
+            if s == 0:
+                _, nxt, _ = ctx.timestep_criterion(TAU, 0.0, DT_MAX, NB, dtm, n, 1)
+            ctx.drift(dtt, pos, vel)
+            ctx.host_kick(HOST, DT_MAX, NB, s, 1, bins, pos, vel)
+        bins = nxt
+        window += sum(sidm.parse_stats(stats[s]).n_events for s in range(S))
+        if (big + 1) % every == 0:
+            e = energy()
+            series.append(abs(e - e0) / abs(e0))
+            events.append(window)
+            window = 0
+    status = ctx.status()
+    ctx.close()
+    return np.array(series), np.array(events), status
+
+
+def _oracle_run(n, big_steps):
+    """The same run through the FP64 oracle; (final relative energy drift, events per big step)."""
+    halo, xo, vo = _initial(n)
+    vmax = ics.nfw_vmax()
+    m = np.full(n, halo.mass)
+
+    def energy(x, v):
+        return halo.mass * (0.5 * (v ** 2).sum() + O.host_phi(HOST, x).sum())
+
+    e0 = energy(xo, vo)
+    bins = np.zeros(n, np.int32)
+    per_big = []
+    delta = DT_MAX / S
+    for big in range(big_steps):
+        nxt, count = bins, 0
+        for s in range(S):
+            vo = O.host_kick(xo, vo, HOST, DT_MAX, bins, NB, s, 0)
+            h, _, _ = O.knn(xo, halo.ids, K, O.MODE_MIXED)
+            ev, _, sump = O.pairs(xo, vo, halo.ids, h, O.MODE_MIXED, (1, S0, vmax), halo.mass, 0.0, SEED, big * S + s,
+                                  0, bins=bins, n_bins=NB, substep=s, dt_max=DT_MAX)
+            vo, _ = O.apply_events(ev, m, vo)
+            count += len(ev)
+            if s == 0:
+                _, nxt = O.timestep(sump, TAU, DT_MAX, 0.0, DT_MAX, NB)
+            xo = xo + vo * delta
+            vo = O.host_kick(xo, vo, HOST, DT_MAX, bins, NB, s, 1)
+        bins = nxt.astype(np.int32)
+        per_big.append(count)
+    return abs(energy(xo, vo) - e0) / abs(e0), np.array(per_big)
+
+
+def test_satellite_1000_big_steps_drift_and_rate_series():
+    series, events, status = _gpu_run(1 << 22, 1000)
+    assert status == 0
+    print("drift every 10 big steps (max, last):", series.max(), series[-1])
+    print("events per 10 big steps (first, last, mean):", events[0], events[-1], events.mean())
+    assert series.max() < 1e-4
+    assert events.min() > 0
+    # no runaway: the scatter rate of the last hundred big steps is within a
+    # factor of two of the first hundred's
+    assert 0.5 < events[-10:].sum() / events[:10].sum() < 2.0
+
+
+def test_satellite_n64_realisation_gpu_and_oracle_statistics():
+    W = 10
+    series, events, status = _gpu_run(1 << 16, W, every=1)
+    assert status == 0
+    drift_o, ev_o = _oracle_run(1 << 16, W)
+    print("events per big step, GPU:", events.tolist(), "oracle:", ev_o.tolist())
+    assert series.max() < 1e-4 and drift_o < 1e-4
+    tot_g, tot_o = events.sum(), ev_o.sum()
+    assert tot_o > 100
+    assert abs(tot_g - tot_o) < 5.0 * math.sqrt(tot_g + tot_o)
