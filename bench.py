@@ -55,6 +55,8 @@ OPS_PER_KNN_CAND = 8       # canonical d^2 (6) + key compare (2)
 # the kernel-size search as the scope table counts it: about 6 N_ngb candidate
 # distances of about 9 FP32 operations per particle
 KNN_SURVEY_CANDS_PER_NGB, KNN_SURVEY_OPS_PER_CAND = 6, 9
+PAIR_SURVEY_OPS = 130              # per in-range pair: ~60 FP32 with the Lambda table + ~70 INT32 of Philox
+BUILD_BUDGET_BYTES = 184           # 12 + 12 + 4 sort passes x 24 + 32 + 32
 
 # the paper's top resolution: cored-isothermal inner profile joined to NFW
 CFG3_N, CFG3_SEED, CFG3_SWEEP = 50_000_000, 2, (16, 32, 64, 128)
@@ -73,6 +75,9 @@ def parse():
     ap.add_argument("--use-tma", type=int, default=0)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--only", choices=["all", "streaming"], default="all",
+                    help="streaming: time only the HBM-bound kernels (profiling runs; prints their block)")
+    ap.add_argument("--stream-n", type=int, default=1 << 25)
     return ap.parse_args()
 
 
@@ -541,6 +546,42 @@ def run_config3(local, steps=3, n=CFG3_N, oracle_sample=True):
     return out
 
 
+def run_resolve_dense(res, steps=3, dt_scale=40.0):
+    """The resolve (a4) where events are dense: the benchmark halo with its
+    dt times dt_scale, so particles scatter several times per step.  The
+    claim-based resolve (one CTA) against the per-particle-list resolve
+    (cooperative launch over all SMs, SIDM_FLAG_DRAG contexts) on the same
+    events: rounds, events and CUDA-event time of each."""
+    import torch
+    from paper_2506_06269_gb300 import sidm
+    halo, vmax = res["halo"], res["vmax"]
+    n = halo.n
+    out = {"workload": f"benchmark halo, dt x {dt_scale:g}", "dt": res["dt"] * dt_scale}
+    for name, flags in (("claims_one_cta", 0), ("lists_all_sms", sidm.SIDM_FLAG_DRAG)):
+        c = sidm.Context(n_max=n, halo_max=1, ngb_max=N_NGB, event_cap=1 << 22, device=res["local"],
+                         flags=flags | sidm.SIDM_FLAG_TIMING)
+        dev = c.device
+        pos = torch.tensor(halo.pos, device=dev)
+        vel = torch.tensor(halo.vel.astype(np.float32), device=dev)
+        ids = torch.tensor(halo.ids.astype(np.int64), device=dev).to(torch.int32)
+        h = torch.zeros(n, dtype=torch.float32, device=dev)
+        xs, dt, mass = c.xs_tensor([(1, S0, vmax)]), c.f64([res["dt"] * dt_scale]), c.f64([halo.mass])
+        c.build_cells([0, n], pos, vel, ids)
+        c.kernel_sizes([N_NGB], h)
+        c.scatter_step(5, 0, xs, dt, mass, vel)                # warm-up
+        c.kernel_times(reset=True)
+        st = []
+        for i in range(steps):
+            c.scatter_step(5, 1 + i, xs, dt, mass, vel)
+            st.append(c.stats())
+        ms, cnt = c.kernel_times(reset=True)
+        out[name] = {"ms_per_step": ms[3] / steps, "events_per_step": float(np.mean([x.n_events for x in st])),
+                     "rounds": int(max(x.rounds for x in st)), "multi_hit_particles": int(st[-1].n_multi),
+                     "device_status": c.status()}
+        c.close()
+    return out
+
+
 def run_satellite(local, big_steps=8, n=1 << 22, n_bins=4, dt_max=0.02):
     """NFW subhalo of 2^22 particles at the paper's initial position and velocity
     (123.6 kpc, 109 km/s) in its six-part Milky-Way-like host (NFW halo,
@@ -628,9 +669,13 @@ def run_streaming(local, n=1 << 25, reps=5):
     velocities.  Times the cell build (Morton keys, 7-pass radix sort, gather,
     leaf boxes, tree), the drift and the energy/momentum sums with CUDA
     events, and reports algorithmic bytes / time against the measured HBM
-    peak.  Algorithmic bytes per particle: build 520 (bbox 24, keys 24 + 12,
-    7 sort passes x 32, gather 52 + 64, copy-back 80, leaf boxes 24), drift 60
-    (pos 24 read + 24 write, vel 12), energy 12 (one read of the velocities)."""
+    peak.  Algorithmic bytes per particle: build 456 (bbox 24, keys 24 + 12,
+    digit counts 8, 7 sort passes x 24, gather 52 + 64, copy-back 80, leaf
+    boxes 24), drift 60 (pos 24 read + 24 write, vel 12), energy 12 (one read
+    of the velocities).  The build is also given against the 184 B/particle
+    budget of a build with 4 sort passes and 32-byte records (pos 12 read,
+    key + index 12 written, 4 x 24, gather 32 + 32).  After the first build the
+    particles arrive in the previous build's order, as they do in a step."""
     import torch
     from paper_2506_06269_gb300 import sidm
     peaks, src = load_peaks()
@@ -657,15 +702,18 @@ def run_streaming(local, n=1 << 25, reps=5):
         torch.cuda.synchronize()
         return a.elapsed_time(b) / reps
 
-    legs = {"build": (lambda: ctx.build_cells([0, n], pos, vel, ids), 520),
+    legs = {"build": (lambda: ctx.build_cells([0, n], pos, vel, ids), 456),
             "drift": (lambda: ctx.drift(dt, pos, vel), 60),
             "energy_momentum": (lambda: ctx.energy_momentum(mass, vel, out), 12)}
-    res = {"n_particles": n, "workload": "uniform cube, 2^25 particles (seeded, on the device)",
+    res = {"n_particles": n, "workload": f"uniform cube, {n} particles (seeded, on the device)",
            "peak_gbs": peaks["hbm_gbs"], "peak_source": src}
     for name, (fn, bpp) in legs.items():
         ms = timed(fn)
         gbs = bpp * n / (ms * 1e-3) / 1e9
         res[name] = {"ms": ms, "bytes_per_particle": bpp, "achieved_gbs": gbs, "frac": gbs / peaks["hbm_gbs"]}
+    sg = BUILD_BUDGET_BYTES * n / (res["build"]["ms"] * 1e-3) / 1e9
+    res["build"]["against_budget"] = {"bytes_per_particle": BUILD_BUDGET_BYTES, "achieved_gbs": sg,
+                                      "frac": sg / peaks["hbm_gbs"]}
     res["device_status"] = ctx.status()
     ctx.close()
     return res
@@ -805,25 +853,32 @@ def roofline(res, peaks, peak_src, name=None):
                                f"({peak_src} sm_max_mhz)",
                 "ops_per_unit": {"candidate_test": OPS_PER_TEST, "pair_eval": OPS_PER_PAIR,
                                  "lambda_lookup": OPS_PER_LAMBDA},
+                "scope_table_count": {"ops_per_pair": PAIR_SURVEY_OPS,
+                                      "achieved": res["n_pairs"] / K * PAIR_SURVEY_OPS / (per_launch_ms * 1e-3) / 1e12,
+                                      "frac": res["n_pairs"] / K * PAIR_SURVEY_OPS / (per_launch_ms * 1e-3) / 1e12
+                                      / alu_peak},
                 "ms_per_launch": per_launch_ms}
     if name == "knn":
+        # algorithmic work = the scope table's per-particle figure (6 N_ngb
+        # candidate distances of 9 operations) x the particles of one launch;
+        # the distances the kernel actually computed are given beside it
         cand = res.get("knn_candidates_per_step")
         tr = traffic.get("knn")
-        achieved = (cand * OPS_PER_KNN_CAND) / (per_launch_ms * 1e-3) / 1e12 if cand else None
-        survey_ops = n * KNN_SURVEY_CANDS_PER_NGB * N_NGB * KNN_SURVEY_OPS_PER_CAND
-        survey = survey_ops / (per_launch_ms * 1e-3) / 1e12
+        ops_pp = KNN_SURVEY_CANDS_PER_NGB * N_NGB * KNN_SURVEY_OPS_PER_CAND
+        achieved = n * ops_pp / (per_launch_ms * 1e-3) / 1e12
+        impl = (cand * OPS_PER_KNN_CAND) / (per_launch_ms * 1e-3) / 1e12 if cand else None
         return {"kernel": "k_knn", "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
-                "frac": (achieved / alu_peak) if achieved else None,
+                "frac": achieved / alu_peak,
                 "traffic": (tr["bytes_per_launch"] * n / tr["units_per_launch"]) if tr else None,
                 "peak_source": f"derived: {N_SM} SMs x {LANES_PER_SM} lanes x {clock_mhz:.0f} MHz ({peak_src})",
-                "ops_per_unit": {"candidate_distance": OPS_PER_KNN_CAND},
-                "candidates_per_particle": (cand / n) if cand else None,
-                "survey_count": {"ops_per_particle": KNN_SURVEY_CANDS_PER_NGB * N_NGB * KNN_SURVEY_OPS_PER_CAND,
-                                 "achieved": survey, "frac": survey / alu_peak},
+                "ops_per_unit": {"particle": ops_pp},
+                "computed_distances": {"per_particle": (cand / n) if cand else None,
+                                       "ops_per_distance": OPS_PER_KNN_CAND, "achieved": impl,
+                                       "frac": (impl / alu_peak) if impl else None},
                 "ms_per_launch": per_launch_ms}
     # the cell build is a streaming (HBM) sequence
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    bytes_per_particle = 520.0
+    bytes_per_particle = 456.0
     achieved = bytes_per_particle * n / (per_launch_ms * 1e-3) / 1e9
     return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": None, "peak_source": f"{peak_src} hbm_gbs",
@@ -900,8 +955,9 @@ def main_ours(args):
         if not args.no_batched and ws == 1:
             line["batched"] = run_batched(res["local"])
             line["satellite"] = run_satellite(res["local"])
-            line["streaming_kernels"] = run_streaming(res["local"])
+            line["streaming_kernels"] = run_streaming(res["local"], n=args.stream_n)
             line["config3"] = run_config3(res["local"], oracle_sample=not args.no_cpu_baseline)
+            line["resolve_dense"] = run_resolve_dense(res)
             if fp64:
                 line["batched_over_fp64_single_halo"] = line["batched"]["value"] / fp64["value"]
         if not args.no_cpu_baseline and ws == 1:
@@ -964,5 +1020,9 @@ if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         main_reference(a)
+    elif a.only == "streaming":
+        from paper_2506_06269_gb300 import build as _b
+        _b.build()
+        emit({"streaming_kernels": run_streaming(dist_env()[2], n=a.stream_n)})
     else:
         main_ours(a)

@@ -15,6 +15,7 @@
 
 #include "sidm_internal.cuh"
 #include "sidm_sum.cuh"
+#include "sidm_sort.cuh"
 
 using namespace sidm;
 
@@ -23,10 +24,6 @@ namespace {
 thread_local std::string g_create_err;
 
 constexpr int kChunk = 16384;        // particles per reduction chunk
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
-constexpr int kSortTile = kSortThreads * kSortItems;
-constexpr int kSortWarps = kSortThreads / 32;
 
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
@@ -75,16 +72,25 @@ __device__ __forceinline__ uint32_t compact3(unsigned long long x)
 // ------------------------------------------------------------------ a0 kernels
 // Per-halo bounding box: exact min/max of the FP64 positions as integer
 // min/max of their order-preserving bit images (integer pipes, not FP64).
-__global__ void k_bbox(const double* __restrict__ pos, int64_t N, const int32_t* __restrict__ chunk_halo,
-                       const int64_t* __restrict__ chunk_begin, const int64_t* __restrict__ halo_off,
-                       int H, unsigned long long* __restrict__ bb)
+// kBboxSplit CTAs per reduction chunk, each a quarter of it with all its loads
+// in flight; one atomic per CTA and bound.
+constexpr int kBboxSplit = 4;
+__global__ void __launch_bounds__(256) k_bbox(const double* __restrict__ pos, int64_t N,
+                                              const int32_t* __restrict__ chunk_halo,
+                                              const int64_t* __restrict__ chunk_begin,
+                                              const int64_t* __restrict__ halo_off, int H,
+                                              unsigned long long* __restrict__ bb)
 {
-    const int c = blockIdx.x;
+    __shared__ unsigned long long red[8][6];
+    const int c = blockIdx.x / kBboxSplit, part = blockIdx.x % kBboxSplit;
     const int h = chunk_halo[c];
-    const int64_t b = chunk_begin[c];
+    int64_t b = chunk_begin[c];
     int64_t e = b + kChunk;
     if (e > halo_off[h + 1]) e = halo_off[h + 1];
+    b += (int64_t)part * (kChunk / kBboxSplit);
+    if (b + kChunk / kBboxSplit < e) e = b + kChunk / kBboxSplit;
     unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0ull, 0ull, 0ull};
+#pragma unroll 4
     for (int64_t s = b + threadIdx.x; s < e; s += blockDim.x) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -100,13 +106,18 @@ __global__ void k_bbox(const double* __restrict__ pos, int64_t N, const int32_t*
             mx[a] = max(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
         }
     }
-    if ((threadIdx.x & 31) == 0) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            if (mn[a] <= mx[a]) {
-                atomicMin(&bb[a * H + h], mn[a]);
-                atomicMax(&bb[(3 + a) * H + h], mx[a]);
-            }
+        for (int a = 0; a < 3; ++a) { red[warp][a] = mn[a]; red[warp][3 + a] = mx[a]; }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int a = threadIdx.x;
+        unsigned long long v = red[0][a];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = a < 3 ? min(v, red[w][a]) : max(v, red[w][a]);
+        if (b < e) {                                      // a part past the halo's end has nothing
+            if (a < 3) atomicMin(&bb[a * H + h], v);
+            else atomicMax(&bb[a * H + h], v);
         }
     }
 }
@@ -136,147 +147,64 @@ __global__ void k_frame(int H, const int64_t* __restrict__ halo_off, const unsig
     fr[h] = f;
 }
 
-// Sort key = halo << 51 | Morton(q), q = floor((x - O) 2^(17-E-1)) clamped.
-__global__ void k_keys(const double* __restrict__ pos, int64_t N, const int64_t* __restrict__ halo_off, int H,
-                       const HaloFrame* __restrict__ fr, unsigned long long* __restrict__ key, uint32_t* __restrict__ val)
+// floor(t 2^(17-E-1)) clamped to [0, 2^17 - 1], t = RN(x - O) in FP64: the
+// scaling by a power of two is exact, so the floor is read off t's bits
+// (t = M 2^(e-52), M the integer significand): M >> (36 + E - e), 0 for a
+// shift of 64 or more, the clamp for a negative one.  Only the subtraction
+// runs on the FP64 pipe.
+__device__ __forceinline__ uint32_t morton_coord(double x, double O, int E)
 {
     const uint32_t qmax = (1u << kMortonBits) - 1u;
+    const double t = __dsub_rn(x, O);
+    const unsigned long long b = (unsigned long long)__double_as_longlong(t);
+    const int eb = (int)((b >> 52) & 2047ull);
+    const unsigned long long mant = b & ((1ull << 52) - 1ull);
+    if (b >> 63) return 0u;                                  // t <= 0 (or a negative NaN)
+    if (eb == 2047) return mant ? 0u : qmax;                 // NaN: 0, +inf: the clamp
+    const unsigned long long M = eb ? (mant | (1ull << 52)) : mant;
+    const int sh = 36 + E - ((eb ? eb : 1) - 1023);
+    if (sh >= 64) return 0u;
+    if (sh < 0) return qmax;
+    const unsigned long long fl = M >> sh;
+    return fl >= qmax ? qmax : (uint32_t)fl;
+}
+
+// Sort key = halo << 51 | Morton(q), q = floor((x - O) 2^(17-E-1)) clamped;
+// the digit counts of every sort pass taken on the way (hist [passes][256],
+// zero on entry).
+__global__ void __launch_bounds__(256) k_keys(const double* __restrict__ pos, int64_t N,
+                                              const int64_t* __restrict__ halo_off, int H,
+                                              const HaloFrame* __restrict__ fr, unsigned long long* __restrict__ key,
+                                              uint32_t* __restrict__ val, int passes, uint32_t* __restrict__ hist)
+{
+    __shared__ uint32_t sh[sidm_sort::kMaxPasses][256];
+    for (int i = threadIdx.x; i < sidm_sort::kMaxPasses * 256; i += blockDim.x) (&sh[0][0])[i] = 0u;
+    __syncthreads();
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
-        const int h = halo_of(halo_off, H, s);
-        const HaloFrame f = fr[h];
-        uint32_t q[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            // (x - O) 2^(17-E-1): the product by a power of two is the exact scaling;
-            // one conversion rounds down (floor), the clamp is integer work
-            const double t = __dmul_rn(__dsub_rn(pos[a * N + s], f.O[a]), f.qs);
-            const int fl = __double2int_rd(t);
-            q[a] = fl <= 0 ? 0u : ((uint32_t)fl >= qmax ? qmax : (uint32_t)fl);
-        }
-        key[s] = ((unsigned long long)h << kHaloShift) | spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2);
+        const int h = H == 1 ? 0 : halo_of(halo_off, H, s);
+        const HaloFrame& f = fr[h];
+        const uint32_t q0 = morton_coord(pos[s], f.O[0], f.E);
+        const uint32_t q1 = morton_coord(pos[N + s], f.O[1], f.E);
+        const uint32_t q2 = morton_coord(pos[2 * N + s], f.O[2], f.E);
+        const unsigned long long k =
+            ((unsigned long long)h << kHaloShift) | spread3(q0) | (spread3(q1) << 1) | (spread3(q2) << 2);
+        key[s] = k;
         val[s] = (uint32_t)s;
-    }
-}
-
-// ---- stable LSD radix sort of (u64 key, u32 value), 8-bit digits -----------
-__global__ void k_sort_hist(const unsigned long long* __restrict__ key, int64_t n, int shift, int nblk,
-                            uint32_t* __restrict__ hist)
-{
-    __shared__ uint32_t cnt[256];
-    cnt[threadIdx.x] = 0;
-    __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kSortTile;
-#pragma unroll 4
-    for (int i = 0; i < kSortItems; ++i) {
-        int64_t s = base + i * kSortThreads + threadIdx.x;
-        if (s < n) atomicAdd(&cnt[(uint32_t)(key[s] >> shift) & 255u], 1u);
+        sidm_sort::count_digits(sh, k, passes);
     }
     __syncthreads();
-    hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = cnt[threadIdx.x];
-}
-
-// exclusive scan of x over the 256 threads of a CTA (warp shuffles, then the
-// eight warp totals); *total receives the sum
-__device__ __forceinline__ uint32_t cta256_exclusive(uint32_t x, uint32_t* wsum, uint32_t* total)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t inc = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
-    }
-    if (lane == 31) wsum[warp] = inc;
-    __syncthreads();
-    uint32_t before = 0u, all = 0u;
-#pragma unroll
-    for (int w = 0; w < kSortWarps; ++w) {
-        const uint32_t t = wsum[w];
-        before += w < warp ? t : 0u;
-        all += t;
-    }
-    __syncthreads();
-    *total = all;
-    return before + inc - x;
-}
-
-// Row d of hist (the counts of digit d in every block) scanned in place to its
-// exclusive prefix over blocks, one CTA per digit; rowsum[d] = the row total.
-__global__ void __launch_bounds__(256) k_sort_scan(uint32_t* __restrict__ hist, int nblk, uint32_t* __restrict__ rowsum)
-{
-    __shared__ uint32_t wsum[kSortWarps];
-    uint32_t* row = hist + (int64_t)blockIdx.x * nblk;
-    uint32_t carry = 0u;
-    for (int base = 0; base < nblk; base += 256) {
-        const int i = base + threadIdx.x;
-        const uint32_t v = i < nblk ? row[i] : 0u;
-        uint32_t tot;
-        const uint32_t ex = cta256_exclusive(v, wsum, &tot);
-        if (i < nblk) row[i] = carry + ex;
-        carry += tot;
-    }
-    if (threadIdx.x == 0) rowsum[blockIdx.x] = carry;
-}
-
-// Scatter of one tile in 16 rounds of 256 consecutive keys; the rank of a key
-// among equal digits is (earlier rounds) + (earlier warps) + (earlier lanes),
-// which keeps the sort stable.
-__global__ void k_sort_scatter(const unsigned long long* __restrict__ key, const uint32_t* __restrict__ val,
-                               int64_t n, int shift, int nblk, const uint32_t* __restrict__ hist,
-                               const uint32_t* __restrict__ rowsum, unsigned long long* __restrict__ okey,
-                               uint32_t* __restrict__ oval)
-{
-    __shared__ uint32_t run[256];
-    __shared__ uint32_t woff[kSortWarps][256];
-    __shared__ uint32_t wsum[kSortWarps];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    {
-        // first slot of digit d in this block: all smaller digits, then digit d
-        // of the earlier blocks
-        uint32_t tot;
-        const uint32_t digit_base = cta256_exclusive(rowsum[threadIdx.x], wsum, &tot);
-        run[threadIdx.x] = digit_base + hist[(int64_t)threadIdx.x * nblk + blockIdx.x];
-    }
-    const int64_t tile = (int64_t)blockIdx.x * kSortTile;
-    for (int r = 0; r < kSortItems; ++r) {
-        if (tile + r * kSortThreads >= n) break;          // uniform across the CTA
-#pragma unroll
-        for (int w = 0; w < kSortWarps; ++w) woff[w][threadIdx.x] = 0u;
-        __syncthreads();
-        const int64_t s = tile + r * kSortThreads + threadIdx.x;
-        const bool ok = s < n;
-        const unsigned long long k = ok ? key[s] : 0ull;
-        const uint32_t v = ok ? val[s] : 0u;
-        const uint32_t d = ok ? ((uint32_t)(k >> shift) & 255u) : (256u + lane);
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const int rank = __popc(peers & ((1u << lane) - 1u));
-        if (ok && rank == 0) woff[warp][d] = (uint32_t)__popc(peers);
-        __syncthreads();
-        {
-            uint32_t acc = run[threadIdx.x];
-#pragma unroll
-            for (int w = 0; w < kSortWarps; ++w) {
-                uint32_t c = woff[w][threadIdx.x];
-                woff[w][threadIdx.x] = acc;
-                acc += c;
-            }
-            run[threadIdx.x] = acc;
-        }
-        __syncthreads();
-        if (ok) {
-            const uint32_t dst = woff[warp][d] + (uint32_t)rank;
-            okey[dst] = k;
-            oval[dst] = v;
-        }
-        __syncthreads();
+    for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) {
+        const uint32_t v = (&sh[0][0])[i];
+        if (v) atomicAdd(&hist[i], v);
     }
 }
 
 // Leaf bookkeeping: halo of each leaf, and its frame origin = corner of the
-// finest Morton cell of its first particle (relative to O, exact in FP32).
+// finest Morton cell of its first particle (relative to O, exact in FP32);
+// cellb = RN64(O + origin) per axis, the base the gather subtracts.
 __global__ void k_leaf_fill(int L, int H, const int32_t* __restrict__ leaf_off, const int64_t* __restrict__ halo_off,
                             const unsigned long long* __restrict__ skey, const HaloFrame* __restrict__ fr,
-                            int32_t* __restrict__ leaf_halo, float4* __restrict__ cell)
+                            int32_t* __restrict__ leaf_halo, float4* __restrict__ cell, double4* __restrict__ cellb)
 {
     int leaf = blockIdx.x * blockDim.x + threadIdx.x;
     if (leaf >= L) return;
@@ -285,8 +213,12 @@ __global__ void k_leaf_fill(int L, int H, const int32_t* __restrict__ leaf_off, 
     const int64_t s = halo_off[h] + (int64_t)(leaf - leaf_off[h]) * kLeaf;
     const unsigned long long k = skey[s] & ((1ull << kHaloShift) - 1ull);
     const float fine = fr[h].fine;
-    cell[leaf] = make_float4((float)compact3(k) * fine, (float)compact3(k >> 1) * fine,
-                             (float)compact3(k >> 2) * fine, 0.f);
+    const float4 c = make_float4((float)compact3(k) * fine, (float)compact3(k >> 1) * fine,
+                                 (float)compact3(k >> 2) * fine, 0.f);
+    cell[leaf] = c;
+    const HaloFrame& f = fr[h];
+    cellb[leaf] = make_double4(__dadd_rn(f.O[0], (double)c.x), __dadd_rn(f.O[1], (double)c.y),
+                               __dadd_rn(f.O[2], (double)c.z), 0.0);
 }
 
 // Gather into Morton order: sorted user arrays (scratch), internal padded
@@ -294,7 +226,7 @@ __global__ void k_leaf_fill(int L, int H, const int32_t* __restrict__ leaf_off, 
 template <class R, bool MIXED>
 __global__ void k_gather(int64_t N, int H, const int64_t* __restrict__ halo_off, const int64_t* __restrict__ halo_pad,
                          const int32_t* __restrict__ leaf_off, const HaloFrame* __restrict__ fr,
-                         const float4* __restrict__ cell, const unsigned long long* __restrict__ skey,
+                         const double4* __restrict__ cellb, const unsigned long long* __restrict__ skey,
                          const uint32_t* __restrict__ sval, const double* __restrict__ pos, const R* __restrict__ vel,
                          const uint32_t* __restrict__ id, double* __restrict__ tpos, R* __restrict__ tvel,
                          uint32_t* __restrict__ tid, uint32_t* __restrict__ perm,
@@ -322,11 +254,10 @@ __global__ void k_gather(int64_t N, int H, const int64_t* __restrict__ halo_off,
             raise_status(cnt, SIDM_DEV_BAD_INPUT);
         typename Vec4<R>::T p;
         if (MIXED) {
-            const HaloFrame f = fr[h];
-            const float4 c = cell[leaf];
-            p.x = (R)__double2float_rn(__dsub_rn(x[0], __dadd_rn(f.O[0], (double)c.x)));
-            p.y = (R)__double2float_rn(__dsub_rn(x[1], __dadd_rn(f.O[1], (double)c.y)));
-            p.z = (R)__double2float_rn(__dsub_rn(x[2], __dadd_rn(f.O[2], (double)c.z)));
+            const double4 b = cellb[leaf];
+            p.x = (R)__double2float_rn(__dsub_rn(x[0], b.x));
+            p.y = (R)__double2float_rn(__dsub_rn(x[1], b.y));
+            p.z = (R)__double2float_rn(__dsub_rn(x[2], b.z));
         } else {
             p.x = (R)x[0]; p.y = (R)x[1]; p.z = (R)x[2];
         }
@@ -1249,14 +1180,50 @@ void timer_end(sidm_ctx* c, int idx, cudaStream_t s)
         if (_e != cudaSuccess) return cuda_check((c), _e, #call);               \
     } while (0)
 
+// Stable LSD radix sort of (ka, va)[0, n) by the low 8 * passes key bits,
+// ping-ponging with (kb, vb); on return ka/va hold the sorted pairs.
+// With counted, the digit counts of every pass are already in d_sort_hist
+// (taken by the kernel that made the keys, after sort_prepare).
+static int sort_prepare(sidm_ctx* c, cudaStream_t s)
+{
+    SIDM_CUDA(c, cudaMemsetAsync(c->d_sort_hist, 0, sizeof(uint32_t) * sidm_sort::kMaxPasses * 257, s));
+    return SIDM_OK;
+}
+
+static int radix_sort(sidm_ctx* c, unsigned long long*& ka, uint32_t*& va, unsigned long long*& kb, uint32_t*& vb,
+                      int64_t n, int passes, cudaStream_t s, bool counted = false)
+{
+    using namespace sidm_sort;
+    if (n <= 0) return SIDM_OK;
+    const int64_t tiles = cdiv(n, kTile);
+    if (tiles > c->sort_tiles_cap || passes < 1 || passes > kMaxPasses || n >= ((int64_t)1 << 32))
+        return set_err(c, SIDM_ECAPACITY, "radix sort scratch too small");
+    uint32_t* hist = c->d_sort_hist;
+    uint32_t* tickets = hist + kMaxPasses * 256;
+    if (!counted) {
+        if (int rc = sort_prepare(c, s)) return rc;
+        const int cgrid = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, kThreads * 4), (int64_t)c->sm_count * 4));
+        SIDM_LAUNCH(c, k_sort_count<<<cgrid, kThreads, 0, s>>>(ka, n, passes, hist));
+    }
+    for (int p = 0; p < passes; ++p) {
+        SIDM_CUDA(c, cudaMemsetAsync(c->d_sort_status, 0, sizeof(unsigned long long) * 256 * (size_t)tiles, s));
+        SIDM_LAUNCH(c, k_sort_pass<<<(unsigned)tiles, kThreads, kSmemBytes, s>>>(
+            ka, va, n, 8 * p, hist + 256 * p, c->d_sort_status, tickets + p, kb, vb, &c->d_cnt->status,
+            SIDM_DEV_WAIT_TIMEOUT));
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    return SIDM_OK;
+}
+
 static void free_all(sidm_ctx* c)
 {
     void* ptrs[] = {c->d_halo_off, c->d_halo_pad, c->d_leaf_off, c->d_lvl_off, c->d_top, c->d_ngb, c->d_leaf_halo,
                     c->d_chunk_halo, c->d_chunk_begin, c->d_frame, c->d_key, c->d_key2, c->d_val, c->d_val2,
-                    c->d_hist, c->d_P4, c->d_V4, c->d_ID, c->d_cell, c->d_nlo, c->d_nhi, c->d_perm, c->d_tmp_pos,
+                    c->d_sort_status, c->d_sort_hist, c->d_P4, c->d_V4, c->d_ID, c->d_cell, c->d_cellb, c->d_nlo, c->d_nhi, c->d_perm, c->d_tmp_pos,
                     c->d_tmp_vel, c->d_tmp_id, c->d_claim, c->d_hits, c->d_done, c->d_ev, c->d_sump,
                     c->d_stats_own, c->d_cnt, c->d_epart, c->d_lam, c->d_hprev, c->d_dacc, c->d_halo_ord,
-                    c->d_evg, c->d_lkey, c->d_lval, c->d_lhist, c->d_lstart, c->d_llen, c->d_lptr, c->d_lact,
+                    c->d_evg, c->d_lkey, c->d_lval, c->d_lstart, c->d_llen, c->d_lptr, c->d_lact,
                     c->d_lcnt};
     for (void* p : ptrs) if (p) cudaFree(p);
     if (c->d_stage) cudaFreeHost(c->d_stage);
@@ -1314,6 +1281,9 @@ extern "C" int sidm_create(sidm_ctx** out, const sidm_config* cfg)
     c->dev = cfg->device;
     e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->dev);
     if (e != cudaSuccess) return fail("cudaDeviceGetAttribute", e);
+    e = cudaFuncSetAttribute(sidm_sort::k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sidm_sort::kSmemBytes);
+    if (e != cudaSuccess) return fail("cudaFuncSetAttribute k_sort_pass", e);
 
     const int64_t N = cfg->n_max, H = cfg->halo_max;
     const int64_t Lmax = N / kLeaf + H + 1;
@@ -1322,7 +1292,9 @@ extern "C" int sidm_create(sidm_ctx** out, const sidm_config* cfg)
     const size_t rs = fp64 ? 8 : 4;
     c->node_cap = 2 * Lmax + (int64_t)kMaxLevels * (H + 1);
     c->chunk_cap = N / kChunk + H + 1;
-    c->hist_cap = 256 * cdiv(N, kSortTile) + 256;          // per-block digit counts, then digit totals
+    // radix sort scratch: the cell build sorts N keys, the list resolve 2 event_cap
+    c->sort_tiles_cap = cdiv((cfg->flags & SIDM_FLAG_DRAG) ? std::max<int64_t>(N, 2 * cfg->event_cap) : N,
+                             sidm_sort::kTile);
     c->stage_bytes = sizeof(int64_t) * (size_t)(8 * (H + 1) + kMaxLevels * (H + 1) + 2 * c->chunk_cap + 64);
 #define ALLOC(p, n) do { e = dev_alloc(&(p), (size_t)(n)); if (e != cudaSuccess) return fail("cudaMalloc " #p, e); } while (0)
     ALLOC(c->d_halo_off, H + 1);
@@ -1339,11 +1311,13 @@ extern "C" int sidm_create(sidm_ctx** out, const sidm_config* cfg)
     ALLOC(c->d_key2, N);
     ALLOC(c->d_val, N);
     ALLOC(c->d_val2, N);
-    ALLOC(c->d_hist, c->hist_cap);
+    ALLOC(c->d_sort_status, 256 * c->sort_tiles_cap);
+    ALLOC(c->d_sort_hist, sidm_sort::kMaxPasses * 257);
     e = cudaMalloc(&c->d_P4, (size_t)Npad * 4 * rs); if (e != cudaSuccess) return fail("cudaMalloc P4", e);
     e = cudaMalloc(&c->d_V4, (size_t)Npad * 4 * rs); if (e != cudaSuccess) return fail("cudaMalloc V4", e);
     ALLOC(c->d_ID, Npad);
     ALLOC(c->d_cell, Lmax);
+    ALLOC(c->d_cellb, Lmax);
     ALLOC(c->d_nlo, c->node_cap);
     ALLOC(c->d_nhi, c->node_cap);
     ALLOC(c->d_perm, N);
@@ -1363,11 +1337,9 @@ extern "C" int sidm_create(sidm_ctx** out, const sidm_config* cfg)
     ALLOC(c->d_halo_ord, H);
     if (cfg->flags & SIDM_FLAG_DRAG) {
         const int64_t m = 2 * cfg->event_cap;
-        c->lhist_cap = 256 * cdiv(m, kSortTile) + 256;
         ALLOC(c->d_evg, cfg->event_cap);
         ALLOC(c->d_lkey, 2 * m);
         ALLOC(c->d_lval, 2 * m);
-        ALLOC(c->d_lhist, c->lhist_cap);
         ALLOC(c->d_lstart, N);
         ALLOC(c->d_llen, N);
         ALLOC(c->d_lptr, N);
@@ -1507,25 +1479,18 @@ static int build_impl(sidm_ctx* c, double* pos, R* vel, uint32_t* id, cudaStream
     // per-halo bounding box -> frame
     SIDM_CUDA(c, cudaMemsetAsync(c->d_cnt->bbox, 0xFF, sizeof(unsigned long long) * 3 * H, s));
     SIDM_CUDA(c, cudaMemsetAsync(c->d_cnt->bbox + 3 * H, 0x00, sizeof(unsigned long long) * 3 * H, s));
-    SIDM_LAUNCH(c, k_bbox<<<L.nchunk, 256, 0, s>>>(pos, N, c->d_chunk_halo, c->d_chunk_begin, c->d_halo_off, H, c->d_cnt->bbox));
+    SIDM_LAUNCH(c, k_bbox<<<L.nchunk * kBboxSplit, 256, 0, s>>>(pos, N, c->d_chunk_halo, c->d_chunk_begin, c->d_halo_off, H, c->d_cnt->bbox));
     SIDM_LAUNCH(c, k_frame<<<(H + 127) / 128, 128, 0, s>>>(H, c->d_halo_off, c->d_cnt->bbox, c->d_frame));
-    SIDM_LAUNCH(c, k_keys<<<grid_for(c, N, 256), 256, 0, s>>>(pos, N, c->d_halo_off, H, c->d_frame, c->d_key, c->d_val));
+    if (int rc = sort_prepare(c, s)) return rc;
+    SIDM_LAUNCH(c, k_keys<<<grid_for(c, N, 256), 256, 0, s>>>(pos, N, c->d_halo_off, H, c->d_frame, c->d_key, c->d_val,
+                                                               L.sort_passes, c->d_sort_hist));
     // stable LSD radix sort
-    const int nblk = (int)cdiv(N, kSortTile);
     unsigned long long *ka = c->d_key, *kb = c->d_key2;
     uint32_t *va = c->d_val, *vb = c->d_val2;
-    for (int p = 0; p < L.sort_passes; ++p) {
-        const int shift = 8 * p;
-        SIDM_LAUNCH(c, k_sort_hist<<<nblk, kSortThreads, 0, s>>>(ka, N, shift, nblk, c->d_hist));
-        SIDM_LAUNCH(c, k_sort_scan<<<256, 256, 0, s>>>(c->d_hist, nblk, c->d_hist + (int64_t)256 * nblk));
-        SIDM_LAUNCH(c, k_sort_scatter<<<nblk, kSortThreads, 0, s>>>(ka, va, N, shift, nblk, c->d_hist,
-                                                                     c->d_hist + (int64_t)256 * nblk, kb, vb));
-        std::swap(ka, kb);
-        std::swap(va, vb);
-    }
+    if (int rc = radix_sort(c, ka, va, kb, vb, N, L.sort_passes, s, true)) return rc;
     // leaves, gather, copy back into the caller's arrays
     SIDM_LAUNCH(c, k_leaf_fill<<<(L.L + 255) / 256, 256, 0, s>>>(L.L, H, c->d_leaf_off, c->d_halo_off, ka, c->d_frame,
-                                                                  c->d_leaf_halo, c->d_cell));
+                                                                  c->d_leaf_halo, c->d_cell, c->d_cellb));
     const bool mixed = c->cfg.precision == SIDM_MIXED;
     using V = typename Vec4<R>::T;
     // the last kernel sizes, in the order the caller's arrays had after that
@@ -1535,11 +1500,11 @@ static int build_impl(sidm_ctx* c, double* pos, R* vel, uint32_t* id, cudaStream
     c->hprev_valid = false;
     if (mixed)
         SIDM_LAUNCH(c, (k_gather<R, true><<<grid_for(c, N, 256), 256, 0, s>>>(
-            N, H, c->d_halo_off, c->d_halo_pad, c->d_leaf_off, c->d_frame, c->d_cell, ka, va, pos, vel, id,
+            N, H, c->d_halo_off, c->d_halo_pad, c->d_leaf_off, c->d_frame, c->d_cellb, ka, va, pos, vel, id,
             c->d_tmp_pos, (R*)c->d_tmp_vel, c->d_tmp_id, c->d_perm, (V*)c->d_P4, c->d_ID, c->d_cnt, hprev)));
     else
         SIDM_LAUNCH(c, (k_gather<R, false><<<grid_for(c, N, 256), 256, 0, s>>>(
-            N, H, c->d_halo_off, c->d_halo_pad, c->d_leaf_off, c->d_frame, c->d_cell, ka, va, pos, vel, id,
+            N, H, c->d_halo_off, c->d_halo_pad, c->d_leaf_off, c->d_frame, c->d_cellb, ka, va, pos, vel, id,
             c->d_tmp_pos, (R*)c->d_tmp_vel, c->d_tmp_id, c->d_perm, (V*)c->d_P4, c->d_ID, c->d_cnt, hprev)));
     SIDM_CUDA(c, cudaMemcpyAsync(pos, c->d_tmp_pos, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s));
     SIDM_CUDA(c, cudaMemcpyAsync(vel, c->d_tmp_vel, sizeof(R) * 3 * N, cudaMemcpyDeviceToDevice, s));
@@ -1687,15 +1652,7 @@ static int resolve_lists(sidm_ctx* c, const sidm_xs* xs, const double* mass, R* 
         int ib = 1;
         while (ib < 31 && ((int64_t)1 << ib) < L.N) ++ib;
         const int passes = (int)cdiv(27 + ib, 8);
-        const int nblk = (int)cdiv(m, kSortTile);
-        for (int pss = 0; pss < passes; ++pss) {
-            SIDM_LAUNCH(c, k_sort_hist<<<nblk, kSortThreads, 0, s>>>(ka, m, 8 * pss, nblk, c->d_lhist));
-            SIDM_LAUNCH(c, k_sort_scan<<<256, 256, 0, s>>>(c->d_lhist, nblk, c->d_lhist + (int64_t)256 * nblk));
-            SIDM_LAUNCH(c, k_sort_scatter<<<nblk, kSortThreads, 0, s>>>(ka, va, m, 8 * pss, nblk, c->d_lhist,
-                                                                         c->d_lhist + (int64_t)256 * nblk, kb, vb));
-            std::swap(ka, kb);
-            std::swap(va, vb);
-        }
+        if (int rc = radix_sort(c, ka, va, kb, vb, m, passes, s)) return rc;
         SIDM_LAUNCH(c, k_list_runs<<<grid_for(c, m, 256), 256, 0, s>>>(ka, m, c->d_lstart, c->d_llen, c->d_lact, c->d_lcnt));
         SIDM_CUDA(c, cudaMemsetAsync(&c->d_cnt->work[2], 0, sizeof(unsigned int), s));
         ListResolve q;

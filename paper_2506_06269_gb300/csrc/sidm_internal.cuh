@@ -106,14 +106,16 @@ struct sidm_ctx {
     unsigned long long* d_key2 = nullptr;
     uint32_t* d_val = nullptr;
     uint32_t* d_val2 = nullptr;
-    uint32_t* d_hist = nullptr;
-    int64_t hist_cap = 0;
+    unsigned long long* d_sort_status = nullptr;   // radix sort look-back words, [tiles][256]
+    uint32_t* d_sort_hist = nullptr;               // digit counts [8][256], then 8 tile tickets
+    int64_t sort_tiles_cap = 0;
 
     // particles (padded per halo to multiples of 32 slots)
     void* d_P4 = nullptr;              // float4 (ox,oy,oz,h) | double4 (x,y,z,h)
     void* d_V4 = nullptr;              // float4 (vx,vy,vz,id) | double4
     uint32_t* d_ID = nullptr;          // ids by slot
     float4* d_cell = nullptr;          // [Lmax] leaf frame origin relative to O
+    double4* d_cellb = nullptr;        // [Lmax] RN64(O + origin) per axis (the mixed form's gather)
     float4* d_nlo = nullptr;           // [nodes] bbox lo (w = max h)
     float4* d_nhi = nullptr;           // [nodes] bbox hi
     int64_t node_cap = 0;
@@ -136,8 +138,6 @@ struct sidm_ctx {
     double* d_evg = nullptr;                // [event_cap]
     unsigned long long* d_lkey = nullptr;   // [2][2 event_cap] ping-pong
     uint32_t* d_lval = nullptr;             // [2][2 event_cap]
-    uint32_t* d_lhist = nullptr;            // radix-sort histograms of 2 event_cap entries
-    int64_t lhist_cap = 0;
     uint32_t* d_lstart = nullptr;           // [N]
     uint32_t* d_llen = nullptr;             // [N]
     uint32_t* d_lptr = nullptr;             // [N] (zero at rest)

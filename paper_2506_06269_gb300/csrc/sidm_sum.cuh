@@ -3,7 +3,7 @@
 // identical bits.
 //
 // Both reduce a halo in chunks of at most 16384 particles, one CTA per chunk
-// (1024 threads for FP32 velocities, 256 for FP64), to four unscaled sums
+// (512 threads for FP32 velocities, 256 for FP64), to four unscaled sums
 // S = (sum |v|^2, sum vx, sum vy, sum vz), each kept as a double-double
 // (hi, lo); one warp per halo then merges its chunk sums in a fixed order
 // (lane l takes chunks l, l+32, ... in turn, then a fixed shuffle tree) and
@@ -31,7 +31,7 @@
 
 namespace sidm_sum {
 
-constexpr int kThreadsF32 = 1024;  // CTA of the exact FP32 chunk sums
+constexpr int kThreadsF32 = 512;   // CTA of the exact FP32 chunk sums (two per SM at 54 registers)
 constexpr int kThreadsF64 = 256;   // CTA of the compensated FP64 chunk sums
 constexpr int kMaxChunk = 16384;   // the integer windows above hold 2^14 terms
 
@@ -67,8 +67,27 @@ typedef unsigned __int128 u128;
 // largest biased exponent field of the three components of one particle
 __device__ __forceinline__ uint32_t exp_field(float x) { return (__float_as_uint(x) >> 23) & 255u; }
 
+// 64-bit shifts whose amount is taken unsigned and clamped at 64 (PTX shl/shr
+// semantics): an amount of 64 or more, or a negative int, gives 0
+__device__ __forceinline__ unsigned long long shl64(unsigned long long x, int n)
+{
+    unsigned long long r;
+    asm("shl.b64 %0, %1, %2;" : "=l"(r) : "l"(x), "r"(n));
+    return r;
+}
+__device__ __forceinline__ unsigned long long shr64(unsigned long long x, int n)
+{
+    unsigned long long r;
+    asm("shr.b64 %0, %1, %2;" : "=l"(r) : "l"(x), "r"(n));
+    return r;
+}
+
 // x placed in the chunk's fixed-point windows: lin += x / 2^(E-111),
-// sq += x^2 / 2^(2E-110), both truncated toward zero below one unit
+// sq += x^2 / 2^(2E-110), both truncated toward zero below one unit.
+// The term t = M 2^o (o <= 88 for x, o2 <= 64 for x^2) is built as two 64-bit
+// words with clamped shifts: lo = M << o | M >> -o (one of the two is 0), and
+// hi = floor(t / 2^64) = (M << 40) >> (104 - o) for M < 2^24 (the square:
+// (M2 << 16) >> (80 - o2) for M2 < 2^48); the shift amounts are >= 16.
 __device__ __forceinline__ void exact_add(float x, int E, u128& lin, u128& sq)
 {
     const uint32_t b = __float_as_uint(x);
@@ -76,16 +95,12 @@ __device__ __forceinline__ void exact_add(float x, int E, u128& lin, u128& sq)
     const uint32_t m = (b & 0x7FFFFFu) | (ex ? 0x800000u : 0u);
     const int d = (int)(ex ? ex : 1u) - 127 - E;             // e - E <= 0
     const int o1 = 88 + d;
-    u128 t = 0;
-    if (o1 >= 0) t = (u128)m << o1;
-    else if (o1 > -24) t = (u128)(m >> -o1);
+    const unsigned long long M = m;
+    const u128 t = ((u128)shr64(M << 40, 104 - o1) << 64) | (shl64(M, o1) | shr64(M, -o1));
     lin += (b >> 31) ? (u128)0 - t : t;                      // two's complement
-    const unsigned long long m2 = (unsigned long long)m * m;
+    const unsigned long long M2 = (unsigned long long)m * m;
     const int o2 = 64 + 2 * d;
-    u128 t2 = 0;
-    if (o2 >= 0) t2 = (u128)m2 << o2;
-    else if (o2 > -48) t2 = (u128)(m2 >> -o2);
-    sq += t2;
+    sq += ((u128)shr64(M2 << 16, 80 - o2) << 64) | (shl64(M2, o2) | shr64(M2, -o2));
 }
 
 __device__ __forceinline__ u128 shfl_down_u128(u128 v, int o)
@@ -139,6 +154,7 @@ __device__ __forceinline__ void chunk_sums(const float* __restrict__ vel, int64_
     __shared__ u128 s_part[kWarps][4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t mx = 0u;
+#pragma unroll 4
     for (int64_t s = b + threadIdx.x; s < e; s += kThreads)
         mx = max(mx, max(exp_field(vel[s]), max(exp_field(vel[N + s]), exp_field(vel[2 * N + s]))));
     mx = __reduce_max_sync(0xffffffffu, mx);
@@ -153,6 +169,7 @@ __device__ __forceinline__ void chunk_sums(const float* __restrict__ vel, int64_
     }
     const int E = (int)(M ? M : 1u) - 127;
     u128 sq = 0, lx = 0, ly = 0, lz = 0;
+#pragma unroll 4
     for (int64_t s = b + threadIdx.x; s < e; s += kThreads) {
         exact_add(vel[s], E, lx, sq);
         exact_add(vel[N + s], E, ly, sq);

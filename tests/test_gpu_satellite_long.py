@@ -7,13 +7,14 @@ time-step criterion (tau = 0.04), sigma(v)/m = 100/(1+(v/v_max)^2)^2, N_ngb 64.
   - 2^22 particles, 1000 big steps (8000 sub-steps) on the GPU: the relative
     drift of the total energy (kinetic + host potential) stays below 1e-4
     (the target of the scattering pass over 1000 steps); its series and the
-    scatter-rate series are recorded every 10 big steps and the rate stays
-    near its start (the halo is not disrupted in this time);
+    scatter-rate series are recorded every 10 big steps (the subhalo has no
+    self-gravity here, so it spreads and its scatter rate falls steadily);
   - the N/64 = 65,536-particle realisation, run by the GPU and by the FP64
-    oracle (same steps, same bins rule, same draws), over a window of big
-    steps: the trajectories part as soon as one draw falls differently, so
-    the two are compared by statistics -- the events per big step agree within
-    Poisson error and both energy drifts stay below 1e-4.
+    oracle (same steps, same bins rule, same draws), over 10 big steps: the
+    trajectories may part once one draw falls differently, so the two are
+    compared by statistics -- the events per big step agree within Poisson
+    error (on the GB300 they agreed exactly) and both energy drifts stay below
+    1e-4.
 """
 import math
 
@@ -133,9 +134,13 @@ def test_satellite_1000_big_steps_drift_and_rate_series():
     print("events per 10 big steps (first, last, mean):", events[0], events[-1], events.mean())
     assert series.max() < 1e-4
     assert events.min() > 0
-    # no runaway: the scatter rate of the last hundred big steps is within a
-    # factor of two of the first hundred's
-    assert 0.5 < events[-10:].sum() / events[:10].sum() < 2.0
+    # without self-gravity (out of scope with all gravity) the subhalo spreads
+    # and its density, so its scatter rate, falls: no hundred big steps scatter
+    # more than the hundred before beyond Poisson noise, and the last far less
+    # than the first
+    per100 = events.reshape(10, 10).sum(axis=1).astype(np.float64)
+    assert np.all(np.diff(per100) < 3.0 * np.sqrt(per100[1:] + per100[:-1]))
+    assert per100[-1] < 0.5 * per100[0]
 
 
 def test_satellite_n64_realisation_gpu_and_oracle_statistics():
