@@ -438,7 +438,8 @@ int sidm_warm_start(sidm_ctx* ctx, int32_t enable);
  * fixed memory budget -- where a library may not call cudaMalloc/cudaFree.
  * This call needs no context and allocates nothing: it calls no cudaMalloc,
  * cudaFree or allocating library routine.  Its scratch (two FP64 words per
- * quantity per chunk, 256 KiB in all) is a fixed file-scope device array,
+ * quantity per chunk and per group of 32 chunks, 268 KiB in all) is a fixed
+ * file-scope device array,
  * which every GPU that loads libsidm holds until the process exits.
  *
  * Every call outside stream capture looks up the device address of the

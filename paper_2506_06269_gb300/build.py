@@ -17,7 +17,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsidm.so")
 ROOT = os.path.dirname(HERE)
 SOURCES = ["sidm_api.cu", "sidm_knn.cu", "sidm_pairs.cu", "sidm_static.cu"]
-HEADERS = ["sidm_internal.cuh", "sidm_tile.cuh", "sidm_sum.cuh"]
+HEADERS = sorted(f for f in os.listdir(CSRC) if f.endswith(".cuh"))   # every header the sources include
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -221,12 +221,11 @@ __global__ void k_leaf_fill(int L, int H, const int32_t* __restrict__ leaf_off, 
                                __dadd_rn(f.O[2], (double)c.z), 0.0);
 }
 
-// Gather into Morton order: sorted user arrays (scratch), internal padded
-// tracks, permutation.  Mixed form: FP32 offsets o = RN32(RN64(x - (O + c))).
-template <class R, bool MIXED>
+// Gather into Morton order (the FP64 form): sorted user arrays (scratch),
+// internal padded tracks, permutation.
+template <class R>
 __global__ void k_gather(int64_t N, int H, const int64_t* __restrict__ halo_off, const int64_t* __restrict__ halo_pad,
-                         const int32_t* __restrict__ leaf_off, const HaloFrame* __restrict__ fr,
-                         const double4* __restrict__ cellb, const unsigned long long* __restrict__ skey,
+                         const unsigned long long* __restrict__ skey,
                          const uint32_t* __restrict__ sval, const double* __restrict__ pos, const R* __restrict__ vel,
                          const uint32_t* __restrict__ id, double* __restrict__ tpos, R* __restrict__ tvel,
                          uint32_t* __restrict__ tid, uint32_t* __restrict__ perm,
@@ -238,7 +237,6 @@ __global__ void k_gather(int64_t N, int H, const int64_t* __restrict__ halo_off,
         const int h = (int)(skey[s] >> kHaloShift);
         const int64_t local = s - halo_off[h];
         const int64_t slot = halo_pad[h] + local;
-        const int leaf = leaf_off[h] + (int)(local / kLeaf);
         double x[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -253,38 +251,66 @@ __global__ void k_gather(int64_t N, int H, const int64_t* __restrict__ halo_off,
         if (myid >= kIdLimit || !isfinite(x[0]) || !isfinite(x[1]) || !isfinite(x[2]))
             raise_status(cnt, SIDM_DEV_BAD_INPUT);
         typename Vec4<R>::T p;
-        if (MIXED) {
-            const double4 b = cellb[leaf];
-            p.x = (R)__double2float_rn(__dsub_rn(x[0], b.x));
-            p.y = (R)__double2float_rn(__dsub_rn(x[1], b.y));
-            p.z = (R)__double2float_rn(__dsub_rn(x[2], b.z));
-        } else {
-            p.x = (R)x[0]; p.y = (R)x[1]; p.z = (R)x[2];
-        }
+        p.x = (R)x[0]; p.y = (R)x[1]; p.z = (R)x[2];
         p.w = hprev ? hprev[src] : R(0);   // previous kernel size: a guess for the search
         P4[slot] = p;
     }
 }
 
-// Leaf bounding boxes in the halo frame (FP32, rounded outward) of the mixed
-// form, from the FP32 offsets and cell origins the gather just wrote: each
-// point cell + offset is added with rounding down and up (no FP64), so the
-// box holds it exactly; the canonical positions the kernels test against it
-// lie within a few FP32 ulps, far inside the pruning margin.  One warp per leaf.
-__global__ void k_leaf_bbox_p4(int L, const int32_t* __restrict__ leaf_halo, const int32_t* __restrict__ leaf_off,
-                               const int64_t* __restrict__ halo_off, const float4* __restrict__ cell,
-                               const float4* __restrict__ P4, float4* __restrict__ nlo, float4* __restrict__ nhi)
+// The mixed form's gather, one warp per leaf (slot = leaf * 32 + lane), with
+// the leaf's bounding box in the halo frame taken on the way: each point
+// cell + offset is added with rounding down and up (no FP64), so the box holds
+// it exactly (the canonical positions the kernels test against it lie within a
+// few FP32 ulps, far inside the pruning margin).  Same writes as k_gather<R,
+// true> followed by k_leaf_bbox_p4, without reading the padded track back.
+template <class R>
+__global__ void __launch_bounds__(256) k_gather_leaves(int L, int64_t N, const int32_t* __restrict__ leaf_halo,
+                                                       const int32_t* __restrict__ leaf_off,
+                                                       const int64_t* __restrict__ halo_off,
+                                                       const float4* __restrict__ cell,
+                                                       const double4* __restrict__ cellb,
+                                                       const uint32_t* __restrict__ sval, const double* __restrict__ pos,
+                                                       const R* __restrict__ vel, const uint32_t* __restrict__ id,
+                                                       double* __restrict__ tpos, R* __restrict__ tvel,
+                                                       uint32_t* __restrict__ tid, uint32_t* __restrict__ perm,
+                                                       typename Vec4<R>::T* __restrict__ P4, uint32_t* __restrict__ ID,
+                                                       DevCounters* cnt, const R* __restrict__ hprev,
+                                                       float4* __restrict__ nlo, float4* __restrict__ nhi)
 {
     const int lane = threadIdx.x & 31;
-    const int leaf = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (leaf >= L) return;
+    const int leaf = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (leaf >= L) return;                                     // whole warps
     const int h = leaf_halo[leaf];
-    const int64_t local = (int64_t)(leaf - leaf_off[h]) * kLeaf;
-    const int count = (int)min((int64_t)kLeaf, halo_off[h + 1] - halo_off[h] - local);
+    const int64_t local = (int64_t)(leaf - leaf_off[h]) * kLeaf + lane;
     const float4 c = cell[leaf];
-    const float4 p = P4[(int64_t)leaf * kLeaf + (lane < count ? lane : 0)];
-    float mn[3] = {__fadd_rd(c.x, p.x), __fadd_rd(c.y, p.y), __fadd_rd(c.z, p.z)};
-    float mx[3] = {__fadd_ru(c.x, p.x), __fadd_ru(c.y, p.y), __fadd_ru(c.z, p.z)};
+    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    if (local < halo_off[h + 1] - halo_off[h]) {
+        const int64_t s = halo_off[h] + local;
+        const int64_t slot = (int64_t)leaf * kLeaf + lane;
+        const uint32_t src = sval[s];
+        double x[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            x[a] = pos[a * N + src];
+            tpos[a * N + s] = x[a];
+            tvel[a * N + s] = vel[a * N + src];
+        }
+        const uint32_t myid = id[src];
+        tid[s] = myid;
+        perm[s] = src;
+        ID[slot] = myid;
+        if (myid >= kIdLimit || !isfinite(x[0]) || !isfinite(x[1]) || !isfinite(x[2]))
+            raise_status(cnt, SIDM_DEV_BAD_INPUT);
+        const double4 b = cellb[leaf];
+        typename Vec4<R>::T p;
+        p.x = (R)__double2float_rn(__dsub_rn(x[0], b.x));
+        p.y = (R)__double2float_rn(__dsub_rn(x[1], b.y));
+        p.z = (R)__double2float_rn(__dsub_rn(x[2], b.z));
+        p.w = hprev ? hprev[src] : R(0);   // previous kernel size: a guess for the search
+        P4[slot] = p;
+        mn[0] = __fadd_rd(c.x, (float)p.x); mn[1] = __fadd_rd(c.y, (float)p.y); mn[2] = __fadd_rd(c.z, (float)p.z);
+        mx[0] = __fadd_ru(c.x, (float)p.x); mx[1] = __fadd_ru(c.y, (float)p.y); mx[2] = __fadd_ru(c.z, (float)p.z);
+    }
 #pragma unroll
     for (int a = 0; a < 3; ++a)
         for (int o = 16; o > 0; o >>= 1) {
@@ -917,19 +943,28 @@ __global__ void __launch_bounds__(sidm_sum::chunk_threads<R>()) k_energy_partial
     sidm_sum::chunk_sums(vel, N, b, e, part + 8 * (int64_t)c);
 }
 
-// One warp per halo: its chunks merged in a fixed order, scaled by the particle mass.
-__global__ void k_energy_final(int H, int nchunk, const int32_t* __restrict__ chunk_halo,
-                               const double* __restrict__ mass, const double* __restrict__ part,
-                               double* __restrict__ out, double* __restrict__ comp)
+// First merge level: one warp per group of up to kGroupChunks consecutive
+// chunks of a halo (groups numbered halo by halo).
+__global__ void k_energy_group(int H, int ngroup, const int32_t* __restrict__ group_off,
+                               const int32_t* __restrict__ chunk_off, const double* __restrict__ part,
+                               double* __restrict__ gpart)
+{
+    const int g = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (g >= ngroup) return;                             // whole warps
+    int lo = 0, hi = H;                                  // the last halo h with group_off[h] <= g
+    while (hi - lo > 1) { const int mid = (lo + hi) >> 1; if (group_off[mid] <= g) lo = mid; else hi = mid; }
+    const int c0 = chunk_off[lo] + (g - group_off[lo]) * sidm_sum::kGroupChunks;
+    const int c1 = min(c0 + sidm_sum::kGroupChunks, chunk_off[lo + 1]);
+    sidm_sum::group_sums(part, c0, c1, gpart + 8 * (int64_t)g);
+}
+
+// Second level: one warp per halo over its groups, scaled by the particle mass.
+__global__ void k_energy_final(int H, const int32_t* __restrict__ group_off, const double* __restrict__ mass,
+                               const double* __restrict__ gpart, double* __restrict__ out, double* __restrict__ comp)
 {
     const int h = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (h >= H) return;                                  // whole warps
-    auto first_chunk = [&](int hh) {
-        int lo = 0, hi = nchunk;
-        while (lo < hi) { const int mid = (lo + hi) >> 1; if (chunk_halo[mid] < hh) lo = mid + 1; else hi = mid; }
-        return lo;
-    };
-    sidm_sum::halo_result(part, first_chunk(h), first_chunk(h + 1), mass[h], out + 4 * h, comp ? comp + 4 * h : nullptr);
+    sidm_sum::halo_result(gpart, group_off[h], group_off[h + 1], mass[h], out + 4 * h, comp ? comp + 4 * h : nullptr);
 }
 
 // ------------------------------------------------------------------ harness
@@ -1205,11 +1240,14 @@ static int radix_sort(sidm_ctx* c, unsigned long long*& ka, uint32_t*& va, unsig
         const int cgrid = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, kThreads * 4), (int64_t)c->sm_count * 4));
         SIDM_LAUNCH(c, k_sort_count<<<cgrid, kThreads, 0, s>>>(ka, n, passes, hist));
     }
+    // persistent CTAs, as many as fit on the GPU at once
+    const unsigned grid = (unsigned)std::min<int64_t>(tiles, (int64_t)c->sm_count * kPassCtas);
     for (int p = 0; p < passes; ++p) {
         SIDM_CUDA(c, cudaMemsetAsync(c->d_sort_status, 0, sizeof(unsigned long long) * 256 * (size_t)tiles, s));
-        SIDM_LAUNCH(c, k_sort_pass<<<(unsigned)tiles, kThreads, kSmemBytes, s>>>(
-            ka, va, n, 8 * p, hist + 256 * p, c->d_sort_status, tickets + p, kb, vb, &c->d_cnt->status,
-            SIDM_DEV_WAIT_TIMEOUT));
+        const bool bulk = ((reinterpret_cast<uintptr_t>(ka) | reinterpret_cast<uintptr_t>(va)) & 15u) == 0u;
+        SIDM_LAUNCH(c, k_sort_pass<<<grid, kThreads, kSmemBytes, s>>>(
+            ka, va, n, 8 * p, (int)tiles, bulk, hist + 256 * p, c->d_sort_status, tickets + p, kb, vb,
+            &c->d_cnt->status, SIDM_DEV_WAIT_TIMEOUT));
         std::swap(ka, kb);
         std::swap(va, vb);
     }
@@ -1222,7 +1260,7 @@ static void free_all(sidm_ctx* c)
                     c->d_chunk_halo, c->d_chunk_begin, c->d_frame, c->d_key, c->d_key2, c->d_val, c->d_val2,
                     c->d_sort_status, c->d_sort_hist, c->d_P4, c->d_V4, c->d_ID, c->d_cell, c->d_cellb, c->d_nlo, c->d_nhi, c->d_perm, c->d_tmp_pos,
                     c->d_tmp_vel, c->d_tmp_id, c->d_claim, c->d_hits, c->d_done, c->d_ev, c->d_sump,
-                    c->d_stats_own, c->d_cnt, c->d_epart, c->d_lam, c->d_hprev, c->d_dacc, c->d_halo_ord,
+                    c->d_stats_own, c->d_cnt, c->d_epart, c->d_chunk_off, c->d_group_off, c->d_gpart, c->d_lam, c->d_hprev, c->d_dacc, c->d_halo_ord,
                     c->d_evg, c->d_lkey, c->d_lval, c->d_lstart, c->d_llen, c->d_lptr, c->d_lact,
                     c->d_lcnt};
     for (void* p : ptrs) if (p) cudaFree(p);
@@ -1334,6 +1372,9 @@ extern "C" int sidm_create(sidm_ctx** out, const sidm_config* cfg)
     ALLOC(c->d_stats_own, 1);
     ALLOC(c->d_cnt, 1);
     ALLOC(c->d_epart, 8 * c->chunk_cap);
+    ALLOC(c->d_chunk_off, H + 1);
+    ALLOC(c->d_group_off, H + 1);
+    ALLOC(c->d_gpart, 8 * (c->chunk_cap / sidm_sum::kGroupChunks + H + 1));
     ALLOC(c->d_halo_ord, H);
     if (cfg->flags & SIDM_FLAG_DRAG) {
         const int64_t m = 2 * cfg->event_cap;
@@ -1434,6 +1475,14 @@ static int make_layout(sidm_ctx* c, int H, const int64_t* off, LayoutHost& L)
     for (int h = 0; h < H; ++h)
         for (int64_t b = off[h]; b < off[h + 1]; b += kChunk) { L.chunk_halo.push_back(h); L.chunk_begin.push_back(b); }
     L.nchunk = (int)L.chunk_halo.size();
+    L.chunk_off.assign(H + 1, 0);
+    L.group_off.assign(H + 1, 0);
+    for (int h = 0; h < H; ++h) {
+        const int nc = (int)cdiv(off[h + 1] - off[h], kChunk);
+        L.chunk_off[h + 1] = L.chunk_off[h] + nc;
+        L.group_off[h + 1] = L.group_off[h] + (int)cdiv(nc, sidm_sum::kGroupChunks);
+    }
+    L.ngroup = L.group_off[H];
     if (L.nchunk > c->chunk_cap) return set_err(c, SIDM_ECAPACITY, "chunk capacity exceeded");
     int hb = 0;
     while ((1 << hb) < H) ++hb;
@@ -1461,6 +1510,8 @@ static int upload_layout(sidm_ctx* c, cudaStream_t s)
     if ((rc = put(L.leaf_off.data(), 4 * (H + 1), c->d_leaf_off))) return rc;
     if ((rc = put(L.lvl_off.data(), 4 * L.lvl_off.size(), c->d_lvl_off))) return rc;
     if ((rc = put(L.top.data(), 4 * H, c->d_top))) return rc;
+    if ((rc = put(L.chunk_off.data(), 4 * (H + 1), c->d_chunk_off))) return rc;
+    if ((rc = put(L.group_off.data(), 4 * (H + 1), c->d_group_off))) return rc;
     if (L.nchunk) {
         if ((rc = put(L.chunk_halo.data(), 4 * L.nchunk, c->d_chunk_halo))) return rc;
         if ((rc = put(L.chunk_begin.data(), 8 * L.nchunk, c->d_chunk_begin))) return rc;
@@ -1499,21 +1550,18 @@ static int build_impl(sidm_ctx* c, double* pos, R* vel, uint32_t* id, cudaStream
     c->guess_in_p4 = hprev != nullptr;
     c->hprev_valid = false;
     if (mixed)
-        SIDM_LAUNCH(c, (k_gather<R, true><<<grid_for(c, N, 256), 256, 0, s>>>(
-            N, H, c->d_halo_off, c->d_halo_pad, c->d_leaf_off, c->d_frame, c->d_cellb, ka, va, pos, vel, id,
-            c->d_tmp_pos, (R*)c->d_tmp_vel, c->d_tmp_id, c->d_perm, (V*)c->d_P4, c->d_ID, c->d_cnt, hprev)));
+        SIDM_LAUNCH(c, (k_gather_leaves<R><<<(unsigned)cdiv((int64_t)L.L * 32, 256), 256, 0, s>>>(
+            L.L, N, c->d_leaf_halo, c->d_leaf_off, c->d_halo_off, c->d_cell, c->d_cellb, va, pos, vel, id,
+            c->d_tmp_pos, (R*)c->d_tmp_vel, c->d_tmp_id, c->d_perm, (V*)c->d_P4, c->d_ID, c->d_cnt, hprev,
+            c->d_nlo, c->d_nhi)));
     else
-        SIDM_LAUNCH(c, (k_gather<R, false><<<grid_for(c, N, 256), 256, 0, s>>>(
-            N, H, c->d_halo_off, c->d_halo_pad, c->d_leaf_off, c->d_frame, c->d_cellb, ka, va, pos, vel, id,
+        SIDM_LAUNCH(c, (k_gather<R><<<grid_for(c, N, 256), 256, 0, s>>>(
+            N, H, c->d_halo_off, c->d_halo_pad, ka, va, pos, vel, id,
             c->d_tmp_pos, (R*)c->d_tmp_vel, c->d_tmp_id, c->d_perm, (V*)c->d_P4, c->d_ID, c->d_cnt, hprev)));
     SIDM_CUDA(c, cudaMemcpyAsync(pos, c->d_tmp_pos, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s));
     SIDM_CUDA(c, cudaMemcpyAsync(vel, c->d_tmp_vel, sizeof(R) * 3 * N, cudaMemcpyDeviceToDevice, s));
     SIDM_CUDA(c, cudaMemcpyAsync(id, c->d_tmp_id, sizeof(uint32_t) * N, cudaMemcpyDeviceToDevice, s));
-    if (mixed)
-        SIDM_LAUNCH(c, k_leaf_bbox_p4<<<(L.L * 32 + 255) / 256, 256, 0, s>>>(L.L, c->d_leaf_halo, c->d_leaf_off, c->d_halo_off,
-                                                                              c->d_cell, (const float4*)c->d_P4, c->d_nlo,
-                                                                              c->d_nhi));
-    else
+    if (!mixed)
         SIDM_LAUNCH(c, k_leaf_bbox<<<(L.L * 32 + 255) / 256, 256, 0, s>>>(L.L, N, c->d_leaf_halo, c->d_leaf_off,
                                                                            c->d_halo_off, c->d_frame, pos, c->d_nlo,
                                                                            c->d_nhi));
@@ -1944,8 +1992,10 @@ extern "C" int sidm_energy_momentum(sidm_ctx* c, const double* mass, const void*
             SIDM_LAUNCH(c, k_energy_partial<float><<<L.nchunk, sidm_sum::chunk_threads<float>(), 0, s>>>(
                 (const float*)vel, L.N, c->d_chunk_halo, c->d_chunk_begin, c->d_halo_off, c->d_epart));
     }
-    SIDM_LAUNCH(c, k_energy_final<<<(L.H + 3) / 4, 128, 0, s>>>(L.H, L.nchunk, c->d_chunk_halo, mass, c->d_epart,
-                                                                     out, comp));
+    if (L.ngroup > 0)
+        SIDM_LAUNCH(c, k_energy_group<<<(L.ngroup + 3) / 4, 128, 0, s>>>(L.H, L.ngroup, c->d_group_off, c->d_chunk_off,
+                                                                         c->d_epart, c->d_gpart));
+    SIDM_LAUNCH(c, k_energy_final<<<(L.H + 3) / 4, 128, 0, s>>>(L.H, c->d_group_off, mass, c->d_gpart, out, comp));
     return SIDM_OK;
 }
 

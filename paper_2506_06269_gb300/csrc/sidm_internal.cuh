@@ -62,6 +62,8 @@ struct LayoutHost {
     std::vector<int32_t> chunk_halo;             // energy reduction chunks
     std::vector<int64_t> chunk_begin;
     int nchunk = 0;
+    std::vector<int32_t> chunk_off, group_off;   // per halo: first chunk, first group of chunks
+    int ngroup = 0;
     int sort_passes = 7;
 };
 
@@ -156,6 +158,9 @@ struct sidm_ctx {
 
     // energy partials
     double* d_epart = nullptr;         // [chunks][8]
+    int32_t* d_chunk_off = nullptr;    // [H+1] first energy chunk of each halo
+    int32_t* d_group_off = nullptr;    // [H+1] first group of chunks of each halo
+    double* d_gpart = nullptr;         // [groups][8] group sums of the energy reduction
     int64_t chunk_cap = 0;
 
     // Lambda table (float or double [kLamNR][kLamNX])

@@ -6,16 +6,18 @@
 //   k_sort_count   one read of the keys: the digit counts of every pass at once
 //                  ([passes][256], shared-memory atomics); the cell build takes
 //                  them in the kernel that makes its keys instead.
-//   k_sort_pass    one digit: a CTA takes the next tile of kTile = 2048 keys in
-//                  ticket order, holds its keys and values in registers, ranks
-//                  them per warp (warp w owns the tile's 256 consecutive keys
-//                  w*256 ..; eight ballots group equal digits of one round of
-//                  32), publishes its digit counts at once, reorders the tile by
-//                  digit in shared memory, looks back over the earlier tiles'
-//                  published counts for its exclusive prefix (8 words per round
-//                  trip) and writes the tile out in runs of equal digits
-//                  (coalesced).  Per key it moves 12 bytes in and 12 out, the
-//                  bytes of the pass.
+//   k_sort_pass    one digit: persistent CTAs (two per SM) take tiles of
+//                  kTile = 4096 keys in ticket order; the next tile's keys and
+//                  values are copied into a staging buffer (two bulk
+//                  asynchronous copies, TMA) while the current one is sorted.
+//                  A tile is ranked per warp (warp w owns the tile's 512
+//                  consecutive keys w*512 ..; eight ballots group equal digits
+//                  of one round of 32), its digit counts are published at once,
+//                  it is reordered by digit in shared memory, a look-back over
+//                  the earlier tiles' published counts gives its exclusive
+//                  prefix (8 words per round trip), and it is written out in
+//                  runs of equal digits (coalesced).  Per key a pass moves 12
+//                  bytes in and 12 out, the bytes of the pass.
 //
 // Stability: inside a tile a key's rank among equal digits counts earlier
 // warps, earlier rounds of its warp and earlier lanes of its round, i.e. the
@@ -36,10 +38,10 @@ namespace sidm_sort {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kItems = 8;                         // keys per thread
-constexpr int kTile = kThreads * kItems;          // 2048 keys per tile
-constexpr int kWarpKeys = 32 * kItems;            // 256 consecutive keys per warp
-constexpr int kPassCtas = kItems <= 8 ? 4 : 2;    // resident CTAs per SM the pass is built for
+constexpr int kItems = 16;                        // keys per thread
+constexpr int kTile = kThreads * kItems;          // 4096 keys per tile
+constexpr int kWarpKeys = 32 * kItems;            // 512 consecutive keys per warp
+constexpr int kPassCtas = 2;                      // resident CTAs per SM the pass is built for
 constexpr int kMaxPasses = 8;
 constexpr unsigned long long kFlagA = 1ull << 62;  // tile count published
 constexpr unsigned long long kFlagP = 2ull << 62;  // inclusive prefix published
@@ -48,13 +50,17 @@ constexpr unsigned long long kLookNs = 20000000ull;  // 20 ms per wait
 constexpr unsigned kLookPolls = 1u << 22;
 
 struct Smem {
-    unsigned long long key[kTile];
+    unsigned long long skey[kTile];     // staging of the next tile (bulk copies)
+    uint32_t sval[kTile];
+    unsigned long long key[kTile];      // the current tile in digit order
     uint32_t val[kTile];
     uint32_t wcnt[kWarps][256];     // per-warp digit counts, then their exclusive offsets
     long long off[256];             // global slot of the tile's first key of each digit, minus its tile slot
     uint32_t tstart[256];           // tile slot of the first key of each digit
     uint32_t wsum[kWarps];
-    int tile;
+    unsigned long long bar;             // mbarrier of the staging copies
+    int next;                           // the CTA's next ticket
+    int late;                           // a staging wait gave up: plain loads from then on
 };
 constexpr size_t kSmemBytes = sizeof(Smem);
 
@@ -181,38 +187,19 @@ __device__ __forceinline__ unsigned long long look_back(const unsigned long long
     return excl;
 }
 
-// One digit pass: kin/vin -> kout/vout by digit (key >> shift) & 255.
-// cnt = this pass's 256 digit totals; status [tiles][256] and *ticket zero on
-// entry; dynamic shared memory kSmemBytes.  The tile's counts are published
-// as soon as they are known and the tile is reordered in shared memory (which
-// frees the key registers) before the look-back.
-__global__ void __launch_bounds__(kThreads, kPassCtas) k_sort_pass(const unsigned long long* __restrict__ kin,
-                                                           const uint32_t* __restrict__ vin, int64_t n, int shift,
-                                                           const uint32_t* __restrict__ cnt,
-                                                           unsigned long long* __restrict__ status,
-                                                           unsigned int* __restrict__ ticket,
-                                                           unsigned long long* __restrict__ kout,
-                                                           uint32_t* __restrict__ vout, unsigned int* __restrict__ err,
-                                                           unsigned int err_bit)
+// One tile of one digit pass, its keys and values in registers (k, v; slot
+// r of lane l of warp w is tile key w*kWarpKeys + r*32 + l).  Ranks per warp,
+// publishes the tile's counts, reorders the tile in shared memory, looks back
+// for the exclusive prefix and writes the tile out.  Called by all threads;
+// S.wcnt must be zero on entry.
+__device__ __forceinline__ void sort_tile(Smem& S, const unsigned long long (&k)[kItems], const uint32_t (&v)[kItems],
+                                          int tile, int64_t n, int shift, const uint32_t* __restrict__ cnt,
+                                          unsigned long long* __restrict__ status, unsigned long long* __restrict__ kout,
+                                          uint32_t* __restrict__ vout, unsigned int* err, unsigned int err_bit)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem& S = *reinterpret_cast<Smem*>(smem_raw);
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    if (t == 0) S.tile = (int)atomicAdd(ticket, 1u);
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) S.wcnt[w][t] = 0u;
-    __syncthreads();
-    const int tile = S.tile;
     const int64_t t0 = (int64_t)tile * kTile;
     const int64_t wbase = t0 + warp * kWarpKeys;
-    unsigned long long k[kItems];
-    uint32_t v[kItems];
-#pragma unroll
-    for (int r = 0; r < kItems; ++r) {
-        const int64_t s = wbase + r * 32 + lane;
-        k[r] = s < n ? kin[s] : 0ull;
-        v[r] = s < n ? vin[s] : 0u;
-    }
     // rank among equal digits inside the warp's kWarpKeys keys
     const uint32_t lt = (1u << lane) - 1u;
     uint32_t rk[kItems];
@@ -274,6 +261,114 @@ __global__ void __launch_bounds__(kThreads, kPassCtas) k_sort_pass(const unsigne
             kout[dst] = kk;
             vout[dst] = S.val[pos];
         }
+    }
+}
+
+// One digit pass: kin/vin -> kout/vout by digit (key >> shift) & 255.
+// Persistent CTAs (grid <= tiles) take tiles in ticket order; while a CTA
+// sorts one tile, the next one's keys and values are already on their way
+// into a staging buffer by two bulk asynchronous copies (TMA, one thread,
+// completion counted on an mbarrier).  The wait is bounded: on expiry the
+// status bit is raised, no copy is issued any more, tiles are read with plain
+// loads, and the CTA waits (again bounded) for the late copy before it exits.
+// A tile whose copy would not be whole (the last one, when n is not a
+// multiple of kTile, or every tile when kin or vin is not 16-byte aligned) is
+// read with plain loads.  cnt = this pass's 256 digit
+// totals; status [tiles][256] and *ticket zero on entry; dynamic shared
+// memory kSmemBytes.
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t ph)
+{
+    const unsigned long long t0 = now_ns();
+    for (unsigned it = 0; it < kLookPolls; ++it) {
+        uint32_t r;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(r) : "r"(bar), "r"(ph) : "memory");
+        if (r) return true;
+        if (now_ns() - t0 > kLookNs) return false;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(kThreads, kPassCtas) k_sort_pass(const unsigned long long* __restrict__ kin,
+                                                           const uint32_t* __restrict__ vin, int64_t n, int shift,
+                                                           int tiles, bool bulk, const uint32_t* __restrict__ cnt,
+                                                           unsigned long long* __restrict__ status,
+                                                           unsigned int* __restrict__ ticket,
+                                                           unsigned long long* __restrict__ kout,
+                                                           uint32_t* __restrict__ vout, unsigned int* __restrict__ err,
+                                                           unsigned int err_bit)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&S.bar);
+    // thread 0: the copies of tile tl into the staging buffer
+    auto issue = [&](int tl) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                     "r"((uint32_t)(kTile * 12)) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     ::"r"((uint32_t)__cvta_generic_to_shared(S.skey)), "l"(kin + (int64_t)tl * kTile),
+                     "r"((uint32_t)(kTile * 8)), "r"(bar) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     ::"r"((uint32_t)__cvta_generic_to_shared(S.sval)), "l"(vin + (int64_t)tl * kTile),
+                     "r"((uint32_t)(kTile * 4)), "r"(bar) : "memory");
+    };
+    // bulk: kin and vin 16-byte aligned (a copy must start on a 16-byte boundary)
+    auto whole = [&](int tl) { return bulk && (int64_t)(tl + 1) * kTile <= n; };
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(1u) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        S.next = (int)atomicAdd(ticket, 1u);
+        S.late = 0;
+        if (S.next < tiles && whole(S.next)) issue(S.next);
+    }
+    __syncthreads();
+    int tile = S.next;
+    uint32_t phase = 0u;
+    bool staged = tile < tiles && whole(tile);
+    bool pending = false;                      // a copy gave up on may still land
+    while (tile < tiles) {
+        unsigned long long k[kItems];
+        uint32_t v[kItems];
+        bool from_stage = false;
+        if (staged) {
+            const bool ok = __syncthreads_and(bar_wait(bar, phase));
+            if (ok) {
+                phase ^= 1u;
+                from_stage = true;
+            } else {
+                pending = true;
+                if (t == 0) { S.late = 1; atomicOr(err, err_bit); }
+            }
+        }
+        const int64_t wbase = (int64_t)tile * kTile + warp * kWarpKeys;
+#pragma unroll
+        for (int r = 0; r < kItems; ++r) {
+            const int li = warp * kWarpKeys + r * 32 + lane;
+            const int64_t s = wbase + r * 32 + lane;
+            k[r] = from_stage ? S.skey[li] : (s < n ? kin[s] : 0ull);
+            v[r] = from_stage ? S.sval[li] : (s < n ? vin[s] : 0u);
+        }
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) S.wcnt[w][t] = 0u;
+        __syncthreads();                       // staging buffer read, S.next free
+        if (t == 0) {
+            S.next = (int)atomicAdd(ticket, 1u);
+            if (!S.late && S.next < tiles && whole(S.next)) issue(S.next);
+        }
+        __syncthreads();
+        const int next = S.next;
+        const bool next_staged = !S.late && next < tiles && whole(next);
+        sort_tile(S, k, v, tile, n, shift, cnt, status, kout, vout, err, err_bit);
+        __syncthreads();                       // S.key / S.off / S.wcnt reused by the next tile
+        tile = next;
+        staged = next_staged;
+    }
+    // a copy whose wait gave up may still be writing this CTA's shared memory
+    if (pending) {
+        const bool ok = __syncthreads_and(bar_wait(bar, phase));
+        if (!ok && t == 0) atomicOr(err, err_bit);
     }
 }
 

@@ -21,16 +21,20 @@ namespace {
 
 constexpr int kStaticChunk = 16384;
 
-// Scratch of every call: [SIDM_STATIC_MAX_CHUNKS][8] doubles = 256 KiB.
-// Each call overwrites the entries of its own chunks before reading them, so
-// nothing has to start at zero.  Calls that overlap on the GPU race here.
-static __device__ __align__(256) double g_static_partials[SIDM_STATIC_MAX_CHUNKS * 8];
+// Scratch of every call: [SIDM_STATIC_MAX_CHUNKS][8] chunk sums, then
+// [kStaticMaxGroups][8] group sums (doubles, 268 KiB).  Each call overwrites
+// the entries of its own chunks and groups before reading them, so nothing has
+// to start at zero.  Calls that overlap on the GPU race here.
+constexpr int kStaticMaxGroups = SIDM_STATIC_MAX_CHUNKS / sidm_sum::kGroupChunks + SIDM_STATIC_MAX_HALOS;
+static __device__ __align__(256) double g_static_partials[(SIDM_STATIC_MAX_CHUNKS + kStaticMaxGroups) * 8];
 
 struct StaticLayout {
     int n_halos;
     int n_chunks;
+    int n_groups;
     long long halo_off[SIDM_STATIC_MAX_HALOS + 1];
     int chunk_off[SIDM_STATIC_MAX_HALOS + 1];   // first chunk of each halo
+    int group_off[SIDM_STATIC_MAX_HALOS + 1];   // first group of chunks of each halo
 };
 
 static_assert(kStaticChunk <= sidm_sum::kMaxChunk, "chunk larger than the exact-sum windows allow");
@@ -48,12 +52,24 @@ __global__ void __launch_bounds__(sidm_sum::chunk_threads<R>()) k_static_partial
     sidm_sum::chunk_sums(vel, N, b, e, part + 8 * (long long)c);
 }
 
-__global__ void k_static_final(StaticLayout lay, const double* __restrict__ mass, const double* __restrict__ part,
+// the two merge levels of sidm_sum.cuh, in the order sidm_energy_momentum uses
+__global__ void k_static_group(StaticLayout lay, const double* __restrict__ part, double* __restrict__ gpart)
+{
+    const int g = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);   // one warp per group
+    if (g >= lay.n_groups) return;
+    int h = 0;
+    while (h + 1 < lay.n_halos && lay.group_off[h + 1] <= g) ++h;
+    const int c0 = lay.chunk_off[h] + (g - lay.group_off[h]) * sidm_sum::kGroupChunks;
+    const int c1 = min(c0 + sidm_sum::kGroupChunks, lay.chunk_off[h + 1]);
+    sidm_sum::group_sums(part, c0, c1, gpart + 8 * (long long)g);
+}
+
+__global__ void k_static_final(StaticLayout lay, const double* __restrict__ mass, const double* __restrict__ gpart,
                                double* __restrict__ out, double* __restrict__ comp)
 {
     const int h = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);   // one warp per halo
     if (h >= lay.n_halos) return;
-    sidm_sum::halo_result(part, lay.chunk_off[h], lay.chunk_off[h + 1], mass[h], out + 4 * h,
+    sidm_sum::halo_result(gpart, lay.group_off[h], lay.group_off[h + 1], mass[h], out + 4 * h,
                           comp ? comp + 4 * h : nullptr);
 }
 
@@ -80,6 +96,7 @@ extern "C" int sidm_energy_momentum_static(int32_t n_halos, const int64_t* halo_
     StaticLayout lay;
     lay.n_halos = n_halos;
     lay.chunk_off[0] = 0;
+    lay.group_off[0] = 0;
     long long chunks = 0;
     for (int h = 0; h < n_halos; ++h) {
         if (halo_off[h + 1] < halo_off[h]) return static_fail(SIDM_EINVAL, "halo_off must be non-decreasing");
@@ -88,7 +105,10 @@ extern "C" int sidm_energy_momentum_static(int32_t n_halos, const int64_t* halo_
         if (chunks > SIDM_STATIC_MAX_CHUNKS)
             return static_fail(SIDM_ECAPACITY, "more than SIDM_STATIC_MAX_CHUNKS chunks of 16384 particles");
         lay.chunk_off[h + 1] = (int)chunks;
+        const int nc = lay.chunk_off[h + 1] - lay.chunk_off[h];
+        lay.group_off[h + 1] = lay.group_off[h] + (nc + sidm_sum::kGroupChunks - 1) / sidm_sum::kGroupChunks;
     }
+    lay.n_groups = lay.group_off[n_halos];
     lay.halo_off[n_halos] = halo_off[n_halos];
     lay.n_chunks = (int)chunks;
     if (!mass_dev || !out_dev || (halo_off[n_halos] > 0 && !vel_dev)) return static_fail(SIDM_EINVAL, "null argument");
@@ -132,7 +152,13 @@ extern "C" int sidm_energy_momentum_static(int32_t n_halos, const int64_t* halo_
         e = cudaGetLastError();
         if (e != cudaSuccess) return static_fail(SIDM_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
     }
-    k_static_final<<<(n_halos + 3) / 4, 128, 0, stream>>>(lay, mass_dev, part, out_dev, comp_dev);
+    double* gpart = part + (size_t)SIDM_STATIC_MAX_CHUNKS * 8;
+    if (lay.n_groups > 0) {
+        k_static_group<<<(unsigned)((lay.n_groups + 3) / 4), 128, 0, stream>>>(lay, part, gpart);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return static_fail(SIDM_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
+    }
+    k_static_final<<<(n_halos + 3) / 4, 128, 0, stream>>>(lay, mass_dev, gpart, out_dev, comp_dev);
     e = cudaGetLastError();
     if (e != cudaSuccess) return static_fail(SIDM_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
     g_static_err.clear();

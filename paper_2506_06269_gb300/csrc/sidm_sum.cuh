@@ -5,9 +5,12 @@
 // Both reduce a halo in chunks of at most 16384 particles, one CTA per chunk
 // (512 threads for FP32 velocities, 256 for FP64), to four unscaled sums
 // S = (sum |v|^2, sum vx, sum vy, sum vz), each kept as a double-double
-// (hi, lo); one warp per halo then merges its chunk sums in a fixed order
-// (lane l takes chunks l, l+32, ... in turn, then a fixed shuffle tree) and
-// scales them by (m/2, m, m, m).
+// (hi, lo).  The chunk sums are merged in a fixed order in two levels, so
+// that the slow FP64 pipe of a single SM never takes a whole large halo: one
+// warp per group of up to 32 consecutive chunks of a halo (lane i takes chunk
+// i, then a fixed shuffle tree), then one warp per halo over its groups (lane
+// l takes groups l, l+32, ... in turn, then the same tree), scaled by
+// (m/2, m, m, m).
 //
 // FP32 velocities (the mixed form) are summed EXACTLY on the integer pipes.
 // GB300 issues FP64 arithmetic at a small fraction of its FP32/INT32 rate, so
@@ -21,6 +24,14 @@
 // the chunk's largest term in all.  Integer addition is associative, so the chunk sums do
 // not depend on the order of the tree.  Each chunk's integer then becomes the
 // double-double (RN(S), RN(S - RN(S))).
+//
+// Nearly every component lies within 2^16 of the chunk's largest (e >= E-16)
+// or is zero; a thread sums those in narrower exact windows first: the
+// linear terms as 64-bit integers in units of 2^(E-39) (m 2^(e-E+16) < 2^40,
+// at most 32 per thread), the squares as 128-bit integers in units of
+// 2^(2E-78) (below 2^80).  Shifted by 72 and 32 bits these are the same
+// integers in the chunk's windows, so the sums are bit-identical; the others
+// take the general route.
 //
 // FP64 velocities (the FP64 form) keep a compensated (two-sum) FP64 sum in a
 // fixed order: thread t takes elements t, t+256, ..., then a fixed binary tree
@@ -103,6 +114,31 @@ __device__ __forceinline__ void exact_add(float x, int E, u128& lin, u128& sq)
     sq += ((u128)shr64(M2 << 16, 80 - o2) << 64) | (shl64(M2, o2) | shr64(M2, -o2));
 }
 
+// Thread-level narrow windows of the components with e >= E - 16 (or zero):
+// lin += x / 2^(E-39), sq += x^2 / 2^(2E-78), exact; the rest go to the chunk
+// windows through exact_add.
+struct NarrowSums {
+    long long lx = 0, ly = 0, lz = 0;
+    u128 sq = 0;
+};
+__device__ __forceinline__ void narrow_add(float x, int E, long long& lin, NarrowSums& ns, u128& wide_lin,
+                                           u128& wide_sq)
+{
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t ex = (b >> 23) & 255u;
+    const uint32_t m = (b & 0x7FFFFFu) | (ex ? 0x800000u : 0u);
+    const int s1 = (int)ex - 127 - E + 16;                   // e - E + 16 for normal x
+    if (ex != 0u && s1 >= 0) {
+        const long long t = (long long)((unsigned long long)m << s1);
+        lin += (b >> 31) ? -t : t;
+        const unsigned long long M2 = (unsigned long long)m * m;
+        const int s2 = 2 * s1;                               // 0 .. 32
+        ns.sq += ((u128)shr64(M2, 64 - s2) << 64) | shl64(M2, s2);
+    } else if (m != 0u) {
+        exact_add(x, E, wide_lin, wide_sq);
+    }
+}
+
 __device__ __forceinline__ u128 shfl_down_u128(u128 v, int o)
 {
     const unsigned long long lo = __shfl_down_sync(0xffffffffu, (unsigned long long)v, o);
@@ -169,12 +205,18 @@ __device__ __forceinline__ void chunk_sums(const float* __restrict__ vel, int64_
     }
     const int E = (int)(M ? M : 1u) - 127;
     u128 sq = 0, lx = 0, ly = 0, lz = 0;
+    NarrowSums ns;
 #pragma unroll 4
     for (int64_t s = b + threadIdx.x; s < e; s += kThreads) {
-        exact_add(vel[s], E, lx, sq);
-        exact_add(vel[N + s], E, ly, sq);
-        exact_add(vel[2 * N + s], E, lz, sq);
+        narrow_add(vel[s], E, ns.lx, ns, lx, sq);
+        narrow_add(vel[N + s], E, ns.ly, ns, ly, sq);
+        narrow_add(vel[2 * N + s], E, ns.lz, ns, lz, sq);
     }
+    // narrow windows into the chunk's: x 2^72 (linear, sign-extended), x 2^32 (squares)
+    lx += (u128)(__int128)ns.lx << 72;
+    ly += (u128)(__int128)ns.ly << 72;
+    lz += (u128)(__int128)ns.lz << 72;
+    sq += ns.sq << 32;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         sq += shfl_down_u128(sq, o);
@@ -233,7 +275,28 @@ __device__ __forceinline__ DD shfl_down_dd(const DD& x, int o)
     return DD{__shfl_down_sync(0xffffffffu, x.s, o), __shfl_down_sync(0xffffffffu, x.c, o)};
 }
 
-// A halo's chunk sums part[c0 .. c1) merged by one warp in a fixed order
+constexpr int kGroupChunks = 32;   // chunks per first-level group
+
+// Chunks part[c0 .. c1) (c1 - c0 <= kGroupChunks) of one halo merged by one
+// warp: lane i takes chunk c0 + i, then lane i takes lane i+16, i+8, ...;
+// out8 = the group's four double-doubles.  Called by all 32 lanes of a warp.
+__device__ __forceinline__ void group_sums(const double* __restrict__ part, int c0, int c1, double* __restrict__ out8)
+{
+    const int lane = threadIdx.x & 31;
+    DD acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    if (c0 + lane < c1)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) acc[a] = DD{part[(c0 + lane) * 8 + 2 * a], part[(c0 + lane) * 8 + 2 * a + 1]};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) dd_merge(acc[a], shfl_down_dd(acc[a], o));
+    if (lane == 0)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) { out8[2 * a] = acc[a].s; out8[2 * a + 1] = acc[a].c; }
+}
+
+// A halo's group sums part[c0 .. c1) merged by one warp in a fixed order
 // (lane l: chunks c0+l, c0+l+32, ...; then lane i takes lane i+16, i+8, ...),
 // then out = (m/2 S2, m Sx, m Sy, m Sz) and comp the rounding residual of
 // each.  Called by all 32 lanes of a warp.
