@@ -180,17 +180,31 @@ __global__ void __launch_bounds__(256) k_keys(const double* __restrict__ pos, in
     __shared__ uint32_t sh[sidm_sort::kMaxPasses][256];
     for (int i = threadIdx.x; i < sidm_sort::kMaxPasses * 256; i += blockDim.x) (&sh[0][0])[i] = 0u;
     __syncthreads();
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
-        const int h = H == 1 ? 0 : halo_of(halo_off, H, s);
-        const HaloFrame& f = fr[h];
-        const uint32_t q0 = morton_coord(pos[s], f.O[0], f.E);
-        const uint32_t q1 = morton_coord(pos[N + s], f.O[1], f.E);
-        const uint32_t q2 = morton_coord(pos[2 * N + s], f.O[2], f.E);
-        const unsigned long long k =
-            ((unsigned long long)h << kHaloShift) | spread3(q0) | (spread3(q1) << 1) | (spread3(q2) << 2);
-        key[s] = k;
-        val[s] = (uint32_t)s;
-        sidm_sort::count_digits(sh, k, passes);
+    // two particles per thread and trip, their six loads issued together
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s0 < N; s0 += 2 * stride) {
+        double x[2][3];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int64_t s = s0 + u * stride;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) x[u][a] = s < N ? pos[a * N + s] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int64_t s = s0 + u * stride;
+            if (s >= N) break;
+            const int h = H == 1 ? 0 : halo_of(halo_off, H, s);
+            const HaloFrame& f = fr[h];
+            const uint32_t q0 = morton_coord(x[u][0], f.O[0], f.E);
+            const uint32_t q1 = morton_coord(x[u][1], f.O[1], f.E);
+            const uint32_t q2 = morton_coord(x[u][2], f.O[2], f.E);
+            const unsigned long long k =
+                ((unsigned long long)h << kHaloShift) | spread3(q0) | (spread3(q1) << 1) | (spread3(q2) << 2);
+            key[s] = k;
+            val[s] = (uint32_t)s;
+            sidm_sort::count_digits(sh, k, passes);
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) {
@@ -972,10 +986,28 @@ template <class R>
 __global__ void k_drift(int64_t N, int H, const int64_t* __restrict__ halo_off, const double* __restrict__ dt,
                         double* __restrict__ pos, const R* __restrict__ vel)
 {
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
-        const double d = dt[halo_of(halo_off, H, s)];
+    // two particles per thread and trip, their loads issued together
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s0 < N; s0 += 2 * stride) {
+        double x[2][3];
+        R v[2][3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) pos[a * N + s] = __fma_rn((double)vel[a * N + s], d, pos[a * N + s]);   // one FP64 op
+        for (int u = 0; u < 2; ++u) {
+            const int64_t s = s0 + u * stride;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                x[u][a] = s < N ? pos[a * N + s] : 0.0;
+                v[u][a] = s < N ? vel[a * N + s] : R(0);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int64_t s = s0 + u * stride;
+            if (s >= N) break;
+            const double d = dt[H == 1 ? 0 : halo_of(halo_off, H, s)];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) pos[a * N + s] = __fma_rn((double)v[u][a], d, x[u][a]);   // one FP64 op
+        }
     }
 }
 

@@ -129,11 +129,12 @@ __device__ __forceinline__ void narrow_add(float x, int E, long long& lin, Narro
     const uint32_t m = (b & 0x7FFFFFu) | (ex ? 0x800000u : 0u);
     const int s1 = (int)ex - 127 - E + 16;                   // e - E + 16 for normal x
     if (ex != 0u && s1 >= 0) {
-        const long long t = (long long)((unsigned long long)m << s1);
+        const unsigned long long tu = (unsigned long long)m << s1;   // < 2^40
+        const long long t = (long long)tu;
         lin += (b >> 31) ? -t : t;
-        const unsigned long long M2 = (unsigned long long)m * m;
-        const int s2 = 2 * s1;                               // 0 .. 32
-        ns.sq += ((u128)shr64(M2, 64 - s2) << 64) | shl64(M2, s2);
+        // x^2 / 2^(2E-78) = t^2 < 2^80: a 64 x 64 -> 128-bit product (multiply
+        // pipe, not the shift/logic pipe the rest of this sum keeps busy)
+        ns.sq += ((u128)__umul64hi(tu, tu) << 64) | (tu * tu);
     } else if (m != 0u) {
         exact_add(x, E, wide_lin, wide_sq);
     }
