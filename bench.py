@@ -945,7 +945,7 @@ def main_ours(args):
             "local_diagnostics": res["local_diag"],
             "tuning_trials": len(res["tuning"]),
             "knn_warm_start": {"ms_per_launch_warm": kms[1] / K, "ms_per_launch_cold": res["knn_cold_ms"],
-                               "note": "kernel sizes start from the previous step's h (bound 1.0625 h_prev); "
+                               "note": "kernel sizes start from the previous step's h (bound knn_slack h_prev); "
                                        "particles with fewer than N_ngb candidates inside are redone cold; "
                                        "results bit-identical to the cold search"},
         }

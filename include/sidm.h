@@ -82,12 +82,12 @@ typedef struct {
     int32_t use_tma;     /* 1: stage candidate tiles with bulk async copies (TMA)    */
     /* launch knobs of the hot kernels; none changes a result (0 = default) */
     int32_t knn_groups;  /* kernel-size search: lane groups of the candidate mask,   */
-                         /*   2, 4 or 8 (default 4; plain-load path)                 */
+                         /*   2, 4 or 8 (default 2; plain-load path)                 */
     int32_t knn_chains;  /*   independent distance chains, 4 or 8 (default 4; 8     */
                          /*   with knn_groups 4 only)                                */
     int32_t knn_flush;   /*   pending keys per lane that trigger a heap merge before */
-                         /*   a tree node's tests, 1..32 (default 16)                */
-    float   knn_slack;   /*   warm-start bound / previous kernel size, 1..2 (1.0625) */
+                         /*   a tree node's tests, 1..32 (default 32)                */
+    float   knn_slack;   /*   warm-start bound / previous kernel size, 1..2 (1.05)   */
     int32_t pair_per_round; /* pair kernel: pairs a lane queues per round, 1..4 (4; mixed-form draws) */
     int32_t knn_batch;   /* kernel-size search: 1 loops over each staged leaf's      */
                          /*   candidates, 2 over compacted batches of them (default 2; */
@@ -413,7 +413,8 @@ int sidm_timestep_criterion(sidm_ctx* ctx, double tau, double dt_min, double dt_
  * last sidm_kernel_sizes call (carried through the permutation, so the
  * caller's arrays must still be in the order that call left them, with the
  * same halo layout and N_ngb).  The search then only admits candidates within
- * 1.0625 times that size; a particle with fewer than N_ngb of them is redone
+ * knn_slack times that size (1.05 by default); a particle with fewer than
+ * N_ngb of them is redone
  * from scratch in the same launch.  The result is the exact k-th distance in
  * every case -- a stale or wrong guess costs time, never accuracy -- so this
  * is the usual SPH practice of starting from the previous smoothing length

@@ -1330,7 +1330,7 @@ extern "C" int sidm_create(sidm_ctx** out, const sidm_config* cfg)
         !(cfg->knn_chains == 0 || cfg->knn_chains == 4 || cfg->knn_chains == 8) || cfg->knn_flush < 0 ||
         cfg->knn_flush > 32 || !(cfg->knn_slack == 0.f || (cfg->knn_slack >= 1.f && cfg->knn_slack <= 2.f)) ||
         cfg->pair_per_round < 0 || cfg->pair_per_round > 4 || cfg->knn_batch < 0 || cfg->knn_batch > 2 ||
-        (cfg->knn_chains == 8 && cfg->knn_groups != 0 && cfg->knn_groups != 4)) {
+        (cfg->knn_chains == 8 && cfg->knn_groups != 4)) {
         g_create_err = "launch knobs out of range (knn_groups 2/4/8, knn_chains 4/8 (8 with 4 groups), "
                        "knn_flush <= 32, knn_slack in [1, 2], pair_per_round <= 4, knn_batch <= 2)";
         return SIDM_EINVAL;

@@ -157,8 +157,10 @@ static_assert(kPend >= kLeaf, "a tile can admit all of its candidates: one empty
 // groups of 32 / G consecutive lanes whose boxes filter the candidates,
 // independent distance chains in the candidate loop, the pending count at
 // which the lists are merged before a tree node's tests, and the warm-start
-// bound factor (previous kernel size times it)
-constexpr int kGroupsDefault = 4;
+// bound factor (previous kernel size times it); the values the autotuner
+// picks on the GB300 for the 2^20 NFW halo at N_ngb = 64 (1.90 ms against
+// 2.00 ms for 4 groups, flush 16 and a bound of 1.0625)
+constexpr int kGroupsDefault = 2;
 // compacted candidate batches (knob knn_batch): candidates that pass the group
 // filter are appended to a per-warp buffer and the distance loop runs over
 // batches of kBatch of them; the buffer holds a batch's leftover (< kBatch)
@@ -168,8 +170,8 @@ constexpr int kBufCap = kBatch + kLeaf;
 static_assert(kPend >= kBatch, "a batch can admit all of its candidates: one empty pending list must hold them");
 constexpr int kChainsDefault = 4;
 constexpr int kBatchDefault = 2;                   // 1: loop per staged leaf, 2: compacted batches
-constexpr int kFlushNodeDefault = 16;
-constexpr float kGuessSlackDefault = 1.0625f;
+constexpr int kFlushNodeDefault = 32;
+constexpr float kGuessSlackDefault = 1.05f;
 
 template <class R>
 __device__ __forceinline__ float to_float_ru(R v)

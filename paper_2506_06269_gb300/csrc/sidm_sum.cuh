@@ -75,8 +75,6 @@ __device__ __forceinline__ void dd_merge(DD& x, const DD& y)
 
 typedef unsigned __int128 u128;
 
-// largest biased exponent field of the three components of one particle
-__device__ __forceinline__ uint32_t exp_field(float x) { return (__float_as_uint(x) >> 23) & 255u; }
 
 // 64-bit shifts whose amount is taken unsigned and clamped at 64 (PTX shl/shr
 // semantics): an amount of 64 or more, or a negative int, gives 0
@@ -190,11 +188,14 @@ __device__ __forceinline__ void chunk_sums(const float* __restrict__ vel, int64_
     __shared__ uint32_t s_max[kWarps];
     __shared__ u128 s_part[kWarps][4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t mx = 0u;
-#pragma unroll 4
+    // the largest |bit pattern| has the largest exponent field (an infinity or
+    // NaN gives 255)
+    uint32_t mb = 0u;
+#pragma unroll 8
     for (int64_t s = b + threadIdx.x; s < e; s += kThreads)
-        mx = max(mx, max(exp_field(vel[s]), max(exp_field(vel[N + s]), exp_field(vel[2 * N + s]))));
-    mx = __reduce_max_sync(0xffffffffu, mx);
+        mb = max(mb, max(__float_as_uint(vel[s]) & 0x7FFFFFFFu,
+                         max(__float_as_uint(vel[N + s]) & 0x7FFFFFFFu, __float_as_uint(vel[2 * N + s]) & 0x7FFFFFFFu)));
+    uint32_t mx = __reduce_max_sync(0xffffffffu, mb) >> 23;
     if (lane == 0) s_max[warp] = mx;
     __syncthreads();
     uint32_t M = 0u;

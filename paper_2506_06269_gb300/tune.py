@@ -37,7 +37,7 @@ PAIR_KNOBS = {
     "pair_warps": (4, 8),
     "pair_per_round": (3, 4),
 }
-DEFAULTS = {"knn_warps": 8, "knn_batch": 2, "knn_groups": 4, "knn_chains": 4, "knn_flush": 16, "knn_slack": 1.0625,
+DEFAULTS = {"knn_warps": 8, "knn_batch": 2, "knn_groups": 2, "knn_chains": 4, "knn_flush": 32, "knn_slack": 1.05,
             "pair_warps": 8, "pair_per_round": 4, "use_tma": 0}
 
 

@@ -194,10 +194,10 @@ def test_launch_knobs_give_identical_bits(precision):
     b = ics.batch([ics.nfw(6000, 21), ics.hernquist(2500, 22), ics.uniform_box(700, 23)])
     ks, xs, dts = [64, 16, 128], [(1, 100.0, 0.3811), (0, 10.0, 1.0), (0, 5.0, 1.0)], [0.2, 0.05, 0.01]
     ref = _two_steps(b, ks, xs, dts, precision, {})
-    for kw in (dict(knn_groups=2), dict(knn_groups=8), dict(knn_chains=8), dict(knn_flush=1),
+    for kw in (dict(knn_groups=4), dict(knn_groups=8), dict(knn_chains=8, knn_groups=4), dict(knn_flush=1),
                dict(knn_flush=32, knn_slack=1.001), dict(knn_slack=2.0), dict(pair_per_round=1),
                dict(pair_per_round=3, knn_groups=8), dict(knn_batch=1), dict(knn_batch=1, knn_groups=2, knn_flush=4),
-               dict(knn_batch=1, knn_chains=8, knn_slack=1.3), dict(knn_groups=2, knn_flush=4, pair_warps=3),
+               dict(knn_batch=1, knn_chains=8, knn_groups=4, knn_slack=1.3), dict(knn_groups=2, knn_flush=4, pair_warps=3),
                dict(use_tma=1)):
         got = _two_steps(b, ks, xs, dts, precision, kw)
         for (h0, v0, e0), (h1, v1, e1) in zip(ref, got):
