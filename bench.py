@@ -54,8 +54,8 @@ OPS_PER_LAMBDA = 50        # sqrt(d^2) + Lambda table (bicubic, 16 loads) + P + 
 OPS_PER_KNN_CAND = 8       # canonical d^2 (6) + key compare (2)
 # the kernel-size search as the scope table counts it: about 6 N_ngb candidate
 # distances of about 9 FP32 operations per particle
-KNN_SURVEY_CANDS_PER_NGB, KNN_SURVEY_OPS_PER_CAND = 6, 9
-PAIR_SURVEY_OPS = 130              # per in-range pair: ~60 FP32 with the Lambda table + ~70 INT32 of Philox
+KNN_SCOPE_CANDS_PER_NGB, KNN_SCOPE_OPS_PER_CAND = 6, 9
+PAIR_SCOPE_OPS = 130              # per in-range pair: ~60 FP32 with the Lambda table + ~70 INT32 of Philox
 BUILD_BUDGET_BYTES = 184           # 12 + 12 + 4 sort passes x 24 + 32 + 32
 
 # the paper's top resolution: cored-isothermal inner profile joined to NFW
@@ -853,9 +853,9 @@ def roofline(res, peaks, peak_src, name=None):
                                f"({peak_src} sm_max_mhz)",
                 "ops_per_unit": {"candidate_test": OPS_PER_TEST, "pair_eval": OPS_PER_PAIR,
                                  "lambda_lookup": OPS_PER_LAMBDA},
-                "scope_table_count": {"ops_per_pair": PAIR_SURVEY_OPS,
-                                      "achieved": res["n_pairs"] / K * PAIR_SURVEY_OPS / (per_launch_ms * 1e-3) / 1e12,
-                                      "frac": res["n_pairs"] / K * PAIR_SURVEY_OPS / (per_launch_ms * 1e-3) / 1e12
+                "scope_table_count": {"ops_per_pair": PAIR_SCOPE_OPS,
+                                      "achieved": res["n_pairs"] / K * PAIR_SCOPE_OPS / (per_launch_ms * 1e-3) / 1e12,
+                                      "frac": res["n_pairs"] / K * PAIR_SCOPE_OPS / (per_launch_ms * 1e-3) / 1e12
                                       / alu_peak},
                 "ms_per_launch": per_launch_ms}
     if name == "knn":
@@ -864,7 +864,7 @@ def roofline(res, peaks, peak_src, name=None):
         # the distances the kernel actually computed are given beside it
         cand = res.get("knn_candidates_per_step")
         tr = traffic.get("knn")
-        ops_pp = KNN_SURVEY_CANDS_PER_NGB * N_NGB * KNN_SURVEY_OPS_PER_CAND
+        ops_pp = KNN_SCOPE_CANDS_PER_NGB * N_NGB * KNN_SCOPE_OPS_PER_CAND
         achieved = n * ops_pp / (per_launch_ms * 1e-3) / 1e12
         impl = (cand * OPS_PER_KNN_CAND) / (per_launch_ms * 1e-3) / 1e12 if cand else None
         return {"kernel": "k_knn", "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
