@@ -349,7 +349,9 @@ def run_ours(args):
 def run_e2e(res, steps):
     """Same metric through the C ABI with host buffers: every step copies its
     inputs (positions, velocities, ids) from pinned host memory and reads the
-    results (velocities and the energy/momentum) back."""
+    results (the reordered positions and ids, the velocities and the
+    energy/momentum) back; the positions and ids are read back on a second
+    stream while the kernel sizes and pairs run."""
     import torch
     ctx = res["ctx"]
     halo = res["halo"]
@@ -363,22 +365,35 @@ def run_e2e(res, steps):
     out_e = torch.empty((steps, 4), dtype=torch.float64).pin_memory()
     energy = torch.zeros(4, dtype=torch.float64, device=ctx.device)
     s = torch.cuda.current_stream()
+    # positions and ids are final once the cells are built (the kernel sizes
+    # and the scatter change only velocities), so their download runs on a
+    # second stream beside the kernel-size and pair kernels; the next upload
+    # waits for it
+    side = torch.cuda.Stream(device=ctx.device)
+    built, copied = torch.cuda.Event(), torch.cuda.Event()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(s)
     for i in range(steps):
+        if i > 0:
+            s.wait_event(copied)
         pos.copy_(hp, non_blocking=True)
         vel.copy_(hv, non_blocking=True)
         ids.copy_(hi, non_blocking=True)
         ctx.drift(dt_t, pos, vel)
         ctx.build_cells([0, n], pos, vel, ids)
+        built.record(s)
+        side.wait_event(built)
+        with torch.cuda.stream(side):
+            hp.copy_(pos, non_blocking=True)
+            hi.copy_(ids, non_blocking=True)
+            copied.record(side)
         ctx.kernel_sizes([N_NGB], h)
         ctx.scatter_step(res["seed"], 10_000 + i, xs, dt_t, mass_t, vel)
         ctx.energy_momentum(mass_t, vel, energy)
-        hp.copy_(pos, non_blocking=True)
         hv.copy_(vel, non_blocking=True)
-        hi.copy_(ids, non_blocking=True)
         out_e[i].copy_(energy, non_blocking=True)
+    s.wait_event(copied)
     e1.record(s)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
