@@ -455,10 +455,22 @@ def cpu_baseline(dt, vmax, threads=None, ns=N_PART // 2):
     t0 = time.perf_counter()
     r = O.step(halo.pos, vel, halo.ids, [0, ns], [N_NGB], [halo.mass], [(1, S0, vmax)], [dt], 1, 0, O.MODE_MIXED)
     sec = time.perf_counter() - t0
-    return {"value": ns / sec, "unit": UNIT, "cores": int(O.num_threads()), "kind": "oracle",
+    cores = int(O.num_threads())
+    # the same oracle on one core, on a 32,768-particle halo (about 8 s)
+    n1 = 32768
+    O.set_num_threads(1)
+    h1 = ics.nfw(n1, SEED_IC)
+    v1 = h1.vel.astype(np.float32).astype(np.float64)
+    t1 = time.perf_counter()
+    O.step(h1.pos, v1, h1.ids, [0, n1], [N_NGB], [h1.mass], [(1, S0, vmax)], [dt], 1, 0, O.MODE_MIXED)
+    sec1 = time.perf_counter() - t1
+    O.set_num_threads(th)
+    return {"value": ns / sec, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"one full oracle step (kNN, pair probabilities with exact Lambda quadrature, draws, "
                       f"sequential scatter) of a {ns}-particle NFW halo drawn like the workload's, same N_ngb/sigma(v)/dt; "
-                      f"{sec:.2f} s", "seconds": sec, "pairs": int(r["stats"][0]["n_pairs"])}
+                      f"{sec:.2f} s", "seconds": sec, "pairs": int(r["stats"][0]["n_pairs"]),
+            "one_core": {"value": n1 / sec1, "unit": UNIT, "cores": 1,
+                         "sample": f"one oracle step of a {n1}-particle halo drawn the same way; {sec1:.2f} s"}}
 
 
 def run_config3(local, steps=3, n=CFG3_N, oracle_sample=True):
