@@ -109,7 +109,7 @@ __device__ __forceinline__ float to_float_ru_p(R v)
 template <class R, bool TMA>
 constexpr size_t pair_warp_bytes()
 {
-    return (TileStageT<R, TMA>::bytes() + kQueue * 8 + kStack * 4 + 64 * 16 + 15) / 16 * 16;
+    return (TileStageT<R, TMA>::bytes() + kQueue * 8 + kStack * 4 + 64 * 16 + 8 * 8 + 15) / 16 * 16;
 }
 
 // MODE kModeDrawExact: form P (and so Lambda) for every in-range pair
@@ -136,14 +136,17 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
     int* stack = (int*)(q_sj + kQueue);
     float4* blo = (float4*)(stack + kStack);
     float4* bhi = blo + 32;
+    // the warp's statistics (64-bit, added to once per query leaf, so the
+    // per-lane counters of a leaf stay 32-bit registers): pairs, P > 1,
+    // |P - u| < 1e-6, tests, Lambda lookups, tiles, most tiles of one leaf
+    unsigned long long* wst = (unsigned long long*)(bhi + 32);
+    if (lane < 8) wst[lane] = 0ull;
     st_pos.init(lane);
     const R* __restrict__ T = (const R*)p.lam;
     const V* __restrict__ P4 = (const V*)p.P4;
     const V* __restrict__ V4 = (const V*)p.V4;
     const uint32_t lt = (1u << lane) - 1u;
 
-    unsigned long long n_pairs = 0ull, n_gt1 = 0ull, n_near = 0ull, n_tested = 0ull, n_lam = 0ull;
-    unsigned long long n_tiles_all = 0ull, n_tiles_max = 0ull;
 
     while (true) {
         int leaf = 0;
@@ -188,7 +191,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
             __syncwarp();
         }
         int qhead = 0, qn = 0;
-        unsigned long long n_tiles = 0ull;
+        uint32_t n_pairs = 0u, n_gt1 = 0u, n_near = 0u, n_tested = 0u, n_lam = 0u, n_tiles = 0u;
 
         // d^2 of a queued pair, recomputed exactly as in the in-range test
         // (candidate shifted into the frame of the query's leaf)
@@ -416,7 +419,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
                 allow = ((cmask >> lane) & 1u) ? qmask : 0u;
                 if (Bl == A) allow &= (1u << lane) - 1u;
             }
-            n_tested += (unsigned long long)__popc(allow);
+            n_tested += (uint32_t)__popc(allow);
             okm &= allow;
             // queue entry of bit t: (query slot, candidate slot)
             const uint32_t own = by_cand ? slotB + lane : slotA;
@@ -441,7 +444,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
                     q_sj[e & (kQueue - 1)] = by_cand ? own : base + t;
                 }
                 qn += c2;
-                n_pairs += (unsigned long long)c2;
+                n_pairs += (uint32_t)c2;
                 while (qn >= 32) run_batch(32);
             }
             __syncwarp();
@@ -555,24 +558,29 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_pairs(PairParam
         // batch per query leaf remains
         if (qn > 0) run_batch(qn);
         if (failed && lane == 0) raise_status(p.cnt, SIDM_DEV_STACK);
-        n_tiles_all += n_tiles;
-        n_tiles_max = n_tiles > n_tiles_max ? n_tiles : n_tiles_max;
+        // this leaf's counts into the warp's 64-bit statistics (the per-lane
+        // ones summed over the warp; pairs and tiles are the same in every lane)
+        {
+            const uint32_t g1 = __reduce_add_sync(0xffffffffu, n_gt1);
+            const uint32_t nr = __reduce_add_sync(0xffffffffu, n_near);
+            const uint32_t te = __reduce_add_sync(0xffffffffu, n_tested);
+            const uint32_t la = __reduce_add_sync(0xffffffffu, n_lam);
+            if (lane == 0) {
+                wst[0] += n_pairs; wst[1] += g1; wst[2] += nr; wst[3] += te; wst[4] += la; wst[5] += n_tiles;
+                wst[6] = max(wst[6], (unsigned long long)n_tiles);
+            }
+            __syncwarp();
+        }
     }
     // warp totals -> step statistics
-    for (int o = 16; o > 0; o >>= 1) {
-        n_gt1 += __shfl_xor_sync(0xffffffffu, n_gt1, o);
-        n_near += __shfl_xor_sync(0xffffffffu, n_near, o);
-        n_tested += __shfl_xor_sync(0xffffffffu, n_tested, o);
-        n_lam += __shfl_xor_sync(0xffffffffu, n_lam, o);
-    }
     if (lane == 0) {
-        if (n_pairs) atomicAdd(&p.st->n_pairs, n_pairs);
-        if (n_gt1) atomicAdd(&p.st->n_p_gt1, n_gt1);
-        if (n_near) atomicAdd(&p.st->n_near, n_near);
-        if (n_tested) atomicAdd(&p.st->n_tested, n_tested);
-        atomicAdd(&p.cnt->diag[4], n_tiles_all);
-        atomicMax(&p.cnt->diag[5], n_tiles_max);
-        if (n_lam) atomicAdd(&p.cnt->diag[6], n_lam);
+        if (wst[0]) atomicAdd(&p.st->n_pairs, wst[0]);
+        if (wst[1]) atomicAdd(&p.st->n_p_gt1, wst[1]);
+        if (wst[2]) atomicAdd(&p.st->n_near, wst[2]);
+        if (wst[3]) atomicAdd(&p.st->n_tested, wst[3]);
+        atomicAdd(&p.cnt->diag[4], wst[5]);
+        atomicMax(&p.cnt->diag[5], wst[6]);
+        if (wst[4]) atomicAdd(&p.cnt->diag[6], wst[4]);
     }
     st_pos.finish(lane, p.cnt);
 }
