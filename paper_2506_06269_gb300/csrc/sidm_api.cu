@@ -486,27 +486,38 @@ __global__ void k_leaf_hmax(int L, int H, const int32_t* __restrict__ leaf_halo,
 }
 
 // One tree level: union of up to kArity children (bbox and max h).
-__global__ void k_tree_level(int lev, int H, const int32_t* __restrict__ lvl_off, float4* __restrict__ nlo,
-                             float4* __restrict__ nhi)
+__global__ void __launch_bounds__(256) k_tree_level(int lev, int H, const int32_t* __restrict__ lvl_off,
+                                                    float4* __restrict__ nlo, float4* __restrict__ nhi)
 {
+    // one warp per node, one child per lane (kArity == 32): every child's box
+    // is loaded at once, then min/max across the warp
+    static_assert(kArity == 32, "one child per lane");
     const int32_t* off = lvl_off + lev * (H + 1);
     const int32_t* coff = lvl_off + (lev - 1) * (H + 1);
     const int total = off[H] - off[0];
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-        const int node = off[0] + t;
-        const int h = bsearch32(off, H, node);
-        const int local = node - off[h];
-        const int c0 = coff[h] + local * kArity;
-        const int c1 = min(c0 + kArity, coff[h + 1]);
-        float4 lo = make_float4(INFINITY, INFINITY, INFINITY, 0.f);
-        float4 hi = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
-        for (int c = c0; c < c1; ++c) {
-            float4 a = nlo[c], b = nhi[c];
-            lo.x = fminf(lo.x, a.x); lo.y = fminf(lo.y, a.y); lo.z = fminf(lo.z, a.z); lo.w = fmaxf(lo.w, a.w);
-            hi.x = fmaxf(hi.x, b.x); hi.y = fmaxf(hi.y, b.y); hi.z = fmaxf(hi.z, b.z);
-        }
+    const int lane = threadIdx.x & 31;
+    const int t = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (t >= total) return;                                  // whole warps
+    const int node = off[0] + t;
+    const int h = bsearch32(off, H, node);
+    const int local = node - off[h];
+    const int c = coff[h] + local * kArity + lane;
+    float4 lo = make_float4(INFINITY, INFINITY, INFINITY, 0.f);
+    float4 hi = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
+    if (c < coff[h + 1]) { lo = nlo[c]; hi = nhi[c]; }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo.x = fminf(lo.x, __shfl_xor_sync(0xffffffffu, lo.x, o));
+        lo.y = fminf(lo.y, __shfl_xor_sync(0xffffffffu, lo.y, o));
+        lo.z = fminf(lo.z, __shfl_xor_sync(0xffffffffu, lo.z, o));
+        lo.w = fmaxf(lo.w, __shfl_xor_sync(0xffffffffu, lo.w, o));
+        hi.x = fmaxf(hi.x, __shfl_xor_sync(0xffffffffu, hi.x, o));
+        hi.y = fmaxf(hi.y, __shfl_xor_sync(0xffffffffu, hi.y, o));
+        hi.z = fmaxf(hi.z, __shfl_xor_sync(0xffffffffu, hi.z, o));
+    }
+    if (lane == 0) {
         nlo[node] = lo;
-        nhi[node] = hi;
+        nhi[node] = make_float4(hi.x, hi.y, hi.z, 0.f);
     }
 }
 
@@ -1599,7 +1610,7 @@ static int build_impl(sidm_ctx* c, double* pos, R* vel, uint32_t* id, cudaStream
                                                                            c->d_nhi));
     for (int l = 1; l < L.nlev; ++l) {
         const int cnt = L.lvl_off[(size_t)l * (H + 1) + H] - L.lvl_off[(size_t)l * (H + 1)];
-        SIDM_LAUNCH(c, k_tree_level<<<std::max(1, (cnt + 255) / 256), 256, 0, s>>>(l, H, c->d_lvl_off, c->d_nlo, c->d_nhi));
+        SIDM_LAUNCH(c, k_tree_level<<<std::max(1, (cnt * 32 + 255) / 256), 256, 0, s>>>(l, H, c->d_lvl_off, c->d_nlo, c->d_nhi));
     }
     return SIDM_OK;
 }
@@ -1676,7 +1687,7 @@ extern "C" int sidm_kernel_sizes(sidm_ctx* c, const int32_t* n_ngb, void* h_dev,
                                                                                c->d_halo_off, (const float4*)c->d_P4, c->d_nlo));
     for (int l = 1; l < L.nlev; ++l) {
         const int cnt = L.lvl_off[(size_t)l * (L.H + 1) + L.H] - L.lvl_off[(size_t)l * (L.H + 1)];
-        SIDM_LAUNCH(c, k_tree_level<<<std::max(1, (cnt + 255) / 256), 256, 0, s>>>(l, L.H, c->d_lvl_off, c->d_nlo, c->d_nhi));
+        SIDM_LAUNCH(c, k_tree_level<<<std::max(1, (cnt * 32 + 255) / 256), 256, 0, s>>>(l, L.H, c->d_lvl_off, c->d_nlo, c->d_nhi));
     }
     c->sized = true;
     return SIDM_OK;
