@@ -90,8 +90,9 @@ typedef struct {
     float   knn_slack;   /*   warm-start bound / previous kernel size, 1..2 (1.05)   */
     int32_t pair_per_round; /* pair kernel: pairs a lane queues per round, 1..4 (4; mixed-form draws) */
     int32_t knn_batch;   /* kernel-size search: 1 loops over each staged leaf's      */
-                         /*   candidates, 2 over compacted batches of them (default 2; */
-                         /*   bulk copies and neighbour lists take 1)                 */
+                         /*   candidates, 2 over compacted batches of them, 3 as 2    */
+                         /*   with warm-started searches in the fixed-bound kernel    */
+                         /*   (default 3; bulk copies and neighbour lists take 1)     */
 } sidm_config;
 
 /* Cross-section per unit mass of one halo (Sect. 3.8, Eq. vel_dep), given as
@@ -414,8 +415,8 @@ int sidm_timestep_criterion(sidm_ctx* ctx, double tau, double dt_min, double dt_
  * caller's arrays must still be in the order that call left them, with the
  * same halo layout and N_ngb).  The search then only admits candidates within
  * knn_slack times that size (1.05 by default); a particle with fewer than
- * N_ngb of them is redone
- * from scratch in the same launch.  The result is the exact k-th distance in
+ * N_ngb of them is redone from scratch by a second, per-lane launch on the
+ * same stream.  The result is the exact k-th distance in
  * every case -- a stale or wrong guess costs time, never accuracy -- so this
  * is the usual SPH practice of starting from the previous smoothing length
  * (Sect. 2: h follows the N_ngb nearest neighbours as particles move).

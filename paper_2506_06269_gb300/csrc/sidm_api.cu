@@ -1299,7 +1299,7 @@ static int radix_sort(sidm_ctx* c, unsigned long long*& ka, uint32_t*& va, unsig
 
 static void free_all(sidm_ctx* c)
 {
-    void* ptrs[] = {c->d_halo_off, c->d_halo_pad, c->d_leaf_off, c->d_lvl_off, c->d_top, c->d_ngb, c->d_leaf_halo,
+    void* ptrs[] = {c->d_halo_off, c->d_halo_pad, c->d_leaf_off, c->d_lvl_off, c->d_top, c->d_ngb, c->d_leaf_halo, c->d_knn_redo,
                     c->d_chunk_halo, c->d_chunk_begin, c->d_frame, c->d_key, c->d_key2, c->d_val, c->d_val2,
                     c->d_sort_status, c->d_sort_hist, c->d_P4, c->d_V4, c->d_ID, c->d_cell, c->d_cellb, c->d_nlo, c->d_nhi, c->d_perm, c->d_tmp_pos,
                     c->d_tmp_vel, c->d_tmp_id, c->d_claim, c->d_hits, c->d_done, c->d_ev, c->d_sump,
@@ -1340,10 +1340,10 @@ extern "C" int sidm_create(sidm_ctx** out, const sidm_config* cfg)
     if (!(cfg->knn_groups == 0 || cfg->knn_groups == 2 || cfg->knn_groups == 4 || cfg->knn_groups == 8) ||
         !(cfg->knn_chains == 0 || cfg->knn_chains == 4 || cfg->knn_chains == 8) || cfg->knn_flush < 0 ||
         cfg->knn_flush > 32 || !(cfg->knn_slack == 0.f || (cfg->knn_slack >= 1.f && cfg->knn_slack <= 2.f)) ||
-        cfg->pair_per_round < 0 || cfg->pair_per_round > 4 || cfg->knn_batch < 0 || cfg->knn_batch > 2 ||
+        cfg->pair_per_round < 0 || cfg->pair_per_round > 4 || cfg->knn_batch < 0 || cfg->knn_batch > 3 ||
         (cfg->knn_chains == 8 && cfg->knn_groups != 4)) {
         g_create_err = "launch knobs out of range (knn_groups 2/4/8, knn_chains 4/8 (8 with 4 groups), "
-                       "knn_flush <= 32, knn_slack in [1, 2], pair_per_round <= 4, knn_batch <= 2)";
+                       "knn_flush <= 32, knn_slack in [1, 2], pair_per_round <= 4, knn_batch <= 3)";
         return SIDM_EINVAL;
     }
     sidm_ctx* c = new sidm_ctx();
@@ -1385,6 +1385,7 @@ extern "C" int sidm_create(sidm_ctx** out, const sidm_config* cfg)
     ALLOC(c->d_top, H);
     ALLOC(c->d_ngb, H);
     ALLOC(c->d_leaf_halo, Lmax);
+    ALLOC(c->d_knn_redo, Lmax);
     ALLOC(c->d_chunk_halo, c->chunk_cap);
     ALLOC(c->d_chunk_begin, c->chunk_cap);
     ALLOC(c->d_frame, H);

@@ -46,6 +46,7 @@ struct DevCounters {
     unsigned int work[4];            // persistent work-queue counters; [2], [3]: grid barrier
     unsigned int status;             // sticky SIDM_DEV_* bits (cleared by sidm_status)
     unsigned int pad;
+    unsigned int knn_redo[2];        // leaves the warm-started search hands to the exhaustive one; its work counter
     unsigned long long diag[8];      // diagnostics (sidm_diagnostics)
     unsigned long long bbox[kMaxHalos * 6];   // ordered bits of per-halo min/max
 };
@@ -97,6 +98,7 @@ struct sidm_ctx {
     int32_t* d_top = nullptr;          // [H]
     int32_t* d_ngb = nullptr;          // [H]
     int32_t* d_leaf_halo = nullptr;    // [Lmax]
+    int32_t* d_knn_redo = nullptr;     // [Lmax] leaves whose warm-started kernel-size search is redone
     int32_t* d_chunk_halo = nullptr;   // [chunks]
     int64_t* d_chunk_begin = nullptr;  // [chunks]
     sidm::HaloFrame* d_frame = nullptr;  // [H]

@@ -49,7 +49,9 @@ struct KnnParams {
     int k_stride;
     int kcap;
     DevCounters* cnt;
-    int work_slot;
+    unsigned int* work;          // persistent work counter (zeroed before the launch)
+    const int32_t* leaf_list;    // NULL: every leaf; else the leaves listed here ...
+    const unsigned int* list_len;  // ... of which there are *list_len
     void* hprev;        // out: h per particle (next call's guess), NULL for neighbour lists
     int use_guess;      // P4.w holds each particle's previous kernel size
     float slack;        // guess bound = previous h * slack
@@ -169,7 +171,7 @@ constexpr int kBatch = 16;
 constexpr int kBufCap = kBatch + kLeaf;
 static_assert(kPend >= kBatch, "a batch can admit all of its candidates: one empty pending list must hold them");
 constexpr int kChainsDefault = 4;
-constexpr int kBatchDefault = 2;                   // 1: loop per staged leaf, 2: compacted batches
+constexpr int kBatchDefault = 3;                   // 1: loop per staged leaf, 2: compacted batches, 3: 2 + fixed-bound warm kernel
 constexpr int kFlushNodeDefault = 32;
 constexpr float kGuessSlackDefault = 1.05f;
 
@@ -221,9 +223,14 @@ __global__ void k_knn(KnnParams p)
 
     while (true) {
         int leaf = 0;
-        if (lane == 0) leaf = (int)atomicAdd(&p.cnt->work[p.work_slot], 1u);
+        if (lane == 0) leaf = (int)atomicAdd(p.work, 1u);
         leaf = __shfl_sync(0xffffffffu, leaf, 0);
-        if (leaf >= p.L) break;
+        if (p.leaf_list) {
+            if ((unsigned)leaf >= *p.list_len) break;
+            leaf = p.leaf_list[leaf];
+        } else if (leaf >= p.L) {
+            break;
+        }
         const int h = p.leaf_halo[leaf];
         const int k = p.ngb[h];
         const int leaf0 = p.leaf_off[h];
@@ -682,46 +689,495 @@ __global__ void k_knn(KnnParams p)
     stage.finish(lane, p.cnt);
 }
 
-template <class R, bool NBR, bool TMA, int G, int CH, bool BATCH = false>
-int launch_t(sidm_ctx* c, void* h_out, uint32_t* nbr, int k_stride, bool use_guess, cudaStream_t s)
+// ---------------------------------------------------------------------------
+// Warm-started search.  From the second call on every particle carries its
+// previous kernel size, and only candidates inside slack x h_prev are admitted
+// (reading C14).  That bound is fixed for the whole query leaf, so:
+//  * the tree walk tests each child's box against the boxes of the lane
+//    groups, each grown by the largest bound of its lanes (one box test per
+//    child and group, no per-lane point tests), and lists the accepted leaves;
+//  * the listed leaves are loaded two ahead; a candidate is kept if it lies
+//    within some group's largest bound of that group's box, a test made in the
+//    query leaf's own frame with directed rounding, where the box gap is a lower
+//    bound of the canonical distance (no margin needed); kept candidates go to a
+//    per-warp ring;
+//  * full batches of kWBatch ring entries are tested against all 32 queries
+//    with branch-free admission: a lane stores every key at its next free slot
+//    and advances the slot only when the key is below its bound;
+//  * the query leaf's own particles are tested first, with the exclusion of
+//    the query itself, so the batch loop needs none.
+// The keys of a lane sit in shared memory as [slot][lane]: slots 0..k-1 are a
+// 4-ary max-heap (filled unsorted, heapified once), slots k..k+2 stay zero (the
+// missing children of the last nodes), and up to kWPend further keys wait
+// there until a merge.  A lane that admits fewer than k keys (its guess was too
+// small) sends its leaf to a list that the exhaustive search redoes, so the
+// result is the same exact k-th distance as a cold search.
+constexpr int kWRing = 40;      // candidate ring entries
+constexpr int kWBatch = 8;      // candidates per batch (batches start at multiples of it: never wrap)
+constexpr int kWList = 64;      // accepted leaves listed before they are streamed
+constexpr int kWStack = 128;    // traversal stack entries (an overflow hands the leaf to the redo)
+constexpr int kWPad = 3;        // zero slots after the heap
+constexpr int kWPend = 32;      // keys a lane may hold beyond k before a merge (room enough that
+                                // merges are rare and most lanes order their heaps together)
+static_assert(kWRing % kWBatch == 0 && kWRing >= kWBatch - 1 + kLeaf, "the ring holds a batch's leftover plus a leaf");
+static_assert(kWPend >= kWBatch, "one batch fits after a merge");
+constexpr int kWarmMaxWarps = 8;   // the kernel's launch bound: 256 threads, two CTAs per SM
+constexpr int kWalkGroups = 8;     // lane groups of the tree walk (4 lanes each)
+// a leaf goes to the per-lane search when the box of a walk group is wider than
+// kSpreadWalk times its largest bound, or a filter group's than kSpreadFilter times
+constexpr float kSpreadWalk = 4.0f;
+constexpr float kSpreadFilter = 6.0f;
+
+template <class R, class K, int G>
+__host__ __device__ constexpr size_t warm_warp_bytes(int kcap)
 {
-    using K = typename KeyOf<R, NBR>::T;
-    KnnParams p;
+    return ((size_t)kWRing * sizeof(typename Vec4<R>::T) + (size_t)(kWList + kWStack) * 4 + (size_t)2 * kWalkGroups * 16 +
+            (size_t)(kcap + kWPad + kWPend) * 32 * sizeof(K) + 15) / 16 * 16;
+}
+
+template <class R, int G>
+__global__ void __launch_bounds__(kWarmMaxWarps * 32, 2) k_knn_warm(KnnParams p, int32_t* redo_list, unsigned int* redo_len)
+{
+    static_assert(G == 2 || G == 4, "lane groups of 16 or 8 lanes");
+    using V = typename Vec4<R>::T;
+    using K = typename KeyOf<R, false>::T;
+    constexpr bool kF32 = sizeof(R) == 4;
+    constexpr int kGL = 32 / G;
+    constexpr unsigned FULL = 0xffffffffu;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned char* base = smem + wid * warm_warp_bytes<R, K, G>(p.kcap);
+    V* ring = (V*)base;
+    int* list = (int*)(base + (size_t)kWRing * sizeof(V));
+    int* stack = list + kWList;
+    float4* wbox = (float4*)(stack + kWStack);         // [kWalkGroups][2]: walk group boxes (halo frame), lo.w = bound
+    K* keys = (K*)(wbox + 2 * kWalkGroups);            // [kcap + kWPad + kWPend][32]
+    const uint32_t lt = (1u << lane) - 1u;
+    const int Hp = p.H + 1;
+    // the lanes redone cold are counted by the per-lane search that redoes them
+    unsigned long long n_cand = 0ull, n_ins = 0ull, n_tiles = 0ull, n_tiles_max = 0ull;
+
+    while (true) {
+        int leaf = 0;
+        if (lane == 0) leaf = (int)atomicAdd(p.work, 1u);
+        leaf = __shfl_sync(FULL, leaf, 0);
+        if (leaf >= p.L) break;
+        const int h = p.leaf_halo[leaf];
+        const int k = p.ngb[h];
+        const int leaf0 = p.leaf_off[h];
+        const int64_t hb = p.halo_off[h];
+        const int64_t nh = p.halo_off[h + 1] - hb;
+        const int A = leaf - leaf0;
+        const int countA = (int)min((int64_t)kLeaf, nh - (int64_t)A * kLeaf);
+        const bool active = lane < countA;
+        const V q = ((const V*)p.P4)[(int64_t)leaf * kLeaf + lane];
+        const unsigned long long tiles0 = n_tiles;
+        // a particle without a previous kernel size sends its leaf to the redo
+        if (__any_sync(FULL, active && !(q.w > R(0)))) {
+            if (lane == 0) { const unsigned r = atomicAdd(redo_len, 1u); redo_list[r] = leaf; }
+            continue;
+        }
+        const HaloFrame fr = p.frame[h];
+        const float4 cA = p.cell[leaf];
+        // the lane's bound key: (slack h_prev)^2 rounded up; inactive lanes admit nothing
+        K root = K(0);
+        float r2walk = -1.0f;                          // the walk's bound in the halo frame (with the margin)
+        if (active) {
+            R r;
+            if constexpr (kF32) r = __fmul_ru((float)q.w, p.slack);
+            else r = __dmul_ru((double)q.w, (double)p.slack);
+            const R b2 = mul_ru(r, r);
+            root = make_key<R, false>(b2, 0u);
+            float rf = to_float_ru<R>(sqrt_ru(b2));
+            rf = __fadd_ru(__fmul_ru(rf, 1.0f + 0x1p-20f), fr.margin);
+            r2walk = __fmul_ru(rf, rf);
+        }
+        // group boxes: the walk's in the halo frame (the frame of the node
+        // boxes), the candidate filter's in the query leaf's frame (mixed form;
+        // the FP64 form filters with the walk's boxes and bounds)
+        float3 pq;
+        if constexpr (kF32) {
+            pq = make_float3(__fadd_rn(cA.x, (float)q.x), __fadd_rn(cA.y, (float)q.y), __fadd_rn(cA.z, (float)q.z));
+        } else {
+            pq = make_float3(__double2float_rn((double)q.x - fr.O[0]), __double2float_rn((double)q.y - fr.O[1]),
+                             __double2float_rn((double)q.z - fr.O[2]));
+        }
+        // walk boxes: groups of 4 lanes (a large bound of one lane grows only its
+        // own group's box); the bound of each group is stored in its lo.w.  On the
+        // halo's sparse outer shell even 4 consecutive particles of the Morton
+        // curve can lie on opposite sides of the halo: a group box much wider
+        // than its bound would accept most of the halo, so such a leaf is left
+        // to the per-lane search (the redo list, warm-started)
+        bool spread = false;
+        {
+            constexpr int kWL = 32 / kWalkGroups;
+            float v[7] = {active ? pq.x : INFINITY, active ? pq.y : INFINITY, active ? pq.z : INFINITY,
+                          active ? -pq.x : INFINITY, active ? -pq.y : INFINITY, active ? -pq.z : INFINITY, -r2walk};
+#pragma unroll
+            for (int o = kWL / 2; o > 0; o >>= 1) {
+#pragma unroll
+                for (int i = 0; i < 7; ++i) v[i] = fminf(v[i], __shfl_xor_sync(FULL, v[i], o));
+            }
+            if (lane % kWL == 0) {
+                wbox[2 * (lane / kWL)] = make_float4(v[0], v[1], v[2], -v[6]);
+                wbox[2 * (lane / kWL) + 1] = make_float4(-v[3], -v[4], -v[5], 0.f);
+                const float ext = fmaxf(fmaxf(-v[3] - v[0], -v[4] - v[1]), -v[5] - v[2]);
+                spread = -v[6] >= 0.f && ext * ext > kSpreadWalk * kSpreadWalk * -v[6];
+            }
+            __syncwarp();
+        }
+        // filter boxes: groups of 32 / G lanes, in the query leaf's frame (mixed
+        // form) or the halo frame (FP64 form, with the walk's bounds)
+        float r2f[G];
+        float4 flo[G], fhi[G];
+        {
+            float v[6];
+            if constexpr (kF32) {
+                v[0] = active ? (float)q.x : INFINITY;  v[1] = active ? (float)q.y : INFINITY;  v[2] = active ? (float)q.z : INFINITY;
+                v[3] = active ? -(float)q.x : INFINITY; v[4] = active ? -(float)q.y : INFINITY; v[5] = active ? -(float)q.z : INFINITY;
+            } else {
+                v[0] = active ? pq.x : INFINITY;  v[1] = active ? pq.y : INFINITY;  v[2] = active ? pq.z : INFINITY;
+                v[3] = active ? -pq.x : INFINITY; v[4] = active ? -pq.y : INFINITY; v[5] = active ? -pq.z : INFINITY;
+            }
+#pragma unroll
+            for (int o = kGL / 2; o > 0; o >>= 1) {
+#pragma unroll
+                for (int i = 0; i < 6; ++i) v[i] = fminf(v[i], __shfl_xor_sync(FULL, v[i], o));
+            }
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                flo[g] = make_float4(__shfl_sync(FULL, v[0], g * kGL), __shfl_sync(FULL, v[1], g * kGL),
+                                     __shfl_sync(FULL, v[2], g * kGL), 0.f);
+                fhi[g] = make_float4(-__shfl_sync(FULL, v[3], g * kGL), -__shfl_sync(FULL, v[4], g * kGL),
+                                     -__shfl_sync(FULL, v[5], g * kGL), 0.f);
+            }
+        }
+        // the filter's bounds: the largest bound key of each group (mixed: the
+        // exact bound; FP64: the walk's, with the margin)
+        auto filter_bounds = [&]() {
+            float b = -1.0f;
+            if constexpr (kF32) { if (active) b = key_d2<R, false>(root); }
+            else b = r2walk;
+#pragma unroll
+            for (int o = kGL / 2; o > 0; o >>= 1) b = fmaxf(b, __shfl_xor_sync(FULL, b, o));
+#pragma unroll
+            for (int g = 0; g < G; ++g) r2f[g] = __shfl_sync(FULL, b, g * kGL);
+        };
+        filter_bounds();
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const float ext = fmaxf(fmaxf(fhi[g].x - flo[g].x, fhi[g].y - flo[g].y), fhi[g].z - flo[g].z);
+            spread = spread || (r2f[g] >= 0.f && ext * ext > kSpreadFilter * kSpreadFilter * r2f[g]);
+        }
+        if (__any_sync(FULL, spread)) {
+            if (lane == 0) { const unsigned r = atomicAdd(redo_len, 1u); redo_list[r] = leaf; }
+            continue;
+        }
+        // zero the slots after the heap of this leaf's k
+        for (int i = 0; i < kWPad; ++i) keys[(k + i) * 32 + lane] = K(0);
+
+        int cnt = 0;                                   // keys held (slots 0..k-1, then k+3..)
+        bool heaped = false;
+        auto sift = [&](int t, K key) {
+            while (true) {
+                const int c0 = 4 * t + 1;
+                if (c0 >= k) break;
+                const K* cp = keys + (size_t)c0 * 32 + lane;
+                K m = cp[0];
+                int j = 0;
+                const K c1 = cp[32], c2 = cp[64], c3 = cp[96];
+                if (c1 > m) { m = c1; j = 1; }
+                if (c2 > m) { m = c2; j = 2; }
+                if (c3 > m) { m = c3; j = 3; }
+                if (!(m > key)) break;
+                keys[t * 32 + lane] = m;
+                t = c0 + j;
+            }
+            keys[t * 32 + lane] = key;
+        };
+        // merge the waiting keys into the heap (each lane its own column)
+        auto flush = [&]() {
+            if (active && cnt >= k) {
+                if (!heaped) {
+                    for (int t = (k - 2) / 4; t >= 0; --t) sift(t, keys[t * 32 + lane]);
+                    heaped = true;
+                    root = keys[lane];
+                }
+                for (int i = k; i < cnt; ++i) {
+                    const K key = keys[(i + kWPad) * 32 + lane];
+                    if (key < root) {
+                        ++n_ins;
+                        sift(0, key);
+                        root = keys[lane];
+                    }
+                }
+                cnt = k;
+            }
+            filter_bounds();
+        };
+        // distances from every query to the kWBatch entries at src
+        auto batch = [&](const V* src, bool self) {
+            if (__any_sync(FULL, cnt > k + kWPend - kWBatch)) flush();
+            __syncwarp();
+#pragma unroll
+            for (int t = 0; t < kWBatch; t += 4) {
+                K key[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const V cj = src[t + u];
+                    const R dx = sub_rn(cj.x, q.x), dy = sub_rn(cj.y, q.y), dz = sub_rn(cj.z, q.z);
+                    key[u] = make_key<R, false>(fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx))), 0u);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const bool adm = key[u] < root && !(self && t + u == (lane & (kWBatch - 1)));
+                    const int slot = cnt < k ? cnt : cnt + kWPad;
+                    keys[slot * 32 + lane] = key[u];
+                    cnt += adm ? 1 : 0;
+                }
+            }
+            __syncwarp();
+        };
+        V far;
+        far.x = R(INFINITY); far.y = R(INFINITY); far.z = R(INFINITY); far.w = R(0);
+
+        // 1) the query leaf's own particles, two batches of 16 (lanes past the
+        //    leaf's end read as infinitely far)
+        ring[lane] = active ? q : far;
+        __syncwarp();
+        if (active) n_cand += (unsigned long long)countA;
+#pragma unroll
+        for (int b = 0; b < kLeaf; b += kWBatch) batch(ring + b, (lane & ~(kWBatch - 1)) == b);
+        __syncwarp();
+
+        // 2) stream listed leaves: filter, append to the ring, run full batches
+        int head = 0, tail = 0, navail = 0;
+        auto wrap = [](int i) { return i >= kWRing ? i - kWRing : i; };   // i < 2 kWRing
+        auto stage_leaf = [&](int Bl, V c, float4 cB) {
+            const int countB = (int)min((int64_t)kLeaf, nh - (int64_t)Bl * kLeaf);
+            bool reach = false;
+            if constexpr (kF32) {
+                c.x = __fadd_rn(c.x, __fsub_rn(cB.x, cA.x));     // exact shift into the query leaf's frame
+                c.y = __fadd_rn(c.y, __fsub_rn(cB.y, cA.y));
+                c.z = __fadd_rn(c.z, __fsub_rn(cB.z, cA.z));
+                const float3 pc = make_float3(c.x, c.y, c.z);
+#pragma unroll
+                for (int g = 0; g < G; ++g) reach = reach || point_gap2_rd(pc, flo[g], fhi[g]) <= r2f[g];
+            } else {
+                const float3 pc = make_float3(__double2float_rn((double)c.x - fr.O[0]),
+                                              __double2float_rn((double)c.y - fr.O[1]),
+                                              __double2float_rn((double)c.z - fr.O[2]));
+#pragma unroll
+                for (int g = 0; g < G; ++g) reach = reach || point_gap2_rd(pc, flo[g], fhi[g]) <= r2f[g];
+            }
+            const uint32_t m = __ballot_sync(FULL, lane < countB && reach);
+            ++n_tiles;
+            if (m == 0u) return;
+            if ((m >> lane) & 1u) ring[wrap(tail + __popc(m & lt))] = c;
+            const int nm = __popc(m);
+            tail = wrap(tail + nm);
+            navail += nm;
+            __syncwarp();
+            while (navail >= kWBatch) {
+                if (active) n_cand += (unsigned long long)kWBatch;
+                batch(ring + head, false);
+                head = wrap(head + kWBatch);
+                navail -= kWBatch;
+            }
+        };
+        int nl = 0;
+        auto stream_list = [&]() {
+            using CellT = float4;
+            V c0{}, c1{};
+            CellT b0{}, b1{};
+            auto fetch = [&](int i, V& c, CellT& b) {
+                const int Bl = list[i];
+                c = ((const V*)p.P4)[(int64_t)(leaf0 + Bl) * kLeaf + lane];
+                if constexpr (kF32) b = p.cell[leaf0 + Bl];
+            };
+            if (nl > 0) fetch(0, c0, b0);
+            if (nl > 1) fetch(1, c1, b1);
+            for (int i = 0; i < nl; ++i) {
+                V c2{};
+                CellT b2{};
+                if (i + 2 < nl) fetch(i + 2, c2, b2);
+                stage_leaf(list[i], c0, b0);
+                c0 = c1; b0 = b1; c1 = c2; b1 = b2;
+            }
+            nl = 0;
+            __syncwarp();
+        };
+        // tree walk, level by level: the accepted nodes of a level form the
+        // frontier of the next; the child boxes of the next frontier node are
+        // loaded while the current node's children are tested (one child per
+        // lane, against every walk group's box grown by its bound)
+        auto accept = [&](int n, float4 clo, float4 chi) -> uint32_t {
+            bool ok = false;
+            if (lane < n) {
+#pragma unroll
+                for (int g = 0; g < kWalkGroups; ++g) {
+                    const float4 lo = wbox[2 * g];
+                    ok = ok || box_gap2_rd(lo, wbox[2 * g + 1], clo, chi) <= lo.w;
+                }
+            }
+            return __ballot_sync(FULL, ok);
+        };
+        auto add_leaves = [&](uint32_t acc, int first) {
+            if (nl + __popc(acc) > kWList) stream_list();
+            if ((acc >> lane) & 1u) list[nl + __popc(acc & lt)] = first + lane;
+            nl += __popc(acc);
+            __syncwarp();
+        };
+        bool overflow = false;
+        constexpr int kWFront = kWStack / 2;           // two frontier buffers in the stack's space
+        int* front = stack;
+        int* nextf = stack + kWFront;
+        int nf = 0;
+        const int top = p.top[h];
+        const int32_t* loff = p.lvl_off;
+        {
+            const int nb0 = loff[top * Hp + h];
+            const int ntop = loff[top * Hp + h + 1] - nb0;
+            float4 clo = make_float4(0.f, 0.f, 0.f, 0.f), chi = clo;
+            if (lane < ntop) { clo = p.nlo[nb0 + lane]; chi = p.nhi[nb0 + lane]; }
+            const uint32_t acc = accept(ntop, clo, chi);
+            if (top == 0) {
+                add_leaves(acc & ~(1u << A), 0);
+            } else {
+                if ((acc >> lane) & 1u) front[__popc(acc & lt)] = lane;
+                nf = __popc(acc);
+                __syncwarp();
+            }
+        }
+        for (int lev = top; lev > 0 && nf > 0 && !overflow; --lev) {
+            const int cl = lev - 1;
+            const int cb = loff[cl * Hp + h];
+            const int cc = loff[cl * Hp + h + 1] - cb;
+            int nn = 0;
+            float4 lo0 = make_float4(0.f, 0.f, 0.f, 0.f), hi0 = lo0;
+            auto load = [&](int i, float4& lo, float4& hi) {
+                const int first = front[i] * kArity;
+                if (lane < min(kArity, cc - first)) { lo = p.nlo[cb + first + lane]; hi = p.nhi[cb + first + lane]; }
+            };
+            load(0, lo0, hi0);
+            for (int i = 0; i < nf; ++i) {
+                float4 lo1 = make_float4(0.f, 0.f, 0.f, 0.f), hi1 = lo1;
+                if (i + 1 < nf) load(i + 1, lo1, hi1);
+                const int first = front[i] * kArity;
+                const int nch = min(kArity, cc - first);
+                uint32_t acc = accept(nch, lo0, hi0);
+                if (cl == 0) {
+                    if (A >= first && A < first + nch) acc &= ~(1u << (A - first));
+                    add_leaves(acc, first);
+                } else {
+                    const int na = __popc(acc);
+                    if (nn + na > kWFront) { overflow = true; break; }
+                    if ((acc >> lane) & 1u) nextf[nn + __popc(acc & lt)] = first + lane;
+                    nn += na;
+                }
+                lo0 = lo1; hi0 = hi1;
+            }
+            __syncwarp();
+            int* t = front; front = nextf; nextf = t;
+            nf = nn;
+        }
+        stream_list();
+        // the last, partial batch: pad it with infinitely far entries
+        if (navail > 0) {
+            if (lane < kWBatch - navail) ring[wrap(tail + lane)] = far;
+            __syncwarp();
+            if (active) n_cand += (unsigned long long)navail;
+            batch(ring + head, false);
+        }
+        flush();
+        const bool ok = !active || heaped;
+        if (overflow || !__all_sync(FULL, ok)) {
+            if (lane == 0) { const unsigned r = atomicAdd(redo_len, 1u); redo_list[r] = leaf; }
+        } else if (active) {
+            const int64_t u = hb + (int64_t)A * kLeaf + lane;
+            const R hval = sqrt_rn(key_d2<R, false>(root));
+            ((R*)p.h_out)[u] = hval;
+            ((R*)((V*)p.P4 + (int64_t)leaf * kLeaf + lane))[3] = hval;
+            if (p.hprev) ((R*)p.hprev)[u] = hval;
+        }
+        n_tiles_max = n_tiles - tiles0 > n_tiles_max ? n_tiles - tiles0 : n_tiles_max;
+        __syncwarp();
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        n_cand += __shfl_xor_sync(FULL, n_cand, o);
+        n_ins += __shfl_xor_sync(FULL, n_ins, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&p.cnt->diag[0], n_tiles);
+        atomicAdd(&p.cnt->diag[1], n_cand);
+        atomicAdd(&p.cnt->diag[2], n_ins);
+        atomicMax(&p.cnt->diag[3], n_tiles_max);
+    }
+}
+
+void fill_params(sidm_ctx* c, KnnParams& p, void* h_out, uint32_t* nbr, int k_stride, bool use_guess)
+{
     const LayoutHost& L = c->lay;
     p.H = L.H; p.L = L.L;
     p.leaf_halo = c->d_leaf_halo; p.leaf_off = c->d_leaf_off; p.halo_off = c->d_halo_off;
     p.lvl_off = c->d_lvl_off; p.top = c->d_top; p.ngb = c->d_ngb; p.frame = c->d_frame;
     p.cell = c->d_cell; p.nlo = c->d_nlo; p.nhi = c->d_nhi; p.P4 = c->d_P4; p.ID = c->d_ID;
     p.h_out = h_out; p.nbr = nbr; p.k_stride = k_stride; p.kcap = c->kmax_cur; p.cnt = c->d_cnt;
-    p.work_slot = 0;
-    p.hprev = NBR ? nullptr : c->d_hprev;
+    p.work = &c->d_cnt->work[0];
+    p.leaf_list = nullptr; p.list_len = nullptr;
+    p.hprev = nbr ? nullptr : c->d_hprev;
     p.use_guess = use_guess ? 1 : 0;
     p.slack = c->cfg.knn_slack > 0.f ? c->cfg.knn_slack : kGuessSlackDefault;
     p.flush_node = c->cfg.knn_flush > 0 ? c->cfg.knn_flush : kFlushNodeDefault;
-    // warps per CTA: at most the configured number, and of those the one with
-    // the most resident warps per SM (with large N_ngb the per-warp heaps make
-    // two small CTAs hold more warps than one large one); a CTA may use at most
-    // 227 KB of shared memory
-    auto kern = k_knn<R, NBR, TMA, G, CH, BATCH>;
-    const size_t per_warp = knn_warp_bytes_t<R, K, G, BATCH>(p.kcap);
+}
+
+// warps per CTA: at most the configured number, and of those the one with the
+// most resident warps per SM (with large N_ngb the per-warp heaps make two
+// small CTAs hold more warps than one large one); a CTA may use at most 227 KB
+// of shared memory.  Also the persistent grid.
+int pick_shape(sidm_ctx* c, const void* kern, size_t per_warp, int* warps_out, int* grid_out, int max_warps = 16)
+{
     int warps = 0, occ = 0;
-    for (int w = c->knn_warps; w >= 1; --w) {
+    for (int w = std::min(c->knn_warps, max_warps); w >= 1; --w) {
         if ((size_t)w * per_warp > (size_t)227 * 1024) continue;
         int o = 0;
-        const int rc = occupancy(c, (const void*)kern, w * 32, (size_t)w * per_warp, &o);
+        const int rc = occupancy(c, kern, w * 32, (size_t)w * per_warp, &o);
         if (rc) return rc;
         if (o * w > occ * warps) { warps = w; occ = o; }
     }
-    const size_t smem = (size_t)warps * per_warp;
-    cudaError_t e;
     if (warps < 1 || occ < 1) return set_err(c, SIDM_ECAPACITY, "knn kernel does not fit on an SM (ngb_max too large)");
     int grid = c->cfg.grid_ctas > 0 ? c->cfg.grid_ctas : c->sm_count * occ;
-    grid = std::max(1, std::min(grid, (L.L + warps - 1) / warps));
-    c->knn_grid = grid;
-    e = cudaMemsetAsync(&c->d_cnt->work[0], 0, sizeof(unsigned int), s);
-    if (e != cudaSuccess) return cuda_check(c, e, "knn work reset");
+    grid = std::max(1, std::min(grid, (c->lay.L + warps - 1) / warps));
+    *warps_out = warps;
+    *grid_out = grid;
+    return SIDM_OK;
+}
+
+// redo: the leaves the fixed-bound warm kernel listed (their count and the
+// work counter were zeroed before it ran)
+template <class R, bool NBR, bool TMA, int G, int CH, bool BATCH = false>
+int launch_t(sidm_ctx* c, void* h_out, uint32_t* nbr, int k_stride, bool use_guess, cudaStream_t s, bool redo = false)
+{
+    using K = typename KeyOf<R, NBR>::T;
+    KnnParams p;
+    fill_params(c, p, h_out, nbr, k_stride, use_guess);
+    if (redo) {
+        p.leaf_list = c->d_knn_redo;
+        p.list_len = &c->d_cnt->knn_redo[0];
+        p.work = &c->d_cnt->knn_redo[1];
+    }
+    auto kern = k_knn<R, NBR, TMA, G, CH, BATCH>;
+    const size_t per_warp = knn_warp_bytes_t<R, K, G, BATCH>(p.kcap);
+    int warps = 0, grid = 0;
+    if (int rc = pick_shape(c, (const void*)kern, per_warp, &warps, &grid)) return rc;
+    if (!redo) c->knn_grid = grid;
+    cudaError_t e;
+    if (!redo) {
+        e = cudaMemsetAsync(&c->d_cnt->work[0], 0, sizeof(unsigned int), s);
+        if (e != cudaSuccess) return cuda_check(c, e, "knn work reset");
+    }
     const int tidx = timer_begin(c, 1, s);
-    kern<<<grid, warps * 32, smem, s>>>(p);
+    kern<<<grid, warps * 32, (size_t)warps * per_warp, s>>>(p);
     timer_end(c, tidx, s);
     c->launches++;
     e = cudaGetLastError();
@@ -732,17 +1188,50 @@ int launch_t(sidm_ctx* c, void* h_out, uint32_t* nbr, int k_stride, bool use_gue
 // the plain-load kernel-size search with the configured lane groups, chains
 // and candidate loop (per staged leaf, or compacted batches)
 template <class R>
-int launch_tuned(sidm_ctx* c, void* h_out, bool use_guess, cudaStream_t s)
+int launch_tuned(sidm_ctx* c, void* h_out, bool use_guess, cudaStream_t s, bool redo = false)
 {
     const int g = c->cfg.knn_groups > 0 ? c->cfg.knn_groups : kGroupsDefault;
     const int ch = c->cfg.knn_chains > 0 ? c->cfg.knn_chains : kChainsDefault;
-    const bool batch = (c->cfg.knn_batch > 0 ? c->cfg.knn_batch : kBatchDefault) == 2;
+    const bool batch = (c->cfg.knn_batch > 0 ? c->cfg.knn_batch : kBatchDefault) >= 2;
 #define SIDM_KNN_CASE(GG, CC, BB) \
-    if (g == GG && ch == CC && batch == BB) return launch_t<R, false, false, GG, CC, BB>(c, h_out, nullptr, 0, use_guess, s);
+    if (g == GG && ch == CC && batch == BB) return launch_t<R, false, false, GG, CC, BB>(c, h_out, nullptr, 0, use_guess, s, redo);
     SIDM_KNN_CASE(2, 4, false) SIDM_KNN_CASE(4, 4, false) SIDM_KNN_CASE(8, 4, false) SIDM_KNN_CASE(4, 8, false)
     SIDM_KNN_CASE(2, 4, true) SIDM_KNN_CASE(4, 4, true) SIDM_KNN_CASE(8, 4, true) SIDM_KNN_CASE(4, 8, true)
 #undef SIDM_KNN_CASE
     return set_err(c, SIDM_EINVAL, "knn_chains 8 takes knn_groups 4");
+}
+
+// warm-started search with the fixed-bound kernel, then the per-lane search
+// (itself warm-started: a lane whose guess fails there is redone cold) of the
+// leaves it could not finish or left to it
+template <class R, int G>
+int launch_warm(sidm_ctx* c, void* h_out, cudaStream_t s)
+{
+    using K = typename KeyOf<R, false>::T;
+    KnnParams p;
+    fill_params(c, p, h_out, nullptr, 0, true);
+    auto kern = k_knn_warm<R, G>;
+    const size_t per_warp = warm_warp_bytes<R, K, G>(p.kcap);
+    int warps = 0, grid = 0;
+    if (int rc = pick_shape(c, (const void*)kern, per_warp, &warps, &grid, kWarmMaxWarps)) return rc;
+    c->knn_grid = grid;
+    cudaError_t e = cudaMemsetAsync(&c->d_cnt->work[0], 0, sizeof(unsigned int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&c->d_cnt->knn_redo[0], 0, 2 * sizeof(unsigned int), s);
+    if (e != cudaSuccess) return cuda_check(c, e, "knn work reset");
+    const int tidx = timer_begin(c, 1, s);
+    kern<<<grid, warps * 32, (size_t)warps * per_warp, s>>>(p, c->d_knn_redo, &c->d_cnt->knn_redo[0]);
+    timer_end(c, tidx, s);
+    c->launches++;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_check(c, e, "knn launch");
+    return launch_tuned<R>(c, h_out, true, s, true);
+}
+
+template <class R>
+int launch_warm_tuned(sidm_ctx* c, void* h_out, cudaStream_t s)
+{
+    const int g = c->cfg.knn_groups > 0 ? c->cfg.knn_groups : kGroupsDefault;
+    return g == 2 ? launch_warm<R, 2>(c, h_out, s) : launch_warm<R, 4>(c, h_out, s);
 }
 
 }  // namespace
@@ -752,13 +1241,18 @@ int launch_knn(sidm_ctx* c, void* h_out, uint32_t* nbr, int k_stride, bool use_g
     if (c->lay.L == 0) return SIDM_OK;
     const bool tma = c->cfg.use_tma != 0;
     constexpr int G = kGroupsDefault, CH = kChainsDefault;   // neighbour lists and bulk copies: defaults
+    // warm-started searches take the fixed-bound kernel unless the knobs ask for
+    // bulk copies or the earlier combined kernel (knn_batch 1 or 2)
+    const bool warm = use_guess && !tma && (c->cfg.knn_batch > 0 ? c->cfg.knn_batch : kBatchDefault) == 3;
     if (c->cfg.precision == SIDM_FP64) {
         if (nbr) return set_err(c, SIDM_EINVAL, "neighbour lists: mixed form only");
+        if (warm) return launch_warm_tuned<double>(c, h_out, s);
         return tma ? launch_t<double, false, true, G, CH>(c, h_out, nullptr, 0, use_guess, s)
                    : launch_tuned<double>(c, h_out, use_guess, s);
     }
     if (nbr) return tma ? launch_t<float, true, true, G, CH>(c, nullptr, nbr, k_stride, false, s)
                         : launch_t<float, true, false, G, CH>(c, nullptr, nbr, k_stride, false, s);
+    if (warm) return launch_warm_tuned<float>(c, h_out, s);
     return tma ? launch_t<float, false, true, G, CH>(c, h_out, nullptr, 0, use_guess, s)
                : launch_tuned<float>(c, h_out, use_guess, s);
 }

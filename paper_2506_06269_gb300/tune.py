@@ -6,8 +6,9 @@ leaf size that defines the canonical FP32 distance is not a knob):
 
   kernel-size search (k_knn)     knn_warps (CTA size), knn_groups (lane groups of
                                  the candidate mask), knn_chains (independent
-                                 distance chains), knn_batch (loop per staged leaf
-                                 or over compacted batches), knn_flush (merge
+                                 distance chains), knn_batch (loop per staged leaf,
+                                 over compacted batches, or those plus the
+                                 fixed-bound warm-start kernel), knn_flush (merge
                                  threshold before node tests), knn_slack
                                  (warm-start bound)
   pair kernel (k_pairs)          pair_warps, pair_per_round (pairs a lane queues
@@ -27,7 +28,7 @@ import numpy as np
 
 KNN_KNOBS = {
     "knn_warps": (4, 8),
-    "knn_batch": (1, 2),
+    "knn_batch": (1, 2, 3),
     "knn_groups": (2, 4, 8),
     "knn_chains": (4, 8),
     "knn_flush": (8, 16, 32),
@@ -37,7 +38,7 @@ PAIR_KNOBS = {
     "pair_warps": (4, 8),
     "pair_per_round": (3, 4),
 }
-DEFAULTS = {"knn_warps": 8, "knn_batch": 2, "knn_groups": 2, "knn_chains": 4, "knn_flush": 32, "knn_slack": 1.05,
+DEFAULTS = {"knn_warps": 8, "knn_batch": 3, "knn_groups": 2, "knn_chains": 4, "knn_flush": 32, "knn_slack": 1.05,
             "pair_warps": 8, "pair_per_round": 4, "use_tma": 0}
 
 

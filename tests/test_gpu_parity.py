@@ -198,7 +198,7 @@ def test_launch_knobs_give_identical_bits(precision):
                dict(knn_flush=32, knn_slack=1.001), dict(knn_slack=2.0), dict(pair_per_round=1),
                dict(pair_per_round=3, knn_groups=8), dict(knn_batch=1), dict(knn_batch=1, knn_groups=2, knn_flush=4),
                dict(knn_batch=1, knn_chains=8, knn_groups=4, knn_slack=1.3), dict(knn_groups=2, knn_flush=4, pair_warps=3),
-               dict(use_tma=1)):
+               dict(use_tma=1), dict(knn_batch=2), dict(knn_batch=3, knn_groups=4, knn_slack=1.001)):
         got = _two_steps(b, ks, xs, dts, precision, kw)
         for (h0, v0, e0), (h1, v1, e1) in zip(ref, got):
             assert np.array_equal(h0, h1) and np.array_equal(v0, v1) and np.array_equal(e0, e1), kw

@@ -51,7 +51,7 @@ def test_create_rejects_bad_configuration():
     for kw in (dict(n_max=0), dict(halo_max=0), dict(halo_max=5000), dict(ngb_max=200), dict(event_cap=0),
                dict(precision=7), dict(knn_warps=17), dict(pair_warps=9), dict(pair_warps=-1),
                dict(knn_groups=3), dict(knn_chains=6), dict(knn_flush=33), dict(knn_slack=0.5),
-               dict(knn_slack=2.5), dict(pair_per_round=5), dict(knn_batch=3),
+               dict(knn_slack=2.5), dict(pair_per_round=5), dict(knn_batch=4),
                dict(knn_chains=8, knn_groups=2), dict(knn_chains=8)):
         base = dict(n_max=16, halo_max=1, ngb_max=8, event_cap=16, precision=0)
         base.update(kw)
