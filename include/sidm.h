@@ -87,7 +87,7 @@ typedef struct {
                          /*   with knn_groups 4 only)                                */
     int32_t knn_flush;   /*   pending keys per lane that trigger a heap merge before */
                          /*   a tree node's tests, 1..32 (default 32)                */
-    float   knn_slack;   /*   warm-start bound / previous kernel size, 1..2 (1.05)   */
+    float   knn_slack;   /*   warm-start bound / previous kernel size, 1..2 (1.07)   */
     int32_t pair_per_round; /* pair kernel: pairs a lane queues per round, 1..4 (4; mixed-form draws) */
     int32_t knn_batch;   /* kernel-size search: 1 loops over each staged leaf's      */
                          /*   candidates, 2 over compacted batches of them, 3 as 2    */
@@ -414,7 +414,7 @@ int sidm_timestep_criterion(sidm_ctx* ctx, double tau, double dt_min, double dt_
  * last sidm_kernel_sizes call (carried through the permutation, so the
  * caller's arrays must still be in the order that call left them, with the
  * same halo layout and N_ngb).  The search then only admits candidates within
- * knn_slack times that size (1.05 by default); a particle with fewer than
+ * knn_slack times that size (1.07 by default); a particle with fewer than
  * N_ngb of them is redone from scratch by a second, per-lane launch on the
  * same stream.  The result is the exact k-th distance in
  * every case -- a stale or wrong guess costs time, never accuracy -- so this

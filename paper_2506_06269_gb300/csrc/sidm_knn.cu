@@ -159,9 +159,9 @@ static_assert(kPend >= kLeaf, "a tile can admit all of its candidates: one empty
 // groups of 32 / G consecutive lanes whose boxes filter the candidates,
 // independent distance chains in the candidate loop, the pending count at
 // which the lists are merged before a tree node's tests, and the warm-start
-// bound factor (previous kernel size times it); the values the autotuner
-// picks on the GB300 for the 2^20 NFW halo at N_ngb = 64 (1.90 ms against
-// 2.00 ms for 4 groups, flush 16 and a bound of 1.0625)
+// bound factor (previous kernel size times it); values the autotuner picks on
+// the GB300 for the 2^20 NFW halo at N_ngb = 64 (with the fixed-bound warm
+// kernel: 1.47 ms per search at a bound of 1.07, 1.52 ms at 1.05)
 constexpr int kGroupsDefault = 2;
 // compacted candidate batches (knob knn_batch): candidates that pass the group
 // filter are appended to a per-warp buffer and the distance loop runs over
@@ -173,7 +173,7 @@ static_assert(kPend >= kBatch, "a batch can admit all of its candidates: one emp
 constexpr int kChainsDefault = 4;
 constexpr int kBatchDefault = 3;                   // 1: loop per staged leaf, 2: compacted batches, 3: 2 + fixed-bound warm kernel
 constexpr int kFlushNodeDefault = 32;
-constexpr float kGuessSlackDefault = 1.05f;
+constexpr float kGuessSlackDefault = 1.07f;
 
 template <class R>
 __device__ __forceinline__ float to_float_ru(R v)
@@ -696,7 +696,8 @@ __global__ void k_knn(KnnParams p)
 //  * the tree walk tests each child's box against the boxes of the lane
 //    groups, each grown by the largest bound of its lanes (one box test per
 //    child and group, no per-lane point tests), and lists the accepted leaves;
-//  * the listed leaves are loaded two ahead; a candidate is kept if it lies
+//  * the listed leaves are loaded two ahead (the walk itself goes level by
+//    level, loading the next frontier node's child boxes during the tests); a candidate is kept if it lies
 //    within some group's largest bound of that group's box, a test made in the
 //    query leaf's own frame with directed rounding, where the box gap is a lower
 //    bound of the canonical distance (no margin needed); kept candidates go to a
@@ -722,11 +723,11 @@ constexpr int kWPend = 32;      // keys a lane may hold beyond k before a merge 
 static_assert(kWRing % kWBatch == 0 && kWRing >= kWBatch - 1 + kLeaf, "the ring holds a batch's leftover plus a leaf");
 static_assert(kWPend >= kWBatch, "one batch fits after a merge");
 constexpr int kWarmMaxWarps = 8;   // the kernel's launch bound: 256 threads, two CTAs per SM
-constexpr int kWalkGroups = 8;     // lane groups of the tree walk (4 lanes each)
+constexpr int kWalkGroups = 4;     // lane groups of the tree walk (8 lanes each)
 // a leaf goes to the per-lane search when the box of a walk group is wider than
 // kSpreadWalk times its largest bound, or a filter group's than kSpreadFilter times
-constexpr float kSpreadWalk = 4.0f;
-constexpr float kSpreadFilter = 6.0f;
+constexpr float kSpreadWalk = 3.0f;
+constexpr float kSpreadFilter = 4.0f;
 
 template <class R, class K, int G>
 __host__ __device__ constexpr size_t warm_warp_bytes(int kcap)
@@ -802,9 +803,9 @@ __global__ void __launch_bounds__(kWarmMaxWarps * 32, 2) k_knn_warm(KnnParams p,
             pq = make_float3(__double2float_rn((double)q.x - fr.O[0]), __double2float_rn((double)q.y - fr.O[1]),
                              __double2float_rn((double)q.z - fr.O[2]));
         }
-        // walk boxes: groups of 4 lanes (a large bound of one lane grows only its
+        // walk boxes: groups of 8 lanes (a large bound of one lane grows only its
         // own group's box); the bound of each group is stored in its lo.w.  On the
-        // halo's sparse outer shell even 4 consecutive particles of the Morton
+        // halo's sparse outer shell a few consecutive particles of the Morton
         // curve can lie on opposite sides of the halo: a group box much wider
         // than its bound would accept most of the halo, so such a leaf is left
         // to the per-lane search (the redo list, warm-started)

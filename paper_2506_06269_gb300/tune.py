@@ -32,13 +32,13 @@ KNN_KNOBS = {
     "knn_groups": (2, 4, 8),
     "knn_chains": (4, 8),
     "knn_flush": (8, 16, 32),
-    "knn_slack": (1.03, 1.04, 1.05, 1.0625, 1.08),
+    "knn_slack": (1.04, 1.05, 1.07, 1.08, 1.1),
 }
 PAIR_KNOBS = {
     "pair_warps": (4, 8),
     "pair_per_round": (3, 4),
 }
-DEFAULTS = {"knn_warps": 8, "knn_batch": 3, "knn_groups": 2, "knn_chains": 4, "knn_flush": 32, "knn_slack": 1.05,
+DEFAULTS = {"knn_warps": 8, "knn_batch": 3, "knn_groups": 2, "knn_chains": 4, "knn_flush": 32, "knn_slack": 1.07,
             "pair_warps": 8, "pair_per_round": 4, "use_tma": 0}
 
 

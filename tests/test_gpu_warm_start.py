@@ -1,7 +1,7 @@
 """Warm-started kernel sizes (sidm_warm_start) are bit-identical to cold ones.
 
 The search seeded with the previous step's h only admits candidates inside
-knn_slack h_prev (1.05 by default) and redoes, from scratch, every particle that finds fewer than
+knn_slack h_prev (1.07 by default) and redoes, from scratch, every particle that finds fewer than
 N_ngb of them; the k-th distance is exact either way (Sect. 2 kernel size).
 These tests run a warm and a cold context side by side on identical inputs
 through drift + rebuild steps, including steps whose guesses are stale (large
