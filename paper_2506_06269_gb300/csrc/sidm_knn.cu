@@ -693,15 +693,16 @@ __global__ void k_knn(KnnParams p)
 // Warm-started search.  From the second call on every particle carries its
 // previous kernel size, and only candidates inside slack x h_prev are admitted
 // (reading C14).  That bound is fixed for the whole query leaf, so:
-//  * the tree walk tests each child's box against the boxes of the lane
-//    groups, each grown by the largest bound of its lanes (one box test per
-//    child and group, no per-lane point tests), and lists the accepted leaves;
-//  * the listed leaves are loaded two ahead (the walk itself goes level by
-//    level, loading the next frontier node's child boxes during the tests); a candidate is kept if it lies
-//    within some group's largest bound of that group's box, a test made in the
-//    query leaf's own frame with directed rounding, where the box gap is a lower
-//    bound of the canonical distance (no margin needed); kept candidates go to a
-//    per-warp ring;
+//  * the tree is walked level by level (the child boxes of the next frontier
+//    node load while the current one is tested); each child's box is tested
+//    against the boxes of the walk's lane groups, each grown by the largest
+//    bound of its lanes (one box test per child and group, no per-lane point
+//    tests), and the accepted leaves are listed;
+//  * the listed leaves are loaded two ahead; a candidate is kept if it lies
+//    within some filter group's largest bound of that group's box, a test made
+//    in the query leaf's own frame with directed rounding, where the box gap is
+//    a lower bound of the canonical distance (no margin needed); kept
+//    candidates go to a per-warp ring;
 //  * full batches of kWBatch ring entries are tested against all 32 queries
 //    with branch-free admission: a lane stores every key at its next free slot
 //    and advances the slot only when the key is below its bound;
@@ -710,13 +711,16 @@ __global__ void k_knn(KnnParams p)
 // The keys of a lane sit in shared memory as [slot][lane]: slots 0..k-1 are a
 // 4-ary max-heap (filled unsorted, heapified once), slots k..k+2 stay zero (the
 // missing children of the last nodes), and up to kWPend further keys wait
-// there until a merge.  A lane that admits fewer than k keys (its guess was too
-// small) sends its leaf to a list that the exhaustive search redoes, so the
-// result is the same exact k-th distance as a cold search.
+// there until a merge.  A leaf goes to a list that the per-lane search (k_knn,
+// warm-started, failing lanes cold) then redoes when a lane admits fewer than k
+// keys (its guess was too small), when a group box is much wider than its
+// bound (see kSpreadWalk), or when the walk's frontier overflows; so the result
+// is the same exact k-th distance as a cold search.
 constexpr int kWRing = 40;      // candidate ring entries
 constexpr int kWBatch = 8;      // candidates per batch (batches start at multiples of it: never wrap)
 constexpr int kWList = 64;      // accepted leaves listed before they are streamed
-constexpr int kWStack = 128;    // traversal stack entries (an overflow hands the leaf to the redo)
+constexpr int kWStack = 128;    // two frontier buffers of the walk, 64 nodes each (an overflow
+                                // hands the leaf to the redo)
 constexpr int kWPad = 3;        // zero slots after the heap
 constexpr int kWPend = 32;      // keys a lane may hold beyond k before a merge (room enough that
                                 // merges are rare and most lanes order their heaps together)
@@ -750,8 +754,8 @@ __global__ void __launch_bounds__(kWarmMaxWarps * 32, 2) k_knn_warm(KnnParams p,
     unsigned char* base = smem + wid * warm_warp_bytes<R, K, G>(p.kcap);
     V* ring = (V*)base;
     int* list = (int*)(base + (size_t)kWRing * sizeof(V));
-    int* stack = list + kWList;
-    float4* wbox = (float4*)(stack + kWStack);         // [kWalkGroups][2]: walk group boxes (halo frame), lo.w = bound
+    int* fbuf = list + kWList;                         // [2][kWStack / 2] frontier buffers of the walk
+    float4* wbox = (float4*)(fbuf + kWStack);          // [kWalkGroups][2]: walk group boxes (halo frame), lo.w = bound
     K* keys = (K*)(wbox + 2 * kWalkGroups);            // [kcap + kWPad + kWPend][32]
     const uint32_t lt = (1u << lane) - 1u;
     const int Hp = p.H + 1;
@@ -795,7 +799,7 @@ __global__ void __launch_bounds__(kWarmMaxWarps * 32, 2) k_knn_warm(KnnParams p,
         }
         // group boxes: the walk's in the halo frame (the frame of the node
         // boxes), the candidate filter's in the query leaf's frame (mixed form;
-        // the FP64 form filters with the walk's boxes and bounds)
+        // the FP64 form filters in the halo frame, with the walk's bounds)
         float3 pq;
         if constexpr (kF32) {
             pq = make_float3(__fadd_rn(cA.x, (float)q.x), __fadd_rn(cA.y, (float)q.y), __fadd_rn(cA.z, (float)q.z));
@@ -1030,9 +1034,9 @@ __global__ void __launch_bounds__(kWarmMaxWarps * 32, 2) k_knn_warm(KnnParams p,
             __syncwarp();
         };
         bool overflow = false;
-        constexpr int kWFront = kWStack / 2;           // two frontier buffers in the stack's space
-        int* front = stack;
-        int* nextf = stack + kWFront;
+        constexpr int kWFront = kWStack / 2;
+        int* front = fbuf;
+        int* nextf = fbuf + kWFront;
         int nf = 0;
         const int top = p.top[h];
         const int32_t* loff = p.lvl_off;
